@@ -1,0 +1,19 @@
+"""FP64 CPU oracle for the LLOID multirate SVD matched filter and its trigger generator.
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously correct
+restatement of the filtering stage of Sec. II.A (with the readings listed in
+each module's docstring).  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import it; the CUDA library never does, and
+the two share no code.  Inputs come from the separate ``synth`` module.
+
+Pins (tests/test_oracle_pins.py) tie it to things other than itself: brute
+force sums, SVD invariants (orthonormality, Eckart-Young), the reduction of
+the multirate path to the direct correlation for one untruncated full-rate
+slice, resampler closed forms, the noise-free injection recovering its
+amplitude and phase, white-noise statistics (E|rho|^2 = 2), tabulated values
+of I0, window-max brute force and shift invariance.
+"""
+from .resample import bessel_i0, decimate, halfband, kaiser, upsample
+from .svdbank import OracleBank, OracleSlice, bank_from_arrays, build_bank, slice_filters, truncated_svd
+from .lloid import (causal_correlate, complex_snr, decimation_cascade, direct_snr, lloid_levels,
+                    lloid_snr, triggers, window_maxima)

@@ -1,0 +1,306 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test names the plausible oracle mistake it would catch.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.signal
+import scipy.special
+
+import oracle
+import synth
+from oracle.resample import HALF_K
+
+
+# ---------------------------------------------------------------- helpers
+def brute_correlate(filters, d, delay):
+    R, Q = filters.shape
+    out = np.zeros((R, d.shape[0]))
+    for r in range(R):
+        for m in range(d.shape[0]):
+            acc = 0.0
+            for q in range(Q):
+                i = m - delay - q
+                if 0 <= i < d.shape[0]:
+                    acc += filters[r, q] * d[i]
+            out[r, m] = acc
+    return out
+
+
+def small_bin(n_templates=6, duration=2.0, f0=1024.0, slices=None):
+    slices = slices or [synth.SliceSpec(f0, 0.0, 0.5), synth.SliceSpec(f0 / 4, 0.5, duration)]
+    spec = synth.BinSpec(n_templates, 1.0, 3.0, f0, duration, slices)
+    h, _ = synth.template_bank(spec.n_templates, spec.mc_lo, spec.mc_hi, f0, duration, 9, 0, 0)
+    return spec, h
+
+
+def dtft(g, w):
+    j = np.arange(-(g.shape[0] // 2), g.shape[0] // 2 + 1)
+    return np.real(np.exp(-1j * np.outer(w, j)) @ g)
+
+
+# ---------------------------------------------------------------- P1 brute force
+def test_p1_fft_correlation_matches_brute_force():
+    """Catches: off-by-one delay, reversed filter, FFT wrap-around."""
+    g = np.random.default_rng(1)
+    f = g.standard_normal((3, 7))
+    d = g.standard_normal(41)
+    for delay in (0, 5, 40, 60):
+        ref = brute_correlate(f, d, delay)
+        got = oracle.causal_correlate(f, d, delay)
+        assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_p1_direct_snr_brute_force_small():
+    g = np.random.default_rng(2)
+    h = g.standard_normal((4, 64))
+    d = g.standard_normal(300).astype(np.float32)
+    ref = brute_correlate(h, d.astype(np.float64), 0)
+    got = oracle.direct_snr(h, d)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_p1_golden_hand_worked_fir():
+    """Hand-worked example of step a2 stored under tests/golden (integers, exact)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "fir_hand_worked.txt")
+    rows = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        key, val = line.split("=")
+        rows[key.strip()] = [float(v) for v in val.split()]
+    v = np.array(rows["v"])[None, :]
+    d = np.array(rows["d"])
+    got = oracle.causal_correlate(v, d, int(rows["D"][0]))[0]
+    assert np.allclose(got, rows["o"], atol=1e-12)
+
+
+# ---------------------------------------------------------------- P2 SVD invariants
+def test_p2_svd_invariants():
+    """Catches: transposed basis/mixing, sigma^2 vs sigma truncation, wrong slice sampling."""
+    spec, h = small_bin()
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    full = oracle.build_bank(h, spec.top_rate_hz, spec.slices, frac=1.0)
+    for s, sf, sp in zip(bank.slices, full.slices, spec.slices):
+        H = oracle.slice_filters(h, spec.top_rate_hz, sp.rate_hz, sp.t_start_s, sp.t_end_s)
+        L = s.basis.shape[0]
+        assert np.abs(s.basis @ s.basis.T - np.eye(L)).max() <= 1e-12
+        err = np.linalg.norm(H - s.mixing @ s.basis) ** 2
+        tail = float((s.sigma[L:] ** 2).sum())
+        assert abs(err - tail) <= 1e-10 * float((s.sigma ** 2).sum())
+        power = np.cumsum(s.sigma ** 2)
+        assert power[L - 1] >= 0.9999 * power[-1]
+        if L > 1:
+            assert power[L - 2] < 0.9999 * power[-1]
+        assert np.abs(sf.mixing @ sf.basis - H).max() <= 1e-12 * np.abs(H).max()
+
+
+def test_p2_slice_filter_indexing():
+    """H_s[a, q] = 2^k h[a, t_s f0 + q 2^k]: checked on a ramp template."""
+    h = np.arange(2 * 1 * 64, dtype=np.float64).reshape(2, 64)
+    H = oracle.slice_filters(h, 64.0, 16.0, 0.25, 1.0)         # k = 2, j0 = 16, Q = 12
+    assert H.shape == (2, 12)
+    assert H[0, 0] == 4 * h[0, 16] and H[1, 11] == 4 * h[1, 16 + 44]
+
+
+# ---------------------------------------------------------------- P3 special case
+def test_p3_full_rate_untruncated_equals_direct():
+    """Two slices both at f0, no truncation: the SVD path is the direct sum exactly.
+
+    Catches: wrong delay D_s, reversed taps, mixing/basis transposed, dropped slice.
+    """
+    f0 = 512.0
+    spec, h = small_bin(n_templates=4, duration=1.0, f0=f0,
+                        slices=[synth.SliceSpec(f0, 0.0, 0.25), synth.SliceSpec(f0, 0.25, 1.0)])
+    bank = oracle.build_bank(h, f0, spec.slices, frac=1.0)
+    d = synth.white_noise(2048, 7, 0, 0)
+    x_svd = oracle.lloid_snr(bank, d)
+    x_dir = oracle.direct_snr(h, d)
+    assert np.abs(x_svd - x_dir).max() <= 1e-12 * np.abs(x_dir).max()
+
+
+# ---------------------------------------------------------------- P4 resampler
+def test_p4_halfband_structure():
+    g = oracle.halfband()
+    K2 = 2 * HALF_K
+    assert g.shape == (4 * HALF_K + 1,)
+    assert np.array_equal(g, g[::-1])
+    assert abs(g.sum() - 1.0) <= 1e-15 * 4
+    assert g[K2] == 0.5
+    for j in range(-K2, K2 + 1):
+        if j != 0 and j % 2 == 0:
+            assert g[K2 + j] == 0.0
+
+
+def test_p4_bessel_and_kaiser_match_library():
+    """The I0 power series and the Kaiser window against scipy's independent routines."""
+    for x in (0.0, 0.5, 1.0, 2.0, 5.0, 8.6):
+        assert abs(oracle.bessel_i0(x) - scipy.special.i0(x)) <= 1e-13 * scipy.special.i0(x)
+    w = oracle.kaiser(2 * HALF_K, 8.6)
+    ref = scipy.signal.windows.kaiser(4 * HALF_K + 1, 8.6, sym=True)
+    assert np.abs(w - ref).max() <= 1e-13
+
+
+def test_p4_passband_and_stopband():
+    """|H - 1| <= 1e-4 up to 0.8 of the decimated Nyquist; >= 80 dB rejection beyond 1.2 of it."""
+    g = oracle.halfband()
+    w_pass = np.linspace(0, 0.8 * np.pi / 2, 400)
+    w_stop = np.linspace(1.2 * np.pi / 2, np.pi, 400)
+    assert np.abs(dtft(g, w_pass) - 1.0).max() <= 1e-4
+    assert np.abs(dtft(g, w_stop)).max() <= 1e-4
+    # halfband symmetry H(w) + H(pi - w) = 1
+    w = np.linspace(0, np.pi, 101)
+    assert np.abs(dtft(g, w) + dtft(g, np.pi - w) - 1.0).max() <= 1e-13
+
+
+def test_p4_tone_through_decimate_and_upsample():
+    """A band-limited tone survives decimation and interpolation (amplitude, phase, alignment)."""
+    g = oracle.halfband()
+    n = 4096
+    t = np.arange(n)
+    f = 0.8 * 0.25                       # cycles per input sample: 0.8 of the output Nyquist
+    x = np.cos(2 * np.pi * f * t + 0.3)
+    y = oracle.decimate(x, g)
+    m = np.arange(y.shape[0])
+    ref = np.cos(2 * np.pi * f * 2 * m + 0.3)
+    inner = slice(64, y.shape[0] - 64)
+    assert np.abs(y[inner] - ref[inner]).max() <= 1e-4
+    z = oracle.upsample(y, g)
+    inner2 = slice(256, n - 256)
+    assert np.abs(z[inner2] - x[inner2]).max() <= 2e-4
+    assert np.array_equal(z[0::2][100:200], y[100:200])      # even outputs are copies
+
+
+# ---------------------------------------------------------------- P5 / P8 injection
+@pytest.fixture(scope="module")
+def cfg_small():
+    spec = synth.SMALL_BIN
+    h, _ = synth.template_bank(16, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 3, 0, 0)
+    return spec, h
+
+
+def test_p5_p8_injection_recovered_untruncated(cfg_small):
+    """Noise-free injection at A = 12: |rho(n_c)| = A within 1e-3 and arg rho = phi0 within 0.05.
+
+    Catches: the 2^k slice gain, the x2 interpolation gain, level misalignment, phase sign.
+    """
+    spec, h = cfg_small
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices, frac=1.0)
+    n = 12 * 2048
+    for i, phi0 in ((3, 0.7), (11, -2.0)):
+        d = np.zeros(n, np.float32)
+        n_c = 10 * 2048 + 5
+        synth.inject(d, h, i, n_c, 12.0, phi0)
+        rho = oracle.complex_snr(oracle.lloid_snr(bank, d))[i, n_c]
+        assert abs(abs(rho) - 12.0) <= 12e-3
+        assert abs(math.remainder(np.angle(rho) - phi0, 2 * math.pi)) <= 0.05
+
+
+def test_p6_truncation_bound(cfg_small):
+    """|x_svd - x_dir| <= A |h - h_hat|_w + 1e-3 A on the injected filter pair (Cauchy-Schwarz)."""
+    spec, h = cfg_small
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    n = 12 * 2048
+    i, n_c, A = 5, 10 * 2048, 12.0
+    d = np.zeros(n, np.float32)
+    synth.inject(d, h, i, n_c, A, 0.4)
+    xs = oracle.lloid_snr(bank, d)[:, n_c]
+    xd = oracle.direct_snr(h, d)[:, n_c]
+    for a in (2 * i, 2 * i + 1):
+        werr = 0.0
+        for s, sp in zip(bank.slices, spec.slices):
+            H = oracle.slice_filters(h, spec.top_rate_hz, sp.rate_hz, sp.t_start_s, sp.t_end_s)
+            werr += 2.0 ** (-s.level) * float(((H[a] - s.mixing[a] @ s.basis) ** 2).sum())
+        assert abs(xs[a] - xd[a]) <= A * math.sqrt(werr) + 1e-3 * A
+
+
+# ---------------------------------------------------------------- P7 gain chain
+def test_p7_impulse_response_energy(cfg_small):
+    """Unit-norm templates: the multirate path's impulse-response energy is 1 per real filter.
+
+    White noise then gives E|rho|^2 = 2.  The path is periodically time varying
+    (period 2^kmax), so the energy is averaged over the 4 impulse phases.
+    """
+    spec, h = cfg_small
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices, frac=1.0)
+    n = 12 * 2048
+    energies = []
+    for phase in range(4):
+        d = np.zeros(n, np.float32)
+        d[2048 + phase] = 1.0
+        x = oracle.lloid_snr(bank, d)
+        energies.append((x ** 2).sum(axis=1))
+    e = np.mean(energies, axis=0)
+    assert np.abs(e - 1.0).max() <= 2e-3
+
+
+def test_p7_rice_mean_over_seeds():
+    """Unit-norm template at amplitude A in unit white noise: mean |rho(n_c)| = Rice mean.
+
+    Rice(A, 1) mean = sqrt(pi/2) L_{1/2}(-A^2/2); checked over 240 seeds at 3 sigma.
+    Uses a one-slice top-rate bank (untruncated) so that the run stays short.
+    """
+    f0 = 1024.0
+    h, _ = synth.template_bank(2, 1.0, 1.5, f0, 1.0, 4, 0, 0)
+    bank = oracle.build_bank(h, f0, [synth.SliceSpec(f0, 0.0, 0.5), synth.SliceSpec(f0 / 2, 0.5, 1.0)],
+                             frac=1.0)
+    A, n, n_c = 3.0, 2048, 1500
+    vals = []
+    for seed in range(240):
+        d = synth.white_noise(n, 99, 0, seed)
+        synth.inject(d, h, 0, n_c, A, 0.3)
+        vals.append(abs(oracle.complex_snr(oracle.lloid_snr(bank, d))[0, n_c]))
+    x = -A * A / 2
+    lag = math.exp(x / 2) * ((1 - x) * scipy.special.i0(-x / 2) - x * scipy.special.i1(-x / 2))
+    mean = math.sqrt(math.pi / 2) * lag
+    var = 2 + A * A - mean ** 2
+    assert abs(np.mean(vals) - mean) <= 3 * math.sqrt(var / len(vals))
+
+
+# ---------------------------------------------------------------- P9 window max
+def test_p9_window_max_brute_force_with_ties():
+    """First-index tie-break, strict '>' threshold, windows on absolute multiples of W."""
+    g = np.random.default_rng(5)
+    x = g.standard_normal((6, 100))
+    x[0, 13] = 5.0; x[1, 13] = 0.0
+    x[0, 17] = 3.0; x[1, 17] = 4.0               # |rho| = 5 tie, later index
+    x[2, 40:] = 0.0; x[3, 40:] = 0.0
+    x[2, 44] = 2.0; x[2, 47] = -2.0              # tie with opposite signs
+    W = 20
+    wins, n_star, amax, ph = oracle.window_maxima(x, W, 100)
+    for wi, w in enumerate(wins):
+        for i in range(3):
+            best, arg = -1.0, -1
+            for n in range(w * W, (w + 1) * W):
+                v = math.hypot(x[2 * i, n], x[2 * i + 1, n])
+                if v > best:
+                    best, arg = v, n
+            assert n_star[wi, i] == arg and abs(amax[wi, i] - best) <= 1e-15
+    assert n_star[0, 0] == 13 and n_star[2, 1] == 44
+    trig = oracle.triggers(x, W, 5.0, 100)
+    assert all(t[3] > 5.0 for t in trig)
+    assert not any(t[0] == 0 and t[2] == 0 for t in trig)     # |rho| = 5 is not > 5
+
+
+# ---------------------------------------------------------------- P10 shift invariance
+def test_p10_shift_by_rate_period_is_exact(cfg_small):
+    """Prepending 2^kmax zeros shifts the output by exactly 2^kmax samples.
+
+    Every rate's signal starts at its own index 0, so the first template length
+    plus the resampler spans is a start-up transient and is excluded, and so is
+    the end, where the shifted input lost its last samples.
+    """
+    spec, h = cfg_small
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    d = synth.white_noise(12 * 2048, 8, 0, 0)
+    sh = 2 ** bank.k_max
+    d2 = np.concatenate([np.zeros(sh, np.float32), d[:-sh]])
+    x1 = oracle.lloid_snr(bank, d)
+    x2 = oracle.lloid_snr(bank, d2)
+    skip = int(spec.duration_s * spec.top_rate_hz) + 8 * 2 * HALF_K * sh
+    end = d.shape[0] - sh - 8 * 2 * HALF_K * sh          # the dropped tail reaches back this far
+    assert np.abs(x2[:, skip + sh:end + sh] - x1[:, skip:end]).max() <= 1e-12 * np.abs(x1).max()
