@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput benchmark: template-seconds filtered per second on B300 (paper Eq. 1, cores = 1 per GPU).
+
+Workload (per GPU rank): one production-shaped SVD bin of 1000 templates
+(60 s Newtonian chirps, chirp mass 1.0-1.5 Msun, six time slices at 4096 ...
+128 Hz, SVD truncated at 99.99% of sigma^2) on two detectors (H1, L1: two
+units, independent seeded white noise, injections at SNR 8-30).  A step is one
+grouped push of ``--push-seconds`` of strain to both units: decimation, basis
+FIR, mixing, up-sampling + sum, window maxima and trigger hand-off.  Data are
+synthetic (seeded white Gaussian noise; random-parameter chirps).
+
+The device-timed value has the strain already resident in HBM; L2 is flushed
+(256 MB write) between timed steps, outside the step's events.  ``e2e`` runs
+the same steps through the C ABI from host buffers, with the host->device
+strain copies and the trigger read-back inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "template-seconds filtered/s on 1 B300 (FP32 vs BF16/FP8 grouped); p99 latency"
+UNIT = "template-s/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="lloid", choices=["lloid", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp8"])
+    p.add_argument("--push-seconds", type=int, default=16)
+    p.add_argument("--templates", type=int, default=1000)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=8.0, help="strain seconds per oracle worker")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- workload
+def production_bank_templates(bin_index: int, n_templates: int):
+    spec = synth.scaled_bin(synth.PRODUCTION_BIN, n_templates)
+    h, _ = synth.template_bank(spec.n_templates, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s,
+                               2, bin_index, 0)
+    return spec, h
+
+
+def make_strain(bin_index: int, detector: int, seconds: int, f0: float, h, n_templates: int):
+    n = int(seconds * f0)
+    d = synth.white_noise(n, 2, bin_index, detector + 1)
+    for inj in synth.injection_plan(max(1, seconds // 80), n_templates, n, f0, 80.0, 8.0, 30.0, bin_index, detector):
+        synth.inject(d, h, inj.template, inj.n_c, inj.amplitude, inj.phi0)
+    return d
+
+
+def algorithmic_model(bank, units: int, B_s: float):
+    """Per-stage algorithmic FLOPs and HBM bytes of one push (all units)."""
+    f0 = bank.top_rate_hz
+    M2 = 2 * bank.n_templates
+    levels = {}
+    for s in bank.slices:
+        k = int(round(math.log2(f0 / s.rate_hz)))
+        levels.setdefault(k, []).append(s)
+    kmax = max(levels)
+    fl = {k: 0.0 for k in ("fir", "mix", "upsample", "decimate", "trigger")}
+    by = {k: 0.0 for k in fl}
+    for s in bank.slices:
+        L, Q = s.basis.shape
+        N = B_s * s.rate_hz
+        fl["fir"] += 2.0 * L * Q * N
+        by["fir"] += 4.0 * (L * Q + N + L * N)
+    for k, ss in levels.items():
+        Lk = sum(s.basis.shape[0] for s in ss)
+        N = B_s * f0 / 2 ** k
+        fl["mix"] += 2.0 * M2 * Lk * N
+        by["mix"] += 4.0 * (M2 * Lk + Lk * N + M2 * N * (2 if k < kmax else 1))
+    for k in range(1, kmax + 1):
+        N = B_s * f0 / 2 ** k
+        fl["upsample"] += M2 * (2 * N) * 17
+        by["upsample"] += 4.0 * M2 * (N + 2 * N)
+        fl["decimate"] += 2 * N * 17
+        by["decimate"] += 4.0 * (3 * N)
+    fl["trigger"] = 3.0 * M2 / 2 * B_s * f0
+    by["trigger"] = 4.0 * M2 * B_s * f0
+    return {k: fl[k] * units for k in fl}, {k: by[k] * units for k in by}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+def _oracle_worker(args):
+    """One oracle run (FP64, BLAS 1 thread): SVD path + window maxima on a strain excerpt."""
+    bank, strain, win_len, threshold = args
+    from threadpoolctl import threadpool_limits
+    import oracle
+    with threadpool_limits(1):
+        t = time.perf_counter()
+        x = oracle.lloid_snr(bank, strain)
+        oracle.triggers(x, win_len, threshold, x.shape[1])
+        return time.perf_counter() - t
+
+
+def oracle_bank(h, spec):
+    import oracle
+    return oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+
+
+def cpu_baseline(h, spec, seconds: float, workers: int):
+    """The oracle as it stands on `workers` host processes, each on its own excerpt."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    ob = oracle_bank(h, spec)
+    f0 = spec.top_rate_hz
+    n = int(seconds * f0) // 32 * 32
+    jobs = [(ob, synth.white_noise(n, 7, w, 0), int(f0), 6.0) for w in range(workers)]
+    ctx = mp.get_context("spawn")
+    t = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+        list(ex.map(_oracle_worker, jobs))
+    wall = time.perf_counter() - t
+    value = workers * spec.n_templates * (n / f0) / wall
+    return {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{workers} processes x {n / f0:.0f} s excerpt of one unit of the production bin "
+                      f"({spec.n_templates} templates), FP64 SVD path + window maxima, BLAS 1 thread each; "
+                      f"wall {wall:.1f} s incl. process start"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, same metric and workload shape."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec, h = production_bank_templates(0, args.templates)
+    ob = oracle_bank(h, spec)
+    f0 = spec.top_rate_hz
+    n = int(min(args.cpu_seconds, 4.0) * f0) // 32 * 32
+    times = []
+    for step in range(args.warmup + args.steps):
+        d = synth.white_noise(n, 8, 0, step)
+        dt = _oracle_worker((ob, d, int(f0), 6.0))
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = args.steps * spec.n_templates * (n / f0) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"production bin ({spec.n_templates} templates, 6 slices 4096-128 Hz), "
+                                   f"one unit, {n / f0:.0f} s excerpt per step", "templates": spec.n_templates},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n / f0:.0f} s excerpt per step, one process, BLAS 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2410_16416_b300 as lloid
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    spec, h = production_bank_templates(rank, args.templates)
+    bank = lloid.decompose(h, spec.top_rate_hz, spec.slices)
+    f0 = int(spec.top_rate_hz)
+    B = args.push_seconds * f0
+    total_s = (args.warmup + args.steps) * args.push_seconds
+    strains = [make_strain(rank, det, total_s, f0, h, spec.n_templates) for det in (0, 1)]
+    dev = [torch.from_numpy(s).cuda() for s in strains]
+    stream = torch.cuda.current_stream()
+    ctx = lloid.Context(local, stream=stream.cuda_stream)
+    units = [ctx.create_unit(bank, detector=det, precision=args.precision, threshold=6.0, refine_threshold=5.5,
+                             window_s=1.0, max_push_samples=B) for det in (0, 1)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    t = 0
+    for _ in range(args.warmup):
+        ctx.push_group(units, [d[t:t + B] for d in dev], [t, t], True)
+        t += B
+    ctx.pop_triggers()
+    barrier()
+    ctx.profile(True)
+    st0 = ctx.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    w0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ctx.push_group(units, [d[t:t + B] for d in dev], [t, t], True)
+        ev[i][1].record(stream)
+        t += B
+    barrier()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    st1 = ctx.stats()
+    stages = ctx.stage_times()
+    ctx.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    if dist is not None:
+        tt = torch.tensor([dev_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dev_s = float(tt.item())
+    tpl_s_rank = len(units) * spec.n_templates * args.push_seconds * args.steps
+    value = world * tpl_s_rank / dev_s
+    trig = ctx.pop_triggers()
+
+    # e2e: host strain in, triggers out, through the C ABI
+    e2e = None
+    if rank == 0 or dist is not None:
+        ctx2 = lloid.Context(local, stream=stream.cuda_stream)
+        u2 = [ctx2.create_unit(bank, detector=det, precision=args.precision, threshold=6.0, refine_threshold=5.5,
+                               window_s=1.0, max_push_samples=B) for det in (0, 1)]
+        t2 = 0
+        for _ in range(args.warmup):
+            ctx2.push_group(u2, [s[t2:t2 + B] for s in strains], [t2, t2], False)
+            ctx2.pop_triggers()
+            t2 += B
+        barrier()
+        s0 = ctx2.stats()
+        w1 = time.perf_counter()
+        for i in range(args.steps):
+            ctx2.push_group(u2, [s[t2:t2 + B] for s in strains], [t2, t2], False)
+            ctx2.pop_triggers()
+            t2 += B
+        ctx2.sync()
+        ctx2.pop_triggers()
+        e2e_wall = time.perf_counter() - w1
+        s1 = ctx2.stats()
+        e2e = {"value": world * tpl_s_rank / e2e_wall, "unit": UNIT,
+               "h2d_bytes_per_step": (s1["h2d_bytes"] - s0["h2d_bytes"]) // args.steps,
+               "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // args.steps}
+        ctx2.close()
+
+    # roofline of the dominant stage
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    alu_peak_tflops = 148 * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 FFMA lanes x 2 FLOP x max clock
+    flops, bytes_ = algorithmic_model(bank, len(units), args.push_seconds)
+    busy = {k: v[0] for k, v in stages.items() if v[1] > 0}
+    dom = max(busy, key=busy.get)
+    dom_ms, dom_n = stages[dom]
+    t_alu = flops.get(dom, 0.0) / (alu_peak_tflops * 1e12)
+    t_hbm = bytes_.get(dom, 0.0) / (hbm_peak * 1e9)
+    per_launch_s = dom_ms / 1e3 / dom_n
+    per_launch_units = args.steps / dom_n
+    if t_alu >= t_hbm:
+        achieved = flops[dom] * per_launch_units / per_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak_tflops, "traffic": None,
+                "kernel": dom, "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 FLOP x max SM clock"}
+    else:
+        achieved = bytes_[dom] * per_launch_units / per_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": dom, "peak_source": "measured hbm_gbs"}
+    total_stage_ms = sum(busy.values())
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16",
+                                                             "fp8": "e4m3"}[args.precision],
+            "data": "synthetic (seeded white noise, random-parameter Newtonian chirp bank, injections)",
+            "config": {"workload": f"production bin: {spec.n_templates} templates x 2 detectors, 6 slices "
+                                   f"4096-128 Hz, L={bank.basis_counts()}, {args.push_seconds} s pushes",
+                       "templates": spec.n_templates, "units_per_gpu": len(units), "push_seconds": args.push_seconds,
+                       "precision": args.precision, "parallelism": f"units sharded, {world} GPU(s)",
+                       "l2": "flushed between steps (256 MB write outside the step events)"},
+            "roofline": roof, "e2e": e2e,
+            "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+            "clocks": clk,
+            "stages_ms_share": {k: round(v / total_stage_ms, 4) for k, v in busy.items()},
+            "wall_s": wall, "triggers": int(len(trig))}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(h, spec, args.cpu_seconds, max(1, min(os.cpu_count() or 1, 16)))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * lloid.h - C ABI of the B300 multirate SVD matched filter (LLOID) and its
+ * device-side trigger generator.
+ *
+ * The operation is the filtering stage of Sec. II.A of "Scalable
+ * matched-filtering pipeline for gravitational-wave searches of compact binary
+ * mergers" (arXiv:2410.16416): whitened strain is down-sampled to each time
+ * slice's rate, cross-correlated with the slice's orthonormal SVD basis
+ * filters, the orthogonal SNR series are multiplied by the SVD coefficients,
+ * the per-slice SNR segments are up-sampled and summed, and per-window |SNR|
+ * maxima above a threshold become triggers with their phase (Sec. II.A and the
+ * Fig. 1 caption); the trigger generator runs on the device so that only the
+ * reduced trigger set crosses to the host (Sec. II.B).  Several SVD banks are
+ * filtered in one grouped launch per stage (Sec. II.B).
+ *
+ * Notation: f0 = top rate; n = absolute top-rate sample index (n >= 0, the
+ * strain is zero before n = 0); M templates per bank, real filter a = 2i + p
+ * (p = 0 cosine phase, p = 1 sine phase); slice s at rate f_s = f0 / 2^k_s
+ * covers tau in [t_s, t_{s+1}) seconds before coalescence, has Q_s taps,
+ * delay D_s = t_s f_s and L_s basis vectors.
+ *
+ * Conventions: status 0 = OK, negative = error (SB_E*); sb_last_error() gives
+ * a message for the calling thread's last failure.  The caller owns every host
+ * array it passes; the library copies what it needs before returning.  The
+ * library owns all device memory it allocates.  Nothing here blocks on the GPU
+ * except where stated.
+ */
+#ifndef LLOID_H
+#define LLOID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SB_OK        0
+#define SB_EINVAL   (-1)  /* bad argument or bank shape                       */
+#define SB_ENOMEM   (-2)  /* a device or pinned allocation failed             */
+#define SB_EBUSY    (-3)  /* admission refused: HBM budget of the context full */
+#define SB_EGAP     (-4)  /* t0 not contiguous with the unit's previous push   */
+#define SB_ETIMEOUT (-5)  /* a bounded device wait expired                    */
+#define SB_ECUDA    (-6)  /* a CUDA runtime call failed (message has details)  */
+#define SB_EOVERFLOW (-7) /* trigger buffer overflow (triggers were dropped)   */
+
+/* ---- arithmetic of the two GEMM-shaped steps (basis FIR, reconstruction) */
+#define SB_FP32 0   /* FP32 operands, FP32 accumulate (SIMT)                  */
+#define SB_BF16 1   /* BF16 operands, FP32 accumulate (tensor cores)          */
+#define SB_FP16 2   /* FP16 operands, FP32 accumulate (tensor cores)          */
+#define SB_FP8  3   /* E4M3 operands with per-vector scales, FP32 accumulate  */
+
+/* ---- sb_desc.flags --------------------------------------------------- */
+#define SB_FLAG_KEEP_SNR 1  /* keep the last push's top-rate SNR readable (sb_unit_snr) */
+
+/* ---- trigger flags --------------------------------------------------- */
+#define SB_TRIG_REFINED 1   /* SNR recomputed in FP32 around the peak           */
+
+/* One time slice of an SVD bank (Sec. II.A "time slices ... SVD").
+ * basis : [n_basis * n_taps] row-major; row l is v_l[q], q = 0 is the tap
+ *         t_start_s seconds before coalescence, q grows back in time.
+ * mixing: [2M * n_basis] row-major; row a = 2i + p holds the coefficients
+ *         of real filter a on the basis vectors (h_{a,s} ~= sum_l M[a,l] v_l).
+ * rate_hz must be top_rate_hz / 2^k (k >= 0); (t_end_s - t_start_s) * rate_hz
+ * and t_start_s * rate_hz must be integers.                                   */
+typedef struct sb_slice {
+    double rate_hz;
+    double t_start_s;
+    double t_end_s;
+    int32_t n_basis;
+    int32_t n_taps;
+    const double *basis;
+    const double *mixing;
+} sb_slice;
+
+/* One SVD bank (one template group for one detector, Sec. IV: "one SVD bank
+ * for each instrument").
+ * template_ids: [n_templates] ids copied into triggers (NULL: 0..M-1).
+ * threshold: a window maximum triggers when |rho| > threshold.
+ * refine_threshold: in SB_BF16/SB_FP16/SB_FP8 modes, window maxima above this
+ *   are recomputed in FP32 (0 disables refinement).
+ * window_s: trigger window length (windows start at multiples of window_s*f0).
+ * max_push_samples: the largest n_samples a filter_push will pass (top rate). */
+typedef struct sb_desc {
+    int32_t n_templates;
+    int32_t n_slices;
+    double top_rate_hz;
+    const sb_slice *slices;
+    const int64_t *template_ids;
+    int32_t precision;
+    int32_t flags;
+    float threshold;
+    float refine_threshold;
+    double window_s;
+    int64_t max_push_samples;
+} sb_desc;
+
+/* One trigger: the |rho| maximum of one template in one window (Sec. II.A).
+ * sample = absolute top-rate index n* of the maximum (first one on ties),
+ * window = n* / (window_s * f0), snr = |rho(n*)|,
+ * phase = atan2(x_{2i+1}(n*), x_{2i}(n*)) in radians.                        */
+typedef struct sb_trigger {
+    int64_t unit;
+    int64_t template_id;
+    int64_t sample;
+    int64_t window;
+    float snr;
+    float phase;
+    int32_t flags;
+    int32_t reserved;
+} sb_trigger;
+
+/* Read-only facts about a unit (for tests, benchmarks and admission). */
+typedef struct sb_unit_info {
+    int64_t unit;             /* id used in triggers                           */
+    int32_t n_templates;
+    int32_t n_slices;
+    int32_t k_max;            /* deepest level: lowest rate = f0 / 2^k_max      */
+    int32_t precision;
+    int64_t latency_samples;  /* top-rate look-ahead: after pushing T samples,  */
+                              /* SNR is final for n < T - latency_samples       */
+    int64_t samples_pushed;   /* T                                              */
+    int64_t device_bytes;     /* device memory held by this unit                */
+    int64_t flops_per_second; /* algorithmic FLOPs per second of data (FIR+mix) */
+} sb_unit_info;
+
+typedef struct sb_ctx sb_ctx;
+typedef struct sb_unit sb_unit;
+
+/* Context: one CUDA device, one stream, one HBM budget, one trigger queue.
+ * device: CUDA ordinal; stream: a cudaStream_t to launch on (NULL: the
+ * library creates its own); hbm_budget_bytes: device bytes the context may
+ * hold for units (<= 0: 90% of free memory at creation). */
+int sb_ctx_create(int32_t device, void *stream, int64_t hbm_budget_bytes, sb_ctx **out);
+int sb_ctx_destroy(sb_ctx *ctx);
+/* Block until all work queued on the context's stream has finished. */
+int sb_ctx_sync(sb_ctx *ctx);
+
+/* Create one (bank, detector) unit: validates the bank, copies the host
+ * arrays, converts them to the working precision, allocates the unit's
+ * device state (zeroed histories) and admits it against the budget.
+ * Returns SB_EBUSY (nothing allocated) when the budget cannot hold it. */
+int svdbank_create(sb_ctx *ctx, const sb_desc *desc, int32_t detector, sb_unit **out);
+int svdbank_destroy(sb_unit *unit);
+int sb_unit_query(const sb_unit *unit, sb_unit_info *info);
+
+/* Validate a bank description and report the unit it would create (k_max,
+ * latency, device bytes, FLOPs) without touching any device.  Fields of
+ * *info that need a live unit (unit, samples_pushed) are set to 0. */
+int svdbank_plan(const sb_desc *desc, sb_unit_info *info);
+
+/* Push the next n_samples top-rate samples of whitened strain to one unit.
+ * strain: host pointer (on_device = 0) or device pointer (on_device = 1),
+ * FP32, contiguous.  t0_sample must equal the unit's samples pushed so far
+ * (SB_EGAP otherwise); n_samples must be a multiple of 2^k_max and at most
+ * max_push_samples.  The host buffer may be reused when the call returns.
+ * Work is queued on the context's stream; triggers of every window the push
+ * completes become available to triggers_pop once that work has finished. */
+int filter_push(sb_unit *unit, const float *strain, int64_t n_samples, int64_t t0_sample,
+                int32_t on_device);
+
+/* Push one buffer to each of n units at once: every stage runs as one grouped
+ * launch over all units (Sec. II.B: same-rate slices of several banks are
+ * stacked and filtered together).  All units must belong to ctx; strains[u],
+ * t0_samples[u] as in filter_push; n_samples is common to all units. */
+int filter_push_group(sb_ctx *ctx, int32_t n_units, sb_unit *const *units,
+                      const float *const *strains, int64_t n_samples,
+                      const int64_t *t0_samples, int32_t on_device);
+
+/* Move up to cap finished triggers into out (never blocks on queued work).
+ * *n_out = number written.  Triggers come out push by push, and within a push
+ * sorted by (window, unit, template).  Returns SB_EOVERFLOW once if triggers
+ * were dropped because a push produced more than its buffer holds. */
+int triggers_pop(sb_ctx *ctx, sb_trigger *out, int64_t cap, int64_t *n_out);
+
+/* Debug read-back (blocks): the top-rate SNR series x_a[n] of the unit's last
+ * push, written row-major [2M][*n] into host_out (capacity cap floats), for
+ * n in [*first_sample, *first_sample + *n).  Needs SB_FLAG_KEEP_SNR. */
+int sb_unit_snr(sb_unit *unit, float *host_out, int64_t cap, int64_t *first_sample, int64_t *n);
+
+/* ---- instrumentation ------------------------------------------------- */
+/* Stages of a push, in launch order (indices of sb_ctx_stage_times). */
+#define SB_STAGE_HISTORY   0  /* history shifts of the decimated strain          */
+#define SB_STAGE_STRAIN    1  /* new strain into the top-rate buffer             */
+#define SB_STAGE_DECIMATE  2  /* a1: halfband decimation cascade                 */
+#define SB_STAGE_FIR       3  /* a2: basis FIR (Toeplitz GEMM)                   */
+#define SB_STAGE_UPSAMPLE  4  /* a4: interpolation by two                        */
+#define SB_STAGE_MIX       5  /* a3: reconstruction (mixing) GEMM                */
+#define SB_STAGE_TRIGGER   6  /* a5: window maxima, threshold, phase             */
+#define SB_STAGE_SNRHIST   7  /* SNR history for the next push's interpolators   */
+#define SB_N_STAGES        8
+
+/* Cumulative counters of a context since creation. */
+typedef struct sb_ctx_stats {
+    int64_t pushes;          /* filter_push / filter_push_group calls          */
+    int64_t kernel_launches; /* this library's kernels launched                */
+    int64_t h2d_bytes;       /* host -> device bytes copied by pushes          */
+    int64_t d2h_bytes;       /* device -> host bytes copied for triggers       */
+    int64_t triggers;        /* triggers delivered by triggers_pop             */
+} sb_ctx_stats;
+int sb_ctx_get_stats(sb_ctx *ctx, sb_ctx_stats *out);
+
+/* enable != 0: bracket every kernel launch with CUDA events on the context's
+ * stream; enable == 0: stop.  Enabling clears previously collected times. */
+int sb_ctx_profile(sb_ctx *ctx, int32_t enable);
+/* Blocks until queued work is done, then writes per stage the summed kernel
+ * time (ms) and the number of launches since profiling was enabled
+ * (arrays of n_stages entries; n_stages <= SB_N_STAGES). */
+int sb_ctx_stage_times(sb_ctx *ctx, double *ms, int64_t *launches, int32_t n_stages);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char *sb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LLOID_H */

@@ -1,0 +1,260 @@
+"""ctypes binding of ``liblloid.so`` (include/lloid.h): argument marshalling only.
+
+Every step of the filter runs in the library's CUDA kernels; this module only
+converts Python/numpy/torch arguments into the C structures and pointers the
+C ABI takes.  There is no CPU fallback: if the library is missing, importing
+this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblloid.so")
+
+SB_OK, SB_EINVAL, SB_ENOMEM, SB_EBUSY, SB_EGAP, SB_ETIMEOUT, SB_ECUDA, SB_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6, -7
+PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3}
+SB_FLAG_KEEP_SNR = 1
+SB_TRIG_REFINED = 1
+
+
+class SbSlice(C.Structure):
+    _fields_ = [("rate_hz", C.c_double), ("t_start_s", C.c_double), ("t_end_s", C.c_double),
+                ("n_basis", C.c_int32), ("n_taps", C.c_int32),
+                ("basis", C.POINTER(C.c_double)), ("mixing", C.POINTER(C.c_double))]
+
+
+class SbDesc(C.Structure):
+    _fields_ = [("n_templates", C.c_int32), ("n_slices", C.c_int32), ("top_rate_hz", C.c_double),
+                ("slices", C.POINTER(SbSlice)), ("template_ids", C.POINTER(C.c_int64)),
+                ("precision", C.c_int32), ("flags", C.c_int32), ("threshold", C.c_float),
+                ("refine_threshold", C.c_float), ("window_s", C.c_double), ("max_push_samples", C.c_int64)]
+
+
+class SbTrigger(C.Structure):
+    _fields_ = [("unit", C.c_int64), ("template_id", C.c_int64), ("sample", C.c_int64), ("window", C.c_int64),
+                ("snr", C.c_float), ("phase", C.c_float), ("flags", C.c_int32), ("reserved", C.c_int32)]
+
+
+class SbUnitInfo(C.Structure):
+    _fields_ = [("unit", C.c_int64), ("n_templates", C.c_int32), ("n_slices", C.c_int32), ("k_max", C.c_int32),
+                ("precision", C.c_int32), ("latency_samples", C.c_int64), ("samples_pushed", C.c_int64),
+                ("device_bytes", C.c_int64), ("flops_per_second", C.c_int64)]
+
+
+class SbCtxStats(C.Structure):
+    _fields_ = [("pushes", C.c_int64), ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64), ("triggers", C.c_int64)]
+
+
+STAGES = ["history", "strain", "decimate", "fir", "upsample", "mix", "trigger", "snr_history"]
+
+TRIGGER_DTYPE = np.dtype([("unit", "<i8"), ("template_id", "<i8"), ("sample", "<i8"), ("window", "<i8"),
+                          ("snr", "<f4"), ("phase", "<f4"), ("flags", "<i4"), ("reserved", "<i4")])
+assert TRIGGER_DTYPE.itemsize == C.sizeof(SbTrigger)
+
+# name -> (restype, argtypes): every entry point declared in include/lloid.h
+SIGNATURES = {
+    "sb_ctx_create": (C.c_int, [C.c_int32, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
+    "sb_ctx_destroy": (C.c_int, [C.c_void_p]),
+    "sb_ctx_sync": (C.c_int, [C.c_void_p]),
+    "svdbank_create": (C.c_int, [C.c_void_p, C.POINTER(SbDesc), C.c_int32, C.POINTER(C.c_void_p)]),
+    "svdbank_destroy": (C.c_int, [C.c_void_p]),
+    "sb_unit_query": (C.c_int, [C.c_void_p, C.POINTER(SbUnitInfo)]),
+    "svdbank_plan": (C.c_int, [C.POINTER(SbDesc), C.POINTER(SbUnitInfo)]),
+    "filter_push": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32]),
+    "filter_push_group": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                    C.c_int64, C.POINTER(C.c_int64), C.c_int32]),
+    "triggers_pop": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "sb_unit_snr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "sb_ctx_get_stats": (C.c_int, [C.c_void_p, C.POINTER(SbCtxStats)]),
+    "sb_ctx_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sb_ctx_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
+    "sb_last_error": (C.c_char_p, []),
+}
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2410_16416_b300.build` "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load_library()
+
+
+class LloidError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib.sb_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+def _check(rc: int, where: str) -> int:
+    if rc != SB_OK:
+        raise LloidError(rc, where)
+    return rc
+
+
+def _ptr(a) -> int:
+    """Device or host data pointer of a torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def make_desc(bank, precision: str = "fp32", threshold: float = 6.0, refine_threshold: float = 0.0,
+              window_s: float = 1.0, max_push_samples: int = 0, keep_snr: bool = False,
+              template_ids: Optional[Sequence[int]] = None):
+    """(SbDesc, keep-alive list) for a bank; the arrays must outlive the C call."""
+    keep = []
+    sl = (SbSlice * len(bank.slices))()
+    for i, s in enumerate(bank.slices):
+        basis = np.ascontiguousarray(s.basis, dtype=np.float64)
+        mixing = np.ascontiguousarray(s.mixing, dtype=np.float64)
+        keep += [basis, mixing]
+        sl[i] = SbSlice(float(s.rate_hz), float(s.t_start_s), float(s.t_end_s), basis.shape[0], basis.shape[1],
+                        basis.ctypes.data_as(C.POINTER(C.c_double)), mixing.ctypes.data_as(C.POINTER(C.c_double)))
+    keep.append(sl)
+    ids = None
+    if template_ids is not None:
+        ids = np.ascontiguousarray(template_ids, dtype=np.int64)
+        keep.append(ids)
+    d = SbDesc(int(bank.n_templates), len(bank.slices), float(bank.top_rate_hz), sl,
+               ids.ctypes.data_as(C.POINTER(C.c_int64)) if ids is not None else None,
+               PRECISION[precision], SB_FLAG_KEEP_SNR if keep_snr else 0, float(threshold),
+               float(refine_threshold), float(window_s), int(max_push_samples))
+    return d, keep
+
+
+def plan(bank, **kw) -> SbUnitInfo:
+    """svdbank_plan: validate a bank and report latency, bytes and FLOPs (no device needed)."""
+    d, keep = make_desc(bank, **kw)
+    info = SbUnitInfo()
+    _check(lib.svdbank_plan(C.byref(d), C.byref(info)), "svdbank_plan")
+    return info
+
+
+class Context:
+    """sb_ctx: one device, one stream, one HBM budget, one trigger queue."""
+
+    def __init__(self, device: int = 0, stream=None, hbm_budget_bytes: int = 0):
+        h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(int(stream))
+        _check(lib.sb_ctx_create(device, s, int(hbm_budget_bytes), C.byref(h)), "sb_ctx_create")
+        self.handle = h
+        self.units: List["Unit"] = []
+
+    def close(self):
+        if self.handle:
+            lib.sb_ctx_destroy(self.handle)       # also destroys the context's units
+            self.handle = None
+            for u in self.units:
+                u.handle = None
+            self.units = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        _check(lib.sb_ctx_sync(self.handle), "sb_ctx_sync")
+
+    def stats(self) -> dict:
+        st = SbCtxStats()
+        _check(lib.sb_ctx_get_stats(self.handle, C.byref(st)), "sb_ctx_get_stats")
+        return {k: getattr(st, k) for k, _ in SbCtxStats._fields_}
+
+    def profile(self, enable: bool):
+        _check(lib.sb_ctx_profile(self.handle, int(bool(enable))), "sb_ctx_profile")
+
+    def stage_times(self) -> dict:
+        """{stage: (ms summed over launches, launches)} since profile(True); blocks."""
+        n = len(STAGES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        _check(lib.sb_ctx_stage_times(self.handle, ms, cnt, n), "sb_ctx_stage_times")
+        return {STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+    def create_unit(self, bank, detector: int = 0, **kw) -> "Unit":
+        """svdbank_create from any bank with n_templates, top_rate_hz and slices
+        (rate_hz, t_start_s, t_end_s, basis [L, Q], mixing [2M, L]); keywords as make_desc."""
+        d, keep = make_desc(bank, **kw)
+        h = C.c_void_p()
+        _check(lib.svdbank_create(self.handle, C.byref(d), int(detector), C.byref(h)), "svdbank_create")
+        u = Unit(self, h)
+        self.units.append(u)
+        return u
+
+    def push_group(self, units: Sequence["Unit"], strains: Sequence, t0: Sequence[int], on_device: bool):
+        n = len(units)
+        hs = (C.c_void_p * n)(*[u.handle.value for u in units])
+        ps = (C.c_void_p * n)(*[_ptr(s) for s in strains])
+        ts = (C.c_int64 * n)(*[int(t) for t in t0])
+        ns = int(strains[0].shape[0])
+        _check(lib.filter_push_group(self.handle, n, hs, ps, ns, ts, int(bool(on_device))), "filter_push_group")
+        for u in units:
+            u.last_push_len = ns
+
+    def pop_triggers(self, cap: int = 1 << 16) -> np.ndarray:
+        """triggers_pop until empty; returns a structured array (TRIGGER_DTYPE)."""
+        chunks = []
+        while True:
+            buf = np.empty(cap, dtype=TRIGGER_DTYPE)
+            n = C.c_int64()
+            _check(lib.triggers_pop(self.handle, buf.ctypes.data, cap, C.byref(n)), "triggers_pop")
+            chunks.append(buf[: n.value])
+            if n.value < cap:
+                break
+        return np.concatenate(chunks) if chunks else np.empty(0, dtype=TRIGGER_DTYPE)
+
+
+class Unit:
+    """sb_unit: one SVD bank on one detector."""
+
+    def __init__(self, ctx: Context, handle: C.c_void_p):
+        self.ctx = ctx
+        self.handle = handle
+        self.last_push_len = 0
+
+    def info(self) -> SbUnitInfo:
+        i = SbUnitInfo()
+        _check(lib.sb_unit_query(self.handle, C.byref(i)), "sb_unit_query")
+        return i
+
+    def push(self, strain, t0: Optional[int] = None):
+        """filter_push: strain is a numpy FP32 array (host) or a CUDA torch tensor (device)."""
+        on_device = hasattr(strain, "is_cuda") and strain.is_cuda
+        if not on_device:
+            strain = np.ascontiguousarray(strain, dtype=np.float32)
+        if t0 is None:
+            t0 = self.info().samples_pushed
+        _check(lib.filter_push(self.handle, C.c_void_p(_ptr(strain)), int(strain.shape[0]), int(t0),
+                               int(on_device)), "filter_push")
+        self.last_push_len = int(strain.shape[0])
+
+    def snr(self):
+        """(first_sample, x [2M, n]) of the last push (needs keep_snr=True); blocks."""
+        M2 = 2 * self.info().n_templates
+        first, n = C.c_int64(), C.c_int64()
+        buf = np.empty(M2 * max(1, self.last_push_len), dtype=np.float32)
+        _check(lib.sb_unit_snr(self.handle, buf.ctypes.data, buf.size, C.byref(first), C.byref(n)), "sb_unit_snr")
+        return first.value, buf[: M2 * n.value].reshape(M2, n.value)
+
+    def destroy(self):
+        if self.handle and self.ctx.handle:
+            lib.svdbank_destroy(self.handle)
+            self.ctx.units.remove(self)
+        self.handle = None

@@ -1,0 +1,279 @@
+// SIMT kernels of the LLOID hot path: halfband decimation (a1), interpolation
+// (a4), history copies, the FP32 GEMM used for the basis FIR (a2, Toeplitz B
+// operand) and the mixing step (a3) in SB_FP32 mode, and the window-maximum
+// trigger generator (a5).  Every kernel walks a device task list so that one
+// launch serves all units of a grouped push.
+#include "lloid_internal.h"
+
+namespace lloid {
+
+// ---------------------------------------------------------------------------
+// a1: decimation by two with the halfband kernel (g[0] = 1/2, odd taps only).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) decimate_kernel(const DecimTask *__restrict__ tasks, Halfband g) {
+    const DecimTask t = tasks[blockIdx.y];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= t.n_out) return;
+    if (t.first_m + p < 0) {               // every rate's signal starts at index 0
+        t.out[p] = 0.0f;
+        return;
+    }
+    const float *c = t.in + t.in_base + 2 * (int64_t)p;
+    float acc = 0.5f * c[0];
+#pragma unroll
+    for (int k = 0; k < kOddTaps; ++k) acc = fmaf(g.odd[k], c[-(2 * k + 1)] + c[2 * k + 1], acc);
+    t.out[p] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// a4 (up-sampling half): y'[n] = sum_m 2 g[n - 2m] y[m]; even n copy y[n/2].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float vread(const UpTask &t, int row, int64_t pos) {
+    return pos < t.n_hist ? t.hist[row * t.ld_hist + pos] : t.cur[row * t.ld_cur + (pos - t.n_hist)];
+}
+
+__global__ void __launch_bounds__(256) upsample_kernel(const UpTask *__restrict__ tasks, Halfband g) {
+    const UpTask t = tasks[blockIdx.z];
+    const int row = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= t.rows || p >= t.n_out) return;
+    float v = 0.0f;
+    if (t.first_n + p >= 0) {
+        const int64_t nrel = (int64_t)p - t.lam_out;
+        if ((nrel & 1) == 0) {
+            v = vread(t, row, nrel / 2 + t.in_off);
+        } else {
+            const int64_t lo = (nrel - 1) / 2 + t.in_off;   // m for j = +1
+#pragma unroll
+            for (int k = 0; k < kOddTaps; ++k)
+                v = fmaf(2.0f * g.odd[k], vread(t, row, lo - k) + vread(t, row, lo + 1 + k), v);
+        }
+    }
+    t.out[row * t.ld_out + p] = v;
+}
+
+// ---------------------------------------------------------------------------
+// history shifts: dst[r][i] = [hist | cur][r][off + i]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) copy_kernel(const CopyTask *__restrict__ tasks) {
+    const CopyTask t = tasks[blockIdx.z];
+    const int row = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= t.rows || i >= t.n) return;
+    const int64_t pos = (int64_t)t.off + i;
+    const float v = pos < t.n_hist ? t.hist[row * t.ld_hist + pos] : t.cur[row * t.ld_cur + (pos - t.n_hist)];
+    t.dst[row * t.ld_dst + i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 tiled GEMM over a task list (64 x 128 tile, 256 threads, 4x8 per thread).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_task_by_tile(const GemmTask *tasks, int n, int tile) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) gemm_fp32_kernel(const GemmTask *__restrict__ tasks, int n_tasks) {
+    constexpr int TM = kGemmTM, TN = kGemmTN, TK = kGemmTK;
+    __shared__ __align__(16) float As[TK][TM + 4];
+    __shared__ __align__(16) float Bs[TK][TN];
+    const int ti = find_task_by_tile(tasks, n_tasks, blockIdx.x);
+    const GemmTask t = tasks[ti];
+    const int local = blockIdx.x - t.tile_begin;
+    const int m0 = (local / t.tiles_n) * TM;
+    const int n0 = (local % t.tiles_n) * TN;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+    // loader coordinates
+    const int a_r = tid >> 2, a_c = (tid & 3) * 4;      // A: 64 rows x 16 k
+    const int b_r = tid >> 4, b_c = (tid & 15) * 8;     // B: 16 k x 128 cols
+
+    for (int k0 = 0; k0 < t.K; k0 += TK) {
+        {
+            const int gm = m0 + a_r;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int gk = k0 + a_c + i;
+                As[a_c + i][a_r] = (gm < t.M && gk < t.K) ? t.A[gm * t.lda + gk] : 0.0f;
+            }
+        }
+        {
+            const int gk = k0 + b_r;
+            if (t.toeplitz) {
+                const float *x = t.B + t.ldb - gk;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int gn = n0 + b_c + j;
+                    Bs[b_r][b_c + j] = (gk < t.K && gn < t.N) ? x[gn] : 0.0f;
+                }
+            } else {
+                const float *brow = t.B + (int64_t)gk * t.ldb;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int gn = n0 + b_c + j;
+                    Bs[b_r][b_c + j] = (gk < t.K && gn < t.N) ? brow[gn] : 0.0f;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TK; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[k][64 + tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + ty * 4 + i;
+        if (gm >= t.M) continue;
+        float *crow = t.C + (int64_t)gm * t.ldc;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+            if (gn < t.N) crow[gn] = t.beta ? crow[gn] + acc[i][j] : acc[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a5: per (template, window) maximum of |rho|^2 (first index on ties), strict
+// threshold, phase; one warp per (unit, template, window segment).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool better(float m_a, int64_t n_a, float m_b, int64_t n_b) {
+    return m_a > m_b || (m_a == m_b && n_a < n_b);
+}
+
+__device__ __forceinline__ int find_task_by_warp(const WinTask *tasks, int n, int w) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].warp_begin <= w) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restrict__ tasks, int n_tasks,
+                                                         int total_warps, TrigOut out) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= total_warps) return;
+    const WinTask &t = tasks[find_task_by_warp(tasks, n_tasks, gw)];
+    const int local = gw - t.warp_begin;
+    const int i = local / t.n_seg;
+    const int s = local % t.n_seg;
+    const int64_t start_abs = t.first_n > 0 ? t.first_n : 0;
+    const int64_t end_abs = t.first_n + t.n;
+    const int64_t w = start_abs / t.win_len + s;
+    const int64_t seg_lo = max(w * t.win_len, start_abs);
+    const int64_t seg_hi = min((w + 1) * t.win_len, end_abs);
+    const float *xc = t.x + (int64_t)(2 * i) * t.ldx;    // column p <-> absolute n = first_n + p
+    const float *xs = xc + t.ldx;
+
+    float best = -1.0f;
+    int64_t bn = INT64_MAX;
+    for (int64_t n = seg_lo + lane; n < seg_hi; n += 32) {
+        const float c = xc[n - t.first_n], q = xs[n - t.first_n];
+        const float m2 = fmaf(q, q, c * c);
+        if (m2 > best) { best = m2; bn = n; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
+        if (better(ob, on, best, bn)) { best = ob; bn = on; }
+    }
+    if (lane != 0) return;
+    float re = 0.0f, im = 0.0f;
+    if (bn != INT64_MAX) { re = xc[bn - t.first_n]; im = xs[bn - t.first_n]; }
+    if (s == 0) {                          // the open window carried over from the last push
+        const WinState st = t.state_in[i];
+        if (st.mag2 >= 0.0f && !(best > st.mag2)) { best = st.mag2; bn = st.n; re = st.re; im = st.im; }
+    }
+    const bool complete = (w + 1) * t.win_len <= end_abs;
+    if (complete) {
+        if (bn != INT64_MAX && sqrtf(best) > t.threshold) {
+            const int slot = atomicAdd(out.count, 1);
+            if (slot < out.cap) {
+                DevTrigger r;
+                r.unit = t.unit_id;
+                r.template_id = t.template_ids[i];
+                r.sample = bn;
+                r.window = w;
+                r.snr = sqrtf(best);
+                r.phase = atan2f(im, re);
+                r.flags = 0;
+                r.reserved = 0;
+                out.buf[slot] = r;
+            } else {
+                atomicExch(out.count + 1, 1);
+            }
+        }
+    }
+    if (s == t.n_seg - 1) {
+        WinState ns;
+        if (complete) { ns.mag2 = -1.0f; ns.re = ns.im = 0.0f; ns.n = -1; }
+        else { ns.mag2 = best; ns.re = re; ns.im = im; ns.n = bn; }
+        t.state_out[i] = ns;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,
+                            cudaStream_t s) {
+    if (n_tasks == 0 || max_out <= 0) return cudaSuccess;
+    dim3 grid((max_out + 255) / 256, n_tasks);
+    decimate_kernel<<<grid, 256, 0, s>>>(d_tasks, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upsample(const UpTask *d_tasks, int n_tasks, int max_rows, int max_out,
+                            const Halfband &g, cudaStream_t s) {
+    if (n_tasks == 0 || max_out <= 0 || max_rows <= 0) return cudaSuccess;
+    dim3 grid((max_out + 255) / 256, max_rows, n_tasks);
+    upsample_kernel<<<grid, 256, 0, s>>>(d_tasks, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const CopyTask *d_tasks, int n_tasks, int max_rows, int max_n, cudaStream_t s) {
+    if (n_tasks == 0 || max_n <= 0 || max_rows <= 0) return cudaSuccess;
+    dim3 grid((max_n + 255) / 256, max_rows, n_tasks);
+    copy_kernel<<<grid, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_fp32(const GemmTask *d_tasks, int n_tasks, int total_tiles, cudaStream_t s) {
+    if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
+    gemm_fp32_kernel<<<total_tiles, 256, 0, s>>>(d_tasks, n_tasks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_max(const WinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
+                              cudaStream_t s) {
+    if (n_tasks == 0 || total_warps == 0) return cudaSuccess;
+    const int blocks = (total_warps * 32 + 255) / 256;
+    window_max_kernel<<<blocks, 256, 0, s>>>(d_tasks, n_tasks, total_warps, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lloid

@@ -1,0 +1,1062 @@
+// Host runtime and C ABI of the LLOID filter (include/lloid.h).
+//
+// Per unit (one SVD bank on one detector) the device holds, for every level k
+// (rate f0/2^k): the decimated strain with its history (ping-pong buffers),
+// the basis filters of the slices at that level, the level's stacked mixing
+// matrix, the basis outputs of the current push, the level's SNR block and
+// the short SNR history the interpolator needs.  A push runs every stage as
+// one launch over all units of the group (task lists, Sec. II.B), then the
+// window-max trigger generator, and copies only the triggers back (Sec. II.B).
+//
+// Streaming bookkeeping (all per level k, in level-k samples, T = top-rate
+// samples pushed so far, a multiple of 2^k_max):
+//   decimated strain is final for  m <  A_k = T/2^k - e_k,
+//       e_0 = 0, e_{k+1} = ceil((e_k + 1 + 2K)/2) - 1   (the halfband look-ahead);
+//   SNR at level k is produced for m < Y_k = T/2^k - Lam_k,
+//       Lam_k >= e_k - D_s for every slice s at level k (its FIR needs d up to m - D_s),
+//       Lam_{k-1} >= 2 Lam_k + 2K + 1                 (interpolation look-ahead).
+// Every push therefore produces exactly B/2^k new samples at every level and
+// the top-rate SNR x[n] is final for n < T - Lam_0.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lloid.h"
+#include "lloid_internal.h"
+
+using namespace lloid;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(SB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// halfband taps: g[0] = 1/2, odd taps ~ sinc(j/2) * Kaiser_{beta=8.6}(j), |j| <= 2K,
+// scaled so that the odd taps sum to 1/2 (unit DC gain, H(w) + H(pi-w) = 1).
+// ---------------------------------------------------------------------------
+static double i0_series(double x) {
+    double sum = 1.0, term = 1.0;
+    for (int k = 1; k < 80; ++k) {
+        term *= (0.5 * x / k) * (0.5 * x / k);
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+static Halfband make_halfband() {
+    const double beta = 8.6, half_width = 2.0 * kHalfK;
+    const double pi = 3.14159265358979323846;
+    double taps[kOddTaps], total = 0.0;
+    for (int t = 0; t < kOddTaps; ++t) {
+        const double j = 2.0 * t + 1.0;
+        const double arg = pi * j / 2.0;
+        const double r = std::sqrt(std::max(0.0, 1.0 - (j / half_width) * (j / half_width)));
+        taps[t] = std::sin(arg) / arg * i0_series(beta * r) / i0_series(beta);
+        total += 2.0 * taps[t];                        // taps at +j and -j
+    }
+    Halfband g;
+    for (int t = 0; t < kOddTaps; ++t) g.odd[t] = (float)(taps[t] * 0.5 / total);
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// objects
+// ---------------------------------------------------------------------------
+struct SliceDev {
+    int level = 0, L = 0, Q = 0;
+    int64_t D = 0;
+    float *V = nullptr;       // [L x Q]
+    int o_row = 0;            // first row in the level's basis-output block
+};
+
+struct LevelDev {
+    int k = 0;
+    int Lk = 0;               // basis vectors of all slices at this level
+    int64_t e = 0, lam = 0, Hd = 0, Hy = 0, Bk_max = 0;
+    float *dbuf[2] = {nullptr, nullptr};
+    int dcur = 0;
+    int64_t last_Bk = 0;
+    float *ynew = nullptr;    // [2M x ldy]
+    int64_t ldy = 0;
+    float *yhist[2] = {nullptr, nullptr};   // [2M x Hy]
+    int ycur = 0;
+    float *Mcat = nullptr;    // [2M x Lk]
+    float *obuf = nullptr;    // [Lk x Bk_max]
+    std::vector<int> slices;
+};
+
+struct TriggerSlot {
+    DevTrigger *dbuf = nullptr;
+    int32_t *dcount = nullptr;
+    int64_t cap = 0;
+    DevTrigger *hbuf = nullptr;      // pinned, eager part
+    int32_t *hcount = nullptr;       // pinned [2]
+    int eager = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+};
+
+struct TaskArena {
+    char *h = nullptr;               // pinned
+    char *d = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool used = false;
+};
+
+struct sb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t pop_stream = nullptr;
+    bool own_stream = false;
+    int64_t budget = 0, used = 0;
+    Halfband g;
+    int64_t next_unit_id = 0;
+    std::vector<sb_unit *> units;
+    std::vector<TriggerSlot> slots;
+    std::deque<int> pending;         // slot indices in push order
+    int next_slot = 0;
+    std::vector<TaskArena> arenas;
+    int next_arena = 0;
+    std::deque<sb_trigger> ready;
+    bool overflow = false;
+    std::mutex mu;
+    sb_ctx_stats stats{};
+    // profiling: event pairs around each launch, summed per stage on query
+    bool prof = false;
+    struct Mark { int stage; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+struct sb_unit {
+    sb_ctx *ctx = nullptr;
+    int64_t id = 0;
+    int32_t detector = 0;
+    int M = 0, precision = 0, flags = 0;
+    float thr = 0.f, refine_thr = 0.f;
+    double f0 = 0.0;
+    int64_t win_len = 0;
+    int kmax = 0;
+    int64_t Bmax = 0;
+    int64_t T = 0;
+    int64_t last_B = 0;
+    std::vector<SliceDev> slices;
+    std::vector<LevelDev> levels;
+    WinState *wstate[2] = {nullptr, nullptr};
+    int wcur = 0;
+    int64_t *tids = nullptr;
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    int64_t flops_per_s = 0;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+static int dev_alloc(sb_unit *u, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    u->allocs.push_back(*p);
+    return SB_OK;
+}
+
+static void free_unit_memory(sb_unit *u) {
+    for (void *p : u->allocs) cudaFree(p);
+    u->allocs.clear();
+}
+
+static void release_marks(sb_ctx *c);
+
+static int activate(sb_ctx *ctx) {
+    CK(cudaSetDevice(ctx->device));
+    return SB_OK;
+}
+
+// Layout parameters of one unit, computed before any allocation (admission).
+struct Plan {
+    int kmax = 0;
+    std::vector<int64_t> e, lam, Hd, Hy, Lk;
+    int64_t bytes = 0;
+};
+
+static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &P) {
+    const int S = d->n_slices;
+    levels_of_slice.assign(S, 0);
+    int kmax = 0;
+    for (int s = 0; s < S; ++s) {
+        const sb_slice &sl = d->slices[s];
+        if (!(sl.rate_hz > 0) || sl.n_basis <= 0 || sl.n_taps <= 0 || !sl.basis || !sl.mixing)
+            return fail(SB_EINVAL, "slice " + std::to_string(s) + ": bad rate, shape or null array");
+        const double ratio = d->top_rate_hz / sl.rate_hz;
+        const int k = (int)std::lround(std::log2(ratio));
+        if (k < 0 || k > 16 || std::fabs(std::ldexp(sl.rate_hz, k) - d->top_rate_hz) > 1e-9 * d->top_rate_hz)
+            return fail(SB_EINVAL, "slice " + std::to_string(s) + ": rate must be top_rate / 2^k");
+        const double dq = (sl.t_end_s - sl.t_start_s) * sl.rate_hz;
+        const double dd = sl.t_start_s * sl.rate_hz;
+        if (sl.t_start_s < 0 || std::fabs(dq - std::llround(dq)) > 1e-6 || std::fabs(dd - std::llround(dd)) > 1e-6 ||
+            std::llround(dq) != sl.n_taps)
+            return fail(SB_EINVAL, "slice " + std::to_string(s) + ": span must hold n_taps samples on its rate grid");
+        levels_of_slice[s] = k;
+        kmax = std::max(kmax, k);
+    }
+    P.kmax = kmax;
+    const int NL = kmax + 1;
+    P.e.assign(NL, 0);
+    P.lam.assign(NL, 0);
+    P.Hd.assign(NL, 0);
+    P.Hy.assign(NL, 0);
+    P.Lk.assign(NL, 0);
+    for (int k = 0; k + 1 < NL; ++k) P.e[k + 1] = (P.e[k] + 1 + 2 * kHalfK + 1) / 2 - 1;   // ceil(x/2) - 1
+    std::vector<int64_t> minD(NL, INT64_MAX);
+    for (int s = 0; s < S; ++s) {
+        const int k = levels_of_slice[s];
+        minD[k] = std::min<int64_t>(minD[k], std::llround(d->slices[s].t_start_s * d->slices[s].rate_hz));
+        P.Lk[k] += d->slices[s].n_basis;
+    }
+    for (int k = kmax; k >= 0; --k) {
+        int64_t lam = 0;
+        if (k < kmax) lam = 2 * P.lam[k + 1] + 2 * kHalfK + 1;
+        if (minD[k] != INT64_MAX) lam = std::max(lam, P.e[k] - minD[k]);
+        P.lam[k] = std::max<int64_t>(lam, 0);
+    }
+    for (int k = 0; k < NL; ++k) {
+        int64_t hd = 0;
+        if (k < kmax) hd = 2 * P.e[k + 1] - P.e[k] + 2 * kHalfK;
+        for (int s = 0; s < S; ++s) {
+            if (levels_of_slice[s] != k) continue;
+            const int64_t D = std::llround(d->slices[s].t_start_s * d->slices[s].rate_hz);
+            hd = std::max(hd, P.lam[k] - P.e[k] + D + d->slices[s].n_taps - 1);
+        }
+        P.Hd[k] = round_up(std::max<int64_t>(hd, 1), 32);
+        if (k >= 1) P.Hy[k] = round_up((P.lam[k - 1] + 2 * kHalfK) / 2 + 1 - P.lam[k], 4);
+    }
+    // bytes
+    const int64_t M2 = 2 * (int64_t)d->n_templates;
+    int64_t b = 0;
+    for (int k = 0; k < NL; ++k) {
+        const int64_t Bk = d->max_push_samples >> k;
+        const int64_t ldy = round_up(Bk, 4);
+        b += 2 * (P.Hd[k] + Bk) * 4;                 // decimated strain ping-pong
+        b += M2 * ldy * 4;                           // SNR block
+        b += 2 * M2 * P.Hy[k] * 4;                   // SNR history ping-pong
+        b += M2 * P.Lk[k] * 4 + P.Lk[k] * Bk * 4;    // mixing + basis outputs
+    }
+    for (int s = 0; s < S; ++s) b += (int64_t)d->slices[s].n_basis * d->slices[s].n_taps * 4;
+    b += 2 * (int64_t)d->n_templates * sizeof(WinState) + d->n_templates * 8;
+    P.bytes = b;
+    return SB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" int sb_ctx_create(int32_t device, void *stream, int64_t hbm_budget_bytes, sb_ctx **out) {
+    if (!out) return fail(SB_EINVAL, "out is null");
+    *out = nullptr;
+    int n = 0;
+    CK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(SB_EINVAL, "no such CUDA device");
+    sb_ctx *c = new sb_ctx();
+    c->device = device;
+    if (activate(c) != SB_OK) { delete c; return SB_ECUDA; }
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(SB_ECUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&c->pop_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return fail(SB_ECUDA, "cudaStreamCreate failed");
+    }
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { delete c; return fail(SB_ECUDA, "cudaMemGetInfo failed"); }
+    c->budget = hbm_budget_bytes > 0 ? hbm_budget_bytes : (int64_t)(0.9 * (double)fr);
+    c->g = make_halfband();
+    c->slots.resize(8);
+    for (auto &s : c->slots) {
+        if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost(&s.hcount, 2 * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&s.dcount, 2 * sizeof(int32_t)) != cudaSuccess) {
+            sb_ctx_destroy(c);
+            return fail(SB_ENOMEM, "trigger slot allocation failed");
+        }
+    }
+    c->arenas.resize(4);
+    for (auto &a : c->arenas) {
+        if (cudaEventCreateWithFlags(&a.ev, cudaEventDisableTiming) != cudaSuccess) {
+            sb_ctx_destroy(c);
+            return fail(SB_ECUDA, "event creation failed");
+        }
+    }
+    *out = c;
+    return SB_OK;
+}
+
+extern "C" int sb_ctx_destroy(sb_ctx *c) {
+    if (!c) return SB_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    while (!c->units.empty()) svdbank_destroy(c->units.back());
+    for (auto &s : c->slots) {
+        if (s.dbuf) cudaFree(s.dbuf);
+        if (s.dcount) cudaFree(s.dcount);
+        if (s.hbuf) cudaFreeHost(s.hbuf);
+        if (s.hcount) cudaFreeHost(s.hcount);
+        if (s.ev) cudaEventDestroy(s.ev);
+    }
+    for (auto &a : c->arenas) {
+        if (a.h) cudaFreeHost(a.h);
+        if (a.d) cudaFree(a.d);
+        if (a.ev) cudaEventDestroy(a.ev);
+    }
+    release_marks(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->pop_stream) cudaStreamDestroy(c->pop_stream);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return SB_OK;
+}
+
+extern "C" int sb_ctx_sync(sb_ctx *c) {
+    if (!c) return fail(SB_EINVAL, "ctx is null");
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    CK(cudaStreamSynchronize(c->stream));
+    return SB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// units
+// ---------------------------------------------------------------------------
+static int validate_desc(const sb_desc *d, std::vector<int> &lvl, Plan &P) {
+    if (!d) return fail(SB_EINVAL, "null description");
+    if (d->n_templates <= 0 || d->n_slices <= 0 || !d->slices || !(d->top_rate_hz > 0) || !(d->window_s > 0) ||
+        d->max_push_samples <= 0)
+        return fail(SB_EINVAL, "bad bank description (templates, slices, rate, window or max_push_samples)");
+    if (d->precision != SB_FP32)
+        return fail(SB_EINVAL, "precision mode not available in this build");
+    const double wl = d->window_s * d->top_rate_hz;
+    if (std::fabs(wl - std::llround(wl)) > 1e-6 || std::llround(wl) < 1)
+        return fail(SB_EINVAL, "window_s * top_rate_hz must be a positive integer");
+    int rc = plan_unit(d, lvl, P);
+    if (rc) return rc;
+    if (d->max_push_samples % (1LL << P.kmax))
+        return fail(SB_EINVAL, "max_push_samples must be a multiple of 2^k_max");
+    return SB_OK;
+}
+
+static int64_t plan_flops(const sb_desc *d) {
+    double f = 0.0;
+    for (int s = 0; s < d->n_slices; ++s) {
+        const sb_slice &sl = d->slices[s];
+        f += 2.0 * sl.n_basis * (sl.n_taps + 2.0 * d->n_templates) * sl.rate_hz;
+    }
+    return (int64_t)std::llround(f);
+}
+
+extern "C" int svdbank_plan(const sb_desc *d, sb_unit_info *info) {
+    if (!d || !info) return fail(SB_EINVAL, "null argument");
+    std::vector<int> lvl;
+    Plan P;
+    int rc = validate_desc(d, lvl, P);
+    if (rc) return rc;
+    std::memset(info, 0, sizeof(*info));
+    info->n_templates = d->n_templates;
+    info->n_slices = d->n_slices;
+    info->k_max = P.kmax;
+    info->precision = d->precision;
+    info->latency_samples = P.lam[0];
+    info->device_bytes = P.bytes;
+    info->flops_per_second = plan_flops(d);
+    return SB_OK;
+}
+
+extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_unit **out) {
+    if (!c || !d || !out) return fail(SB_EINVAL, "null argument");
+    *out = nullptr;
+    std::vector<int> lvl;
+    Plan P;
+    int rc = validate_desc(d, lvl, P);
+    if (rc) return rc;
+    const double wl = d->window_s * d->top_rate_hz;
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (c->used + P.bytes > c->budget)
+            return fail(SB_EBUSY, "HBM budget exhausted: unit needs " + std::to_string(P.bytes) + " bytes, " +
+                                      std::to_string(c->budget - c->used) + " free in budget");
+        c->used += P.bytes;
+    }
+    sb_unit *u = new sb_unit();
+    u->ctx = c;
+    u->detector = detector;
+    u->M = d->n_templates;
+    u->precision = d->precision;
+    u->flags = d->flags;
+    u->thr = d->threshold;
+    u->refine_thr = d->refine_threshold;
+    u->f0 = d->top_rate_hz;
+    u->win_len = std::llround(wl);
+    u->kmax = P.kmax;
+    u->Bmax = d->max_push_samples;
+    u->bytes = P.bytes;
+    const int64_t M2 = 2 * (int64_t)u->M;
+    auto cleanup = [&](int code) {
+        free_unit_memory(u);
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            c->used -= u->bytes;
+        }
+        delete u;
+        return code;
+    };
+    u->levels.resize(P.kmax + 1);
+    for (int k = 0; k <= P.kmax; ++k) {
+        LevelDev &L = u->levels[k];
+        L.k = k;
+        L.e = P.e[k];
+        L.lam = P.lam[k];
+        L.Hd = P.Hd[k];
+        L.Hy = P.Hy[k];
+        L.Lk = (int)P.Lk[k];
+        L.Bk_max = u->Bmax >> k;
+        L.ldy = round_up(L.Bk_max, 4);
+        for (int b = 0; b < 2; ++b) {
+            if ((rc = dev_alloc(u, (void **)&L.dbuf[b], (L.Hd + L.Bk_max) * 4))) return cleanup(rc);
+            if (cudaMemset(L.dbuf[b], 0, (L.Hd + L.Bk_max) * 4) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
+        }
+        if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return cleanup(rc);
+        if (L.Hy > 0) {
+            for (int b = 0; b < 2; ++b) {
+                if ((rc = dev_alloc(u, (void **)&L.yhist[b], M2 * L.Hy * 4))) return cleanup(rc);
+                if (cudaMemset(L.yhist[b], 0, M2 * L.Hy * 4) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
+            }
+        }
+        if (L.Lk > 0) {
+            if ((rc = dev_alloc(u, (void **)&L.Mcat, M2 * L.Lk * 4))) return cleanup(rc);
+            if ((rc = dev_alloc(u, (void **)&L.obuf, (int64_t)L.Lk * L.Bk_max * 4))) return cleanup(rc);
+        }
+    }
+    // slices: basis filters and the per-level stacked mixing matrices
+    std::vector<std::vector<float>> mcat(P.kmax + 1);
+    for (int k = 0; k <= P.kmax; ++k) mcat[k].assign(M2 * u->levels[k].Lk, 0.0f);
+    std::vector<int> row_of_level(P.kmax + 1, 0);
+    u->flops_per_s = plan_flops(d);
+    for (int s = 0; s < d->n_slices; ++s) {
+        const sb_slice &sl = d->slices[s];
+        SliceDev sd;
+        sd.level = lvl[s];
+        sd.L = sl.n_basis;
+        sd.Q = sl.n_taps;
+        sd.D = std::llround(sl.t_start_s * sl.rate_hz);
+        sd.o_row = row_of_level[sd.level];
+        row_of_level[sd.level] += sd.L;
+        std::vector<float> v((size_t)sd.L * sd.Q);
+        for (size_t i = 0; i < v.size(); ++i) v[i] = (float)sl.basis[i];
+        if ((rc = dev_alloc(u, (void **)&sd.V, v.size() * 4))) return cleanup(rc);
+        if (cudaMemcpy(sd.V, v.data(), v.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(SB_ECUDA, "basis upload"));
+        const int Lk = u->levels[sd.level].Lk;
+        for (int64_t a = 0; a < M2; ++a)
+            for (int l = 0; l < sd.L; ++l) mcat[sd.level][a * Lk + sd.o_row + l] = (float)sl.mixing[a * sd.L + l];
+        u->levels[sd.level].slices.push_back(s);
+        u->slices.push_back(sd);
+    }
+    for (int k = 0; k <= P.kmax; ++k) {
+        LevelDev &L = u->levels[k];
+        if (L.Lk == 0) continue;
+        if (cudaMemcpy(L.Mcat, mcat[k].data(), mcat[k].size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(SB_ECUDA, "mixing upload"));
+    }
+    // trigger state and template ids
+    std::vector<WinState> ws(u->M);
+    for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = 0.0f; w.n = -1; }
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dev_alloc(u, (void **)&u->wstate[b], u->M * sizeof(WinState)))) return cleanup(rc);
+        if (cudaMemcpy(u->wstate[b], ws.data(), u->M * sizeof(WinState), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(SB_ECUDA, "state upload"));
+    }
+    std::vector<int64_t> ids(u->M);
+    for (int i = 0; i < u->M; ++i) ids[i] = d->template_ids ? d->template_ids[i] : i;
+    if ((rc = dev_alloc(u, (void **)&u->tids, u->M * 8))) return cleanup(rc);
+    if (cudaMemcpy(u->tids, ids.data(), u->M * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup(fail(SB_ECUDA, "template id upload"));
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        u->id = c->next_unit_id++;
+        c->units.push_back(u);
+    }
+    *out = u;
+    return SB_OK;
+}
+
+extern "C" int svdbank_destroy(sb_unit *u) {
+    if (!u) return SB_OK;
+    sb_ctx *c = u->ctx;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_unit_memory(u);
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->used -= u->bytes;
+        c->units.erase(std::remove(c->units.begin(), c->units.end(), u), c->units.end());
+    }
+    delete u;
+    return SB_OK;
+}
+
+extern "C" int sb_unit_query(const sb_unit *u, sb_unit_info *info) {
+    if (!u || !info) return fail(SB_EINVAL, "null argument");
+    info->unit = u->id;
+    info->n_templates = u->M;
+    info->n_slices = (int32_t)u->slices.size();
+    info->k_max = u->kmax;
+    info->precision = u->precision;
+    info->latency_samples = u->levels[0].lam;
+    info->samples_pushed = u->T;
+    info->device_bytes = u->bytes;
+    info->flops_per_second = u->flops_per_s;
+    return SB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// instrumentation
+// ---------------------------------------------------------------------------
+static cudaEvent_t pool_event(sb_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Runs one stage's launches (fn returns a cudaError_t and adds its kernel
+// count to *n); with profiling on, brackets them with events.
+template <class F>
+static int run_stage(sb_ctx *c, int stage, F fn) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->prof) {
+        a = pool_event(c);
+        b = pool_event(c);
+        CK(cudaEventRecord(a, c->stream));
+    }
+    int n = 0;
+    cudaError_t e = fn(&n);
+    if (e != cudaSuccess) return fail(SB_ECUDA, std::string("stage launch: ") + cudaGetErrorString(e));
+    c->stats.kernel_launches += (stage == SB_STAGE_STRAIN) ? 0 : n;
+    if (c->prof) {
+        CK(cudaEventRecord(b, c->stream));
+        c->marks.push_back({stage, a, b});
+    }
+    return SB_OK;
+}
+
+extern "C" int sb_ctx_get_stats(sb_ctx *c, sb_ctx_stats *out) {
+    if (!c || !out) return fail(SB_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    *out = c->stats;
+    return SB_OK;
+}
+
+static void release_marks(sb_ctx *c) {
+    for (auto &m : c->marks) {
+        c->ev_pool.push_back(m.a);
+        c->ev_pool.push_back(m.b);
+    }
+    c->marks.clear();
+}
+
+extern "C" int sb_ctx_profile(sb_ctx *c, int32_t enable) {
+    if (!c) return fail(SB_EINVAL, "ctx is null");
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaStreamSynchronize(c->stream));
+    if (enable) release_marks(c);
+    c->prof = enable != 0;
+    return SB_OK;
+}
+
+extern "C" int sb_ctx_stage_times(sb_ctx *c, double *ms, int64_t *launches, int32_t n_stages) {
+    if (!c || !ms || !launches || n_stages < 0 || n_stages > SB_N_STAGES) return fail(SB_EINVAL, "bad argument");
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < n_stages; ++i) { ms[i] = 0.0; launches[i] = 0; }
+    for (auto &m : c->marks) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, m.a, m.b));
+        if (m.stage < n_stages) { ms[m.stage] += t; launches[m.stage] += 1; }
+    }
+    return SB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// triggers
+// ---------------------------------------------------------------------------
+static int drain_slot(sb_ctx *c, TriggerSlot &s, bool block) {
+    if (!s.pending) return SB_OK;
+    if (block) {
+        CK(cudaEventSynchronize(s.ev));
+    } else {
+        cudaError_t q = cudaEventQuery(s.ev);
+        if (q == cudaErrorNotReady) return 1;
+        if (q != cudaSuccess) return fail(SB_ECUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(q));
+    }
+    int64_t n = s.hcount[0];
+    if (s.hcount[1]) c->overflow = true;
+    if (n > s.cap) n = s.cap;
+    std::vector<sb_trigger> tr((size_t)n);
+    const int64_t ne = std::min<int64_t>(n, s.eager);
+    if (ne > 0) std::memcpy(tr.data(), s.hbuf, ne * sizeof(sb_trigger));
+    if (n > ne) {
+        CK(cudaMemcpyAsync(tr.data() + ne, s.dbuf + ne, (n - ne) * sizeof(sb_trigger), cudaMemcpyDeviceToHost,
+                           c->pop_stream));
+        CK(cudaStreamSynchronize(c->pop_stream));
+        c->stats.d2h_bytes += (n - ne) * (int64_t)sizeof(sb_trigger);
+    }
+    std::sort(tr.begin(), tr.end(), [](const sb_trigger &a, const sb_trigger &b) {
+        if (a.window != b.window) return a.window < b.window;
+        if (a.unit != b.unit) return a.unit < b.unit;
+        return a.template_id < b.template_id;
+    });
+    for (auto &t : tr) c->ready.push_back(t);
+    s.pending = false;
+    return SB_OK;
+}
+
+static int drain_ready_slots(sb_ctx *c, bool block_all) {
+    while (!c->pending.empty()) {
+        const int idx = c->pending.front();
+        int rc = drain_slot(c, c->slots[idx], block_all);
+        if (rc == 1) break;                      // not finished yet
+        if (rc < 0) return rc;
+        c->pending.pop_front();
+    }
+    return SB_OK;
+}
+
+extern "C" int triggers_pop(sb_ctx *c, sb_trigger *out, int64_t cap, int64_t *n_out) {
+    if (!c || !n_out || (cap > 0 && !out)) return fail(SB_EINVAL, "null argument");
+    *n_out = 0;
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    std::lock_guard<std::mutex> lk(c->mu);
+    int rc = drain_ready_slots(c, false);
+    if (rc < 0) return rc;
+    int64_t n = 0;
+    while (n < cap && !c->ready.empty()) {
+        out[n++] = c->ready.front();
+        c->ready.pop_front();
+    }
+    *n_out = n;
+    c->stats.triggers += n;
+    if (c->overflow) {
+        c->overflow = false;
+        return fail(SB_EOVERFLOW, "a push produced more triggers than its buffer holds; some were dropped");
+    }
+    return SB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// push
+// ---------------------------------------------------------------------------
+struct Packer {
+    std::vector<char> buf;
+    size_t add(const void *p, size_t bytes) {
+        size_t off = round_up((int64_t)buf.size(), 256);
+        buf.resize(off + bytes);
+        if (bytes) std::memcpy(buf.data() + off, p, bytes);
+        return off;
+    }
+};
+
+static int arena_acquire(sb_ctx *c, size_t bytes, TaskArena *&out) {
+    TaskArena &a = c->arenas[c->next_arena];
+    c->next_arena = (c->next_arena + 1) % (int)c->arenas.size();
+    if (a.used) CK(cudaEventSynchronize(a.ev));
+    if (a.cap < bytes) {
+        if (a.h) cudaFreeHost(a.h);
+        if (a.d) cudaFree(a.d);
+        a.h = nullptr;
+        a.d = nullptr;
+        size_t cap = (size_t)round_up((int64_t)bytes * 2, 1 << 16);
+        CK(cudaMallocHost(&a.h, cap));
+        CK(cudaMalloc(&a.d, cap));
+        a.cap = cap;
+    }
+    out = &a;
+    return SB_OK;
+}
+
+static int slot_acquire(sb_ctx *c, int64_t need, TriggerSlot *&out, int &idx) {
+    idx = c->next_slot;
+    c->next_slot = (c->next_slot + 1) % (int)c->slots.size();
+    TriggerSlot &s = c->slots[idx];
+    if (s.pending) {
+        // ring full: finish the oldest pushes first (keeps trigger order)
+        while (!c->pending.empty()) {
+            const int j = c->pending.front();
+            int rc = drain_slot(c, c->slots[j], true);
+            if (rc < 0) return rc;
+            c->pending.pop_front();
+            if (j == idx) break;
+        }
+    }
+    if (s.cap < need) {
+        if (s.dbuf) cudaFree(s.dbuf);
+        if (s.hbuf) cudaFreeHost(s.hbuf);
+        s.dbuf = nullptr;
+        s.hbuf = nullptr;
+        const int64_t cap = round_up(std::max<int64_t>(need, 1024), 1024);
+        CK(cudaMalloc(&s.dbuf, cap * sizeof(DevTrigger)));
+        s.eager = (int)std::min<int64_t>(cap, 64);
+        CK(cudaMallocHost(&s.hbuf, s.eager * sizeof(DevTrigger)));
+        s.cap = cap;
+    }
+    out = &s;
+    return SB_OK;
+}
+
+extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *units, const float *const *strains,
+                                 int64_t B, const int64_t *t0, int32_t on_device) {
+    if (!c || n_units <= 0 || !units || !strains || !t0) return fail(SB_EINVAL, "null or empty argument");
+    if (B <= 0) return fail(SB_EINVAL, "n_samples must be positive");
+    for (int i = 0; i < n_units; ++i) {
+        sb_unit *u = units[i];
+        if (!u || u->ctx != c) return fail(SB_EINVAL, "unit does not belong to this context");
+        if (!strains[i]) return fail(SB_EINVAL, "null strain pointer");
+        if (t0[i] != u->T)
+            return fail(SB_EGAP, "unit " + std::to_string(u->id) + ": t0 " + std::to_string(t0[i]) +
+                                     " is not contiguous with samples pushed so far (" + std::to_string(u->T) + ")");
+        if (B % (1LL << u->kmax)) return fail(SB_EINVAL, "n_samples must be a multiple of 2^k_max");
+        if (B > u->Bmax) return fail(SB_EINVAL, "n_samples exceeds max_push_samples");
+        for (int j = 0; j < i; ++j)
+            if (units[j] == u) return fail(SB_EINVAL, "a unit appears twice in one group");
+    }
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t st = c->stream;
+    int kall = 0;
+    for (int i = 0; i < n_units; ++i) kall = std::max(kall, units[i]->kmax);
+
+    std::vector<CopyTask> dcopy, ycopy;
+    std::vector<std::vector<DecimTask>> decim(kall);
+    std::vector<GemmTask> fir;
+    std::vector<std::vector<UpTask>> ups(kall + 1);
+    std::vector<std::vector<GemmTask>> recon(kall + 1);
+    std::vector<WinTask> win;
+    int max_hd = 0, max_hy = 0, max_rows = 0;
+    int64_t trig_need = 0;
+
+    for (int i = 0; i < n_units; ++i) {
+        sb_unit *u = units[i];
+        const int64_t Tp = u->T;
+        const int M2 = 2 * u->M;
+        max_rows = std::max(max_rows, M2);
+        for (int k = 0; k <= u->kmax; ++k) {
+            LevelDev &L = u->levels[k];
+            const int nb = 1 - L.dcur;
+            CopyTask ct{};
+            ct.cur = L.dbuf[L.dcur];
+            ct.dst = L.dbuf[nb];
+            ct.rows = 1;
+            ct.n = (int32_t)L.Hd;
+            ct.off = (int32_t)L.last_Bk;
+            dcopy.push_back(ct);
+            max_hd = std::max<int>(max_hd, (int)L.Hd);
+            const int64_t Bk = B >> k;
+            if (k < u->kmax) {
+                LevelDev &N = u->levels[k + 1];
+                DecimTask dt{};
+                dt.in = L.dbuf[nb];
+                dt.out = N.dbuf[1 - N.dcur] + N.Hd;
+                dt.in_base = L.Hd + L.e - 2 * N.e;
+                dt.first_m = (Tp >> (k + 1)) - N.e;
+                dt.n_out = (int32_t)(B >> (k + 1));
+                decim[k].push_back(dt);
+            }
+            for (int s : L.slices) {
+                const SliceDev &sd = u->slices[s];
+                GemmTask g{};
+                g.A = sd.V;
+                g.lda = sd.Q;
+                g.B = L.dbuf[nb];
+                g.ldb = L.Hd + L.e - L.lam - sd.D;
+                g.C = L.obuf + (int64_t)sd.o_row * L.Bk_max;
+                g.ldc = L.Bk_max;
+                g.M = sd.L;
+                g.N = (int32_t)Bk;
+                g.K = sd.Q;
+                g.beta = 0;
+                g.toeplitz = 1;
+                fir.push_back(g);
+            }
+            if (k < u->kmax) {
+                LevelDev &N = u->levels[k + 1];
+                UpTask ut{};
+                ut.hist = N.yhist[N.ycur];
+                ut.cur = N.ynew;
+                ut.out = L.ynew;
+                ut.ld_hist = N.Hy;
+                ut.ld_cur = N.ldy;
+                ut.ld_out = L.ldy;
+                ut.n_hist = (int32_t)N.Hy;
+                ut.rows = M2;
+                ut.n_out = (int32_t)Bk;
+                ut.lam_out = (int32_t)L.lam;
+                ut.in_off = (int32_t)(N.lam + N.Hy);
+                ut.first_n = (Tp >> k) - L.lam;
+                ups[k].push_back(ut);
+            }
+            if (L.Lk > 0) {
+                GemmTask g{};
+                g.A = L.Mcat;
+                g.lda = L.Lk;
+                g.B = L.obuf;
+                g.ldb = L.Bk_max;
+                g.C = L.ynew;
+                g.ldc = L.ldy;
+                g.M = M2;
+                g.N = (int32_t)Bk;
+                g.K = L.Lk;
+                g.beta = k < u->kmax ? 1 : 0;
+                g.toeplitz = 0;
+                recon[k].push_back(g);
+            }
+            if (k >= 1 && L.Hy > 0) {
+                CopyTask yt{};
+                yt.hist = L.yhist[L.ycur];
+                yt.cur = L.ynew;
+                yt.dst = L.yhist[1 - L.ycur];
+                yt.ld_hist = L.Hy;
+                yt.ld_cur = L.ldy;
+                yt.ld_dst = L.Hy;
+                yt.n_hist = (int32_t)L.Hy;
+                yt.rows = M2;
+                yt.n = (int32_t)L.Hy;
+                yt.off = (int32_t)Bk;
+                ycopy.push_back(yt);
+                max_hy = std::max<int>(max_hy, (int)L.Hy);
+            }
+        }
+        // trigger generator on the top level
+        LevelDev &L0 = u->levels[0];
+        const int64_t first_n = Tp - L0.lam;
+        const int64_t start = std::max<int64_t>(first_n, 0), end = first_n + B;
+        if (end > start) {
+            WinTask w{};
+            w.x = L0.ynew;
+            w.ldx = L0.ldy;
+            w.state_in = u->wstate[u->wcur];
+            w.state_out = u->wstate[1 - u->wcur];
+            w.template_ids = u->tids;
+            w.first_n = first_n;
+            w.unit_id = u->id;
+            w.win_len = u->win_len;
+            w.n = (int32_t)B;
+            w.M = u->M;
+            w.n_seg = (int32_t)((end - 1) / u->win_len - start / u->win_len + 1);
+            w.threshold = u->thr;
+            win.push_back(w);
+            trig_need += (int64_t)u->M * w.n_seg;
+        }
+    }
+
+    // tile / warp offsets
+    auto assign_tiles = [](std::vector<GemmTask> &v) {
+        int tot = 0;
+        for (auto &g : v) {
+            g.tiles_n = (g.N + kGemmTN - 1) / kGemmTN;
+            const int tiles_m = (g.M + kGemmTM - 1) / kGemmTM;
+            g.tile_begin = tot;
+            tot += tiles_m * g.tiles_n;
+        }
+        return tot;
+    };
+    const int fir_tiles = assign_tiles(fir);
+    std::vector<int> recon_tiles(kall + 1);
+    for (int k = 0; k <= kall; ++k) recon_tiles[k] = assign_tiles(recon[k]);
+    int win_warps = 0;
+    for (auto &w : win) {
+        w.warp_begin = win_warps;
+        win_warps += w.M * w.n_seg;
+    }
+
+    // pack task lists (and host strain) into one pinned block
+    Packer pk;
+    const size_t o_dcopy = pk.add(dcopy.data(), dcopy.size() * sizeof(CopyTask));
+    std::vector<size_t> o_decim(kall), o_ups(kall + 1), o_recon(kall + 1);
+    for (int k = 0; k < kall; ++k) o_decim[k] = pk.add(decim[k].data(), decim[k].size() * sizeof(DecimTask));
+    const size_t o_fir = pk.add(fir.data(), fir.size() * sizeof(GemmTask));
+    for (int k = 0; k <= kall; ++k) {
+        o_ups[k] = pk.add(ups[k].data(), ups[k].size() * sizeof(UpTask));
+        o_recon[k] = pk.add(recon[k].data(), recon[k].size() * sizeof(GemmTask));
+    }
+    const size_t o_win = pk.add(win.data(), win.size() * sizeof(WinTask));
+    const size_t o_ycopy = pk.add(ycopy.data(), ycopy.size() * sizeof(CopyTask));
+    std::vector<size_t> o_strain(n_units, 0);
+    if (!on_device)
+        for (int i = 0; i < n_units; ++i) o_strain[i] = pk.add(strains[i], B * sizeof(float));
+
+    TaskArena *ar = nullptr;
+    int rc = arena_acquire(c, pk.buf.size(), ar);
+    if (rc) return rc;
+    std::memcpy(ar->h, pk.buf.data(), pk.buf.size());
+    CK(cudaMemcpyAsync(ar->d, ar->h, pk.buf.size(), cudaMemcpyHostToDevice, st));
+    char *D = ar->d;
+
+    // 1. history shifts of the decimated strain
+    if ((rc = run_stage(c, SB_STAGE_HISTORY, [&](int *n) {
+             *n = dcopy.empty() ? 0 : 1;
+             return launch_copy((CopyTask *)(D + o_dcopy), (int)dcopy.size(), 1, max_hd, st);
+         })))
+        return rc;
+    // 2. new top-rate strain
+    if ((rc = run_stage(c, SB_STAGE_STRAIN, [&](int *n) {
+             for (int i = 0; i < n_units; ++i) {
+                 LevelDev &L0 = units[i]->levels[0];
+                 float *dst = L0.dbuf[1 - L0.dcur] + L0.Hd;
+                 const void *src = on_device ? (const void *)strains[i] : (const void *)(D + o_strain[i]);
+                 cudaError_t e = cudaMemcpyAsync(dst, src, B * sizeof(float), cudaMemcpyDeviceToDevice, st);
+                 if (e != cudaSuccess) return e;
+             }
+             return cudaSuccess;
+         })))
+        return rc;
+    // 3. a1 decimation cascade
+    for (int k = 0; k < kall; ++k)
+        if ((rc = run_stage(c, SB_STAGE_DECIMATE, [&](int *n) {
+                 *n = decim[k].empty() ? 0 : 1;
+                 return launch_decimate((DecimTask *)(D + o_decim[k]), (int)decim[k].size(), (int)(B >> (k + 1)),
+                                        c->g, st);
+             })))
+            return rc;
+    // 4. a2 basis FIR, all slices of all units at once
+    if ((rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
+             *n = fir.empty() ? 0 : 1;
+             return launch_gemm_fp32((GemmTask *)(D + o_fir), (int)fir.size(), fir_tiles, st);
+         })))
+        return rc;
+    // 5. a4 + a3 from the lowest rate up
+    for (int k = kall; k >= 0; --k) {
+        if (!ups[k].empty() &&
+            (rc = run_stage(c, SB_STAGE_UPSAMPLE, [&](int *n) {
+                 *n = 1;
+                 return launch_upsample((UpTask *)(D + o_ups[k]), (int)ups[k].size(), max_rows, (int)(B >> k),
+                                        c->g, st);
+             })))
+            return rc;
+        if (!recon[k].empty() &&
+            (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
+                 *n = 1;
+                 return launch_gemm_fp32((GemmTask *)(D + o_recon[k]), (int)recon[k].size(), recon_tiles[k], st);
+             })))
+            return rc;
+    }
+    // 6. a5 trigger generator
+    TriggerSlot *slot = nullptr;
+    int slot_idx = 0;
+    if ((rc = slot_acquire(c, trig_need, slot, slot_idx))) return rc;
+    CK(cudaMemsetAsync(slot->dcount, 0, 2 * sizeof(int32_t), st));
+    TrigOut to{slot->dbuf, slot->dcount, (int32_t)slot->cap};
+    if ((rc = run_stage(c, SB_STAGE_TRIGGER, [&](int *n) {
+             *n = win.empty() ? 0 : 1;
+             return launch_window_max((WinTask *)(D + o_win), (int)win.size(), win_warps, to, st);
+         })))
+        return rc;
+    // 7. SNR history for the interpolators of the next push
+    if ((rc = run_stage(c, SB_STAGE_SNRHIST, [&](int *n) {
+             *n = ycopy.empty() ? 0 : 1;
+             return launch_copy((CopyTask *)(D + o_ycopy), (int)ycopy.size(), max_rows, max_hy, st);
+         })))
+        return rc;
+    // 8. triggers to the host (count plus an eager prefix; the rest on demand)
+    CK(cudaMemcpyAsync(slot->hcount, slot->dcount, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(slot->hbuf, slot->dbuf, slot->eager * sizeof(DevTrigger), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(slot->ev, st));
+    slot->pending = true;
+    c->pending.push_back(slot_idx);
+    CK(cudaEventRecord(ar->ev, st));
+    ar->used = true;
+    c->stats.pushes += 1;
+    c->stats.h2d_bytes += (int64_t)pk.buf.size();
+    c->stats.d2h_bytes += 2 * sizeof(int32_t) + slot->eager * (int64_t)sizeof(DevTrigger);
+
+    // 9. advance host bookkeeping
+    for (int i = 0; i < n_units; ++i) {
+        sb_unit *u = units[i];
+        for (int k = 0; k <= u->kmax; ++k) {
+            LevelDev &L = u->levels[k];
+            L.dcur = 1 - L.dcur;
+            L.last_Bk = B >> k;
+            if (k >= 1 && L.Hy > 0) L.ycur = 1 - L.ycur;
+        }
+        const int64_t first_n = u->T - u->levels[0].lam;
+        if (first_n + B > std::max<int64_t>(first_n, 0)) u->wcur = 1 - u->wcur;
+        u->T += B;
+        u->last_B = B;
+    }
+    return SB_OK;
+}
+
+extern "C" int filter_push(sb_unit *u, const float *strain, int64_t n, int64_t t0, int32_t on_device) {
+    if (!u) return fail(SB_EINVAL, "unit is null");
+    sb_unit *const us[1] = {u};
+    const float *const ss[1] = {strain};
+    const int64_t ts[1] = {t0};
+    return filter_push_group(u->ctx, 1, us, ss, n, ts, on_device);
+}
+
+extern "C" int sb_unit_snr(sb_unit *u, float *host_out, int64_t cap, int64_t *first_sample, int64_t *n) {
+    if (!u || !first_sample || !n) return fail(SB_EINVAL, "null argument");
+    if (!(u->flags & SB_FLAG_KEEP_SNR)) return fail(SB_EINVAL, "unit was created without SB_FLAG_KEEP_SNR");
+    sb_ctx *c = u->ctx;
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    CK(cudaStreamSynchronize(c->stream));
+    const int64_t B = u->last_B;
+    const int64_t first = u->T - B - u->levels[0].lam;
+    const int64_t p0 = first < 0 ? std::min<int64_t>(-first, B) : 0;
+    const int64_t nv = B - p0;
+    *first_sample = first + p0;
+    *n = nv;
+    const int64_t M2 = 2 * (int64_t)u->M;
+    if (nv <= 0) return SB_OK;
+    if (!host_out || cap < M2 * nv) return fail(SB_EINVAL, "host buffer too small");
+    LevelDev &L0 = u->levels[0];
+    CK(cudaMemcpy2D(host_out, nv * sizeof(float), L0.ynew + p0, L0.ldy * sizeof(float), nv * sizeof(float), M2,
+                    cudaMemcpyDeviceToHost));
+    return SB_OK;
+}
+
+extern "C" const char *sb_last_error(void) { return g_err.c_str(); }

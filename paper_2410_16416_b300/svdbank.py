@@ -1,0 +1,61 @@
+"""Host-side setup: time-slice a template group and decompose each slice by SVD.
+
+This is the setup stage of Sec. II.A (templates grouped, split into time
+slices sampled at their own rates, each slice decomposed by SVD into
+orthonormal basis filters and coefficients).  It runs once per bank, in FP64
+on the host; its output is what ``svdbank_create`` consumes.
+
+Slice s covers [t_s, t_{s+1}) seconds before coalescence at rate
+f_s = f0 / 2^k.  Its filter matrix takes every 2^k-th template sample starting
+t_s f0 samples before coalescence, scaled by 2^k (the decimated data carry
+1/2^k of the band's samples).  The SVD keeps the fewest basis vectors whose
+squared singular values reach ``keep_power`` of the total.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Sequence
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class BankSlice:
+    rate_hz: float
+    t_start_s: float
+    t_end_s: float
+    basis: np.ndarray      # [L, Q]: orthonormal rows
+    mixing: np.ndarray     # [2M, L]
+
+
+@dataclasses.dataclass
+class SVDBank:
+    n_templates: int
+    top_rate_hz: float
+    slices: List[BankSlice]
+
+    def basis_counts(self) -> List[int]:
+        return [s.basis.shape[0] for s in self.slices]
+
+
+def decompose(templates: np.ndarray, top_rate_hz: float, slice_specs: Sequence,
+              keep_power: float = 0.9999) -> SVDBank:
+    """templates: [2M, N] real filters (row 2i cosine, 2i+1 sine), sample j = j/f0 s before coalescence."""
+    twoM, N = templates.shape
+    out = []
+    for sp in slice_specs:
+        level = int(round(math.log2(top_rate_hz / sp.rate_hz)))
+        stride = 1 << level
+        first = int(round(sp.t_start_s * top_rate_hz))
+        taps = int(round((sp.t_end_s - sp.t_start_s) * sp.rate_hz))
+        cols = first + stride * np.arange(taps)
+        if cols[-1] >= N:
+            raise ValueError("slice extends past the template length")
+        H = float(stride) * templates[:, cols]
+        u, sig, vt = np.linalg.svd(H, full_matrices=False)
+        energy = np.cumsum(sig * sig)
+        rank = min(int(np.searchsorted(energy, keep_power * energy[-1])) + 1, sig.size)
+        out.append(BankSlice(sp.rate_hz, sp.t_start_s, sp.t_end_s,
+                             np.ascontiguousarray(vt[:rank]), np.ascontiguousarray(u[:, :rank] * sig[:rank])))
+    return SVDBank(twoM // 2, top_rate_hz, out)

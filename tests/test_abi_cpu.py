@@ -1,0 +1,108 @@
+"""Host-side checks of the C-ABI library (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+import paper_2410_16416_b300 as lloid
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "lloid.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", txt, flags=re.M))
+
+
+def test_library_exports_every_declared_symbol():
+    names = header_functions()
+    assert {"svdbank_create", "filter_push", "triggers_pop", "svdbank_plan"} <= names
+    lib = C.CDLL(lloid.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert names <= set(lloid.SIGNATURES), "binding misses a declared entry point"
+
+
+def test_context_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lloid.LloidError) as e:
+        lloid.Context(0)
+    assert e.value.code == lloid.SB_ECUDA
+
+
+def _small_bank(n=8):
+    spec = synth.SMALL_BIN
+    h, _ = synth.template_bank(n, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 1, 0, 0)
+    return lloid.decompose(h, spec.top_rate_hz, spec.slices), h
+
+
+def independent_latency(levels_d, kmax, K=16):
+    """Re-derive the streaming look-ahead: e_{k+1} = ceil((e_k+1+2K)/2)-1,
+    Lam_k = max(2 Lam_{k+1} + 2K + 1, e_k - min D at k, 0)."""
+    e = [0]
+    for _ in range(kmax):
+        x = e[-1] + 1 + 2 * K
+        e.append(-(-x // 2) - 1)
+    lam = [0] * (kmax + 1)
+    for k in range(kmax, -1, -1):
+        v = 0 if k == kmax else 2 * lam[k + 1] + 2 * K + 1
+        if k in levels_d:
+            v = max(v, e[k] - min(levels_d[k]))
+        lam[k] = max(v, 0)
+    return lam[0]
+
+
+def test_plan_reports_latency_and_flops():
+    bank, _ = _small_bank()
+    info = lloid.plan(bank, max_push_samples=2048 * 4)
+    assert info.k_max == 2
+    assert info.latency_samples == independent_latency({0: [0], 2: [512]}, 2)
+    flops = sum(2 * s.basis.shape[0] * (s.basis.shape[1] + 2 * bank.n_templates) * s.rate_hz for s in bank.slices)
+    assert info.flops_per_second == round(flops)
+    # a production-shaped slice layout (delays at each level)
+    spec = synth.PRODUCTION_BIN
+    lv = {}
+    for sp in spec.slices:
+        k = int(round(np.log2(spec.top_rate_hz / sp.rate_hz)))
+        lv.setdefault(k, []).append(int(round(sp.t_start_s * sp.rate_hz)))
+    assert independent_latency(lv, 5) == 1023
+
+
+def test_plan_rejects_bad_banks():
+    bank, _ = _small_bank()
+    good = dict(max_push_samples=2048)
+    lloid.plan(bank, **good)
+    with pytest.raises(lloid.LloidError) as e:
+        lloid.plan(bank, max_push_samples=2046)              # not a multiple of 2^k_max
+    assert e.value.code == lloid.SB_EINVAL
+    with pytest.raises(lloid.LloidError):
+        lloid.plan(bank, max_push_samples=2048, window_s=1.0 / 3)
+    with pytest.raises(lloid.LloidError):
+        lloid.plan(bank, max_push_samples=0)
+    import copy
+    bad = copy.deepcopy(bank)
+    bad.slices[1].rate_hz = 600.0                             # not top / 2^k
+    with pytest.raises(lloid.LloidError):
+        lloid.plan(bad, **good)
+    bad = copy.deepcopy(bank)
+    bad.slices[1].basis = bad.slices[1].basis[:, :-1]         # taps do not fill the span
+    with pytest.raises(lloid.LloidError):
+        lloid.plan(bad, **good)
+
+
+def test_host_decomposition_matches_oracle_bank():
+    """The product's host-side SVD setup and the oracle's agree (ranks, reconstructions)."""
+    bank, h = _small_bank(12)
+    ob = oracle.build_bank(h, synth.SMALL_BIN.top_rate_hz, synth.SMALL_BIN.slices)
+    for s, o in zip(bank.slices, ob.slices):
+        assert s.basis.shape == o.basis.shape
+        assert np.abs(s.mixing @ s.basis - o.mixing @ o.basis).max() <= 1e-10
+        assert np.abs(s.basis @ s.basis.T - np.eye(s.basis.shape[0])).max() <= 1e-12

@@ -1,0 +1,201 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+FP32 mode bar: |rho_gpu - rho_oracle| <= 1e-4 max(1, |rho_oracle|) on every
+template and every produced sample; triggers equal wherever the decision is
+not within that tolerance of a tie.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import check_triggers, push_and_collect, rho_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def lloid():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2410_16416_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def small_case():
+    """64-template bin, slices [0,1) s @ 2048 Hz and [1,8) s @ 512 Hz, 16 s of noise + one A = 12 injection."""
+    spec = synth.SMALL_BIN
+    h, _ = synth.template_bank(spec.n_templates, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 1, 0, 0)
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    n = 16 * 2048
+    d = synth.white_noise(n, 1, 0, 0)
+    synth.inject(d, h, 17, 12 * 2048 + 777, 12.0, 1.1)
+    x = oracle.lloid_snr(bank, d)
+    return spec, h, bank, d, x
+
+
+def test_fp32_small_bin_matches_oracle(lloid, small_case):
+    spec, h, bank, d, x = small_case
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, precision="fp32", threshold=6.0, window_s=1.0, max_push_samples=4096, keep_snr=True)
+    lat = u.info().latency_samples
+    (xg,) = push_and_collect(ctx, [u], [d], [2048] * 16)
+    n_valid = d.shape[0] - lat
+    assert xg.shape == (128, n_valid)
+    err = rho_error(xg, x)
+    assert err <= TOL_FP32, err
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    matched = check_triggers(trig, x, 2048, 6.0, n_valid, 2 * TOL_FP32)
+    assert matched >= 1
+    inj = trig[(trig["template_id"] == 17) & (trig["window"] == 12)]
+    assert len(inj) == 1 and abs(inj["snr"][0] - 12.0) < 1.0
+    ctx.close()
+
+
+def test_fp32_every_window_max_matches_oracle(lloid, small_case):
+    """Threshold 0: every (template, window) maximum is a trigger; all are compared."""
+    spec, h, bank, d, x = small_case
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, threshold=0.0, max_push_samples=8192)
+    for t in range(0, d.shape[0], 8192):
+        u.push(d[t:t + 8192], t)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    n_valid = d.shape[0] - u.info().latency_samples
+    assert check_triggers(trig, x, 2048, 0.0, n_valid, 2 * TOL_FP32) == 64 * (n_valid // 2048)
+    ctx.close()
+
+
+def test_streaming_is_bitwise_independent_of_buffer_sizes(lloid, small_case):
+    spec, h, bank, d, x = small_case
+    runs = []
+    for sizes in ([2048] * 16, [8192] * 4, [4, 2044, 4096, 12, 6132, 8192, 8192, 4092]):
+        assert sum(sizes) == d.shape[0]
+        ctx = lloid.Context(0)
+        u = ctx.create_unit(bank, max_push_samples=8192, keep_snr=True)
+        (xg,) = push_and_collect(ctx, [u], [d], sizes)
+        ctx.sync()
+        runs.append((xg, np.sort(ctx.pop_triggers(), order=["window", "template_id"])))
+        ctx.close()
+    for xg, tr in runs[1:]:
+        assert np.array_equal(xg, runs[0][0])
+        assert np.array_equal(tr, runs[0][1])
+
+
+def _shape_banks(n, max_templates=40):
+    banks = []
+    for b in range(n):
+        sb = synth.shape_only_bank(1000 + b, dur_range=(2.0, 6.0), l_range=(5, 40), max_templates=max_templates)
+        banks.append(sb)
+    return banks
+
+
+def test_group_equals_alone_bitwise(lloid):
+    """One unit's SNR and triggers are identical alone and inside a grouped push (uneven shapes)."""
+    banks = _shape_banks(4)
+    n = 6 * 4096
+    strains = [synth.white_noise(n, 3, b, 0) for b in range(len(banks))]
+    sizes = [4096] * 6
+    ctx = lloid.Context(0)
+    units = [ctx.create_unit(b, threshold=3.0, max_push_samples=4096, keep_snr=True) for b in banks]
+    grouped = push_and_collect(ctx, units, strains, sizes)
+    ctx.sync()
+    tg = ctx.pop_triggers()
+    ctx.close()
+    for i, b in enumerate(banks):
+        c2 = lloid.Context(0)
+        u = c2.create_unit(b, threshold=3.0, max_push_samples=4096, keep_snr=True)
+        (alone,) = push_and_collect(c2, [u], [strains[i]], sizes)
+        c2.sync()
+        ta = c2.pop_triggers()
+        c2.close()
+        assert np.array_equal(alone, grouped[i])
+        mine = tg[tg["unit"] == i]
+        assert np.array_equal(np.sort(ta[["template_id", "sample", "window", "snr", "phase"]], order=["window", "template_id"]),
+                              np.sort(mine[["template_id", "sample", "window", "snr", "phase"]], order=["window", "template_id"]))
+
+
+def test_grouped_uneven_banks_match_oracle(lloid):
+    """Ragged shapes (M, L, Q, slice counts) in one grouped push, each unit against the oracle."""
+    banks = _shape_banks(3, max_templates=37)
+    n = 6 * 4096
+    strains = [synth.white_noise(n, 4, b, 0) for b in range(len(banks))]
+    ctx = lloid.Context(0)
+    units = [ctx.create_unit(b, threshold=4.0, max_push_samples=8192, keep_snr=True) for b in banks]
+    outs = push_and_collect(ctx, units, strains, [8192, 4096, 8192, 4096])
+    for b, d, xg in zip(banks, strains, outs):
+        ob = oracle.bank_from_arrays(b.n_templates, b.top_rate_hz, b.slices)
+        xo = oracle.lloid_snr(ob, d)
+        assert rho_error(xg, xo) <= TOL_FP32
+    ctx.close()
+
+
+def test_device_resident_strain_matches_host_strain(lloid, small_case):
+    spec, h, bank, d, x = small_case
+    res = []
+    for on_dev in (False, True):
+        ctx = lloid.Context(0)
+        u = ctx.create_unit(bank, max_push_samples=4096, keep_snr=True)
+        dd = torch.from_numpy(d).cuda() if on_dev else None
+        (xg,) = push_and_collect(ctx, [u], [d], [4096] * 8, on_device=on_dev, device_strains=[dd] if on_dev else None)
+        res.append(xg)
+        ctx.close()
+    assert np.array_equal(res[0], res[1])
+
+
+def test_error_statuses(lloid, small_case):
+    spec, h, bank, d, x = small_case
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, max_push_samples=4096)
+    u.push(d[:2048], 0)
+    with pytest.raises(lloid.LloidError) as e:
+        u.push(d[4096:6144], 4096)                          # gap
+    assert e.value.code == lloid.SB_EGAP
+    with pytest.raises(lloid.LloidError) as e:
+        u.push(d[2048:2050], 2048)                          # not a multiple of 2^k_max
+    assert e.value.code == lloid.SB_EINVAL
+    with pytest.raises(lloid.LloidError) as e:
+        u.push(np.zeros(8192, np.float32), 2048)            # over max_push_samples
+    assert e.value.code == lloid.SB_EINVAL
+    small = lloid.Context(0, hbm_budget_bytes=1 << 20)
+    with pytest.raises(lloid.LloidError) as e:
+        small.create_unit(bank, max_push_samples=4096)
+    assert e.value.code == lloid.SB_EBUSY
+    small.close()
+    ctx.close()
+
+
+def test_production_bin_sampled_templates(lloid):
+    """1000-template, 6-slice bin (4096 ... 128 Hz): 128 s through the GPU in 16-s pushes;
+    the oracle recomputes 24 sampled templates (their SNR rows are independent)."""
+    spec = synth.PRODUCTION_BIN
+    h, _ = synth.template_bank(spec.n_templates, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 2, 0, 0)
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    n = 128 * 4096
+    d = synth.white_noise(n, 2, 0, 0)
+    synth.inject(d, h, 321, 100 * 4096 + 123, 15.0, 0.4)
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, threshold=6.0, max_push_samples=16 * 4096, keep_snr=True)
+    (xg,) = push_and_collect(ctx, [u], [d], [16 * 4096] * 8)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    ctx.close()
+    pick = np.unique(np.concatenate([np.linspace(0, 999, 23).astype(int), [321]]))
+    rows = np.stack([2 * pick, 2 * pick + 1], axis=1).ravel()
+    sub = oracle.OracleBank(len(pick), bank.top_rate_hz,
+                            [oracle.OracleSlice(s.rate_hz, s.t_start_s, s.t_end_s, s.level, s.delay, s.basis,
+                                                s.mixing[rows], s.sigma) for s in bank.slices])
+    xo = oracle.lloid_snr(sub, d)
+    assert rho_error(xg[rows], xo) <= TOL_FP32
+    n_valid = xg.shape[1]
+    tsub = trig[np.isin(trig["template_id"], pick)]
+    tsub = tsub.copy()
+    tsub["template_id"] = np.searchsorted(pick, tsub["template_id"])
+    check_triggers(tsub, xo, 4096, 6.0, n_valid, 2 * TOL_FP32)
+    hit = trig[(trig["template_id"] == 321) & (trig["window"] == 100)]
+    assert len(hit) == 1 and abs(hit["snr"][0] - 15.0) < 1.0
