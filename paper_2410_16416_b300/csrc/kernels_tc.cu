@@ -1,0 +1,323 @@
+// Tensor-core (tcgen05, sm_103a) kernels of the two GEMM-shaped steps in the
+// 16-bit modes (SB_BF16, SB_FP16; FP32 accumulation in TMEM):
+//
+//  a2 basis FIR as a Hankel GEMM.  Output time m' = 8b + r (b = block of 8
+//     samples, r = phase).  With X[b][j] = x[X0 + 8b + j] the FIR is
+//         o[l][8b + r] = sum_j W[(l,r)][j] X[b][j],
+//         W[(l,r)][j]  = v[l][r + Q - 1 + phi - j]   (0 outside the taps),
+//     so the data operand is a Hankel matrix whose rows start 16 bytes apart.
+//     A plain no-swizzle UMMA descriptor (core matrices 16 B apart along K,
+//     8-row groups 128 B apart) reads it straight from one strain window in
+//     shared memory: the strain is loaded once per tile, never expanded.  The
+//     8-phase weights W (8 L_s rows) are expanded once at bank creation and
+//     streamed by TMA with 128-byte swizzle.
+//  a3 mixing GEMM with time on the TMEM lanes: D[m][a] = sum_l O[m][l] M[a][l],
+//     so every epilogue store writes 32 consecutive time samples of one filter.
+//
+// One CTA = 4 warps: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, then
+// all four warps drain TMEM (each warp owns 32 TMEM lanes).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lloid_internal.h"
+#include "tc_ptx.cuh"
+
+namespace lloid {
+
+using namespace tc;
+
+template <bool BF16>
+struct Half;
+template <>
+struct Half<true> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ T cvt(float v) { return __float2bfloat16_rn(v); }
+};
+template <>
+struct Half<false> {
+    using T = __half;
+    static __device__ __forceinline__ T cvt(float v) { return __float2half_rn(v); }
+};
+
+template <class Task>
+__device__ __forceinline__ int find_tile(const Task *tasks, int n, int tile) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
+    return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// ---------------------------------------------------------------------------
+// FP32 -> 16-bit copies of the decimated strain (FIR data operand)
+// ---------------------------------------------------------------------------
+template <bool BF16>
+__global__ void __launch_bounds__(256) to_half_kernel(const HalfConvTask *__restrict__ tasks) {
+    const HalfConvTask t = tasks[blockIdx.y];
+    using T = typename Half<BF16>::T;
+    T *dst = reinterpret_cast<T *>(t.dst);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = Half<BF16>::cvt(t.src[i]);
+}
+
+// ---------------------------------------------------------------------------
+// a2: Hankel-operand basis FIR
+// ---------------------------------------------------------------------------
+constexpr int kFirStages = 4;
+constexpr int kFirStageBytes = kTcM * 64 * 2;             // 128 rows x 64 K x 2 B
+constexpr int kTmemCols = 256;
+
+template <bool BF16>
+__global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restrict__ tasks, int n_tasks,
+                                                        int *err) {
+    using H = Half<BF16>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = align1024(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + kFirStages;
+    uint64_t *winb = empty + kFirStages;
+    uint64_t *accb = winb + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
+    uint8_t *a_st = smem + 1024;
+    uint8_t *win = a_st + kFirStages * kFirStageBytes;
+
+    const TcFirTask &t = tasks[find_tile(tasks, n_tasks, blockIdx.x)];
+    const int local = blockIdx.x - t.tile_begin;
+    const int mt = local / t.tiles_n, nt = local % t.tiles_n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, kTmemCols);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < kFirStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(winb, 1);
+        mbar_init(accb, 1);
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int nk = t.Kpad / 64;
+
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(t.mapW);
+        const uint32_t wbytes = (uint32_t)(kTcN * 8 + t.Kpad) * 2;
+        mbar_expect_tx(winb, wbytes);
+        bulk_load(win, reinterpret_cast<const uint8_t *>(t.x) + 2 * (t.X0 + (int64_t)8 * kTcN * nt), wbytes, winb);
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % kFirStages;
+            if (kc >= kFirStages && !mbar_wait(&empty[s], ((kc / kFirStages) - 1) & 1, err, 1)) break;
+            mbar_expect_tx(&full[s], kFirStageBytes);
+            tma_load_2d(a_st + s * kFirStageBytes, t.mapW, kc * 64, mt * kTcM, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        if (mbar_wait(winb, 0, err, 2)) {
+            const uint32_t idesc = idesc_f16(kTcM, kTcN, BF16);
+            const uint32_t wa = smem_u32(win);
+            bool ok = true;
+            for (int kc = 0; kc < nk && ok; ++kc) {
+                const int s = kc % kFirStages;
+                if (!mbar_wait(&full[s], (kc / kFirStages) & 1, err, 3)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t aa = smem_u32(a_st + s * kFirStageBytes);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    mma_f16(tmem, desc_k_sw128(aa + kk * 32), desc_hankel(wa + (kc * 64 + kk * 16) * 2), idesc,
+                            (kc | kk) != 0);
+                mma_commit(&empty[s]);
+            }
+            if (ok) mma_commit(accb);
+        }
+    }
+    __syncwarp();
+    const bool have = mbar_wait(accb, 0, err, 4);
+    tc_fence_after();
+    if (have) {
+        // TMEM lane R = 16 r + l_loc (row of W in this tile), column c = block b - 256 nt
+        const int R = warp * 32 + lane;
+        const int r = R >> 4;
+        const int col = t.o_col + mt * 16 + (R & 15);
+        typename H::T *O = reinterpret_cast<typename H::T *>(t.O);
+        const int64_t m_base = (int64_t)8 * kTcN * nt + r;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kTcN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int64_t m = m_base + 8 * (c0 + j);
+                if (m < t.Bk) O[m * t.ldo + col] = H::cvt(__uint_as_float(v[j]));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3: mixing GEMM, time on TMEM lanes: D[m][a] = sum_l O[m][l] Mcat[a][l]
+// ---------------------------------------------------------------------------
+constexpr int kMixStages = 2;
+constexpr int kMixABytes = kTcM * 64 * 2;        // O tile: 128 time rows x 64 l
+constexpr int kMixBBytes = kTcN * 64 * 2;        // Mcat tile: 256 filter rows x 64 l
+constexpr int kMixStageBytes = kMixABytes + kMixBBytes;
+
+template <bool BF16>
+__global__ void __launch_bounds__(128, 1) tc_mix_kernel(const TcMixTask *__restrict__ tasks, int n_tasks,
+                                                        int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = align1024(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + kMixStages;
+    uint64_t *accb = empty + kMixStages;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
+    uint8_t *st = smem + 1024;
+
+    const TcMixTask &t = tasks[find_tile(tasks, n_tasks, blockIdx.x)];
+    const int local = blockIdx.x - t.tile_begin;
+    const int tt = local / t.tiles_a, at = local % t.tiles_a;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, kTmemCols);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < kMixStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int nk = (t.Lk_pad + 63) / 64;
+
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(t.mapO);
+        prefetch_tmap(t.mapM);
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % kMixStages;
+            if (kc >= kMixStages && !mbar_wait(&empty[s], ((kc / kMixStages) - 1) & 1, err, 5)) break;
+            uint8_t *sa = st + s * kMixStageBytes;
+            mbar_expect_tx(&full[s], kMixStageBytes);
+            tma_load_2d(sa, t.mapO, kc * 64, tt * kTcM, &full[s]);
+            tma_load_2d(sa + kMixABytes, t.mapM, kc * 64, at * kTcN, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_f16(kTcM, kTcN, BF16);
+        bool ok = true;
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % kMixStages;
+            if (!mbar_wait(&full[s], (kc / kMixStages) & 1, err, 6)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(st + s * kMixStageBytes);
+            const int nmma = min(4, (t.Lk_pad - kc * 64) / 16);
+            for (int kk = 0; kk < nmma; ++kk)
+                mma_f16(tmem, desc_k_sw128(sa + kk * 32), desc_k_sw128(sa + kMixABytes + kk * 32), idesc,
+                        (kc | kk) != 0);
+            mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(accb);
+    }
+    __syncwarp();
+    const bool have = mbar_wait(accb, 0, err, 7);
+    tc_fence_after();
+    if (have) {
+        const int64_t m = (int64_t)tt * kTcM + warp * 32 + lane;
+        const bool mv = m < t.Bk;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kTcN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+            tmem_ld_wait();
+            if (!mv) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int a = at * kTcN + c0 + j;
+                if (a < t.M2) {
+                    float *p = t.Y + (int64_t)a * t.ldy + m;
+                    const float val = __uint_as_float(v[j]);
+                    *p = t.beta ? *p + val : val;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+size_t tc_fir_smem_bytes(int kpad_max) { return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * 8 + kpad_max) * 2; }
+size_t tc_mix_smem_bytes() { return 1024 + 1024 + kMixStages * kMixStageBytes; }
+
+cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, bool bf16, cudaStream_t s) {
+    if (n_tasks == 0) return cudaSuccess;
+    dim3 grid(64, n_tasks);
+    if (bf16) to_half_kernel<true><<<grid, 256, 0, s>>>(d_tasks);
+    else to_half_kernel<false><<<grid, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, bool bf16, int *err,
+                          cudaStream_t s) {
+    if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
+    const size_t smem = tc_fir_smem_bytes(kpad_max);
+    cudaError_t e;
+    if (bf16) {
+        e = cudaFuncSetAttribute(tc_fir_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        tc_fir_kernel<true><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
+    } else {
+        e = cudaFuncSetAttribute(tc_fir_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        tc_fir_kernel<false><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_mix(const TcMixTask *d_tasks, int n_tasks, int total_tiles, bool bf16, int *err,
+                          cudaStream_t s) {
+    if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
+    const size_t smem = tc_mix_smem_bytes();
+    cudaError_t e;
+    if (bf16) {
+        e = cudaFuncSetAttribute(tc_mix_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        tc_mix_kernel<true><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
+    } else {
+        e = cudaFuncSetAttribute(tc_mix_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        tc_mix_kernel<false><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lloid

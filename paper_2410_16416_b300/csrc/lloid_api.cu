@@ -26,6 +26,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "lloid.h"
 #include "lloid_internal.h"
 
@@ -84,8 +87,13 @@ static Halfband make_halfband() {
 struct SliceDev {
     int level = 0, L = 0, Q = 0;
     int64_t D = 0;
-    float *V = nullptr;       // [L x Q]
+    float *V = nullptr;       // [L x Q] (FP32 mode)
     int o_row = 0;            // first row in the level's basis-output block
+    // tensor-core modes: 8-phase expanded weights and their TMA map
+    void *W16 = nullptr;      // [8 L16 x Kpad] 16-bit
+    CUtensorMap *mapW = nullptr;   // device address
+    int L16 = 0, Kpad = 0, o_col16 = 0;
+    int64_t X0 = 0, phi = 0;
 };
 
 struct LevelDev {
@@ -102,6 +110,13 @@ struct LevelDev {
     float *Mcat = nullptr;    // [2M x Lk]
     float *obuf = nullptr;    // [Lk x Bk_max]
     std::vector<int> slices;
+    // tensor-core modes
+    int Lk_pad = 0;           // sum of the level's L16
+    void *x16 = nullptr;      // 16-bit copy of the decimated strain (+ window slack)
+    int64_t x16_len = 0;
+    void *O16 = nullptr;      // basis outputs [Bk_max x Lk_pad], time-major
+    void *M16 = nullptr;      // stacked mixing [2M x Lk_pad]
+    CUtensorMap *mapO = nullptr, *mapM = nullptr;   // device addresses
 };
 
 struct TriggerSlot {
@@ -109,7 +124,7 @@ struct TriggerSlot {
     int32_t *dcount = nullptr;
     int64_t cap = 0;
     DevTrigger *hbuf = nullptr;      // pinned, eager part
-    int32_t *hcount = nullptr;       // pinned [2]
+    int32_t *hcount = nullptr;       // pinned [3]: count, overflow, device-wait timeout code
     int eager = 0;
     cudaEvent_t ev = nullptr;
     bool pending = false;
@@ -139,6 +154,7 @@ struct sb_ctx {
     int next_arena = 0;
     std::deque<sb_trigger> ready;
     bool overflow = false;
+    int timeout_code = 0;      // first bounded device wait that expired (0: none)
     std::mutex mu;
     sb_ctx_stats stats{};
     // profiling: event pairs around each launch, summed per stage on query
@@ -153,6 +169,7 @@ struct sb_unit {
     int64_t id = 0;
     int32_t detector = 0;
     int M = 0, precision = 0, flags = 0;
+    bool tc = false, bf16 = false;
     float thr = 0.f, refine_thr = 0.f;
     double f0 = 0.0;
     int64_t win_len = 0;
@@ -202,8 +219,14 @@ static int activate(sb_ctx *ctx) {
 struct Plan {
     int kmax = 0;
     std::vector<int64_t> e, lam, Hd, Hy, Lk;
+    // tensor-core layout
+    bool tc = false;
+    std::vector<int64_t> Lk_pad, x16_len;                 // per level
+    std::vector<int64_t> X0, phi, Kpad, L16, o_col16;     // per slice
     int64_t bytes = 0;
 };
+
+static bool is_tc(int precision) { return precision == SB_BF16 || precision == SB_FP16; }
 
 static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &P) {
     const int S = d->n_slices;
@@ -256,6 +279,32 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
         P.Hd[k] = round_up(std::max<int64_t>(hd, 1), 32);
         if (k >= 1) P.Hy[k] = round_up((P.lam[k - 1] + 2 * kHalfK) / 2 + 1 - P.lam[k], 4);
     }
+    // tensor-core layout: every slice's 16-bit window start X0 is a multiple of 8
+    // samples (16 bytes, the TMA/descriptor alignment); phi zero columns pad W.
+    P.tc = is_tc(d->precision);
+    P.Lk_pad.assign(NL, 0);
+    P.x16_len.assign(NL, 0);
+    P.X0.assign(S, 0);
+    P.phi.assign(S, 0);
+    P.Kpad.assign(S, 0);
+    P.L16.assign(S, 0);
+    P.o_col16.assign(S, 0);
+    std::vector<int64_t> kpad_max(NL, 0);
+    for (int s = 0; s < S; ++s) {
+        const int k = levels_of_slice[s];
+        const int64_t D = std::llround(d->slices[s].t_start_s * d->slices[s].rate_hz);
+        const int64_t Q = d->slices[s].n_taps;
+        const int64_t start = P.Hd[k] + P.e[k] - P.lam[k] - D - (Q - 1);    // >= 0 by the choice of Hd
+        P.X0[s] = start & ~int64_t(7);
+        P.phi[s] = start - P.X0[s];
+        P.Kpad[s] = round_up(Q + 7 + P.phi[s], 64);
+        P.L16[s] = round_up(d->slices[s].n_basis, 16);
+        P.o_col16[s] = P.Lk_pad[k];
+        P.Lk_pad[k] += P.L16[s];
+        kpad_max[k] = std::max(kpad_max[k], P.Kpad[s]);
+    }
+    for (int k = 0; k < NL; ++k)
+        P.x16_len[k] = P.Hd[k] + (d->max_push_samples >> k) + 8 * kTcN + kpad_max[k] + 64;
     // bytes
     const int64_t M2 = 2 * (int64_t)d->n_templates;
     int64_t b = 0;
@@ -265,9 +314,13 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
         b += 2 * (P.Hd[k] + Bk) * 4;                 // decimated strain ping-pong
         b += M2 * ldy * 4;                           // SNR block
         b += 2 * M2 * P.Hy[k] * 4;                   // SNR history ping-pong
-        b += M2 * P.Lk[k] * 4 + P.Lk[k] * Bk * 4;    // mixing + basis outputs
+        if (P.tc)
+            b += P.x16_len[k] * 2 + (Bk + kTcM) * P.Lk_pad[k] * 2 + M2 * P.Lk_pad[k] * 2 + 2 * 128;
+        else
+            b += M2 * P.Lk[k] * 4 + P.Lk[k] * Bk * 4;    // mixing + basis outputs
     }
-    for (int s = 0; s < S; ++s) b += (int64_t)d->slices[s].n_basis * d->slices[s].n_taps * 4;
+    for (int s = 0; s < S; ++s)
+        b += P.tc ? 8 * P.L16[s] * P.Kpad[s] * 2 + 128 : (int64_t)d->slices[s].n_basis * d->slices[s].n_taps * 4;
     b += 2 * (int64_t)d->n_templates * sizeof(WinState) + d->n_templates * 8;
     P.bytes = b;
     return SB_OK;
@@ -305,8 +358,8 @@ extern "C" int sb_ctx_create(int32_t device, void *stream, int64_t hbm_budget_by
     c->slots.resize(8);
     for (auto &s : c->slots) {
         if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMallocHost(&s.hcount, 2 * sizeof(int32_t)) != cudaSuccess ||
-            cudaMalloc(&s.dcount, 2 * sizeof(int32_t)) != cudaSuccess) {
+            cudaMallocHost(&s.hcount, 3 * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&s.dcount, 3 * sizeof(int32_t)) != cudaSuccess) {
             sb_ctx_destroy(c);
             return fail(SB_ENOMEM, "trigger slot allocation failed");
         }
@@ -357,12 +410,92 @@ extern "C" int sb_ctx_sync(sb_ctx *c) {
 // ---------------------------------------------------------------------------
 // units
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// tensor-core bank layout
+// ---------------------------------------------------------------------------
+static uint16_t to16(float v, bool bf16) {
+    if (bf16) {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        return *reinterpret_cast<uint16_t *>(&h);
+    }
+    __half h = __float2half_rn(v);
+    return *reinterpret_cast<uint16_t *>(&h);
+}
+
+// 2-D K-major tensor map over a row-major [outer x inner] 16-bit matrix with
+// 128-byte swizzle and a (64 x box_outer) box; out-of-range elements read as 0.
+static int encode_map(CUtensorMap *out, void *base, bool bf16, uint64_t inner, uint64_t outer, uint32_t box_outer) {
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {64, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = cuTensorMapEncodeTiled(out, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                                        2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return SB_OK;
+}
+
+static int upload_map(sb_unit *u, const CUtensorMap &h, CUtensorMap **dev) {
+    int rc = dev_alloc(u, (void **)dev, sizeof(CUtensorMap));
+    if (rc) return rc;
+    CK(cudaMemcpy(*dev, &h, sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    return SB_OK;
+}
+
+// W[(l, r)][j] = v[l][r + Q - 1 + phi - j] (zero outside 0 <= q < Q), rows
+// ordered per 128-row tile t as 16 r + l_loc with l = 16 t + l_loc.
+static int upload_expanded_weights(sb_unit *u, SliceDev &sd, const double *basis) {
+    const int64_t rows = 8 * (int64_t)sd.L16, K = sd.Kpad;
+    std::vector<uint16_t> w((size_t)(rows * K), to16(0.0f, u->bf16));
+    for (int64_t t = 0; t < sd.L16 / 16; ++t)
+        for (int r = 0; r < 8; ++r)
+            for (int ll = 0; ll < 16; ++ll) {
+                const int64_t l = 16 * t + ll;
+                if (l >= sd.L) continue;
+                const int64_t row = 128 * t + 16 * r + ll;
+                for (int64_t j = 0; j < K; ++j) {
+                    const int64_t q = r + sd.Q - 1 + sd.phi - j;
+                    if (q >= 0 && q < sd.Q) w[row * K + j] = to16((float)basis[l * sd.Q + q], u->bf16);
+                }
+            }
+    int rc = dev_alloc(u, &sd.W16, w.size() * 2);
+    if (rc) return rc;
+    CK(cudaMemcpy(sd.W16, w.data(), w.size() * 2, cudaMemcpyHostToDevice));
+    CUtensorMap m;
+    if ((rc = encode_map(&m, sd.W16, u->bf16, K, rows, kTcM))) return rc;
+    return upload_map(u, m, &sd.mapW);
+}
+
+static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d) {
+    const int64_t M2 = 2 * (int64_t)u->M;
+    for (auto &L : u->levels) {
+        if (L.Lk_pad == 0) continue;
+        std::vector<uint16_t> m((size_t)(M2 * L.Lk_pad), to16(0.0f, u->bf16));
+        for (int s : L.slices) {
+            const SliceDev &sd = u->slices[s];
+            const double *mx = d->slices[s].mixing;
+            for (int64_t a = 0; a < M2; ++a)
+                for (int l = 0; l < sd.L; ++l) m[a * L.Lk_pad + sd.o_col16 + l] = to16((float)mx[a * sd.L + l], u->bf16);
+        }
+        CK(cudaMemcpy(L.M16, m.data(), m.size() * 2, cudaMemcpyHostToDevice));
+        CUtensorMap hm, ho;
+        int rc;
+        if ((rc = encode_map(&hm, L.M16, u->bf16, L.Lk_pad, M2, kTcN))) return rc;
+        if ((rc = upload_map(u, hm, &L.mapM))) return rc;
+        if ((rc = encode_map(&ho, L.O16, u->bf16, L.Lk_pad, L.Bk_max + kTcM, kTcM))) return rc;
+        if ((rc = upload_map(u, ho, &L.mapO))) return rc;
+    }
+    return SB_OK;
+}
+
 static int validate_desc(const sb_desc *d, std::vector<int> &lvl, Plan &P) {
     if (!d) return fail(SB_EINVAL, "null description");
     if (d->n_templates <= 0 || d->n_slices <= 0 || !d->slices || !(d->top_rate_hz > 0) || !(d->window_s > 0) ||
         d->max_push_samples <= 0)
         return fail(SB_EINVAL, "bad bank description (templates, slices, rate, window or max_push_samples)");
-    if (d->precision != SB_FP32)
+    if (d->precision != SB_FP32 && !is_tc(d->precision))
         return fail(SB_EINVAL, "precision mode not available in this build");
     const double wl = d->window_s * d->top_rate_hz;
     if (std::fabs(wl - std::llround(wl)) > 1e-6 || std::llround(wl) < 1)
@@ -421,6 +554,8 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
     u->detector = detector;
     u->M = d->n_templates;
     u->precision = d->precision;
+    u->tc = is_tc(d->precision);
+    u->bf16 = d->precision == SB_BF16;
     u->flags = d->flags;
     u->thr = d->threshold;
     u->refine_thr = d->refine_threshold;
@@ -461,9 +596,21 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
                 if (cudaMemset(L.yhist[b], 0, M2 * L.Hy * 4) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
             }
         }
-        if (L.Lk > 0) {
+        if (L.Lk > 0 && !u->tc) {
             if ((rc = dev_alloc(u, (void **)&L.Mcat, M2 * L.Lk * 4))) return cleanup(rc);
             if ((rc = dev_alloc(u, (void **)&L.obuf, (int64_t)L.Lk * L.Bk_max * 4))) return cleanup(rc);
+        }
+        if (u->tc) {
+            L.Lk_pad = (int)P.Lk_pad[k];
+            L.x16_len = P.x16_len[k];
+            if ((rc = dev_alloc(u, &L.x16, L.x16_len * 2))) return cleanup(rc);
+            if (cudaMemset(L.x16, 0, L.x16_len * 2) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
+            if (L.Lk_pad > 0) {
+                const int64_t rows = L.Bk_max + kTcM;
+                if ((rc = dev_alloc(u, &L.O16, rows * L.Lk_pad * 2))) return cleanup(rc);
+                if (cudaMemset(L.O16, 0, rows * L.Lk_pad * 2) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
+                if ((rc = dev_alloc(u, &L.M16, M2 * L.Lk_pad * 2))) return cleanup(rc);
+            }
         }
     }
     // slices: basis filters and the per-level stacked mixing matrices
@@ -480,23 +627,33 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         sd.D = std::llround(sl.t_start_s * sl.rate_hz);
         sd.o_row = row_of_level[sd.level];
         row_of_level[sd.level] += sd.L;
-        std::vector<float> v((size_t)sd.L * sd.Q);
-        for (size_t i = 0; i < v.size(); ++i) v[i] = (float)sl.basis[i];
-        if ((rc = dev_alloc(u, (void **)&sd.V, v.size() * 4))) return cleanup(rc);
-        if (cudaMemcpy(sd.V, v.data(), v.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-            return cleanup(fail(SB_ECUDA, "basis upload"));
-        const int Lk = u->levels[sd.level].Lk;
-        for (int64_t a = 0; a < M2; ++a)
-            for (int l = 0; l < sd.L; ++l) mcat[sd.level][a * Lk + sd.o_row + l] = (float)sl.mixing[a * sd.L + l];
+        if (!u->tc) {
+            std::vector<float> v((size_t)sd.L * sd.Q);
+            for (size_t i = 0; i < v.size(); ++i) v[i] = (float)sl.basis[i];
+            if ((rc = dev_alloc(u, (void **)&sd.V, v.size() * 4))) return cleanup(rc);
+            if (cudaMemcpy(sd.V, v.data(), v.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return cleanup(fail(SB_ECUDA, "basis upload"));
+            const int Lk = u->levels[sd.level].Lk;
+            for (int64_t a = 0; a < M2; ++a)
+                for (int l = 0; l < sd.L; ++l) mcat[sd.level][a * Lk + sd.o_row + l] = (float)sl.mixing[a * sd.L + l];
+        } else {
+            sd.L16 = (int)P.L16[s];
+            sd.Kpad = (int)P.Kpad[s];
+            sd.o_col16 = (int)P.o_col16[s];
+            sd.X0 = P.X0[s];
+            sd.phi = P.phi[s];
+            if ((rc = upload_expanded_weights(u, sd, sl.basis))) return cleanup(rc);
+        }
         u->levels[sd.level].slices.push_back(s);
         u->slices.push_back(sd);
     }
-    for (int k = 0; k <= P.kmax; ++k) {
+    for (int k = 0; k <= P.kmax && !u->tc; ++k) {
         LevelDev &L = u->levels[k];
         if (L.Lk == 0) continue;
         if (cudaMemcpy(L.Mcat, mcat[k].data(), mcat[k].size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(fail(SB_ECUDA, "mixing upload"));
     }
+    if (u->tc && (rc = upload_tc_mixing_and_maps(u, d))) return cleanup(rc);
     // trigger state and template ids
     std::vector<WinState> ws(u->M);
     for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = 0.0f; w.n = -1; }
@@ -636,6 +793,7 @@ static int drain_slot(sb_ctx *c, TriggerSlot &s, bool block) {
     }
     int64_t n = s.hcount[0];
     if (s.hcount[1]) c->overflow = true;
+    if (s.hcount[2]) c->timeout_code = s.hcount[2];
     if (n > s.cap) n = s.cap;
     std::vector<sb_trigger> tr((size_t)n);
     const int64_t ne = std::min<int64_t>(n, s.eager);
@@ -681,6 +839,11 @@ extern "C" int triggers_pop(sb_ctx *c, sb_trigger *out, int64_t cap, int64_t *n_
     }
     *n_out = n;
     c->stats.triggers += n;
+    if (c->timeout_code) {
+        const int code = c->timeout_code;
+        c->timeout_code = 0;
+        return fail(SB_ETIMEOUT, "a tensor-core kernel's bounded wait expired (site " + std::to_string(code) + ")");
+    }
     if (c->overflow) {
         c->overflow = false;
         return fail(SB_EOVERFLOW, "a push produced more triggers than its buffer holds; some were dropped");
@@ -776,6 +939,12 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     std::vector<std::vector<UpTask>> ups(kall + 1);
     std::vector<std::vector<GemmTask>> recon(kall + 1);
     std::vector<WinTask> win;
+    // tensor-core modes, indexed [bf16 ? 1 : 0]
+    std::vector<HalfConvTask> conv[2];
+    std::vector<TcFirTask> tfir[2];
+    std::vector<std::vector<TcMixTask>> tmix[2] = {std::vector<std::vector<TcMixTask>>(kall + 1),
+                                                   std::vector<std::vector<TcMixTask>>(kall + 1)};
+    int kpad_max[2] = {0, 0};
     int max_hd = 0, max_hy = 0, max_rows = 0;
     int64_t trig_need = 0;
 
@@ -806,7 +975,42 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 dt.n_out = (int32_t)(B >> (k + 1));
                 decim[k].push_back(dt);
             }
+            if (u->tc) {
+                const int h = u->bf16 ? 1 : 0;
+                conv[h].push_back(HalfConvTask{L.dbuf[nb], L.x16, L.Hd + Bk});
+                for (int s : L.slices) {
+                    const SliceDev &sd = u->slices[s];
+                    TcFirTask f{};
+                    f.mapW = sd.mapW;
+                    f.x = L.x16;
+                    f.X0 = sd.X0;
+                    f.O = L.O16;
+                    f.ldo = L.Lk_pad;
+                    f.o_col = sd.o_col16;
+                    f.Kpad = sd.Kpad;
+                    f.Bk = (int32_t)Bk;
+                    f.tiles_n = (int32_t)(((Bk + 7) / 8 + kTcN - 1) / kTcN);
+                    f.tiles_m = sd.L16 / 16;
+                    tfir[h].push_back(f);
+                    kpad_max[h] = std::max(kpad_max[h], sd.Kpad);
+                }
+                if (L.Lk_pad > 0) {
+                    TcMixTask mt{};
+                    mt.mapO = L.mapO;
+                    mt.mapM = L.mapM;
+                    mt.Y = L.ynew;
+                    mt.ldy = L.ldy;
+                    mt.Lk_pad = L.Lk_pad;
+                    mt.M2 = M2;
+                    mt.Bk = (int32_t)Bk;
+                    mt.beta = k < u->kmax ? 1 : 0;
+                    mt.tiles_a = (M2 + kTcN - 1) / kTcN;
+                    mt.tiles_t = (int32_t)((Bk + kTcM - 1) / kTcM);
+                    tmix[h][k].push_back(mt);
+                }
+            }
             for (int s : L.slices) {
+                if (u->tc) break;
                 const SliceDev &sd = u->slices[s];
                 GemmTask g{};
                 g.A = sd.V;
@@ -839,7 +1043,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 ut.first_n = (Tp >> k) - L.lam;
                 ups[k].push_back(ut);
             }
-            if (L.Lk > 0) {
+            if (L.Lk > 0 && !u->tc) {
                 GemmTask g{};
                 g.A = L.Mcat;
                 g.lda = L.Lk;
@@ -907,6 +1111,19 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     const int fir_tiles = assign_tiles(fir);
     std::vector<int> recon_tiles(kall + 1);
     for (int k = 0; k <= kall; ++k) recon_tiles[k] = assign_tiles(recon[k]);
+    int tfir_tiles[2] = {0, 0};
+    std::vector<int> tmix_tiles[2] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0)};
+    for (int h = 0; h < 2; ++h) {
+        for (auto &f : tfir[h]) {
+            f.tile_begin = tfir_tiles[h];
+            tfir_tiles[h] += f.tiles_m * f.tiles_n;
+        }
+        for (int k = 0; k <= kall; ++k)
+            for (auto &m : tmix[h][k]) {
+                m.tile_begin = tmix_tiles[h][k];
+                tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
+            }
+    }
     int win_warps = 0;
     for (auto &w : win) {
         w.warp_begin = win_warps;
@@ -924,6 +1141,13 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         o_recon[k] = pk.add(recon[k].data(), recon[k].size() * sizeof(GemmTask));
     }
     const size_t o_win = pk.add(win.data(), win.size() * sizeof(WinTask));
+    size_t o_conv[2], o_tfir[2];
+    std::vector<size_t> o_tmix[2] = {std::vector<size_t>(kall + 1), std::vector<size_t>(kall + 1)};
+    for (int h = 0; h < 2; ++h) {
+        o_conv[h] = pk.add(conv[h].data(), conv[h].size() * sizeof(HalfConvTask));
+        o_tfir[h] = pk.add(tfir[h].data(), tfir[h].size() * sizeof(TcFirTask));
+        for (int k = 0; k <= kall; ++k) o_tmix[h][k] = pk.add(tmix[h][k].data(), tmix[h][k].size() * sizeof(TcMixTask));
+    }
     const size_t o_ycopy = pk.add(ycopy.data(), ycopy.size() * sizeof(CopyTask));
     std::vector<size_t> o_strain(n_units, 0);
     if (!on_device)
@@ -936,6 +1160,11 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     CK(cudaMemcpyAsync(ar->d, ar->h, pk.buf.size(), cudaMemcpyHostToDevice, st));
     char *D = ar->d;
 
+    TriggerSlot *slot = nullptr;
+    int slot_idx = 0;
+    if ((rc = slot_acquire(c, trig_need, slot, slot_idx))) return rc;
+    CK(cudaMemsetAsync(slot->dcount, 0, 3 * sizeof(int32_t), st));
+    int *derr = slot->dcount + 2;
     // 1. history shifts of the decimated strain
     if ((rc = run_stage(c, SB_STAGE_HISTORY, [&](int *n) {
              *n = dcopy.empty() ? 0 : 1;
@@ -962,12 +1191,27 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                                         c->g, st);
              })))
             return rc;
+    // 16-bit copies of the decimated strain for the tensor-core FIR
+    for (int h = 0; h < 2; ++h)
+        if (!conv[h].empty() && (rc = run_stage(c, SB_STAGE_DECIMATE, [&](int *n) {
+                                     *n = 1;
+                                     return launch_to_half((HalfConvTask *)(D + o_conv[h]), (int)conv[h].size(),
+                                                           h == 1, st);
+                                 })))
+            return rc;
     // 4. a2 basis FIR, all slices of all units at once
-    if ((rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
-             *n = fir.empty() ? 0 : 1;
-             return launch_gemm_fp32((GemmTask *)(D + o_fir), (int)fir.size(), fir_tiles, st);
-         })))
+    if (!fir.empty() && (rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
+                             *n = 1;
+                             return launch_gemm_fp32((GemmTask *)(D + o_fir), (int)fir.size(), fir_tiles, st);
+                         })))
         return rc;
+    for (int h = 0; h < 2; ++h)
+        if (!tfir[h].empty() && (rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
+                                     *n = 1;
+                                     return launch_tc_fir((TcFirTask *)(D + o_tfir[h]), (int)tfir[h].size(),
+                                                          tfir_tiles[h], kpad_max[h], h == 1, derr, st);
+                                 })))
+            return rc;
     // 5. a4 + a3 from the lowest rate up
     for (int k = kall; k >= 0; --k) {
         if (!ups[k].empty() &&
@@ -983,12 +1227,16 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                  return launch_gemm_fp32((GemmTask *)(D + o_recon[k]), (int)recon[k].size(), recon_tiles[k], st);
              })))
             return rc;
+        for (int h = 0; h < 2; ++h)
+            if (!tmix[h][k].empty() &&
+                (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
+                     *n = 1;
+                     return launch_tc_mix((TcMixTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(), tmix_tiles[h][k],
+                                          h == 1, derr, st);
+                 })))
+                return rc;
     }
     // 6. a5 trigger generator
-    TriggerSlot *slot = nullptr;
-    int slot_idx = 0;
-    if ((rc = slot_acquire(c, trig_need, slot, slot_idx))) return rc;
-    CK(cudaMemsetAsync(slot->dcount, 0, 2 * sizeof(int32_t), st));
     TrigOut to{slot->dbuf, slot->dcount, (int32_t)slot->cap};
     if ((rc = run_stage(c, SB_STAGE_TRIGGER, [&](int *n) {
              *n = win.empty() ? 0 : 1;
@@ -1002,7 +1250,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
          })))
         return rc;
     // 8. triggers to the host (count plus an eager prefix; the rest on demand)
-    CK(cudaMemcpyAsync(slot->hcount, slot->dcount, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(slot->hcount, slot->dcount, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(slot->hbuf, slot->dbuf, slot->eager * sizeof(DevTrigger), cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(slot->ev, st));
     slot->pending = true;
@@ -1011,7 +1259,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     ar->used = true;
     c->stats.pushes += 1;
     c->stats.h2d_bytes += (int64_t)pk.buf.size();
-    c->stats.d2h_bytes += 2 * sizeof(int32_t) + slot->eager * (int64_t)sizeof(DevTrigger);
+    c->stats.d2h_bytes += 3 * sizeof(int32_t) + slot->eager * (int64_t)sizeof(DevTrigger);
 
     // 9. advance host bookkeeping
     for (int i = 0; i < n_units; ++i) {

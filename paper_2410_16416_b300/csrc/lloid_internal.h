@@ -4,6 +4,7 @@
 // slices of several banks are filtered together).
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace lloid {
@@ -111,6 +112,56 @@ struct TrigOut {
     int32_t *count;      // [0] = triggers written, [1] = overflow flag
     int32_t cap;
 };
+
+// ---- tensor-core path (kernels_tc.cu) ---------------------------------------
+constexpr int kTcM = 128;   // MMA M (rows of the A operand per tile)
+constexpr int kTcN = 256;   // MMA N (columns of the accumulator per tile)
+
+struct HalfConvTask {       // dst[i] = 16-bit(src[i]), i < n
+    const float *src;
+    void *dst;
+    int64_t n;
+};
+
+// a2 on tensor cores.  Tile (mt, nt): W rows [128 mt, 128 mt + 128) (16 basis
+// vectors x 8 phases, row 16 r + l_loc), blocks b in [256 nt, 256 nt + 256).
+struct TcFirTask {
+    const CUtensorMap *mapW;   // W [8 L16 rows x Kpad] 16-bit, K-major, 128-byte swizzle
+    const void *x;             // decimated strain, 16-bit
+    int64_t X0;                // x index of (b = 0, j = 0); multiple of 8
+    void *O;                   // basis outputs, 16-bit, [m][ldo]
+    int64_t ldo;
+    int32_t o_col;             // column of this slice's first basis vector in O
+    int32_t Kpad;              // multiple of 64
+    int32_t Bk;                // outputs m' < Bk are written
+    int32_t tiles_m;           // L16 / 16
+    int32_t tiles_n;
+    int32_t tile_begin;
+};
+
+// a3 on tensor cores.  Tile (tt, at): time rows [128 tt, +128), filters [256 at, +256).
+struct TcMixTask {
+    const CUtensorMap *mapO;   // O [rows x Lk_pad], box 64 x 128
+    const CUtensorMap *mapM;   // Mcat [2M x Lk_pad], box 64 x 256
+    float *Y;                  // level SNR [2M][ldy], FP32
+    int64_t ldy;
+    int32_t Lk_pad;
+    int32_t M2;
+    int32_t Bk;
+    int32_t beta;
+    int32_t tiles_t;           // ceil(Bk / 128)
+    int32_t tiles_a;           // ceil(2M / 256)
+    int32_t tile_begin;
+    int32_t pad;
+};
+
+size_t tc_fir_smem_bytes(int kpad_max);
+size_t tc_mix_smem_bytes();
+cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, bool bf16, cudaStream_t s);
+cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, bool bf16, int *err,
+                          cudaStream_t s);
+cudaError_t launch_tc_mix(const TcMixTask *d_tasks, int n_tasks, int total_tiles, bool bf16, int *err,
+                          cudaStream_t s);
 
 // ---- launchers (kernels_simt.cu) -------------------------------------------
 cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,

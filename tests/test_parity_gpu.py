@@ -74,7 +74,7 @@ def test_fp32_every_window_max_matches_oracle(lloid, small_case):
 def test_streaming_is_bitwise_independent_of_buffer_sizes(lloid, small_case):
     spec, h, bank, d, x = small_case
     runs = []
-    for sizes in ([2048] * 16, [8192] * 4, [4, 2044, 4096, 12, 6132, 8192, 8192, 4092]):
+    for sizes in ([2048] * 16, [8192] * 4, [4, 2044, 4096, 12, 6132, 8192, 8192, 4096]):
         assert sum(sizes) == d.shape[0]
         ctx = lloid.Context(0)
         u = ctx.create_unit(bank, max_push_samples=8192, keep_snr=True)
