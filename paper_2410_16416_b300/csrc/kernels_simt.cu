@@ -28,28 +28,45 @@ __global__ void __launch_bounds__(256) decimate_kernel(const DecimTask *__restri
 // ---------------------------------------------------------------------------
 // a4 (up-sampling half): y'[n] = sum_m 2 g[n - 2m] y[m]; even n copy y[n/2].
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float vread(const UpTask &t, int row, int64_t pos) {
-    return pos < t.n_hist ? t.hist[row * t.ld_hist + pos] : t.cur[row * t.ld_cur + (pos - t.n_hist)];
-}
-
+// One CTA per (task, row, chunk of kUpChunk outputs): the input segment (half
+// the chunk plus the 2K-1 tap halo on each side) is staged in shared memory with
+// coalesced loads, then every output is formed from shared memory.
 __global__ void __launch_bounds__(256) upsample_kernel(const UpTask *__restrict__ tasks, Halfband g) {
-    const UpTask t = tasks[blockIdx.z];
+    constexpr int kSeg = kUpChunk / 2 + 2 * kHalfK + 2;
+    __shared__ float seg[kSeg];
+    const UpTask &t = tasks[blockIdx.z];
     const int row = blockIdx.y;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= t.rows || p >= t.n_out) return;
-    float v = 0.0f;
-    if (t.first_n + p >= 0) {
-        const int64_t nrel = (int64_t)p - t.lam_out;
-        if ((nrel & 1) == 0) {
-            v = vread(t, row, nrel / 2 + t.in_off);
-        } else {
-            const int64_t lo = (nrel - 1) / 2 + t.in_off;   // m for j = +1
-#pragma unroll
-            for (int k = 0; k < kOddTaps; ++k)
-                v = fmaf(2.0f * g.odd[k], vread(t, row, lo - k) + vread(t, row, lo + 1 + k), v);
-        }
+    const int p0 = blockIdx.x * kUpChunk;
+    if (row >= t.rows || p0 >= t.n_out) return;
+    // first input position touched by this chunk: output nrel = p0 - lam_out, tap j = 2K - 1
+    const int64_t nrel0 = (int64_t)p0 - t.lam_out;
+    const int64_t pos_lo = ((nrel0 - (2 * kHalfK - 1)) >> 1) + t.in_off;      // floor division
+    const int64_t n_valid = (int64_t)t.n_hist + t.n_cur;
+    const float *hist = t.hist + row * t.ld_hist;
+    const float *cur = t.cur + row * t.ld_cur;
+    for (int i = threadIdx.x; i < kSeg; i += blockDim.x) {
+        const int64_t pos = pos_lo + i;
+        float v = 0.0f;
+        if (pos >= 0 && pos < n_valid) v = pos < t.n_hist ? hist[pos] : cur[pos - t.n_hist];
+        seg[i] = v;
     }
-    t.out[row * t.ld_out + p] = v;
+    __syncthreads();
+    float *out = t.out + row * t.ld_out;
+    const int p_end = min(t.n_out, p0 + kUpChunk);
+    for (int p = p0 + threadIdx.x; p < p_end; p += blockDim.x) {
+        float v = 0.0f;
+        if (t.first_n + p >= 0) {
+            const int64_t nrel = (int64_t)p - t.lam_out;
+            if ((nrel & 1) == 0) {
+                v = seg[(nrel >> 1) + t.in_off - pos_lo];
+            } else {
+                const int lo = (int)(((nrel - 1) >> 1) + t.in_off - pos_lo);   // m for j = +1
+#pragma unroll
+                for (int k = 0; k < kOddTaps; ++k) v = fmaf(2.0f * g.odd[k], seg[lo - k] + seg[lo + 1 + k], v);
+            }
+        }
+        out[p] = v;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -250,7 +267,7 @@ cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, 
 cudaError_t launch_upsample(const UpTask *d_tasks, int n_tasks, int max_rows, int max_out,
                             const Halfband &g, cudaStream_t s) {
     if (n_tasks == 0 || max_out <= 0 || max_rows <= 0) return cudaSuccess;
-    dim3 grid((max_out + 255) / 256, max_rows, n_tasks);
+    dim3 grid((max_out + kUpChunk - 1) / kUpChunk, max_rows, n_tasks);
     upsample_kernel<<<grid, 256, 0, s>>>(d_tasks, g);
     return cudaGetLastError();
 }

@@ -1040,6 +1040,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 ut.n_out = (int32_t)Bk;
                 ut.lam_out = (int32_t)L.lam;
                 ut.in_off = (int32_t)(N.lam + N.Hy);
+                ut.n_cur = (int32_t)(B >> (k + 1));
                 ut.first_n = (Tp >> k) - L.lam;
                 ups[k].push_back(ut);
             }

@@ -9,12 +9,13 @@ import pytest
 
 import oracle
 import synth
-from helpers import check_triggers, push_and_collect, rho_error
+from helpers import check_triggers, push_and_collect, rho_abs_error, rho_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-4
+TOL_HALF = 0.05          # absolute |SNR| bound of the BF16 / FP16 modes, every sample
 
 
 @pytest.fixture(scope="module")
@@ -199,3 +200,68 @@ def test_production_bin_sampled_templates(lloid):
     check_triggers(tsub, xo, 4096, 6.0, n_valid, 2 * TOL_FP32)
     hit = trig[(trig["template_id"] == 321) & (trig["window"] == 100)]
     assert len(hit) == 1 and abs(hit["snr"][0] - 15.0) < 1.0
+
+
+# ---------------------------------------------------------------- 16-bit tensor-core modes
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_half_small_bin_matches_oracle(lloid, small_case, precision):
+    spec, h, bank, d, x = small_case
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, precision=precision, threshold=6.0, max_push_samples=4096, keep_snr=True)
+    (xg,) = push_and_collect(ctx, [u], [d], [2048] * 16)
+    err = rho_abs_error(xg, x)
+    print(f"{precision}: max |rho| error {err:.4f}")
+    assert err <= TOL_HALF, err
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    n_valid = d.shape[0] - u.info().latency_samples
+    assert check_triggers(trig, x, 2048, 6.0, n_valid, TOL_HALF, absolute=True) >= 1
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_half_streaming_and_grouping_are_deterministic(lloid, precision):
+    """Tensor-core modes: identical bits across push sizes and alone vs grouped."""
+    banks = _shape_banks(3, max_templates=37)
+    n = 6 * 4096
+    strains = [synth.white_noise(n, 6, b, 0) for b in range(len(banks))]
+    ctx = lloid.Context(0)
+    units = [ctx.create_unit(b, precision=precision, threshold=4.0, max_push_samples=8192, keep_snr=True)
+             for b in banks]
+    grouped = push_and_collect(ctx, units, strains, [8192, 4096, 8192, 4096])
+    for b, dd, xg in zip(banks, strains, grouped):
+        ob = oracle.bank_from_arrays(b.n_templates, b.top_rate_hz, b.slices)
+        assert rho_abs_error(xg, oracle.lloid_snr(ob, dd)) <= TOL_HALF
+    ctx.close()
+    c2 = lloid.Context(0)
+    u = c2.create_unit(banks[1], precision=precision, threshold=4.0, max_push_samples=8192, keep_snr=True)
+    (alone,) = push_and_collect(c2, [u], [strains[1]], [4096] * 6)
+    c2.close()
+    assert np.array_equal(alone, grouped[1])
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_half_production_bin_sampled_templates(lloid, precision):
+    spec = synth.PRODUCTION_BIN
+    h, _ = synth.template_bank(spec.n_templates, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 2, 0, 0)
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    n = 96 * 4096
+    d = synth.white_noise(n, 2, 0, 1)
+    synth.inject(d, h, 500, 80 * 4096 + 99, 30.0, -0.8)
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, precision=precision, threshold=6.0, max_push_samples=16 * 4096, keep_snr=True)
+    (xg,) = push_and_collect(ctx, [u], [d], [16 * 4096] * 6)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    ctx.close()
+    pick = np.unique(np.concatenate([np.linspace(0, 999, 15).astype(int), [500]]))
+    rows = np.stack([2 * pick, 2 * pick + 1], axis=1).ravel()
+    sub = oracle.OracleBank(len(pick), bank.top_rate_hz,
+                            [oracle.OracleSlice(s.rate_hz, s.t_start_s, s.t_end_s, s.level, s.delay, s.basis,
+                                                s.mixing[rows], s.sigma) for s in bank.slices])
+    xo = oracle.lloid_snr(sub, d)
+    err = rho_abs_error(xg[rows], xo)
+    print(f"{precision} production: max |rho| error {err:.4f}")
+    assert err <= TOL_HALF
+    hit = trig[(trig["template_id"] == 500) & (trig["window"] == 80)]
+    assert len(hit) == 1 and abs(hit["snr"][0] - 30.0) < 1.5
