@@ -46,7 +46,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lloid", choices=["lloid", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp8"])
+    p.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
+    p.add_argument("--compare", default="fp32,fp16", help="other precisions timed for by_precision ('none': skip)")
     p.add_argument("--push-seconds", type=int, default=16)
     p.add_argument("--templates", type=int, default=1000)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -70,8 +71,12 @@ def make_strain(bin_index: int, detector: int, seconds: int, f0: float, h, n_tem
     return d
 
 
-def algorithmic_model(bank, units: int, B_s: float):
-    """Per-stage algorithmic FLOPs and HBM bytes of one push (all units)."""
+def algorithmic_model(bank, units: int, B_s: float, precision: str = "fp32"):
+    """Per-stage algorithmic FLOPs and HBM bytes of one push (all units).
+
+    Weights and basis outputs move in the operand width (4 bytes in FP32 mode,
+    2 in the 16-bit modes); SNR series are FP32."""
+    w = 4.0 if precision == "fp32" else 2.0
     f0 = bank.top_rate_hz
     M2 = 2 * bank.n_templates
     levels = {}
@@ -85,12 +90,12 @@ def algorithmic_model(bank, units: int, B_s: float):
         L, Q = s.basis.shape
         N = B_s * s.rate_hz
         fl["fir"] += 2.0 * L * Q * N
-        by["fir"] += 4.0 * (L * Q + N + L * N)
+        by["fir"] += w * (L * Q + N + L * N)
     for k, ss in levels.items():
         Lk = sum(s.basis.shape[0] for s in ss)
         N = B_s * f0 / 2 ** k
         fl["mix"] += 2.0 * M2 * Lk * N
-        by["mix"] += 4.0 * (M2 * Lk + Lk * N + M2 * N * (2 if k < kmax else 1))
+        by["mix"] += w * (M2 * Lk + Lk * N) + 4.0 * M2 * N * (2 if k < kmax else 1)
     for k in range(1, kmax + 1):
         N = B_s * f0 / 2 ** k
         fl["upsample"] += M2 * (2 * N) * 17
@@ -236,6 +241,31 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def roofline_of(stages, flops, bytes_, precision, steps, peaks):
+    """Bound, achieved and fraction of the stage that takes the most device time."""
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12            # FP32 FFMA lanes x 2 FLOP x max clock
+    tensor_peak = peaks.get("bf16_tflops", 1800.0)             # dense BF16 = FP16 rate, burst (short steps)
+    busy = {k: v[0] for k, v in stages.items() if v[1] > 0}
+    dom = max(busy, key=busy.get)
+    dom_ms, _ = stages[dom]
+    on_tensor = precision in ("bf16", "fp16") and dom in ("fir", "mix")
+    cpeak = tensor_peak if on_tensor else alu_peak
+    t_c = flops.get(dom, 0.0) / (cpeak * 1e12)
+    t_m = bytes_.get(dom, 0.0) / (hbm_peak * 1e9)
+    secs = dom_ms / 1e3
+    if t_c >= t_m:
+        ach = flops[dom] * steps / secs / 1e12
+        return dom, {"bound": "tensor" if on_tensor else "alu", "achieved": ach, "peak": cpeak, "unit": "TFLOP/s",
+                     "frac": ach / cpeak, "traffic": None, "kernel": dom,
+                     "peak_source": "measured bf16_tflops (burst)" if on_tensor else
+                     "derived: 148 SM x 128 FP32 lanes x 2 FLOP x max SM clock"}
+    ach = bytes_[dom] * steps / secs / 1e9
+    return dom, {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                 "traffic": None, "kernel": dom, "peak_source": "measured hbm_gbs"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -266,120 +296,121 @@ def main():
     strains = [make_strain(rank, det, total_s, f0, h, spec.n_templates) for det in (0, 1)]
     dev = [torch.from_numpy(s).cuda() for s in strains]
     stream = torch.cuda.current_stream()
-    ctx = lloid.Context(local, stream=stream.cuda_stream)
-    units = [ctx.create_unit(bank, detector=det, precision=args.precision, threshold=6.0, refine_threshold=5.5,
-                             window_s=1.0, max_push_samples=B) for det in (0, 1)]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    n_units = 2
+    tpl_s_rank = n_units * spec.n_templates * args.push_seconds * args.steps
 
-    t = 0
-    for _ in range(args.warmup):
-        ctx.push_group(units, [d[t:t + B] for d in dev], [t, t], True)
-        t += B
-    ctx.pop_triggers()
-    barrier()
-    ctx.profile(True)
-    st0 = ctx.stats()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    w0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        ctx.push_group(units, [d[t:t + B] for d in dev], [t, t], True)
-        ev[i][1].record(stream)
-        t += B
-    barrier()
-    wall = time.perf_counter() - w0
-    clk = clocks.stop()
-    st1 = ctx.stats()
-    stages = ctx.stage_times()
-    ctx.profile(False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    dev_s = sum(step_ms) / 1e3
-    if dist is not None:
-        tt = torch.tensor([dev_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dev_s = float(tt.item())
-    tpl_s_rank = len(units) * spec.n_templates * args.push_seconds * args.steps
-    value = world * tpl_s_rank / dev_s
-    trig = ctx.pop_triggers()
+    def device_arm(precision):
+        ctx = lloid.Context(local, stream=stream.cuda_stream)
+        units = [ctx.create_unit(bank, detector=det, precision=precision, threshold=6.0, refine_threshold=5.5,
+                                 window_s=1.0, max_push_samples=B) for det in range(n_units)]
+        t = 0
+        for _ in range(args.warmup):
+            ctx.push_group(units, [d[t:t + B] for d in dev], [t, t], True)
+            t += B
+        ctx.pop_triggers()
+        barrier()
+        ctx.profile(True)
+        st0 = ctx.stats()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier()
+        w0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ctx.push_group(units, [d[t:t + B] for d in dev], [t, t], True)
+            ev[i][1].record(stream)
+            t += B
+        barrier()
+        wall = time.perf_counter() - w0
+        clk = clocks.stop()
+        st1 = ctx.stats()
+        stages = ctx.stage_times()
+        ctx.profile(False)
+        dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        if dist is not None:
+            tt = torch.tensor([dev_s], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dev_s = float(tt.item())
+        trig = ctx.pop_triggers()
+        ctx.close()
+        return {"value": world * tpl_s_rank / dev_s, "dev_s": dev_s, "wall": wall, "clocks": clk,
+                "stages": stages, "launches": st1["kernel_launches"] - st0["kernel_launches"],
+                "triggers": int(len(trig))}
+
+    prim = device_arm(args.precision)
+    others = {}
+    for p in args.compare.split(","):
+        p = p.strip()
+        if p and p != "none" and p != args.precision:
+            others[p] = device_arm(p)
 
     # e2e: host strain in, triggers out, through the C ABI
-    e2e = None
-    if rank == 0 or dist is not None:
-        ctx2 = lloid.Context(local, stream=stream.cuda_stream)
-        u2 = [ctx2.create_unit(bank, detector=det, precision=args.precision, threshold=6.0, refine_threshold=5.5,
-                               window_s=1.0, max_push_samples=B) for det in (0, 1)]
-        t2 = 0
-        for _ in range(args.warmup):
-            ctx2.push_group(u2, [s[t2:t2 + B] for s in strains], [t2, t2], False)
-            ctx2.pop_triggers()
-            t2 += B
-        barrier()
-        s0 = ctx2.stats()
-        w1 = time.perf_counter()
-        for i in range(args.steps):
-            ctx2.push_group(u2, [s[t2:t2 + B] for s in strains], [t2, t2], False)
-            ctx2.pop_triggers()
-            t2 += B
-        ctx2.sync()
+    ctx2 = lloid.Context(local, stream=stream.cuda_stream)
+    u2 = [ctx2.create_unit(bank, detector=det, precision=args.precision, threshold=6.0, refine_threshold=5.5,
+                           window_s=1.0, max_push_samples=B) for det in range(n_units)]
+    t2 = 0
+    for _ in range(args.warmup):
+        ctx2.push_group(u2, [s[t2:t2 + B] for s in strains], [t2, t2], False)
         ctx2.pop_triggers()
-        e2e_wall = time.perf_counter() - w1
-        s1 = ctx2.stats()
-        e2e = {"value": world * tpl_s_rank / e2e_wall, "unit": UNIT,
-               "h2d_bytes_per_step": (s1["h2d_bytes"] - s0["h2d_bytes"]) // args.steps,
-               "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // args.steps}
-        ctx2.close()
+        t2 += B
+    barrier()
+    s0 = ctx2.stats()
+    w1 = time.perf_counter()
+    for i in range(args.steps):
+        ctx2.push_group(u2, [s[t2:t2 + B] for s in strains], [t2, t2], False)
+        ctx2.pop_triggers()
+        t2 += B
+    ctx2.sync()
+    ctx2.pop_triggers()
+    e2e_wall = time.perf_counter() - w1
+    s1 = ctx2.stats()
+    if dist is not None:
+        tt = torch.tensor([e2e_wall], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_wall = float(tt.item())
+    e2e = {"value": world * tpl_s_rank / e2e_wall, "unit": UNIT,
+           "h2d_bytes_per_step": (s1["h2d_bytes"] - s0["h2d_bytes"]) // args.steps,
+           "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // args.steps}
+    ctx2.close()
 
-    # roofline of the dominant stage
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6400.0)
-    sm_max = peaks.get("sm_max_mhz", 2032.0)
-    alu_peak_tflops = 148 * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 FFMA lanes x 2 FLOP x max clock
-    flops, bytes_ = algorithmic_model(bank, len(units), args.push_seconds)
-    busy = {k: v[0] for k, v in stages.items() if v[1] > 0}
-    dom = max(busy, key=busy.get)
-    dom_ms, dom_n = stages[dom]
-    t_alu = flops.get(dom, 0.0) / (alu_peak_tflops * 1e12)
-    t_hbm = bytes_.get(dom, 0.0) / (hbm_peak * 1e9)
-    per_launch_s = dom_ms / 1e3 / dom_n
-    per_launch_units = args.steps / dom_n
-    if t_alu >= t_hbm:
-        achieved = flops[dom] * per_launch_units / per_launch_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak_tflops, "traffic": None,
-                "kernel": dom, "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 FLOP x max SM clock"}
-    else:
-        achieved = bytes_[dom] * per_launch_units / per_launch_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "kernel": dom, "peak_source": "measured hbm_gbs"}
+    flops, bytes_ = algorithmic_model(bank, n_units, args.push_seconds, args.precision)
+    dom, roof = roofline_of(prim["stages"], flops, bytes_, args.precision, args.steps, peaks)
+    busy = {k: v[0] for k, v in prim["stages"].items() if v[1] > 0}
     total_stage_ms = sum(busy.values())
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16",
-                                                             "fp8": "e4m3"}[args.precision],
+    line = {"metric": METRIC, "value": prim["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * prim["dev_s"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision],
             "data": "synthetic (seeded white noise, random-parameter Newtonian chirp bank, injections)",
             "config": {"workload": f"production bin: {spec.n_templates} templates x 2 detectors, 6 slices "
                                    f"4096-128 Hz, L={bank.basis_counts()}, {args.push_seconds} s pushes",
-                       "templates": spec.n_templates, "units_per_gpu": len(units), "push_seconds": args.push_seconds,
-                       "precision": args.precision, "parallelism": f"units sharded, {world} GPU(s)",
+                       "templates": spec.n_templates, "units_per_gpu": n_units,
+                       "push_seconds": args.push_seconds, "precision": args.precision,
+                       "parallelism": f"units sharded, {world} GPU(s)",
                        "l2": "flushed between steps (256 MB write outside the step events)"},
-            "roofline": roof, "e2e": e2e,
-            "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
-            "clocks": clk,
+            "roofline": roof, "e2e": e2e, "gpu_launches": prim["launches"], "clocks": prim["clocks"],
             "stages_ms_share": {k: round(v / total_stage_ms, 4) for k, v in busy.items()},
-            "wall_s": wall, "triggers": int(len(trig))}
+            "by_precision": {p: {"value": r["value"], "ms_per_step": 1e3 * r["dev_s"] / args.steps,
+                                 "gain_vs_fp32": None}
+                             for p, r in [(args.precision, prim), *others.items()]},
+            "wall_s": prim["wall"], "triggers": prim["triggers"]}
+    if "fp32" in line["by_precision"]:
+        ref = line["by_precision"]["fp32"]["value"]
+        for p in line["by_precision"]:
+            line["by_precision"][p]["gain_vs_fp32"] = line["by_precision"][p]["value"] / ref
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h, spec, args.cpu_seconds, max(1, min(os.cpu_count() or 1, 16)))
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 
