@@ -254,8 +254,84 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
 }
 
 // ---------------------------------------------------------------------------
+// a5 after partial maxima: one thread per (unit, template) walks the unit's
+// partial records in time order, closes every window the push completes
+// (threshold, phase, trigger) and keeps the open window's running maximum.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void emit_trigger(const WinFinTask &t, int i, const WinState &b, int64_t w,
+                                             TrigOut out) {
+    if (b.mag2 < 0.0f || !(sqrtf(b.mag2) > t.threshold)) return;
+    const int slot = atomicAdd(out.count, 1);
+    if (slot >= out.cap) {
+        atomicExch(out.count + 1, 1);
+        return;
+    }
+    DevTrigger r;
+    r.unit = t.unit_id;
+    r.template_id = t.template_ids[i];
+    r.sample = b.n;
+    r.window = w;
+    r.snr = sqrtf(b.mag2);
+    r.phase = atan2f(b.im, b.re);
+    r.flags = 0;
+    r.reserved = 0;
+    out.buf[slot] = r;
+}
+
+__device__ __forceinline__ int find_task_by_thread(const WinFinTask *tasks, int n, int g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].thread_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__restrict__ tasks, int n_tasks,
+                                                           int total, TrigOut out) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const WinFinTask &t = tasks[find_task_by_thread(tasks, n_tasks, gid)];
+    const int i = gid - t.thread_begin;
+    WinState best = t.state_in[i];
+    int64_t w_cur = t.start_abs / t.win_len;          // the open window (state) or the push's first window
+    for (int r = 0; r < t.n_rec; ++r) {
+        const WinPart p = t.part[(int64_t)r * t.M + i];
+        if (p.mag2 < 0.0f) continue;
+        const int64_t w = p.n / t.win_len;
+        if (w != w_cur) {                              // records are in time order: w_cur is complete
+            emit_trigger(t, i, best, w_cur, out);
+            best.mag2 = -1.0f;
+            best.n = -1;
+            w_cur = w;
+        }
+        if (p.mag2 > best.mag2) {                      // strict: the earlier sample wins ties
+            best.mag2 = p.mag2;
+            best.re = p.re;
+            best.im = p.im;
+            best.n = p.n;
+        }
+    }
+    WinState ns = best;
+    if ((w_cur + 1) * t.win_len <= t.end_abs) {
+        emit_trigger(t, i, best, w_cur, out);
+        ns.mag2 = -1.0f;
+        ns.re = ns.im = 0.0f;
+        ns.n = -1;
+    }
+    t.state_out[i] = ns;
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_threads, TrigOut out,
+                                cudaStream_t s) {
+    if (n_tasks == 0 || total_threads == 0) return cudaSuccess;
+    win_finalize_kernel<<<(total_threads + 255) / 256, 256, 0, s>>>(d_tasks, n_tasks, total_threads, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,
                             cudaStream_t s) {
     if (n_tasks == 0 || max_out <= 0) return cudaSuccess;

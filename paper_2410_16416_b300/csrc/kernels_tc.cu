@@ -172,28 +172,85 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
 }
 
 // ---------------------------------------------------------------------------
-// a3: mixing GEMM, time on TMEM lanes: D[m][a] = sum_l O[m][l] Mcat[a][l]
+// a3 + a4 (+ a5 partials at the top level): mixing GEMM with the x2
+// interpolation of the coarser level fused into its epilogue.
+//   D[a][m] = sum_l M[a][l] O[m][l]   (TMEM lanes = filters, columns = time)
+//   y_k[a][m] = D[a][m] + sum_j 2 g[j] y_{k+1}[a][(m - j)/2]
+// The coarser level's row segment (<= 164 samples per filter) is staged in
+// shared memory by one TMA load; each thread interpolates its own row segment
+// from registers.  At the top level the epilogue does not store the SNR: it
+// reduces |rho|^2 over its columns into per-window partial maxima.
 // ---------------------------------------------------------------------------
 constexpr int kMixStages = 2;
-constexpr int kMixABytes = kTcM * 64 * 2;        // O tile: 128 time rows x 64 l
-constexpr int kMixBBytes = kTcN * 64 * 2;        // Mcat tile: 256 filter rows x 64 l
+constexpr int kMixRows = 128;                            // filters per tile (MMA M)
+constexpr int kMixCols = 256;                            // time samples per tile (MMA N)
+constexpr int kMixABytes = kMixRows * 64 * 2;            // mixing tile: 128 filters x 64 l
+constexpr int kMixBBytes = kMixCols * 64 * 2;            // basis-output tile: 256 time x 64 l
 constexpr int kMixStageBytes = kMixABytes + kMixBBytes;
+constexpr int kYsBytes = kYsCols * kMixRows * 4;         // staged coarser level (FP32)
+
+// x[j] += interpolated coarser level at column c0 + j.  w[i] holds the staged
+// coarser sample at register index i; PAR = parity of the first column's
+// relative index, REM = offset of the first needed sample inside w.
+template <int PAR, int REM>
+__device__ __forceinline__ void add_interp(float (&x)[32], const float (&w)[52], const Halfband &g) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int base = REM + 16 + ((j + PAR) >> 1);
+        if (((j + PAR) & 1) == 0) {
+            x[j] += w[base];
+        } else {
+            float v = 0.0f;
+#pragma unroll
+            for (int t = 0; t < kOddTaps; ++t) v = fmaf(2.0f * g.odd[t], w[base - t] + w[base + 1 + t], v);
+            x[j] += v;
+        }
+    }
+}
+
+__device__ __forceinline__ void add_interp_dispatch(int sel, float (&x)[32], const float (&w)[52],
+                                                    const Halfband &g) {
+    switch (sel) {
+        case 0: add_interp<0, 0>(x, w, g); break;
+        case 1: add_interp<0, 1>(x, w, g); break;
+        case 2: add_interp<0, 2>(x, w, g); break;
+        case 3: add_interp<0, 3>(x, w, g); break;
+        case 4: add_interp<1, 0>(x, w, g); break;
+        case 5: add_interp<1, 1>(x, w, g); break;
+        case 6: add_interp<1, 2>(x, w, g); break;
+        default: add_interp<1, 3>(x, w, g); break;
+    }
+}
+
+struct SegBest {
+    float mag2, re, im;
+    int64_t n;
+};
 
 template <bool BF16>
-__global__ void __launch_bounds__(128, 1) tc_mix_kernel(const TcMixTask *__restrict__ tasks, int n_tasks,
-                                                        int *err) {
+__global__ void __launch_bounds__(256, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
+                                                          Halfband g, int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + kMixStages;
     uint64_t *accb = empty + kMixStages;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
+    uint64_t *ybar = accb + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(ybar + 1);
     uint8_t *st = smem + 1024;
+    float *ys = reinterpret_cast<float *>(st + kMixStages * kMixStageBytes);
 
-    const TcMixTask &t = tasks[find_tile(tasks, n_tasks, blockIdx.x)];
+    const TcMixUpTask &t = tasks[find_tile(tasks, n_tasks, blockIdx.x)];
     const int local = blockIdx.x - t.tile_begin;
     const int tt = local / t.tiles_a, at = local % t.tiles_a;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (t.Lk_pad + 63) / 64;
+    // coarser-level staging: first needed position A0 - 16, aligned down to 4 floats (16 B) for TMA
+    const int64_t rel0 = (int64_t)kMixCols * tt - t.lam;
+    const int64_t A0 = (rel0 >> 1) + t.in_off;
+    const int64_t xs0 = (A0 - 16) & ~int64_t(3);
+    const int rem = (int)((A0 - 16) - xs0);
+    const int par = (int)(rel0 & 1);
 
     if (warp == 0) {
         tmem_alloc(tslot, kTmemCols);
@@ -205,6 +262,7 @@ __global__ void __launch_bounds__(128, 1) tc_mix_kernel(const TcMixTask *__restr
             mbar_init(&empty[s], 1);
         }
         mbar_init(accb, 1);
+        mbar_init(ybar, 1);
         fence_barrier_init();
         fence_proxy_async();
     }
@@ -212,21 +270,23 @@ __global__ void __launch_bounds__(128, 1) tc_mix_kernel(const TcMixTask *__restr
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const int nk = (t.Lk_pad + 63) / 64;
 
     if (warp == 0 && lane == 0) {
-        prefetch_tmap(t.mapO);
-        prefetch_tmap(t.mapM);
+        if (t.mapYs) {
+            prefetch_tmap(t.mapYs);
+            mbar_expect_tx(ybar, kYsBytes);
+            tma_load_2d(ys, t.mapYs, (int)xs0, at * kMixRows, ybar);
+        }
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % kMixStages;
             if (kc >= kMixStages && !mbar_wait(&empty[s], ((kc / kMixStages) - 1) & 1, err, 5)) break;
             uint8_t *sa = st + s * kMixStageBytes;
             mbar_expect_tx(&full[s], kMixStageBytes);
-            tma_load_2d(sa, t.mapO, kc * 64, tt * kTcM, &full[s]);
-            tma_load_2d(sa + kMixABytes, t.mapM, kc * 64, at * kTcN, &full[s]);
+            tma_load_2d(sa, t.mapM, kc * 64, at * kMixRows, &full[s]);
+            tma_load_2d(sa + kMixABytes, t.mapO, kc * 64, tt * kMixCols, &full[s]);
         }
-    } else if (warp == 1 && lane == 0) {
-        const uint32_t idesc = idesc_f16(kTcM, kTcN, BF16);
+    } else if (warp == 1 && lane == 0 && nk > 0) {
+        const uint32_t idesc = idesc_f16(kMixRows, kMixCols, BF16);
         bool ok = true;
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % kMixStages;
@@ -242,26 +302,76 @@ __global__ void __launch_bounds__(128, 1) tc_mix_kernel(const TcMixTask *__restr
         if (ok) mma_commit(accb);
     }
     __syncwarp();
-    const bool have = mbar_wait(accb, 0, err, 7);
+    bool have = true;
+    if (nk > 0) have = mbar_wait(accb, 0, err, 7);
+    if (t.mapYs && have) have = mbar_wait(ybar, 0, err, 8);
     tc_fence_after();
     if (have) {
-        const int64_t m = (int64_t)tt * kTcM + warp * 32 + lane;
-        const bool mv = m < t.Bk;
+        const int q = warp & 3, h = warp >> 2;          // TMEM lane quarter, column half
+        const int R = 32 * q + lane;
+        const int a = kMixRows * at + R;
+        const float *yrow = ys + R * kYsCols;
+        const bool top = t.part != nullptr;
+        SegBest b0{-1.0f, 0.0f, 0.0f, -1}, b1{-1.0f, 0.0f, 0.0f, -1};
+        const int64_t half_first = t.first_n + (int64_t)kMixCols * tt + 128 * h;   // absolute index
+        const int64_t w_first = top ? (half_first >= 0 ? half_first : 0) / t.win_len : 0;
 #pragma unroll 1
-        for (int c0 = 0; c0 < kTcN; c0 += 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-            tmem_ld_wait();
-            if (!mv) continue;
+        for (int c0 = 128 * h; c0 < 128 * h + 128; c0 += 32) {
+            float x[32];
+            if (nk > 0) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + c0, v);
+                tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int a = at * kTcN + c0 + j;
-                if (a < t.M2) {
-                    float *p = t.Y + (int64_t)a * t.ldy + m;
-                    const float val = __uint_as_float(v[j]);
-                    *p = t.beta ? *p + val : val;
+                for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) x[j] = 0.0f;
+            }
+            if (t.mapYs) {
+                float w[52];
+                const float4 *src = reinterpret_cast<const float4 *>(yrow + (c0 >> 1));
+#pragma unroll
+                for (int i = 0; i < 13; ++i) {
+                    const float4 f = src[i];
+                    w[4 * i] = f.x; w[4 * i + 1] = f.y; w[4 * i + 2] = f.z; w[4 * i + 3] = f.w;
+                }
+                add_interp_dispatch(par * 4 + rem, x, w, g);
+            }
+            const int64_t col0 = (int64_t)kMixCols * tt + c0;
+            const int64_t n0 = t.first_n + col0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (n0 + j < 0) x[j] = 0.0f;                 // every rate starts at index 0
+            if (t.Y && a < t.M2) {
+                float *dst = t.Y + (int64_t)a * t.ldy + col0;
+                if (col0 + 32 <= t.Bk) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        *reinterpret_cast<float4 *>(dst + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < t.Bk) dst[j] = x[j];
                 }
             }
+            if (top) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float p = __shfl_xor_sync(0xffffffffu, x[j], 1);   // other phase of the template
+                    const int64_t n = n0 + j;
+                    if (n < 0 || col0 + j >= t.Bk) continue;
+                    const float m2 = fmaf(p, p, x[j] * x[j]);
+                    SegBest &b = (n / t.win_len == w_first) ? b0 : b1;
+                    if (m2 > b.mag2) { b.mag2 = m2; b.re = x[j]; b.im = p; b.n = n; }
+                }
+            }
+        }
+        if (top && (a & 1) == 0 && a < t.M2) {
+            const int i = a >> 1;
+            WinPart *base = t.part + ((int64_t)(tt * 2 + h) * 2) * t.M;
+            base[i] = WinPart{b0.mag2, b0.re, b0.im, 0, b0.n};
+            base[t.M + i] = WinPart{b1.mag2, b1.re, b1.im, 0, b1.n};
         }
     }
     tc_fence_before();
@@ -276,7 +386,7 @@ __global__ void __launch_bounds__(128, 1) tc_mix_kernel(const TcMixTask *__restr
 // launchers
 // ---------------------------------------------------------------------------
 size_t tc_fir_smem_bytes(int kpad_max) { return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * 8 + kpad_max) * 2; }
-size_t tc_mix_smem_bytes() { return 1024 + 1024 + kMixStages * kMixStageBytes; }
+size_t tc_mixup_smem_bytes() { return 1024 + 1024 + kMixStages * kMixStageBytes + kYsBytes; }
 
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, bool bf16, cudaStream_t s) {
     if (n_tasks == 0) return cudaSuccess;
@@ -303,19 +413,19 @@ cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_mix(const TcMixTask *d_tasks, int n_tasks, int total_tiles, bool bf16, int *err,
-                          cudaStream_t s) {
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g, bool bf16,
+                            int *err, cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    const size_t smem = tc_mix_smem_bytes();
+    const size_t smem = tc_mixup_smem_bytes();
     cudaError_t e;
     if (bf16) {
-        e = cudaFuncSetAttribute(tc_mix_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(tc_mixup_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        tc_mix_kernel<true><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
+        tc_mixup_kernel<true><<<total_tiles, 256, smem, s>>>(d_tasks, n_tasks, g, err);
     } else {
-        e = cudaFuncSetAttribute(tc_mix_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(tc_mixup_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        tc_mix_kernel<false><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
+        tc_mixup_kernel<false><<<total_tiles, 256, smem, s>>>(d_tasks, n_tasks, g, err);
     }
     return cudaGetLastError();
 }

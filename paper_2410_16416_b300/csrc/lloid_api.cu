@@ -117,7 +117,13 @@ struct LevelDev {
     int64_t x16_len = 0;
     void *O16 = nullptr;      // basis outputs [Bk_max x Lk_pad], time-major
     void *M16 = nullptr;      // stacked mixing [2M x Lk_pad]
-    CUtensorMap *mapO = nullptr, *mapM = nullptr;   // device addresses
+    CUtensorMap *mapO = nullptr, *mapM = nullptr;   // device addresses (box 64 x 256 time rows, 64 x 128 filters)
+    // 16-bit modes, levels k >= 1: SNR rows [history (Hy) | new (B_k)] in one buffer, so the
+    // next finer level's epilogue can stage a row segment with one TMA load
+    float *yuni = nullptr;    // [2M x ldu]
+    int64_t ldu = 0;
+    float *ytmp = nullptr;    // [2M x Hy] history shift staging
+    CUtensorMap *mapY = nullptr;
 };
 
 struct TriggerSlot {
@@ -182,6 +188,8 @@ struct sb_unit {
     std::vector<LevelDev> levels;
     WinState *wstate[2] = {nullptr, nullptr};
     int wcur = 0;
+    WinPart *part = nullptr;       // 16-bit modes: top-level partial window maxima (scratch)
+    int64_t part_rec_max = 0;
     int64_t *tids = nullptr;
     std::vector<void *> allocs;
     int64_t bytes = 0;
@@ -315,14 +323,19 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
         b += 2 * (P.Hd[k] + Bk) * 4;                 // decimated strain ping-pong
         b += M2 * ldy * 4;                           // SNR block
         b += 2 * M2 * P.Hy[k] * 4;                   // SNR history ping-pong
-        if (P.tc)
-            b += P.x16_len[k] * 2 + (Bk + kTcM) * P.Lk_pad[k] * 2 + M2 * P.Lk_pad[k] * 2 + 2 * 128;
-        else
+        if (P.tc) {
+            b -= M2 * ldy * 4 + 2 * M2 * P.Hy[k] * 4;   // replaced by the unified level buffer
+            if (k >= 1) b += M2 * round_up(P.Hy[k] + Bk, 4) * 4 + M2 * P.Hy[k] * 4 + 128;
+            else if (d->flags & SB_FLAG_KEEP_SNR) b += M2 * ldy * 4;
+            b += P.x16_len[k] * 2 + (Bk + 256) * P.Lk_pad[k] * 2 + M2 * P.Lk_pad[k] * 2 + 2 * 128;
+        } else {
             b += M2 * P.Lk[k] * 4 + P.Lk[k] * Bk * 4;    // mixing + basis outputs
+        }
     }
     for (int s = 0; s < S; ++s)
         b += P.tc ? 8 * P.L16[s] * P.Kpad[s] * 2 + 128 : (int64_t)d->slices[s].n_basis * d->slices[s].n_taps * 4;
     b += 2 * (int64_t)d->n_templates * sizeof(WinState) + d->n_templates * 8;
+    if (P.tc) b += ((d->max_push_samples + 255) / 256) * 4 * (int64_t)d->n_templates * sizeof(WinPart);
     P.bytes = b;
     return SB_OK;
 }
@@ -456,6 +469,23 @@ static int encode_map(CUtensorMap *out, void *base, bool bf16, uint64_t inner, u
     return SB_OK;
 }
 
+// 2-D FP32 map over a row-major [outer x inner] matrix, no swizzle, box
+// (box_inner x box_outer); out-of-range elements read as 0.
+static int encode_map_f32(CUtensorMap *out, void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                          uint32_t box_outer) {
+    auto encode = tensor_map_encoder();
+    if (!encode) return fail(SB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 4};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SB_ECUDA, "cuTensorMapEncodeTiled (FP32) failed (" + std::to_string((int)r) + ")");
+    return SB_OK;
+}
+
 static int upload_map(sb_unit *u, const CUtensorMap &h, CUtensorMap **dev) {
     int rc = dev_alloc(u, (void **)dev, sizeof(CUtensorMap));
     if (rc) return rc;
@@ -501,10 +531,17 @@ static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d) {
         CK(cudaMemcpy(L.M16, m.data(), m.size() * 2, cudaMemcpyHostToDevice));
         CUtensorMap hm, ho;
         int rc;
-        if ((rc = encode_map(&hm, L.M16, u->bf16, L.Lk_pad, M2, kTcN))) return rc;
+        if ((rc = encode_map(&hm, L.M16, u->bf16, L.Lk_pad, M2, 128))) return rc;
         if ((rc = upload_map(u, hm, &L.mapM))) return rc;
-        if ((rc = encode_map(&ho, L.O16, u->bf16, L.Lk_pad, L.Bk_max + kTcM, kTcM))) return rc;
+        if ((rc = encode_map(&ho, L.O16, u->bf16, L.Lk_pad, L.Bk_max + 256, 256))) return rc;
         if ((rc = upload_map(u, ho, &L.mapO))) return rc;
+    }
+    for (auto &L : u->levels) {
+        if (!L.yuni) continue;
+        CUtensorMap hy;
+        int rc;
+        if ((rc = encode_map_f32(&hy, L.yuni, L.ldu, M2, kYsCols, 128))) return rc;
+        if ((rc = upload_map(u, hy, &L.mapY))) return rc;
     }
     return SB_OK;
 }
@@ -521,6 +558,8 @@ static int validate_desc(const sb_desc *d, std::vector<int> &lvl, Plan &P) {
         return fail(SB_EINVAL, "window_s * top_rate_hz must be a positive integer");
     int rc = plan_unit(d, lvl, P);
     if (rc) return rc;
+    if (P.tc && std::llround(wl) < 128)
+        return fail(SB_EINVAL, "tensor-core modes need window_s * top_rate_hz >= 128");
     if (d->max_push_samples % (1LL << P.kmax))
         return fail(SB_EINVAL, "max_push_samples must be a multiple of 2^k_max");
     return SB_OK;
@@ -608,12 +647,22 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
             if ((rc = dev_alloc(u, (void **)&L.dbuf[b], (L.Hd + L.Bk_max) * 4))) return cleanup(rc);
             if (cudaMemset(L.dbuf[b], 0, (L.Hd + L.Bk_max) * 4) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
         }
-        if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return cleanup(rc);
-        if (L.Hy > 0) {
-            for (int b = 0; b < 2; ++b) {
-                if ((rc = dev_alloc(u, (void **)&L.yhist[b], M2 * L.Hy * 4))) return cleanup(rc);
-                if (cudaMemset(L.yhist[b], 0, M2 * L.Hy * 4) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
+        if (!u->tc) {
+            if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return cleanup(rc);
+            if (L.Hy > 0) {
+                for (int b = 0; b < 2; ++b) {
+                    if ((rc = dev_alloc(u, (void **)&L.yhist[b], M2 * L.Hy * 4))) return cleanup(rc);
+                    if (cudaMemset(L.yhist[b], 0, M2 * L.Hy * 4) != cudaSuccess)
+                        return cleanup(fail(SB_ECUDA, "memset"));
+                }
             }
+        } else if (k >= 1) {
+            L.ldu = round_up(L.Hy + L.Bk_max, 4);
+            if ((rc = dev_alloc(u, (void **)&L.yuni, M2 * L.ldu * 4))) return cleanup(rc);
+            if (cudaMemset(L.yuni, 0, M2 * L.ldu * 4) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
+            if ((rc = dev_alloc(u, (void **)&L.ytmp, M2 * L.Hy * 4))) return cleanup(rc);
+        } else if (u->flags & SB_FLAG_KEEP_SNR) {
+            if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return cleanup(rc);
         }
         if (L.Lk > 0 && !u->tc) {
             if ((rc = dev_alloc(u, (void **)&L.Mcat, M2 * L.Lk * 4))) return cleanup(rc);
@@ -625,7 +674,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
             if ((rc = dev_alloc(u, &L.x16, L.x16_len * 2))) return cleanup(rc);
             if (cudaMemset(L.x16, 0, L.x16_len * 2) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
             if (L.Lk_pad > 0) {
-                const int64_t rows = L.Bk_max + kTcM;
+                const int64_t rows = L.Bk_max + 256;
                 if ((rc = dev_alloc(u, &L.O16, rows * L.Lk_pad * 2))) return cleanup(rc);
                 if (cudaMemset(L.O16, 0, rows * L.Lk_pad * 2) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
                 if ((rc = dev_alloc(u, &L.M16, M2 * L.Lk_pad * 2))) return cleanup(rc);
@@ -673,6 +722,10 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
             return cleanup(fail(SB_ECUDA, "mixing upload"));
     }
     if (u->tc && (rc = upload_tc_mixing_and_maps(u, d))) return cleanup(rc);
+    if (u->tc) {
+        u->part_rec_max = ((u->Bmax + 255) / 256) * 4;
+        if ((rc = dev_alloc(u, (void **)&u->part, u->part_rec_max * u->M * sizeof(WinPart)))) return cleanup(rc);
+    }
     // trigger state and template ids
     std::vector<WinState> ws(u->M);
     for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = 0.0f; w.n = -1; }
@@ -961,8 +1014,10 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     // tensor-core modes, indexed [bf16 ? 1 : 0]
     std::vector<HalfConvTask> conv[2];
     std::vector<TcFirTask> tfir[2];
-    std::vector<std::vector<TcMixTask>> tmix[2] = {std::vector<std::vector<TcMixTask>>(kall + 1),
-                                                   std::vector<std::vector<TcMixTask>>(kall + 1)};
+    std::vector<std::vector<TcMixUpTask>> tmix[2] = {std::vector<std::vector<TcMixUpTask>>(kall + 1),
+                                                     std::vector<std::vector<TcMixUpTask>>(kall + 1)};
+    std::vector<WinFinTask> wfin;
+    std::vector<CopyTask> yshift1, yshift2;
     int kpad_max[2] = {0, 0};
     int max_hd = 0, max_hy = 0, max_rows = 0;
     int64_t trig_need = 0;
@@ -1013,19 +1068,46 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     tfir[h].push_back(f);
                     kpad_max[h] = std::max(kpad_max[h], sd.Kpad);
                 }
-                if (L.Lk_pad > 0) {
-                    TcMixTask mt{};
-                    mt.mapO = L.mapO;
+                {
+                    TcMixUpTask mt{};
                     mt.mapM = L.mapM;
-                    mt.Y = L.ynew;
-                    mt.ldy = L.ldy;
+                    mt.mapO = L.mapO;
+                    mt.mapYs = k < u->kmax ? u->levels[k + 1].mapY : nullptr;
+                    mt.Y = k >= 1 ? L.yuni + L.Hy : L.ynew;
+                    mt.ldy = k >= 1 ? L.ldu : L.ldy;
+                    mt.part = k == 0 ? u->part : nullptr;
+                    mt.first_n = (Tp >> k) - L.lam;
+                    mt.win_len = u->win_len;
                     mt.Lk_pad = L.Lk_pad;
                     mt.M2 = M2;
+                    mt.M = u->M;
                     mt.Bk = (int32_t)Bk;
-                    mt.beta = k < u->kmax ? 1 : 0;
-                    mt.tiles_a = (M2 + kTcN - 1) / kTcN;
-                    mt.tiles_t = (int32_t)((Bk + kTcM - 1) / kTcM);
+                    mt.lam = (int32_t)L.lam;
+                    mt.in_off = k < u->kmax ? (int32_t)(u->levels[k + 1].lam + u->levels[k + 1].Hy) : 0;
+                    mt.tiles_t = (int32_t)((Bk + 255) / 256);
+                    mt.tiles_a = (M2 + 127) / 128;
                     tmix[h][k].push_back(mt);
+                }
+                if (k >= 1) {           // next push's interpolation history: columns [Bk, Bk + Hy) -> [0, Hy)
+                    CopyTask a{};
+                    a.cur = L.yuni;
+                    a.ld_cur = L.ldu;
+                    a.dst = L.ytmp;
+                    a.ld_dst = L.Hy;
+                    a.rows = M2;
+                    a.n = (int32_t)L.Hy;
+                    a.off = (int32_t)Bk;
+                    yshift1.push_back(a);
+                    CopyTask bt{};
+                    bt.cur = L.ytmp;
+                    bt.ld_cur = L.Hy;
+                    bt.dst = L.yuni;
+                    bt.ld_dst = L.ldu;
+                    bt.rows = M2;
+                    bt.n = (int32_t)L.Hy;
+                    bt.off = 0;
+                    yshift2.push_back(bt);
+                    max_hy = std::max<int>(max_hy, (int)L.Hy);
                 }
             }
             for (int s : L.slices) {
@@ -1045,7 +1127,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 g.toeplitz = 1;
                 fir.push_back(g);
             }
-            if (k < u->kmax) {
+            if (k < u->kmax && !u->tc) {
                 LevelDev &N = u->levels[k + 1];
                 UpTask ut{};
                 ut.hist = N.yhist[N.ycur];
@@ -1078,7 +1160,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 g.toeplitz = 0;
                 recon[k].push_back(g);
             }
-            if (k >= 1 && L.Hy > 0) {
+            if (k >= 1 && L.Hy > 0 && !u->tc) {
                 CopyTask yt{};
                 yt.hist = L.yhist[L.ycur];
                 yt.cur = L.ynew;
@@ -1098,7 +1180,22 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         LevelDev &L0 = u->levels[0];
         const int64_t first_n = Tp - L0.lam;
         const int64_t start = std::max<int64_t>(first_n, 0), end = first_n + B;
-        if (end > start) {
+        if (end > start && u->tc) {
+            WinFinTask w{};
+            w.part = u->part;
+            w.state_in = u->wstate[u->wcur];
+            w.state_out = u->wstate[1 - u->wcur];
+            w.template_ids = u->tids;
+            w.unit_id = u->id;
+            w.win_len = u->win_len;
+            w.start_abs = start;
+            w.end_abs = end;
+            w.n_rec = (int32_t)(((B + 255) / 256) * 4);
+            w.M = u->M;
+            w.threshold = u->thr;
+            wfin.push_back(w);
+            trig_need += (int64_t)u->M * ((end - 1) / u->win_len - start / u->win_len + 1);
+        } else if (end > start) {
             WinTask w{};
             w.x = L0.ynew;
             w.ldx = L0.ldy;
@@ -1144,6 +1241,11 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
             }
     }
+    int wfin_threads = 0;
+    for (auto &w : wfin) {
+        w.thread_begin = wfin_threads;
+        wfin_threads += w.M;
+    }
     int win_warps = 0;
     for (auto &w : win) {
         w.warp_begin = win_warps;
@@ -1166,9 +1268,12 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     for (int h = 0; h < 2; ++h) {
         o_conv[h] = pk.add(conv[h].data(), conv[h].size() * sizeof(HalfConvTask));
         o_tfir[h] = pk.add(tfir[h].data(), tfir[h].size() * sizeof(TcFirTask));
-        for (int k = 0; k <= kall; ++k) o_tmix[h][k] = pk.add(tmix[h][k].data(), tmix[h][k].size() * sizeof(TcMixTask));
+        for (int k = 0; k <= kall; ++k) o_tmix[h][k] = pk.add(tmix[h][k].data(), tmix[h][k].size() * sizeof(TcMixUpTask));
     }
     const size_t o_ycopy = pk.add(ycopy.data(), ycopy.size() * sizeof(CopyTask));
+    const size_t o_wfin = pk.add(wfin.data(), wfin.size() * sizeof(WinFinTask));
+    const size_t o_ys1 = pk.add(yshift1.data(), yshift1.size() * sizeof(CopyTask));
+    const size_t o_ys2 = pk.add(yshift2.data(), yshift2.size() * sizeof(CopyTask));
     std::vector<size_t> o_strain(n_units, 0);
     if (!on_device)
         for (int i = 0; i < n_units; ++i) o_strain[i] = pk.add(strains[i], B * sizeof(float));
@@ -1251,22 +1356,28 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             if (!tmix[h][k].empty() &&
                 (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
                      *n = 1;
-                     return launch_tc_mix((TcMixTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(), tmix_tiles[h][k],
-                                          h == 1, derr, st);
+                     return launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
+                                            tmix_tiles[h][k], c->g, h == 1, derr, st);
                  })))
                 return rc;
     }
     // 6. a5 trigger generator
     TrigOut to{slot->dbuf, slot->dcount, (int32_t)slot->cap};
     if ((rc = run_stage(c, SB_STAGE_TRIGGER, [&](int *n) {
-             *n = win.empty() ? 0 : 1;
-             return launch_window_max((WinTask *)(D + o_win), (int)win.size(), win_warps, to, st);
+             *n = (win.empty() ? 0 : 1) + (wfin.empty() ? 0 : 1);
+             cudaError_t e = launch_window_max((WinTask *)(D + o_win), (int)win.size(), win_warps, to, st);
+             if (e != cudaSuccess) return e;
+             return launch_win_finalize((WinFinTask *)(D + o_wfin), (int)wfin.size(), wfin_threads, to, st);
          })))
         return rc;
     // 7. SNR history for the interpolators of the next push
     if ((rc = run_stage(c, SB_STAGE_SNRHIST, [&](int *n) {
-             *n = ycopy.empty() ? 0 : 1;
-             return launch_copy((CopyTask *)(D + o_ycopy), (int)ycopy.size(), max_rows, max_hy, st);
+             *n = (ycopy.empty() ? 0 : 1) + (yshift1.empty() ? 0 : 2);
+             cudaError_t e = launch_copy((CopyTask *)(D + o_ycopy), (int)ycopy.size(), max_rows, max_hy, st);
+             if (e != cudaSuccess) return e;
+             e = launch_copy((CopyTask *)(D + o_ys1), (int)yshift1.size(), max_rows, max_hy, st);
+             if (e != cudaSuccess) return e;
+             return launch_copy((CopyTask *)(D + o_ys2), (int)yshift2.size(), max_rows, max_hy, st);
          })))
         return rc;
     // 8. triggers to the host (count plus an eager prefix; the rest on demand)
@@ -1288,7 +1399,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             LevelDev &L = u->levels[k];
             L.dcur = 1 - L.dcur;
             L.last_Bk = B >> k;
-            if (k >= 1 && L.Hy > 0) L.ycur = 1 - L.ycur;
+            if (k >= 1 && L.Hy > 0 && !u->tc) L.ycur = 1 - L.ycur;
         }
         const int64_t first_n = u->T - u->levels[0].lam;
         if (first_n + B > std::max<int64_t>(first_n, 0)) u->wcur = 1 - u->wcur;

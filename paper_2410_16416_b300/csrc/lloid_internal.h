@@ -140,29 +140,57 @@ struct TcFirTask {
     int32_t tile_begin;
 };
 
-// a3 on tensor cores.  Tile (tt, at): time rows [128 tt, +128), filters [256 at, +256).
-struct TcMixTask {
-    const CUtensorMap *mapO;   // O [rows x Lk_pad], box 64 x 128
-    const CUtensorMap *mapM;   // Mcat [2M x Lk_pad], box 64 x 256
-    float *Y;                  // level SNR [2M][ldy], FP32
-    int64_t ldy;
-    int32_t Lk_pad;
-    int32_t M2;
-    int32_t Bk;
-    int32_t beta;
-    int32_t tiles_t;           // ceil(Bk / 128)
-    int32_t tiles_a;           // ceil(2M / 256)
-    int32_t tile_begin;
+// Partial window maximum of one template over one column run of one tile.
+struct WinPart {
+    float mag2;                // |rho|^2 (-1: no valid sample)
+    float re, im;
     int32_t pad;
+    int64_t n;                 // absolute top-rate sample
+};
+
+constexpr int kYsCols = 164;   // staged coarser-level samples per filter row (row stride 4 mod 32 words)
+
+// a3 + a4 on tensor cores (+ a5 partial maxima at the top level).
+// Tile (tt, at): time columns [256 tt, +256) of this level, filters [128 at, +128).
+struct TcMixUpTask {
+    const CUtensorMap *mapM;   // A: mixing [2M x Lk_pad] 16-bit, box 64 x 128 (unused when Lk_pad = 0)
+    const CUtensorMap *mapO;   // B: basis outputs [rows x Lk_pad] 16-bit, box 64 x 256
+    const CUtensorMap *mapYs;  // coarser level y_{k+1}, FP32 [2M x ldu], box 164 x 128; null at the deepest level
+    float *Y;                  // this level's first new column (row a at Y + a ldy); null: not stored
+    int64_t ldy;
+    WinPart *part;             // top level: partials [((tt*2 + half)*2 + seg) * M + i]; null below
+    int64_t first_n;           // absolute index (this level's rate) of column 0
+    int64_t win_len;           // top level: window length in samples (>= 128)
+    int32_t Lk_pad, M2, M, Bk;
+    int32_t lam;               // Lambda of this level
+    int32_t in_off;            // Lambda_{k+1} + Hy_{k+1}: coarser position of (relative index 0) / 2
+    int32_t tiles_t, tiles_a, tile_begin, pad;
+};
+
+// Window bookkeeping after the top-level partial maxima: merges a unit's
+// partials (in time order) with the open window's state, emits triggers.
+struct WinFinTask {
+    const WinPart *part;       // [n_rec][M]
+    const WinState *state_in;
+    WinState *state_out;
+    const int64_t *template_ids;
+    int64_t unit_id;
+    int64_t win_len;
+    int64_t start_abs, end_abs; // valid absolute samples of this push: [start_abs, end_abs)
+    int32_t n_rec, M;
+    int32_t thread_begin;
+    float threshold;
 };
 
 size_t tc_fir_smem_bytes(int kpad_max);
-size_t tc_mix_smem_bytes();
+size_t tc_mixup_smem_bytes();
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, bool bf16, cudaStream_t s);
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, bool bf16, int *err,
                           cudaStream_t s);
-cudaError_t launch_tc_mix(const TcMixTask *d_tasks, int n_tasks, int total_tiles, bool bf16, int *err,
-                          cudaStream_t s);
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g, bool bf16,
+                            int *err, cudaStream_t s);
+cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_threads, TrigOut out,
+                                cudaStream_t s);
 
 // ---- launchers (kernels_simt.cu) -------------------------------------------
 cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,
