@@ -208,6 +208,33 @@ int sb_ctx_profile(sb_ctx *ctx, int32_t enable);
  * (arrays of n_stages entries; n_stages <= SB_N_STAGES). */
 int sb_ctx_stage_times(sb_ctx *ctx, double *ms, int64_t *launches, int32_t n_stages);
 
+/* Window maxima and triggers of a caller's top-rate SNR block without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc/cudaFree while they run (a serving
+ * loop replaying CUDA graphs, or a process whose device memory belongs to a
+ * pool it does not own), where allocating would synchronise the device or
+ * fail.
+ * x: device FP32 [2M][ldx], row a = 2i + p (p = 0 cosine, 1 sine phase);
+ * column c is absolute top-rate sample first_sample + c.  Every window
+ * [w window_len, (w+1) window_len) lying entirely inside
+ * [max(0, first_sample), first_sample + n_samples) gives its |rho| maximum
+ * (first sample on ties); a trigger (unit = -1, template_id from the device
+ * array template_ids or i when NULL) is written to the device array out when
+ * |rho| > threshold.  out_count: device int32[2] = {triggers, overflow flag},
+ * zeroed by the call; at most cap triggers are stored.  Work is queued on
+ * stream (a cudaStream_t; NULL = legacy default stream) and nothing blocks.
+ * Scratch: a fixed device array of 2^18 partial records (6 MiB) that every
+ * GPU loading this library holds until the process exits; a call needs
+ * 2 * M * ceil(n_samples / 256) records and returns SB_EINVAL (see
+ * sb_last_error) beyond that, or when window_len < 256.  The first call on a
+ * device looks up the array's device address (make that first call before any
+ * stream capture).  All calls share the array: calls that overlap on the GPU
+ * (other streams, other threads) race; serialise them. */
+int sb_window_triggers_noalloc(const float *x, int64_t ldx, int32_t n_templates, int64_t n_samples,
+                               int64_t first_sample, int64_t window_len, float threshold,
+                               const int64_t *template_ids, sb_trigger *out, int32_t *out_count, int32_t cap,
+                               void *stream);
+
 /* Message describing the calling thread's last error ("" if none). */
 const char *sb_last_error(void);
 

@@ -74,6 +74,9 @@ SIGNATURES = {
     "sb_ctx_get_stats": (C.c_int, [C.c_void_p, C.POINTER(SbCtxStats)]),
     "sb_ctx_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "sb_ctx_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
+    "sb_window_triggers_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
+                                             C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                             C.c_void_p]),
     "sb_last_error": (C.c_char_p, []),
 }
 

@@ -1439,3 +1439,5 @@ extern "C" int sb_unit_snr(sb_unit *u, float *host_out, int64_t cap, int64_t *fi
 }
 
 extern "C" const char *sb_last_error(void) { return g_err.c_str(); }
+
+void set_last_error(const std::string &msg) { g_err = msg; }
