@@ -258,77 +258,81 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
 // partial records in time order, closes every window the push completes
 // (threshold, phase, trigger) and keeps the open window's running maximum.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void emit_trigger(const WinFinTask &t, int i, const WinState &b, int64_t w,
-                                             TrigOut out) {
-    if (b.mag2 < 0.0f || !(sqrtf(b.mag2) > t.threshold)) return;
-    const int slot = atomicAdd(out.count, 1);
-    if (slot >= out.cap) {
-        atomicExch(out.count + 1, 1);
-        return;
-    }
-    DevTrigger r;
-    r.unit = t.unit_id;
-    r.template_id = t.template_ids[i];
-    r.sample = b.n;
-    r.window = w;
-    r.snr = sqrtf(b.mag2);
-    r.phase = atan2f(b.im, b.re);
-    r.flags = 0;
-    r.reserved = 0;
-    out.buf[slot] = r;
-}
-
-__device__ __forceinline__ int find_task_by_thread(const WinFinTask *tasks, int n, int g) {
+__device__ __forceinline__ int find_task_by_warp(const WinFinTask *tasks, int n, int w) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (tasks[mid].thread_begin <= g) lo = mid; else hi = mid - 1;
+        if (tasks[mid].warp_begin <= w) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
 __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__restrict__ tasks, int n_tasks,
-                                                           int total, TrigOut out) {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= total) return;
-    const WinFinTask &t = tasks[find_task_by_thread(tasks, n_tasks, gid)];
-    const int i = gid - t.thread_begin;
-    WinState best = t.state_in[i];
-    int64_t w_cur = t.start_abs / t.win_len;          // the open window (state) or the push's first window
-    for (int r = 0; r < t.n_rec; ++r) {
-        const WinPart p = t.part[(int64_t)r * t.M + i];
-        if (p.mag2 < 0.0f) continue;
-        const int64_t w = p.n / t.win_len;
-        if (w != w_cur) {                              // records are in time order: w_cur is complete
-            emit_trigger(t, i, best, w_cur, out);
-            best.mag2 = -1.0f;
-            best.n = -1;
-            w_cur = w;
-        }
-        if (p.mag2 > best.mag2) {                      // strict: the earlier sample wins ties
-            best.mag2 = p.mag2;
-            best.re = p.re;
-            best.im = p.im;
-            best.n = p.n;
+                                                           int total_warps, TrigOut out) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= total_warps) return;
+    const WinFinTask &t = tasks[find_task_by_warp(tasks, n_tasks, gw)];
+    const int local = gw - t.warp_begin;
+    const int i = local / t.n_win, s = local % t.n_win;
+    const int64_t w = t.start_abs / t.win_len + s;
+    const int64_t lo = max(w * t.win_len, t.start_abs) - t.first_n;        // push columns of window w
+    const int64_t hi = min((w + 1) * t.win_len, t.end_abs) - t.first_n;
+    const int r0 = (int)(lo / 128) * 2, r1 = (int)((hi - 1) / 128) * 2 + 2;
+    const WinPart *rec = t.part + (int64_t)i * t.n_rec;
+    float best = -1.0f, re = 0.0f, im = 0.0f;
+    int64_t bn = INT64_MAX;
+    for (int r = r0 + lane; r < r1; r += 32) {
+        const WinPart p = rec[r];
+        if (p.mag2 < 0.0f || p.n / t.win_len != w) continue;
+        if (p.mag2 > best || (p.mag2 == best && p.n < bn)) { best = p.mag2; bn = p.n; re = p.re; im = p.im; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
+        const float ore = __shfl_xor_sync(0xffffffffu, re, off);
+        const float oim = __shfl_xor_sync(0xffffffffu, im, off);
+        if (ob > best || (ob == best && on < bn)) { best = ob; bn = on; re = ore; im = oim; }
+    }
+    if (lane != 0) return;
+    if (s == 0) {                          // the window left open by the previous push (earlier samples)
+        const WinState st = t.state_in[i];
+        if (st.mag2 >= 0.0f && !(best > st.mag2)) { best = st.mag2; bn = st.n; re = st.re; im = st.im; }
+    }
+    const bool complete = (w + 1) * t.win_len <= t.end_abs;
+    if (complete && bn != INT64_MAX && sqrtf(best) > t.threshold) {
+        const int slot = atomicAdd(out.count, 1);
+        if (slot < out.cap) {
+            DevTrigger r;
+            r.unit = t.unit_id;
+            r.template_id = t.template_ids[i];
+            r.sample = bn;
+            r.window = w;
+            r.snr = sqrtf(best);
+            r.phase = atan2f(im, re);
+            r.flags = 0;
+            r.reserved = 0;
+            out.buf[slot] = r;
+        } else {
+            atomicExch(out.count + 1, 1);
         }
     }
-    WinState ns = best;
-    if ((w_cur + 1) * t.win_len <= t.end_abs) {
-        emit_trigger(t, i, best, w_cur, out);
-        ns.mag2 = -1.0f;
-        ns.re = ns.im = 0.0f;
-        ns.n = -1;
+    if (s == t.n_win - 1) {
+        WinState ns;
+        if (complete || bn == INT64_MAX) { ns.mag2 = -1.0f; ns.re = ns.im = 0.0f; ns.n = -1; }
+        else { ns.mag2 = best; ns.re = re; ns.im = im; ns.n = bn; }
+        t.state_out[i] = ns;
     }
-    t.state_out[i] = ns;
 }
 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_threads, TrigOut out,
+cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                                 cudaStream_t s) {
-    if (n_tasks == 0 || total_threads == 0) return cudaSuccess;
-    win_finalize_kernel<<<(total_threads + 255) / 256, 256, 0, s>>>(d_tasks, n_tasks, total_threads, out);
+    if (n_tasks == 0 || total_warps == 0) return cudaSuccess;
+    win_finalize_kernel<<<(total_warps * 32 + 255) / 256, 256, 0, s>>>(d_tasks, n_tasks, total_warps, out);
     return cudaGetLastError();
 }
 

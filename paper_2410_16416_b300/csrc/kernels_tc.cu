@@ -368,10 +368,9 @@ __global__ void __launch_bounds__(256, 1) tc_mixup_kernel(const TcMixUpTask *__r
             }
         }
         if (top && (a & 1) == 0 && a < t.M2) {
-            const int i = a >> 1;
-            WinPart *base = t.part + ((int64_t)(tt * 2 + h) * 2) * t.M;
-            base[i] = WinPart{b0.mag2, b0.re, b0.im, 0, b0.n};
-            base[t.M + i] = WinPart{b1.mag2, b1.re, b1.im, 0, b1.n};
+            WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (tt * 2 + h) * 2;
+            base[0] = WinPart{b0.mag2, b0.re, b0.im, 0, b0.n};
+            base[1] = WinPart{b1.mag2, b1.re, b1.im, 0, b1.n};
         }
     }
     tc_fence_before();

@@ -1086,6 +1086,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     mt.in_off = k < u->kmax ? (int32_t)(u->levels[k + 1].lam + u->levels[k + 1].Hy) : 0;
                     mt.tiles_t = (int32_t)((Bk + 255) / 256);
                     mt.tiles_a = (M2 + 127) / 128;
+                    mt.n_rec = mt.tiles_t * 4;
                     tmix[h][k].push_back(mt);
                 }
                 if (k >= 1) {           // next push's interpolation history: columns [Bk, Bk + Hy) -> [0, Hy)
@@ -1188,13 +1189,15 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             w.template_ids = u->tids;
             w.unit_id = u->id;
             w.win_len = u->win_len;
+            w.first_n = first_n;
             w.start_abs = start;
             w.end_abs = end;
             w.n_rec = (int32_t)(((B + 255) / 256) * 4);
             w.M = u->M;
+            w.n_win = (int32_t)((end - 1) / u->win_len - start / u->win_len + 1);
             w.threshold = u->thr;
             wfin.push_back(w);
-            trig_need += (int64_t)u->M * ((end - 1) / u->win_len - start / u->win_len + 1);
+            trig_need += (int64_t)u->M * w.n_win;
         } else if (end > start) {
             WinTask w{};
             w.x = L0.ynew;
@@ -1241,10 +1244,10 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
             }
     }
-    int wfin_threads = 0;
+    int wfin_warps = 0;
     for (auto &w : wfin) {
-        w.thread_begin = wfin_threads;
-        wfin_threads += w.M;
+        w.warp_begin = wfin_warps;
+        wfin_warps += w.M * w.n_win;
     }
     int win_warps = 0;
     for (auto &w : win) {
@@ -1367,7 +1370,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
              *n = (win.empty() ? 0 : 1) + (wfin.empty() ? 0 : 1);
              cudaError_t e = launch_window_max((WinTask *)(D + o_win), (int)win.size(), win_warps, to, st);
              if (e != cudaSuccess) return e;
-             return launch_win_finalize((WinFinTask *)(D + o_wfin), (int)wfin.size(), wfin_threads, to, st);
+             return launch_win_finalize((WinFinTask *)(D + o_wfin), (int)wfin.size(), wfin_warps, to, st);
          })))
         return rc;
     // 7. SNR history for the interpolators of the next push

@@ -158,28 +158,32 @@ struct TcMixUpTask {
     const CUtensorMap *mapYs;  // coarser level y_{k+1}, FP32 [2M x ldu], box 164 x 128; null at the deepest level
     float *Y;                  // this level's first new column (row a at Y + a ldy); null: not stored
     int64_t ldy;
-    WinPart *part;             // top level: partials [((tt*2 + half)*2 + seg) * M + i]; null below
+    WinPart *part;             // top level: partials [i][n_rec], record (tt*2 + half)*2 + seg; null below
     int64_t first_n;           // absolute index (this level's rate) of column 0
     int64_t win_len;           // top level: window length in samples (>= 128)
     int32_t Lk_pad, M2, M, Bk;
     int32_t lam;               // Lambda of this level
     int32_t in_off;            // Lambda_{k+1} + Hy_{k+1}: coarser position of (relative index 0) / 2
-    int32_t tiles_t, tiles_a, tile_begin, pad;
+    int32_t tiles_t, tiles_a, tile_begin, n_rec;
 };
 
-// Window bookkeeping after the top-level partial maxima: merges a unit's
-// partials (in time order) with the open window's state, emits triggers.
+// Window bookkeeping after the top-level partial maxima: one warp per
+// (unit, template, window touched by the push) reduces that window's records,
+// merges the open window's state (first window), emits the trigger of a
+// completed window and stores the state of the one left open (last window).
 struct WinFinTask {
-    const WinPart *part;       // [n_rec][M]
+    const WinPart *part;       // [M][n_rec]; record r covers push columns [128 (r/2), +128), seg r%2
     const WinState *state_in;
     WinState *state_out;
     const int64_t *template_ids;
     int64_t unit_id;
     int64_t win_len;
+    int64_t first_n;           // absolute sample of push column 0
     int64_t start_abs, end_abs; // valid absolute samples of this push: [start_abs, end_abs)
-    int32_t n_rec, M;
-    int32_t thread_begin;
+    int32_t n_rec, M, n_win;
+    int32_t warp_begin;
     float threshold;
+    int32_t pad;
 };
 
 size_t tc_fir_smem_bytes(int kpad_max);
@@ -189,7 +193,7 @@ cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles
                           cudaStream_t s);
 cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g, bool bf16,
                             int *err, cudaStream_t s);
-cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_threads, TrigOut out,
+cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                                 cudaStream_t s);
 
 // ---- launchers (kernels_simt.cu) -------------------------------------------
