@@ -43,8 +43,8 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=240)       # 240 + 16 pushes of 16 s = 4096 s of strain
+    p.add_argument("--warmup", type=int, default=16)
     p.add_argument("--impl", default="lloid", choices=["lloid", "reference"])
     p.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
     p.add_argument("--compare", default="fp32,fp16", help="other precisions timed for by_precision ('none': skip)")
@@ -123,7 +123,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None

@@ -176,9 +176,8 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
 // interpolation of the coarser level fused into its epilogue.
 //   D[a][m] = sum_l M[a][l] O[m][l]   (TMEM lanes = filters, columns = time)
 //   y_k[a][m] = D[a][m] + sum_j 2 g[j] y_{k+1}[a][(m - j)/2]
-// The coarser level's row segment (<= 164 samples per filter) is staged in
-// shared memory by one TMA load; each thread interpolates its own row segment
-// from registers.  At the top level the epilogue does not store the SNR: it
+// Each thread owns one filter row: it reads the coarser level's row segment
+// (52 samples per 32 outputs, through L1) and interpolates from registers.  At the top level the epilogue does not store the SNR: it
 // reduces |rho|^2 over its columns into per-window partial maxima.
 // ---------------------------------------------------------------------------
 constexpr int kMixStages = 2;
@@ -187,7 +186,6 @@ constexpr int kMixCols = 256;                            // time samples per til
 constexpr int kMixABytes = kMixRows * 64 * 2;            // mixing tile: 128 filters x 64 l
 constexpr int kMixBBytes = kMixCols * 64 * 2;            // basis-output tile: 256 time x 64 l
 constexpr int kMixStageBytes = kMixABytes + kMixBBytes;
-constexpr int kYsBytes = kYsCols * kMixRows * 4;         // staged coarser level (FP32)
 
 // x[j] += interpolated coarser level at column c0 + j.  w[i] holds the staged
 // coarser sample at register index i; PAR = parity of the first column's
@@ -228,24 +226,23 @@ struct SegBest {
 };
 
 template <bool BF16>
-__global__ void __launch_bounds__(256, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
+__global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
                                                           Halfband g, int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + kMixStages;
     uint64_t *accb = empty + kMixStages;
-    uint64_t *ybar = accb + 1;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(ybar + 1);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
     uint8_t *st = smem + 1024;
-    float *ys = reinterpret_cast<float *>(st + kMixStages * kMixStageBytes);
 
     const TcMixUpTask &t = tasks[find_tile(tasks, n_tasks, blockIdx.x)];
     const int local = blockIdx.x - t.tile_begin;
     const int tt = local / t.tiles_a, at = local % t.tiles_a;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (t.Lk_pad + 63) / 64;
-    // coarser-level staging: first needed position A0 - 16, aligned down to 4 floats (16 B) for TMA
+    // coarser-level window of chunk c0 starts at position A0 - 16 + c0/2 (A0: position of
+    // relative column 0 halved); loads start 16-byte aligned at xs0 + c0/2, REM floats earlier
     const int64_t rel0 = (int64_t)kMixCols * tt - t.lam;
     const int64_t A0 = (rel0 >> 1) + t.in_off;
     const int64_t xs0 = (A0 - 16) & ~int64_t(3);
@@ -262,7 +259,6 @@ __global__ void __launch_bounds__(256, 1) tc_mixup_kernel(const TcMixUpTask *__r
             mbar_init(&empty[s], 1);
         }
         mbar_init(accb, 1);
-        mbar_init(ybar, 1);
         fence_barrier_init();
         fence_proxy_async();
     }
@@ -272,11 +268,6 @@ __global__ void __launch_bounds__(256, 1) tc_mixup_kernel(const TcMixUpTask *__r
     const uint32_t tmem = *tslot;
 
     if (warp == 0 && lane == 0) {
-        if (t.mapYs) {
-            prefetch_tmap(t.mapYs);
-            mbar_expect_tx(ybar, kYsBytes);
-            tma_load_2d(ys, t.mapYs, (int)xs0, at * kMixRows, ybar);
-        }
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % kMixStages;
             if (kc >= kMixStages && !mbar_wait(&empty[s], ((kc / kMixStages) - 1) & 1, err, 5)) break;
@@ -304,73 +295,98 @@ __global__ void __launch_bounds__(256, 1) tc_mixup_kernel(const TcMixUpTask *__r
     __syncwarp();
     bool have = true;
     if (nk > 0) have = mbar_wait(accb, 0, err, 7);
-    if (t.mapYs && have) have = mbar_wait(ybar, 0, err, 8);
     tc_fence_after();
     if (have) {
-        const int q = warp & 3, h = warp >> 2;          // TMEM lane quarter, column half
-        const int R = 32 * q + lane;
+        const int R = warp * 32 + lane;                  // TMEM lane = filter row in the tile
         const int a = kMixRows * at + R;
-        const float *yrow = ys + R * kYsCols;
+        const bool row_ok = a < t.M2;
+        const float *src = t.Ysrc ? t.Ysrc + (int64_t)(row_ok ? a : 0) * t.ld_src : nullptr;
         const bool top = t.part != nullptr;
-        SegBest b0{-1.0f, 0.0f, 0.0f, -1}, b1{-1.0f, 0.0f, 0.0f, -1};
-        const int64_t half_first = t.first_n + (int64_t)kMixCols * tt + 128 * h;   // absolute index
-        const int64_t w_first = top ? (half_first >= 0 ? half_first : 0) / t.win_len : 0;
 #pragma unroll 1
-        for (int c0 = 128 * h; c0 < 128 * h + 128; c0 += 32) {
-            float x[32];
-            if (nk > 0) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + c0, v);
-                tmem_ld_wait();
-#pragma unroll
-                for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) x[j] = 0.0f;
+        for (int h = 0; h < 2; ++h) {
+            SegBest b0{-1.0f, 0.0f, 0.0f, -1}, b1{-1.0f, 0.0f, 0.0f, -1};
+            // top level: columns [vlo, vhi) of this half are real samples (n >= 0, inside the push);
+            // columns >= cb belong to the next window (window length >= 128 columns)
+            int vlo = 0, vhi = 0, cb = 1 << 30;
+            if (top) {
+                const int64_t hcol0 = (int64_t)kMixCols * tt + 128 * h;
+                const int64_t half_first = t.first_n + hcol0;
+                vlo = half_first < 0 ? (int)min((int64_t)128, -half_first) : 0;
+                vhi = (int)min((int64_t)128, (int64_t)t.Bk - hcol0);
+                const int64_t a0 = half_first + vlo;
+                const int64_t wend = (a0 >= 0 ? a0 / t.win_len + 1 : 1) * t.win_len;
+                cb = (int)min((int64_t)(1 << 30), wend - half_first);
             }
-            if (t.mapYs) {
-                float w[52];
-                const float4 *src = reinterpret_cast<const float4 *>(yrow + (c0 >> 1));
+#pragma unroll 1
+            for (int c0 = 128 * h; c0 < 128 * h + 128; c0 += 32) {
+                float x[32];
+                if (nk > 0) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + c0, v);
+                    tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 13; ++i) {
-                    const float4 f = src[i];
-                    w[4 * i] = f.x; w[4 * i + 1] = f.y; w[4 * i + 2] = f.z; w[4 * i + 3] = f.w;
-                }
-                add_interp_dispatch(par * 4 + rem, x, w, g);
-            }
-            const int64_t col0 = (int64_t)kMixCols * tt + c0;
-            const int64_t n0 = t.first_n + col0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (n0 + j < 0) x[j] = 0.0f;                 // every rate starts at index 0
-            if (t.Y && a < t.M2) {
-                float *dst = t.Y + (int64_t)a * t.ldy + col0;
-                if (col0 + 32 <= t.Bk) {
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4)
-                        *reinterpret_cast<float4 *>(dst + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+                    for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (col0 + j < t.Bk) dst[j] = x[j];
+                    for (int j = 0; j < 32; ++j) x[j] = 0.0f;
                 }
-            }
-            if (top) {
+                if (src) {
+                    float w[52];
+                    const int64_t p0 = xs0 + (c0 >> 1);
+                    if (p0 >= 0 && p0 + 52 <= t.n_src) {
+                        const float4 *s4 = reinterpret_cast<const float4 *>(src + p0);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float p = __shfl_xor_sync(0xffffffffu, x[j], 1);   // other phase of the template
-                    const int64_t n = n0 + j;
-                    if (n < 0 || col0 + j >= t.Bk) continue;
-                    const float m2 = fmaf(p, p, x[j] * x[j]);
-                    SegBest &b = (n / t.win_len == w_first) ? b0 : b1;
-                    if (m2 > b.mag2) { b.mag2 = m2; b.re = x[j]; b.im = p; b.n = n; }
+                        for (int i = 0; i < 13; ++i) {
+                            const float4 f = __ldg(s4 + i);
+                            w[4 * i] = f.x; w[4 * i + 1] = f.y; w[4 * i + 2] = f.z; w[4 * i + 3] = f.w;
+                        }
+                    } else {                                    // row edge: positions outside read as 0
+#pragma unroll
+                        for (int i = 0; i < 52; ++i) {
+                            const int64_t p = p0 + i;
+                            w[i] = (p >= 0 && p < t.n_src) ? __ldg(src + p) : 0.0f;
+                        }
+                    }
+                    add_interp_dispatch(par * 4 + rem, x, w, g);
+                }
+                const int64_t col0 = (int64_t)kMixCols * tt + c0;
+                const int64_t n0 = t.first_n + col0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (n0 + j < 0) x[j] = 0.0f;             // every rate starts at index 0
+                if (t.Y && row_ok) {
+                    float *dst = t.Y + (int64_t)a * t.ldy + col0;
+                    if (col0 + 32 <= t.Bk) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            *reinterpret_cast<float4 *>(dst + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (col0 + j < t.Bk) dst[j] = x[j];
+                    }
+                }
+                if (top) {
+                    const int cl = c0 - 128 * h;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float p = __shfl_xor_sync(0xffffffffu, x[j], 1);   // other phase of the template
+                        const int c = cl + j;
+                        if (c < vlo || c >= vhi) continue;
+                        const float m2 = fmaf(p, p, x[j] * x[j]);
+                        if (c < cb) {
+                            if (m2 > b0.mag2) { b0.mag2 = m2; b0.re = x[j]; b0.im = p; b0.n = n0 + j; }
+                        } else {
+                            if (m2 > b1.mag2) { b1.mag2 = m2; b1.re = x[j]; b1.im = p; b1.n = n0 + j; }
+                        }
+                    }
                 }
             }
-        }
-        if (top && (a & 1) == 0 && a < t.M2) {
-            WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (tt * 2 + h) * 2;
-            base[0] = WinPart{b0.mag2, b0.re, b0.im, 0, b0.n};
-            base[1] = WinPart{b1.mag2, b1.re, b1.im, 0, b1.n};
+            if (top && (a & 1) == 0 && row_ok) {
+                WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (tt * 2 + h) * 2;
+                base[0] = WinPart{b0.mag2, b0.re, b0.im, 0, b0.n};
+                base[1] = WinPart{b1.mag2, b1.re, b1.im, 0, b1.n};
+            }
         }
     }
     tc_fence_before();
@@ -385,7 +401,7 @@ __global__ void __launch_bounds__(256, 1) tc_mixup_kernel(const TcMixUpTask *__r
 // launchers
 // ---------------------------------------------------------------------------
 size_t tc_fir_smem_bytes(int kpad_max) { return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * 8 + kpad_max) * 2; }
-size_t tc_mixup_smem_bytes() { return 1024 + 1024 + kMixStages * kMixStageBytes + kYsBytes; }
+size_t tc_mixup_smem_bytes() { return 1024 + 1024 + kMixStages * kMixStageBytes; }
 
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, bool bf16, cudaStream_t s) {
     if (n_tasks == 0) return cudaSuccess;
@@ -420,11 +436,11 @@ cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_t
     if (bf16) {
         e = cudaFuncSetAttribute(tc_mixup_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        tc_mixup_kernel<true><<<total_tiles, 256, smem, s>>>(d_tasks, n_tasks, g, err);
+        tc_mixup_kernel<true><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, g, err);
     } else {
         e = cudaFuncSetAttribute(tc_mixup_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        tc_mixup_kernel<false><<<total_tiles, 256, smem, s>>>(d_tasks, n_tasks, g, err);
+        tc_mixup_kernel<false><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, g, err);
     }
     return cudaGetLastError();
 }

@@ -123,7 +123,6 @@ struct LevelDev {
     float *yuni = nullptr;    // [2M x ldu]
     int64_t ldu = 0;
     float *ytmp = nullptr;    // [2M x Hy] history shift staging
-    CUtensorMap *mapY = nullptr;
 };
 
 struct TriggerSlot {
@@ -469,23 +468,6 @@ static int encode_map(CUtensorMap *out, void *base, bool bf16, uint64_t inner, u
     return SB_OK;
 }
 
-// 2-D FP32 map over a row-major [outer x inner] matrix, no swizzle, box
-// (box_inner x box_outer); out-of-range elements read as 0.
-static int encode_map_f32(CUtensorMap *out, void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                          uint32_t box_outer) {
-    auto encode = tensor_map_encoder();
-    if (!encode) return fail(SB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {inner * 4};
-    cuuint32_t box[2] = {box_inner, box_outer};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(SB_ECUDA, "cuTensorMapEncodeTiled (FP32) failed (" + std::to_string((int)r) + ")");
-    return SB_OK;
-}
-
 static int upload_map(sb_unit *u, const CUtensorMap &h, CUtensorMap **dev) {
     int rc = dev_alloc(u, (void **)dev, sizeof(CUtensorMap));
     if (rc) return rc;
@@ -535,13 +517,6 @@ static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d) {
         if ((rc = upload_map(u, hm, &L.mapM))) return rc;
         if ((rc = encode_map(&ho, L.O16, u->bf16, L.Lk_pad, L.Bk_max + 256, 256))) return rc;
         if ((rc = upload_map(u, ho, &L.mapO))) return rc;
-    }
-    for (auto &L : u->levels) {
-        if (!L.yuni) continue;
-        CUtensorMap hy;
-        int rc;
-        if ((rc = encode_map_f32(&hy, L.yuni, L.ldu, M2, kYsCols, 128))) return rc;
-        if ((rc = upload_map(u, hy, &L.mapY))) return rc;
     }
     return SB_OK;
 }
@@ -1072,7 +1047,12 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     TcMixUpTask mt{};
                     mt.mapM = L.mapM;
                     mt.mapO = L.mapO;
-                    mt.mapYs = k < u->kmax ? u->levels[k + 1].mapY : nullptr;
+                    if (k < u->kmax) {
+                        const LevelDev &N = u->levels[k + 1];
+                        mt.Ysrc = N.yuni;
+                        mt.ld_src = N.ldu;
+                        mt.n_src = N.Hy + (B >> (k + 1));
+                    }
                     mt.Y = k >= 1 ? L.yuni + L.Hy : L.ynew;
                     mt.ldy = k >= 1 ? L.ldu : L.ldy;
                     mt.part = k == 0 ? u->part : nullptr;

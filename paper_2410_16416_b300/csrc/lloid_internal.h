@@ -148,14 +148,13 @@ struct WinPart {
     int64_t n;                 // absolute top-rate sample
 };
 
-constexpr int kYsCols = 164;   // staged coarser-level samples per filter row (row stride 4 mod 32 words)
-
 // a3 + a4 on tensor cores (+ a5 partial maxima at the top level).
 // Tile (tt, at): time columns [256 tt, +256) of this level, filters [128 at, +128).
 struct TcMixUpTask {
     const CUtensorMap *mapM;   // A: mixing [2M x Lk_pad] 16-bit, box 64 x 128 (unused when Lk_pad = 0)
     const CUtensorMap *mapO;   // B: basis outputs [rows x Lk_pad] 16-bit, box 64 x 256
-    const CUtensorMap *mapYs;  // coarser level y_{k+1}, FP32 [2M x ldu], box 164 x 128; null at the deepest level
+    const float *Ysrc;         // coarser level y_{k+1}: row a at Ysrc + a ld_src (n_src columns); null at the deepest level
+    int64_t ld_src, n_src;
     float *Y;                  // this level's first new column (row a at Y + a ldy); null: not stored
     int64_t ldy;
     WinPart *part;             // top level: partials [i][n_rec], record (tt*2 + half)*2 + seg; null below
