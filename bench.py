@@ -295,7 +295,10 @@ def main():
     total_s = (args.warmup + args.steps) * args.push_seconds
     strains = [make_strain(rank, det, total_s, f0, h, spec.n_templates) for det in (0, 1)]
     dev = [torch.from_numpy(s).cuda() for s in strains]
-    stream = torch.cuda.current_stream()
+    # One non-default stream for the library, the L2 flush and the timing events.
+    # (torch's default stream has handle 0, which the C ABI reads as "no stream".)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     n_units = 2
     tpl_s_rank = n_units * spec.n_templates * args.push_seconds * args.steps

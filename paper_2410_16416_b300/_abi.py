@@ -152,8 +152,10 @@ class Context:
     """sb_ctx: one device, one stream, one HBM budget, one trigger queue."""
 
     def __init__(self, device: int = 0, stream=None, hbm_budget_bytes: int = 0):
+        """stream: a cudaStream_t handle (int) the library launches on; None or 0
+        (torch's default stream) makes the library create its own stream."""
         h = C.c_void_p()
-        s = None if stream is None else C.c_void_p(int(stream))
+        s = None if not stream else C.c_void_p(int(stream))
         _check(lib.sb_ctx_create(device, s, int(hbm_budget_bytes), C.byref(h)), "sb_ctx_create")
         self.handle = h
         self.units: List["Unit"] = []
