@@ -188,7 +188,8 @@ int sb_unit_snr(sb_unit *unit, float *host_out, int64_t cap, int64_t *first_samp
 #define SB_STAGE_MIX       5  /* a3: reconstruction (mixing) GEMM                */
 #define SB_STAGE_TRIGGER   6  /* a5: window maxima, threshold, phase             */
 #define SB_STAGE_SNRHIST   7  /* SNR history for the next push's interpolators   */
-#define SB_N_STAGES        8
+#define SB_STAGE_REFINE    8  /* a6: FP32 recomputation of candidate maxima       */
+#define SB_N_STAGES        9
 
 /* Cumulative counters of a context since creation. */
 typedef struct sb_ctx_stats {

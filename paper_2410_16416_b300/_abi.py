@@ -51,7 +51,7 @@ class SbCtxStats(C.Structure):
                 ("d2h_bytes", C.c_int64), ("triggers", C.c_int64)]
 
 
-STAGES = ["history", "strain", "decimate", "fir", "upsample", "mix", "trigger", "snr_history"]
+STAGES = ["history", "strain", "decimate", "fir", "upsample", "mix", "trigger", "snr_history", "refine"]
 
 TRIGGER_DTYPE = np.dtype([("unit", "<i8"), ("template_id", "<i8"), ("sample", "<i8"), ("window", "<i8"),
                           ("snr", "<f4"), ("phase", "<f4"), ("flags", "<i4"), ("reserved", "<i4")])

@@ -1,0 +1,223 @@
+// a6: FP32 refinement of candidate window maxima in the 16-bit modes.
+//
+// After the top level's partial maxima are known, every partial record whose
+// |rho| exceeds the refine threshold is recomputed in FP32: the 256-sample
+// tile it belongs to is re-filtered from the FP32 decimated strain and the
+// FP32 basis (one pass per tile, shared by every template that has a
+// candidate there), then each candidate's two real filters are mixed with the
+// FP32 coefficients, interpolated level by level in FP32, and the record's
+// maximum is taken again over the same samples.  The refined records then go
+// through the usual window bookkeeping and carry SB_TRIG_REFINED.
+//
+// Level ranges of a tile (absolute indices): the top level covers the tile's
+// samples [n_lo, n_hi]; level k+1 needs [ceil((lo_k - 31)/2), floor((hi_k + 31)/2)]
+// for the interpolation into level k.
+#include <algorithm>
+
+#include "lloid_internal.h"
+
+namespace lloid {
+
+__device__ __forceinline__ int64_t floor_div2(int64_t v) { return v >> 1; }
+__device__ __forceinline__ int64_t ceil_div2(int64_t v) { return -((-v) >> 1); }
+
+// level ranges of tile tt of unit u
+__device__ __forceinline__ void tile_ranges(const RefUnit &u, int tt, int64_t *lo, int64_t *hi) {
+    const int64_t c0 = (int64_t)kRefTile * tt;
+    const int64_t c1 = min(c0 + kRefTile, (int64_t)u.B) - 1;
+    lo[0] = u.first_n + c0;
+    hi[0] = u.first_n + c1;
+    for (int k = 0; k < u.kmax; ++k) {
+        lo[k + 1] = ceil_div2(lo[k] - (2 * kHalfK - 1));
+        hi[k + 1] = floor_div2(hi[k] + (2 * kHalfK - 1));
+    }
+}
+
+// R1a: flag tiles that hold a candidate record.
+__global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restrict__ units, int n_units,
+                                                          int *__restrict__ flags) {
+    const RefUnit &u = units[blockIdx.y];
+    const int64_t total = (int64_t)u.M * u.n_rec;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const WinPart p = u.part[idx];
+        if (p.mag2 > u.thr2) flags[u.flag_off + (int)((idx % u.n_rec) / 4)] = 1;
+    }
+}
+
+// R1b: one thread per (unit, tile): flagged tiles get a slot (capacity-limited).
+__global__ void __launch_bounds__(256) refine_slot_kernel(const RefUnit *__restrict__ units, int n_units,
+                                                          int *__restrict__ flags, RefSlot *__restrict__ slots,
+                                                          int *__restrict__ counters, int cap) {
+    const RefUnit &u = units[blockIdx.y];
+    const int tt = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tt >= u.tiles_t) return;
+    int *f = flags + u.flag_off + tt;
+    if (*f == 0) { *f = -1; return; }
+    const int s = atomicAdd(&counters[0], 1);
+    if (s < cap) {
+        slots[s] = RefSlot{(int)blockIdx.y, tt};
+        *f = s;
+    } else {
+        *f = -1;
+        atomicExch(&counters[2], 1);                // not every candidate could be refined
+    }
+}
+
+// R2: FP32 basis outputs of one slot's tile at every level: o[l][m - lo_k].
+// Block (slot, work item = slice x block of 8 basis vectors); threads over m.
+__global__ void __launch_bounds__(256) refine_fir_kernel(const RefUnit *__restrict__ units,
+                                                         const RefSlot *__restrict__ slots,
+                                                         const int *__restrict__ counters, float *__restrict__ obuf,
+                                                         int64_t slot_floats) {
+    const int s = blockIdx.x;
+    if (s >= counters[0] || s >= (int)gridDim.x) return;
+    const RefSlot sl = slots[s];
+    const RefUnit &u = units[sl.unit];
+    int item = blockIdx.y, si = 0;
+    for (; si < u.n_slices; ++si) {
+        const int nb = (u.sl_L[si] + 7) / 8;
+        if (item < nb) break;
+        item -= nb;
+    }
+    if (si >= u.n_slices) return;
+    const int k = u.sl_level[si];
+    int64_t lo[kRefMaxLevels], hi[kRefMaxLevels];
+    tile_ranges(u, sl.tt, lo, hi);
+    const int len = (int)(hi[k] - lo[k] + 1);
+    const int L = u.sl_L[si], Q = u.sl_Q[si];
+    const int l0 = item * 8;
+    const float *V = u.sl_V[si];
+    const float *d = u.lv_d[k];
+    float *o = obuf + (int64_t)s * slot_floats + u.lv_off[k];
+    for (int mi = threadIdx.x; mi < len; mi += blockDim.x) {
+        const int64_t m = lo[k] + mi;
+        // position of d[m - D - q] in the level buffer
+        const int64_t p0 = m - u.sl_D[si] - u.lv_origin[k];
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (m >= 0) {
+            for (int q = 0; q < Q; ++q) {
+                const int64_t p = p0 - q;
+                const float dv = (p >= 0 && p < u.lv_len[k]) ? d[p] : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (l0 + j < L) acc[j] = fmaf(V[(int64_t)(l0 + j) * Q + q], dv, acc[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (l0 + j < L) o[(int64_t)(u.sl_row[si] + l0 + j) * kRefRange(k) + mi] = acc[j];
+    }
+}
+
+// R3: one block per candidate record: FP32 mixing + interpolation of its two
+// real filters over the tile, then the record's maximum is taken again.
+__global__ void __launch_bounds__(128) refine_candidate_kernel(const RefUnit *__restrict__ units, int n_units,
+                                                               const int *__restrict__ flags,
+                                                               const int *__restrict__ counters,
+                                                               const float *__restrict__ obuf, int64_t slot_floats,
+                                                               Halfband g, int cand_cap) {
+    __shared__ float ya[2][kRefRange(0)], yb[2][kRefRange(0)];
+    __shared__ float red_m[128];
+    __shared__ int red_c[128];
+    // candidate = (unit, template, record) enumerated over all records above threshold
+    const int u_idx = blockIdx.y;
+    const RefUnit &u = units[u_idx];
+    const int64_t total = (int64_t)u.M * u.n_rec;
+    for (int64_t idx = blockIdx.x; idx < total; idx += gridDim.x) {
+        WinPart rec = u.part[idx];
+        if (!(rec.mag2 > u.thr2)) continue;
+        const int i = (int)(idx / u.n_rec), r = (int)(idx % u.n_rec);
+        const int tt = r / 4;
+        const int slot = flags[u.flag_off + tt];
+        if (slot < 0) continue;
+        int64_t lo[kRefMaxLevels], hi[kRefMaxLevels];
+        tile_ranges(u, tt, lo, hi);
+        const float *ob = obuf + (int64_t)slot * slot_floats;
+        float(*yc)[kRefRange(0)] = ya;      // level k (being built)
+        float(*yp)[kRefRange(0)] = yb;      // level k+1
+        for (int k = u.kmax; k >= 0; --k) {
+            const int len = (int)(hi[k] - lo[k] + 1);
+            for (int t = threadIdx.x; t < 2 * len; t += blockDim.x) {
+                const int row = t / len, mi = t % len;
+                const int64_t m = lo[k] + mi;
+                float v = 0.0f;
+                if (m >= 0) {
+                    if (k < u.kmax) {           // interpolation from level k+1 (absolute index arithmetic)
+                        const int64_t base = lo[k + 1];
+                        if ((m & 1) == 0) {
+                            v = yp[row][(m >> 1) - base];
+                        } else {
+                            const int64_t mlo = (m - 1) >> 1;
+                            float acc = 0.0f;
+#pragma unroll
+                            for (int q = 0; q < kOddTaps; ++q)
+                                acc = fmaf(2.0f * g.odd[q], yp[row][mlo - q - base] + yp[row][mlo + 1 + q - base], acc);
+                            v = acc;
+                        }
+                    }
+                    const int Lk = u.lv_Lk[k];
+                    if (Lk > 0) {
+                        const float *Mrow = u.lv_M[k] + (int64_t)(2 * i + row) * Lk;
+                        const float *o = ob + u.lv_off[k] + mi;
+                        float c = 0.0f;
+                        for (int l = 0; l < Lk; ++l) c = fmaf(Mrow[l], o[(int64_t)l * kRefRange(k)], c);
+                        v += c;
+                    }
+                }
+                yc[row][mi] = v;
+            }
+            __syncthreads();
+            float(*tmp)[kRefRange(0)] = yc;
+            yc = yp;
+            yp = tmp;
+        }
+        // yp holds level 0 over [lo[0], hi[0]]; the record covers one half and one window
+        const int h = (r / 2) % 2;
+        const int64_t w = rec.n / u.win_len;
+        const int c_lo = 128 * h, c_hi = min(c_lo + 128, (int)(hi[0] - lo[0] + 1));
+        float best = -1.0f;
+        int bc = -1;
+        for (int c = c_lo + threadIdx.x; c < c_hi; c += blockDim.x) {
+            const int64_t n = lo[0] + c;
+            if (n < 0 || n / u.win_len != w) continue;
+            const float m2 = fmaf(yp[1][c], yp[1][c], yp[0][c] * yp[0][c]);
+            if (m2 > best) { best = m2; bc = c; }
+        }
+        red_m[threadIdx.x] = best;
+        red_c[threadIdx.x] = bc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int t = 1; t < blockDim.x; ++t)
+                if (red_m[t] > best || (red_m[t] == best && red_c[t] >= 0 && (bc < 0 || red_c[t] < bc))) {
+                    best = red_m[t];
+                    bc = red_c[t];
+                }
+            if (bc >= 0) {
+                rec.mag2 = best;
+                rec.re = yp[0][bc];
+                rec.im = yp[1][bc];
+                rec.n = lo[0] + bc;
+                rec.flags = SB_TRIG_REFINED_BIT;
+                u.part[idx] = rec;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_refine(const RefUnit *d_units, int n_units, int max_tiles, int64_t max_records, int *flags,
+                          RefSlot *slots, int *counters, int cap, float *obuf, int64_t slot_floats,
+                          int max_items, const Halfband &g, cudaStream_t s) {
+    if (n_units == 0) return cudaSuccess;
+    const int fb = (int)std::min<int64_t>(1024, (max_records + 255) / 256);
+    refine_flag_kernel<<<dim3(fb, n_units), 256, 0, s>>>(d_units, n_units, flags);
+    refine_slot_kernel<<<dim3((max_tiles + 255) / 256, n_units), 256, 0, s>>>(d_units, n_units, flags, slots,
+                                                                               counters, cap);
+    refine_fir_kernel<<<dim3(cap, max_items), 256, 0, s>>>(d_units, slots, counters, obuf, slot_floats);
+    refine_candidate_kernel<<<dim3(148, n_units), 128, 0, s>>>(d_units, n_units, flags, counters, obuf,
+                                                               slot_floats, g, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace lloid

@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
         WinState ns;
         if (complete) { ns.mag2 = -1.0f; ns.re = ns.im = 0.0f; ns.n = -1; }
         else { ns.mag2 = best; ns.re = re; ns.im = im; ns.n = bn; }
+        ns.flags = 0;
         t.state_out[i] = ns;
     }
 }
@@ -282,10 +283,13 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
     const WinPart *rec = t.part + (int64_t)i * t.n_rec;
     float best = -1.0f, re = 0.0f, im = 0.0f;
     int64_t bn = INT64_MAX;
+    int fl = 0;
     for (int r = r0 + lane; r < r1; r += 32) {
         const WinPart p = rec[r];
         if (p.mag2 < 0.0f || p.n / t.win_len != w) continue;
-        if (p.mag2 > best || (p.mag2 == best && p.n < bn)) { best = p.mag2; bn = p.n; re = p.re; im = p.im; }
+        if (p.mag2 > best || (p.mag2 == best && p.n < bn)) {
+            best = p.mag2; bn = p.n; re = p.re; im = p.im; fl = p.flags;
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -293,12 +297,15 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
         const int64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
         const float ore = __shfl_xor_sync(0xffffffffu, re, off);
         const float oim = __shfl_xor_sync(0xffffffffu, im, off);
-        if (ob > best || (ob == best && on < bn)) { best = ob; bn = on; re = ore; im = oim; }
+        const int ofl = __shfl_xor_sync(0xffffffffu, fl, off);
+        if (ob > best || (ob == best && on < bn)) { best = ob; bn = on; re = ore; im = oim; fl = ofl; }
     }
     if (lane != 0) return;
     if (s == 0) {                          // the window left open by the previous push (earlier samples)
         const WinState st = t.state_in[i];
-        if (st.mag2 >= 0.0f && !(best > st.mag2)) { best = st.mag2; bn = st.n; re = st.re; im = st.im; }
+        if (st.mag2 >= 0.0f && !(best > st.mag2)) {
+            best = st.mag2; bn = st.n; re = st.re; im = st.im; fl = st.flags;
+        }
     }
     const bool complete = (w + 1) * t.win_len <= t.end_abs;
     if (complete && bn != INT64_MAX && sqrtf(best) > t.threshold) {
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
             r.window = w;
             r.snr = sqrtf(best);
             r.phase = atan2f(im, re);
-            r.flags = 0;
+            r.flags = fl;
             r.reserved = 0;
             out.buf[slot] = r;
         } else {
@@ -320,8 +327,8 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
     }
     if (s == t.n_win - 1) {
         WinState ns;
-        if (complete || bn == INT64_MAX) { ns.mag2 = -1.0f; ns.re = ns.im = 0.0f; ns.n = -1; }
-        else { ns.mag2 = best; ns.re = re; ns.im = im; ns.n = bn; }
+        if (complete || bn == INT64_MAX) { ns.mag2 = -1.0f; ns.re = ns.im = 0.0f; ns.n = -1; ns.flags = 0; }
+        else { ns.mag2 = best; ns.re = re; ns.im = im; ns.n = bn; ns.flags = fl; }
         t.state_out[i] = ns;
     }
 }

@@ -198,10 +198,11 @@ __device__ __forceinline__ void add_interp(float (&x)[32], const float (&w)[52],
         if (((j + PAR) & 1) == 0) {
             x[j] += w[base];
         } else {
-            float v = 0.0f;
+            float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};      // four independent chains
 #pragma unroll
-            for (int t = 0; t < kOddTaps; ++t) v = fmaf(2.0f * g.odd[t], w[base - t] + w[base + 1 + t], v);
-            x[j] += v;
+            for (int t = 0; t < kOddTaps; ++t)
+                v[t & 3] = fmaf(2.0f * g.odd[t], w[base - t] + w[base + 1 + t], v[t & 3]);
+            x[j] += (v[0] + v[1]) + (v[2] + v[3]);
         }
     }
 }

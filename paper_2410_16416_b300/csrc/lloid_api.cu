@@ -163,6 +163,13 @@ struct sb_ctx {
     int timeout_code = 0;      // first bounded device wait that expired (0: none)
     std::mutex mu;
     sb_ctx_stats stats{};
+    // FP32 refinement scratch (grown on demand, shared by the pushes of this context)
+    int *ref_flags = nullptr;
+    int64_t ref_flags_cap = 0;
+    RefSlot *ref_slots = nullptr;
+    int *ref_counters = nullptr;
+    float *ref_obuf = nullptr;
+    int64_t ref_slot_floats = 0;
     // profiling: event pairs around each launch, summed per stage on query
     bool prof = false;
     struct Mark { int stage; cudaEvent_t a, b; };
@@ -176,6 +183,7 @@ struct sb_unit {
     int32_t detector = 0;
     int M = 0, precision = 0, flags = 0;
     bool tc = false, bf16 = false;
+    bool refine = false;           // 16-bit modes with a refine threshold: FP32 copies kept for a6
     float thr = 0.f, refine_thr = 0.f;
     double f0 = 0.0;
     int64_t win_len = 0;
@@ -282,7 +290,8 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
         for (int s = 0; s < S; ++s) {
             if (levels_of_slice[s] != k) continue;
             const int64_t D = std::llround(d->slices[s].t_start_s * d->slices[s].rate_hz);
-            hd = std::max(hd, P.lam[k] - P.e[k] + D + d->slices[s].n_taps - 1);
+            // 16-bit modes: 128 extra samples for the FP32 refinement's halo below the push
+            hd = std::max(hd, P.lam[k] - P.e[k] + D + d->slices[s].n_taps - 1 + (is_tc(d->precision) ? 128 : 0));
         }
         P.Hd[k] = round_up(std::max<int64_t>(hd, 1), 32);
         if (k >= 1) P.Hy[k] = round_up((P.lam[k - 1] + 2 * kHalfK) / 2 + 1 - P.lam[k], 4);
@@ -335,6 +344,9 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
         b += P.tc ? 8 * P.L16[s] * P.Kpad[s] * 2 + 128 : (int64_t)d->slices[s].n_basis * d->slices[s].n_taps * 4;
     b += 2 * (int64_t)d->n_templates * sizeof(WinState) + d->n_templates * 8;
     if (P.tc) b += ((d->max_push_samples + 255) / 256) * 4 * (int64_t)d->n_templates * sizeof(WinPart);
+    if (P.tc && d->refine_threshold > 0.0f)            // FP32 basis and mixing for the refinement
+        for (int s = 0; s < S; ++s)
+            b += (int64_t)d->slices[s].n_basis * (d->slices[s].n_taps + M2) * 4;
     P.bytes = b;
     return SB_OK;
 }
@@ -407,6 +419,10 @@ extern "C" int sb_ctx_destroy(sb_ctx *c) {
     }
     release_marks(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->ref_flags) cudaFree(c->ref_flags);
+    if (c->ref_slots) cudaFree(c->ref_slots);
+    if (c->ref_counters) cudaFree(c->ref_counters);
+    if (c->ref_obuf) cudaFree(c->ref_obuf);
     if (c->pop_stream) cudaStreamDestroy(c->pop_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -535,6 +551,9 @@ static int validate_desc(const sb_desc *d, std::vector<int> &lvl, Plan &P) {
     if (rc) return rc;
     if (P.tc && std::llround(wl) < 128)
         return fail(SB_EINVAL, "tensor-core modes need window_s * top_rate_hz >= 128");
+    if (P.tc && d->refine_threshold > 0.0f && (P.kmax >= kRefMaxLevels || d->n_slices > kRefMaxSlices))
+        return fail(SB_EINVAL, "refinement supports at most " + std::to_string(kRefMaxLevels) + " levels and " +
+                                   std::to_string(kRefMaxSlices) + " slices");
     if (d->max_push_samples % (1LL << P.kmax))
         return fail(SB_EINVAL, "max_push_samples must be a multiple of 2^k_max");
     return SB_OK;
@@ -589,6 +608,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
     u->precision = d->precision;
     u->tc = is_tc(d->precision);
     u->bf16 = d->precision == SB_BF16;
+    u->refine = u->tc && d->refine_threshold > 0.0f;
     u->flags = d->flags;
     u->thr = d->threshold;
     u->refine_thr = d->refine_threshold;
@@ -639,8 +659,10 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         } else if (u->flags & SB_FLAG_KEEP_SNR) {
             if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return cleanup(rc);
         }
-        if (L.Lk > 0 && !u->tc) {
+        if (L.Lk > 0 && (!u->tc || u->refine)) {
             if ((rc = dev_alloc(u, (void **)&L.Mcat, M2 * L.Lk * 4))) return cleanup(rc);
+        }
+        if (L.Lk > 0 && !u->tc) {
             if ((rc = dev_alloc(u, (void **)&L.obuf, (int64_t)L.Lk * L.Bk_max * 4))) return cleanup(rc);
         }
         if (u->tc) {
@@ -670,7 +692,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         sd.D = std::llround(sl.t_start_s * sl.rate_hz);
         sd.o_row = row_of_level[sd.level];
         row_of_level[sd.level] += sd.L;
-        if (!u->tc) {
+        if (!u->tc || u->refine) {
             std::vector<float> v((size_t)sd.L * sd.Q);
             for (size_t i = 0; i < v.size(); ++i) v[i] = (float)sl.basis[i];
             if ((rc = dev_alloc(u, (void **)&sd.V, v.size() * 4))) return cleanup(rc);
@@ -679,7 +701,8 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
             const int Lk = u->levels[sd.level].Lk;
             for (int64_t a = 0; a < M2; ++a)
                 for (int l = 0; l < sd.L; ++l) mcat[sd.level][a * Lk + sd.o_row + l] = (float)sl.mixing[a * sd.L + l];
-        } else {
+        }
+        if (u->tc) {
             sd.L16 = (int)P.L16[s];
             sd.Kpad = (int)P.Kpad[s];
             sd.o_col16 = (int)P.o_col16[s];
@@ -690,7 +713,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         u->levels[sd.level].slices.push_back(s);
         u->slices.push_back(sd);
     }
-    for (int k = 0; k <= P.kmax && !u->tc; ++k) {
+    for (int k = 0; k <= P.kmax && (!u->tc || u->refine); ++k) {
         LevelDev &L = u->levels[k];
         if (L.Lk == 0) continue;
         if (cudaMemcpy(L.Mcat, mcat[k].data(), mcat[k].size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -703,7 +726,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
     }
     // trigger state and template ids
     std::vector<WinState> ws(u->M);
-    for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = 0.0f; w.n = -1; }
+    for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = 0.0f; w.flags = 0; w.n = -1; }
     for (int b = 0; b < 2; ++b) {
         if ((rc = dev_alloc(u, (void **)&u->wstate[b], u->M * sizeof(WinState)))) return cleanup(rc);
         if (cudaMemcpy(u->wstate[b], ws.data(), u->M * sizeof(WinState), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -992,6 +1015,9 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     std::vector<std::vector<TcMixUpTask>> tmix[2] = {std::vector<std::vector<TcMixUpTask>>(kall + 1),
                                                      std::vector<std::vector<TcMixUpTask>>(kall + 1)};
     std::vector<WinFinTask> wfin;
+    std::vector<RefUnit> refu;
+    int64_t ref_flag_total = 0, ref_slot_floats = 0, ref_max_records = 0;
+    int ref_max_tiles = 0, ref_max_items = 0;
     std::vector<CopyTask> yshift1, yshift2;
     int kpad_max[2] = {0, 0};
     int max_hd = 0, max_hy = 0, max_rows = 0;
@@ -1161,6 +1187,48 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         LevelDev &L0 = u->levels[0];
         const int64_t first_n = Tp - L0.lam;
         const int64_t start = std::max<int64_t>(first_n, 0), end = first_n + B;
+        if (end > start && u->refine) {
+            RefUnit r{};
+            r.part = u->part;
+            r.first_n = first_n;
+            r.win_len = u->win_len;
+            r.thr2 = u->refine_thr * u->refine_thr;
+            r.kmax = u->kmax;
+            r.M = u->M;
+            r.tiles_t = (int32_t)((B + kRefTile - 1) / kRefTile);
+            r.n_rec = r.tiles_t * 4;
+            r.B = (int32_t)B;
+            r.flag_off = (int32_t)ref_flag_total;
+            r.n_slices = (int32_t)u->slices.size();
+            int64_t off = 0;
+            for (int k = 0; k <= u->kmax; ++k) {
+                LevelDev &L = u->levels[k];
+                r.lv_d[k] = L.dbuf[1 - L.dcur];
+                r.lv_origin[k] = (Tp >> k) - L.e - L.Hd;
+                r.lv_len[k] = L.Hd + (B >> k);
+                r.lv_M[k] = L.Mcat;
+                r.lv_Lk[k] = L.Lk;
+                r.lv_off[k] = off;
+                off += (int64_t)L.Lk * kRefRange(k);
+            }
+            int items = 0;
+            for (size_t si = 0; si < u->slices.size(); ++si) {
+                const SliceDev &sd = u->slices[si];
+                r.sl_V[si] = sd.V;
+                r.sl_D[si] = sd.D;
+                r.sl_L[si] = sd.L;
+                r.sl_Q[si] = sd.Q;
+                r.sl_row[si] = sd.o_row;
+                r.sl_level[si] = sd.level;
+                items += (sd.L + 7) / 8;
+            }
+            ref_flag_total += r.tiles_t;
+            ref_slot_floats = std::max(ref_slot_floats, off);
+            ref_max_records = std::max<int64_t>(ref_max_records, (int64_t)r.M * r.n_rec);
+            ref_max_tiles = std::max(ref_max_tiles, (int)r.tiles_t);
+            ref_max_items = std::max(ref_max_items, items);
+            refu.push_back(r);
+        }
         if (end > start && u->tc) {
             WinFinTask w{};
             w.part = u->part;
@@ -1255,6 +1323,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     }
     const size_t o_ycopy = pk.add(ycopy.data(), ycopy.size() * sizeof(CopyTask));
     const size_t o_wfin = pk.add(wfin.data(), wfin.size() * sizeof(WinFinTask));
+    const size_t o_refu = pk.add(refu.data(), refu.size() * sizeof(RefUnit));
     const size_t o_ys1 = pk.add(yshift1.data(), yshift1.size() * sizeof(CopyTask));
     const size_t o_ys2 = pk.add(yshift2.data(), yshift2.size() * sizeof(CopyTask));
     std::vector<size_t> o_strain(n_units, 0);
@@ -1343,6 +1412,32 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                                             tmix_tiles[h][k], c->g, h == 1, derr, st);
                  })))
                 return rc;
+    }
+    // a6: FP32 refinement of the top level's candidate maxima (16-bit modes)
+    if (!refu.empty()) {
+        constexpr int kRefCap = 64;
+        if (c->ref_flags_cap < ref_flag_total || c->ref_slot_floats < ref_slot_floats || !c->ref_counters) {
+            CK(cudaStreamSynchronize(st));
+            if (c->ref_flags) cudaFree(c->ref_flags);
+            if (c->ref_obuf) cudaFree(c->ref_obuf);
+            c->ref_flags = nullptr;
+            c->ref_obuf = nullptr;
+            c->ref_flags_cap = std::max(ref_flag_total, 2 * c->ref_flags_cap);
+            c->ref_slot_floats = std::max(ref_slot_floats, c->ref_slot_floats);
+            CK(cudaMalloc(&c->ref_flags, c->ref_flags_cap * sizeof(int)));
+            CK(cudaMalloc(&c->ref_obuf, (size_t)kRefCap * c->ref_slot_floats * sizeof(float)));
+            if (!c->ref_slots) CK(cudaMalloc(&c->ref_slots, kRefCap * sizeof(RefSlot)));
+            if (!c->ref_counters) CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
+        }
+        CK(cudaMemsetAsync(c->ref_flags, 0, ref_flag_total * sizeof(int), st));
+        CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
+        if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
+                 *n = 4;
+                 return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_tiles, ref_max_records,
+                                      c->ref_flags, c->ref_slots, c->ref_counters, kRefCap, c->ref_obuf,
+                                      c->ref_slot_floats, std::max(1, ref_max_items), c->g, st);
+             })))
+            return rc;
     }
     // 6. a5 trigger generator
     TrigOut to{slot->dbuf, slot->dcount, (int32_t)slot->cap};

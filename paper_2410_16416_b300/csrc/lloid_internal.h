@@ -82,8 +82,10 @@ struct GemmTask {
 struct WinState {        // running maximum of one template in its open window
     float mag2;          // |rho|^2 (-1: empty)
     float re, im;
+    int32_t flags;       // SB_TRIG_* bits of the maximum
     int64_t n;
 };
+constexpr int32_t SB_TRIG_REFINED_BIT = 1;
 
 struct DevTrigger {      // layout-identical to sb_trigger
     int64_t unit, template_id, sample, window;
@@ -144,7 +146,7 @@ struct TcFirTask {
 struct WinPart {
     float mag2;                // |rho|^2 (-1: no valid sample)
     float re, im;
-    int32_t pad;
+    int32_t flags;             // SB_TRIG_* bits (refined)
     int64_t n;                 // absolute top-rate sample
 };
 
@@ -194,6 +196,34 @@ cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_t
                             int *err, cudaStream_t s);
 cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                                 cudaStream_t s);
+
+// ---- FP32 refinement of candidate maxima (kernels_refine.cu) ----------------
+constexpr int kRefTile = 256;            // top-level samples per refinement tile (= mixing tile)
+constexpr int kRefMaxLevels = 8;
+constexpr int kRefMaxSlices = 12;
+__host__ __device__ constexpr int kRefRange(int k) { return (kRefTile >> k) + 66; }   // samples of a tile at level k
+
+struct RefUnit {                         // one unit of a push with refinement on
+    WinPart *part;                       // [M][n_rec] top-level partial maxima (refined in place)
+    int64_t first_n;                     // absolute top-level index of push column 0
+    int64_t win_len;
+    float thr2;                          // refine threshold squared
+    int32_t kmax, M, n_rec, tiles_t, B, flag_off, n_slices, pad;
+    const float *lv_d[kRefMaxLevels];    // FP32 decimated strain of this push, position 0 = absolute lv_origin
+    int64_t lv_origin[kRefMaxLevels], lv_len[kRefMaxLevels];
+    const float *lv_M[kRefMaxLevels];    // FP32 stacked mixing [2M][Lk]
+    int32_t lv_Lk[kRefMaxLevels];
+    int64_t lv_off[kRefMaxLevels];       // float offset of level k's [Lk][kRefRange(k)] block in a slot
+    const float *sl_V[kRefMaxSlices];    // FP32 basis [L][Q]
+    int64_t sl_D[kRefMaxSlices];
+    int32_t sl_L[kRefMaxSlices], sl_Q[kRefMaxSlices], sl_row[kRefMaxSlices], sl_level[kRefMaxSlices];
+};
+struct RefSlot {
+    int32_t unit, tt;
+};
+cudaError_t launch_refine(const RefUnit *d_units, int n_units, int max_tiles, int64_t max_records, int *flags,
+                          RefSlot *slots, int *counters, int cap, float *obuf, int64_t slot_floats,
+                          int max_items, const Halfband &g, cudaStream_t s);
 
 // ---- launchers (kernels_simt.cu) -------------------------------------------
 cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,

@@ -265,3 +265,50 @@ def test_half_production_bin_sampled_templates(lloid, precision):
     assert err <= TOL_HALF
     hit = trig[(trig["template_id"] == 500) & (trig["window"] == 80)]
     assert len(hit) == 1 and abs(hit["snr"][0] - 30.0) < 1.5
+
+
+# ---------------------------------------------------------------- a6 FP32 refinement
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_refined_window_maxima_match_oracle(lloid, small_case, precision):
+    """Window maxima above the refine threshold are recomputed in FP32: every
+    trigger (threshold 6 > refine 5.5) is flagged refined and equals the FP64
+    oracle's window maximum to FP32 accuracy."""
+    spec, h, bank, d, x = small_case
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, precision=precision, threshold=6.0, refine_threshold=5.5, max_push_samples=4096)
+    for t in range(0, d.shape[0], 4096):
+        u.push(d[t:t + 4096], t)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    n_valid = d.shape[0] - u.info().latency_samples
+    assert len(trig) >= 1 and np.all(trig["flags"] & lloid.SB_TRIG_REFINED)
+    assert check_triggers(trig, x, 2048, 6.0, n_valid, 2 * TOL_FP32) >= 1
+    ctx.close()
+
+
+def test_refined_production_injection(lloid):
+    """Production bin, BF16: the SNR-30 injection's trigger after refinement is within 1e-3 of the oracle."""
+    spec = synth.PRODUCTION_BIN
+    h, _ = synth.template_bank(spec.n_templates, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 2, 0, 0)
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    n = 96 * 4096
+    d = synth.white_noise(n, 2, 0, 1)
+    synth.inject(d, h, 500, 80 * 4096 + 99, 30.0, -0.8)
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, precision="bf16", threshold=6.0, refine_threshold=5.5, max_push_samples=16 * 4096)
+    for t in range(0, n, 16 * 4096):
+        u.push(d[t:t + 16 * 4096], t)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    ctx.close()
+    hit = trig[(trig["template_id"] == 500) & (trig["window"] == 80)]
+    assert len(hit) == 1 and hit["flags"][0] & lloid.SB_TRIG_REFINED
+    rows = np.array([1000, 1001])
+    sub = oracle.OracleBank(1, bank.top_rate_hz,
+                            [oracle.OracleSlice(s.rate_hz, s.t_start_s, s.t_end_s, s.level, s.delay, s.basis,
+                                                s.mixing[rows], s.sigma) for s in bank.slices])
+    xo = oracle.lloid_snr(sub, d)
+    wins, n_star, amax, ph = oracle.window_maxima(xo, 4096, 81 * 4096, 80 * 4096)
+    print("refined", hit["snr"][0], "oracle", amax[0, 0], "samples", hit["sample"][0], n_star[0, 0])
+    assert abs(hit["snr"][0] - amax[0, 0]) <= 1e-3
+    assert hit["sample"][0] == n_star[0, 0]
