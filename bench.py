@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--templates", type=int, default=1000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=8.0, help="strain seconds per oracle worker")
+    p.add_argument("--workload", default="production", choices=["production", "batch"],
+                   help="production: one 1000-template bin x 2 detectors; batch: --bins uneven bins x 2 detectors")
+    p.add_argument("--bins", type=int, default=200)
     return p.parse_args()
 
 
@@ -288,28 +291,45 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    spec, h = production_bank_templates(rank, args.templates)
-    bank = lloid.decompose(h, spec.top_rate_hz, spec.slices)
-    f0 = int(spec.top_rate_hz)
+    if args.workload == "production":
+        spec, h = production_bank_templates(rank, args.templates)
+        bank = lloid.decompose(h, spec.top_rate_hz, spec.slices)
+        banks = [bank]
+        f0 = int(spec.top_rate_hz)
+    else:                       # uneven shape-only bins; rank r takes bins r, r + world, ...
+        banks = [synth.shape_only_bank(b) for b in range(rank, args.bins, world)]
+        spec, h, bank = None, None, banks[0]
+        f0 = int(banks[0].top_rate_hz)
     B = args.push_seconds * f0
     total_s = (args.warmup + args.steps) * args.push_seconds
-    strains = [make_strain(rank, det, total_s, f0, h, spec.n_templates) for det in (0, 1)]
+    if spec is not None:
+        strains = [make_strain(rank, det, total_s, f0, h, spec.n_templates) for det in (0, 1)]
+    else:                       # every bank of a detector filters that detector's strain
+        strains = [synth.white_noise(int(total_s * f0), 3, rank, det) for det in (0, 1)]
     dev = [torch.from_numpy(s).cuda() for s in strains]
+    unit_specs = [(b, det) for b in banks for det in (0, 1)]
+    n_templates_all = sum(b.n_templates for b, _ in unit_specs)
     # One non-default stream for the library, the L2 flush and the timing events.
     # (torch's default stream has handle 0, which the C ABI reads as "no stream".)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    n_units = 2
-    tpl_s_rank = n_units * spec.n_templates * args.push_seconds * args.steps
+    n_units = len(unit_specs)
+    tpl_s_rank = n_templates_all * args.push_seconds * args.steps
+
+    def make_units(ctx, precision):
+        return [ctx.create_unit(b, detector=det, precision=precision, threshold=6.0, refine_threshold=5.5,
+                                window_s=1.0, max_push_samples=B) for b, det in unit_specs]
 
     def device_arm(precision):
         ctx = lloid.Context(local, stream=stream.cuda_stream)
-        units = [ctx.create_unit(bank, detector=det, precision=precision, threshold=6.0, refine_threshold=5.5,
-                                 window_s=1.0, max_push_samples=B) for det in range(n_units)]
+        tc0 = time.perf_counter()
+        units = make_units(ctx, precision)
+        create_s = time.perf_counter() - tc0
+        dets = [det for _, det in unit_specs]
         t = 0
         for _ in range(args.warmup):
-            ctx.push_group(units, [d[t:t + B] for d in dev], [t, t], True)
+            ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
             t += B
         ctx.pop_triggers()
         barrier()
@@ -324,7 +344,7 @@ def main():
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            ctx.push_group(units, [d[t:t + B] for d in dev], [t, t], True)
+            ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
             ev[i][1].record(stream)
             t += B
         barrier()
@@ -340,7 +360,7 @@ def main():
             dev_s = float(tt.item())
         trig = ctx.pop_triggers()
         ctx.close()
-        return {"value": world * tpl_s_rank / dev_s, "dev_s": dev_s, "wall": wall, "clocks": clk,
+        return {"value": world * tpl_s_rank / dev_s, "dev_s": dev_s, "wall": wall, "clocks": clk, "create_s": create_s,
                 "stages": stages, "launches": st1["kernel_launches"] - st0["kernel_launches"],
                 "triggers": int(len(trig))}
 
@@ -353,18 +373,18 @@ def main():
 
     # e2e: host strain in, triggers out, through the C ABI
     ctx2 = lloid.Context(local, stream=stream.cuda_stream)
-    u2 = [ctx2.create_unit(bank, detector=det, precision=args.precision, threshold=6.0, refine_threshold=5.5,
-                           window_s=1.0, max_push_samples=B) for det in range(n_units)]
+    u2 = make_units(ctx2, args.precision)
+    dets = [det for _, det in unit_specs]
     t2 = 0
     for _ in range(args.warmup):
-        ctx2.push_group(u2, [s[t2:t2 + B] for s in strains], [t2, t2], False)
+        ctx2.push_group(u2, [strains[det][t2:t2 + B] for det in dets], [t2] * n_units, False)
         ctx2.pop_triggers()
         t2 += B
     barrier()
     s0 = ctx2.stats()
     w1 = time.perf_counter()
     for i in range(args.steps):
-        ctx2.push_group(u2, [s[t2:t2 + B] for s in strains], [t2, t2], False)
+        ctx2.push_group(u2, [strains[det][t2:t2 + B] for det in dets], [t2] * n_units, False)
         ctx2.pop_triggers()
         t2 += B
     ctx2.sync()
@@ -385,7 +405,12 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    flops, bytes_ = algorithmic_model(bank, n_units, args.push_seconds, args.precision)
+    flops, bytes_ = {}, {}
+    for b, _ in unit_specs:
+        f1, b1 = algorithmic_model(b, 1, args.push_seconds, args.precision)
+        for k in f1:
+            flops[k] = flops.get(k, 0.0) + f1[k]
+            bytes_[k] = bytes_.get(k, 0.0) + b1[k]
     dom, roof = roofline_of(prim["stages"], flops, bytes_, args.precision, args.steps, peaks)
     busy = {k: v[0] for k, v in prim["stages"].items() if v[1] > 0}
     total_stage_ms = sum(busy.values())
@@ -394,9 +419,13 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision],
             "data": "synthetic (seeded white noise, random-parameter Newtonian chirp bank, injections)",
-            "config": {"workload": f"production bin: {spec.n_templates} templates x 2 detectors, 6 slices "
-                                   f"4096-128 Hz, L={bank.basis_counts()}, {args.push_seconds} s pushes",
-                       "templates": spec.n_templates, "units_per_gpu": n_units,
+            "config": {"workload": (f"production bin: {spec.n_templates} templates x 2 detectors, 6 slices "
+                                    f"4096-128 Hz, L={bank.basis_counts()}, {args.push_seconds} s pushes")
+                       if spec is not None else
+                       (f"batch: {len(banks)} uneven SVD bins x 2 detectors ({n_units} units, "
+                        f"{n_templates_all} templates; M logU[200,2000], 3-8 slices, 2-120 s templates, "
+                        f"L logU[50,600]), one grouped push per step, {args.push_seconds} s pushes"),
+                       "templates": n_templates_all, "units_per_gpu": n_units, "setup_s": prim["create_s"],
                        "push_seconds": args.push_seconds, "precision": args.precision,
                        "parallelism": f"units sharded, {world} GPU(s)",
                        "l2": "flushed between steps (256 MB write outside the step events)"},
@@ -410,7 +439,7 @@ def main():
         ref = line["by_precision"]["fp32"]["value"]
         for p in line["by_precision"]:
             line["by_precision"][p]["gain_vs_fp32"] = line["by_precision"][p]["value"] / ref
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and spec is not None:
         line["cpu_baseline"] = cpu_baseline(h, spec, args.cpu_seconds, max(1, min(os.cpu_count() or 1, 16)))
     if rank == 0:
         print(json.dumps(line), flush=True)

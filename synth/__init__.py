@@ -206,7 +206,8 @@ def shape_only_bank(bin_index: int, top_rate_hz: float = 4096.0,
     M ~ logU[200, 2000], S ~ U{3..8} slices at rates top/2^s, durations
     ~ logU[2, 120] s, slice boundaries t_s = T (s/S)^2 rounded to 1/f_s,
     L_s ~ logU[50, 600] capped at min(2M, Q_s).  Basis rows are orthonormal
-    (QR of a Gaussian); mixing rows are Gaussian, rescaled so that the summed
+    (randomly chosen, randomly signed DCT-II basis vectors); mixing rows are
+    Gaussian, rescaled so that the summed
     white-noise variance of every real filter, sum_s 2^-k_s |M_s[a,:]|^2, is 1.
     """
     g = rng(KIND_SHAPE, bin_index)
@@ -234,9 +235,13 @@ def shape_only_bank(bin_index: int, top_rate_hz: float = 4096.0,
         Q = int(round((bounds[s + 1] - bounds[s]) * f_s))
         L = int(round(math.exp(g.uniform(math.log(l_range[0]), math.log(l_range[1])))))
         L = max(1, min(L, 2 * M, Q))
-        Z = g.standard_normal((Q, L))
-        q, _ = np.linalg.qr(Z)                 # [Q, L] orthonormal columns
-        V = np.ascontiguousarray(q.T)          # [L, Q] orthonormal rows
+        # L distinct DCT-II basis vectors of length Q with random signs: orthonormal rows
+        freq = np.sort(g.choice(Q, size=L, replace=False))
+        sign = np.where(g.random(L) < 0.5, -1.0, 1.0)
+        qq = np.arange(Q) + 0.5
+        V = np.cos(np.pi * freq[:, None] * qq[None, :] / Q) * np.sqrt(2.0 / Q)
+        V[freq == 0] *= np.sqrt(0.5)
+        V *= sign[:, None]
         Mx = g.standard_normal((2 * M, L))
         weight += (Mx ** 2).sum(axis=1) * 2.0 ** (-s)
         raw.append((f_s, bounds[s], bounds[s + 1], V, Mx))
