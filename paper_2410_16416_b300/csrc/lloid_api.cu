@@ -1220,7 +1220,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 r.sl_Q[si] = sd.Q;
                 r.sl_row[si] = sd.o_row;
                 r.sl_level[si] = sd.level;
-                items += (sd.L + 7) / 8;
+                items += ((sd.L + kGemmTM - 1) / kGemmTM) * ((kRefRange(sd.level) + kGemmTN - 1) / kGemmTN);
             }
             ref_flag_total += r.tiles_t;
             ref_slot_floats = std::max(ref_slot_floats, off);
@@ -1424,18 +1424,20 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             c->ref_obuf = nullptr;
             c->ref_flags_cap = std::max(ref_flag_total, 2 * c->ref_flags_cap);
             c->ref_slot_floats = std::max(ref_slot_floats, c->ref_slot_floats);
-            CK(cudaMalloc(&c->ref_flags, c->ref_flags_cap * sizeof(int)));
+            CK(cudaMalloc(&c->ref_flags, 3 * c->ref_flags_cap * sizeof(int)));
             CK(cudaMalloc(&c->ref_obuf, (size_t)kRefCap * c->ref_slot_floats * sizeof(float)));
             if (!c->ref_slots) CK(cudaMalloc(&c->ref_slots, kRefCap * sizeof(RefSlot)));
             if (!c->ref_counters) CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
         }
         CK(cudaMemsetAsync(c->ref_flags, 0, ref_flag_total * sizeof(int), st));
+        CK(cudaMemsetAsync(c->ref_flags + c->ref_flags_cap, 0x7f, c->ref_flags_cap * sizeof(int), st));  // first column
+        CK(cudaMemsetAsync(c->ref_flags + 2 * c->ref_flags_cap, 0x80, c->ref_flags_cap * sizeof(int), st)); // last
         CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
         if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
                  *n = 4;
-                 return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_tiles, ref_max_records,
-                                      c->ref_flags, c->ref_slots, c->ref_counters, kRefCap, c->ref_obuf,
-                                      c->ref_slot_floats, std::max(1, ref_max_items), c->g, st);
+                 return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_tiles, c->ref_flags_cap,
+                                      ref_max_records, c->ref_flags, c->ref_slots, c->ref_counters, kRefCap,
+                                      c->ref_obuf, c->ref_slot_floats, std::max(1, ref_max_items), c->g, st);
              })))
             return rc;
     }

@@ -199,6 +199,7 @@ cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int tota
 
 // ---- FP32 refinement of candidate maxima (kernels_refine.cu) ----------------
 constexpr int kRefTile = 256;            // top-level samples per refinement tile (= mixing tile)
+constexpr int kRefR = 8;                 // refined samples on either side of a candidate maximum
 constexpr int kRefMaxLevels = 8;
 constexpr int kRefMaxSlices = 12;
 __host__ __device__ constexpr int kRefRange(int k) { return (kRefTile >> k) + 66; }   // samples of a tile at level k
@@ -221,9 +222,10 @@ struct RefUnit {                         // one unit of a push with refinement o
 struct RefSlot {
     int32_t unit, tt;
 };
-cudaError_t launch_refine(const RefUnit *d_units, int n_units, int max_tiles, int64_t max_records, int *flags,
-                          RefSlot *slots, int *counters, int cap, float *obuf, int64_t slot_floats,
-                          int max_items, const Halfband &g, cudaStream_t s);
+// flags: 3 x max_tiles_total ints: flag/slot, then the first and last refined column per tile
+cudaError_t launch_refine(const RefUnit *d_units, int n_units, int max_tiles, int64_t max_tiles_total,
+                          int64_t max_records, int *flags, RefSlot *slots, int *counters, int cap, float *obuf,
+                          int64_t slot_floats, int max_items, const Halfband &g, cudaStream_t s);
 
 // ---- launchers (kernels_simt.cu) -------------------------------------------
 cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,
