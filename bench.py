@@ -411,6 +411,7 @@ def main():
         for k in f1:
             flops[k] = flops.get(k, 0.0) + f1[k]
             bytes_[k] = bytes_.get(k, 0.0) + b1[k]
+    flops["refine"], bytes_["refine"] = 0.0, 0.0          # data-dependent: no fixed algorithmic work
     dom, roof = roofline_of(prim["stages"], flops, bytes_, args.precision, args.steps, peaks)
     busy = {k: v[0] for k, v in prim["stages"].items() if v[1] > 0}
     total_stage_ms = sum(busy.values())
