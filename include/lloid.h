@@ -120,7 +120,8 @@ typedef struct sb_unit_info {
     int64_t latency_samples;  /* top-rate look-ahead: after pushing T samples,  */
                               /* SNR is final for n < T - latency_samples       */
     int64_t samples_pushed;   /* T                                              */
-    int64_t device_bytes;     /* device memory held by this unit                */
+    int64_t device_bytes;     /* device memory of this unit's own state (bank   */
+                              /* data shared by several units is not included)  */
     int64_t flops_per_second; /* algorithmic FLOPs per second of data (FIR+mix) */
 } sb_unit_info;
 
@@ -142,6 +143,15 @@ int sb_ctx_sync(sb_ctx *ctx);
  * Returns SB_EBUSY (nothing allocated) when the budget cannot hold it. */
 int svdbank_create(sb_ctx *ctx, const sb_desc *desc, int32_t detector, sb_unit **out);
 int svdbank_destroy(sb_unit *unit);
+
+/* A new unit that filters with the same SVD bank as src (same precision,
+ * thresholds, window and push size) but has its own streaming state: the
+ * read-only bank data on the device (basis, mixing, their converted forms and
+ * template ids) is shared and freed with the last unit that uses it.  This is
+ * "the same SVD bank provided multiple times" of the paper's GPU benchmark
+ * (Sec. IV), and the two detectors of one bin when their banks coincide.
+ * Admission charges only the new unit's state (SB_EBUSY when it does not fit). */
+int svdbank_create_like(sb_ctx *ctx, sb_unit *src, int32_t detector, sb_unit **out);
 int sb_unit_query(const sb_unit *unit, sb_unit_info *info);
 
 /* Validate a bank description and report the unit it would create (k_max,
@@ -166,6 +176,13 @@ int filter_push(sb_unit *unit, const float *strain, int64_t n_samples, int64_t t
 int filter_push_group(sb_ctx *ctx, int32_t n_units, sb_unit *const *units,
                       const float *const *strains, int64_t n_samples,
                       const int64_t *t0_samples, int32_t on_device);
+
+/* Progress of the context's pushes (never blocks): *pushed = filter_push /
+ * filter_push_group calls so far, *completed = how many of them (the oldest
+ * ones) have finished on the device with their triggers moved to the host
+ * queue that triggers_pop reads.  Push i (0-based, in call order) is complete
+ * when *completed > i. */
+int sb_ctx_progress(sb_ctx *ctx, int64_t *pushed, int64_t *completed);
 
 /* Move up to cap finished triggers into out (never blocks on queued work).
  * *n_out = number written.  Triggers come out push by push, and within a push

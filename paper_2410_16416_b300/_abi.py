@@ -64,12 +64,14 @@ SIGNATURES = {
     "sb_ctx_sync": (C.c_int, [C.c_void_p]),
     "svdbank_create": (C.c_int, [C.c_void_p, C.POINTER(SbDesc), C.c_int32, C.POINTER(C.c_void_p)]),
     "svdbank_destroy": (C.c_int, [C.c_void_p]),
+    "svdbank_create_like": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "sb_unit_query": (C.c_int, [C.c_void_p, C.POINTER(SbUnitInfo)]),
     "svdbank_plan": (C.c_int, [C.POINTER(SbDesc), C.POINTER(SbUnitInfo)]),
     "filter_push": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32]),
     "filter_push_group": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                     C.c_int64, C.POINTER(C.c_int64), C.c_int32]),
     "triggers_pop": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "sb_ctx_progress": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sb_unit_snr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sb_ctx_get_stats": (C.c_int, [C.c_void_p, C.POINTER(SbCtxStats)]),
     "sb_ctx_profile": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -177,6 +179,12 @@ class Context:
     def sync(self):
         _check(lib.sb_ctx_sync(self.handle), "sb_ctx_sync")
 
+    def progress(self):
+        """(pushes issued, pushes completed with triggers host-visible); never blocks."""
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib.sb_ctx_progress(self.handle, C.byref(a), C.byref(b)), "sb_ctx_progress")
+        return a.value, b.value
+
     def stats(self) -> dict:
         st = SbCtxStats()
         _check(lib.sb_ctx_get_stats(self.handle, C.byref(st)), "sb_ctx_get_stats")
@@ -199,6 +207,14 @@ class Context:
         d, keep = make_desc(bank, **kw)
         h = C.c_void_p()
         _check(lib.svdbank_create(self.handle, C.byref(d), int(detector), C.byref(h)), "svdbank_create")
+        u = Unit(self, h)
+        self.units.append(u)
+        return u
+
+    def create_like(self, src: "Unit", detector: int = 0) -> "Unit":
+        """svdbank_create_like: a unit sharing src's bank data, with its own streaming state."""
+        h = C.c_void_p()
+        _check(lib.svdbank_create_like(self.handle, src.handle, int(detector), C.byref(h)), "svdbank_create_like")
         u = Unit(self, h)
         self.units.append(u)
         return u

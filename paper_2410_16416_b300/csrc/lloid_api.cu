@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -148,6 +149,7 @@ struct sb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t pop_stream = nullptr;
+    cudaStream_t alloc_stream = nullptr;
     bool own_stream = false;
     int64_t budget = 0, used = 0;
     Halfband g;
@@ -159,6 +161,7 @@ struct sb_ctx {
     std::vector<TaskArena> arenas;
     int next_arena = 0;
     std::deque<sb_trigger> ready;
+    int64_t pushes_completed = 0;    // pushes whose trigger slots have been drained
     bool overflow = false;
     int timeout_code = 0;      // first bounded device wait that expired (0: none)
     std::mutex mu;
@@ -170,6 +173,7 @@ struct sb_ctx {
     int *ref_counters = nullptr;
     float *ref_obuf = nullptr;
     int64_t ref_slot_floats = 0;
+    int ref_cap = 0;
     // profiling: event pairs around each launch, summed per stage on query
     bool prof = false;
     struct Mark { int stage; cudaEvent_t a, b; };
@@ -177,8 +181,19 @@ struct sb_ctx {
     std::vector<cudaEvent_t> ev_pool;
 };
 
+// Read-only bank data (basis, mixing, their 16-bit forms and TMA maps, template
+// ids), shared by every unit made from the same bank with svdbank_create_like.
+struct Weights {
+    sb_ctx *ctx = nullptr;
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    ~Weights();
+};
+
 struct sb_unit {
     sb_ctx *ctx = nullptr;
+    std::shared_ptr<Weights> w;
+    int64_t state_bytes = 0;
     int64_t id = 0;
     int32_t detector = 0;
     int M = 0, precision = 0, flags = 0;
@@ -208,19 +223,45 @@ struct sb_unit {
 // ---------------------------------------------------------------------------
 static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+Weights::~Weights() {
+    if (!ctx) return;
+    for (void *p : allocs) cudaFreeAsync(p, ctx->stream);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->used -= bytes;
+}
+
+// Unit memory comes from the device's stream-ordered pool: allocated on the
+// context's allocation stream (synchronised at once, so host copies may follow)
+// and returned with cudaFreeAsync on the work stream after the unit's last use,
+// so that retiring a unit never stalls queued work.
 static int dev_alloc(sb_unit *u, void **p, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocAsync(p, bytes, u->ctx->alloc_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->ctx->alloc_stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(SB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return fail(SB_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     }
     u->allocs.push_back(*p);
+    u->state_bytes += (int64_t)bytes;
+    return SB_OK;
+}
+
+static int dev_alloc_w(sb_unit *u, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, u->ctx->alloc_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->ctx->alloc_stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SB_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    }
+    u->w->allocs.push_back(*p);
+    u->w->bytes += (int64_t)bytes;
     return SB_OK;
 }
 
 static void free_unit_memory(sb_unit *u) {
-    for (void *p : u->allocs) cudaFree(p);
+    for (void *p : u->allocs) cudaFreeAsync(p, u->ctx->stream);
     u->allocs.clear();
 }
 
@@ -372,7 +413,8 @@ extern "C" int sb_ctx_create(int32_t device, void *stream, int64_t hbm_budget_by
         }
         c->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&c->pop_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&c->pop_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->alloc_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete c;
         return fail(SB_ECUDA, "cudaStreamCreate failed");
     }
@@ -423,7 +465,9 @@ extern "C" int sb_ctx_destroy(sb_ctx *c) {
     if (c->ref_slots) cudaFree(c->ref_slots);
     if (c->ref_counters) cudaFree(c->ref_counters);
     if (c->ref_obuf) cudaFree(c->ref_obuf);
+    if (c->stream) cudaStreamSynchronize(c->stream);      // unit memory returned on the work stream
     if (c->pop_stream) cudaStreamDestroy(c->pop_stream);
+    if (c->alloc_stream) cudaStreamDestroy(c->alloc_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return SB_OK;
@@ -484,8 +528,8 @@ static int encode_map(CUtensorMap *out, void *base, bool bf16, uint64_t inner, u
     return SB_OK;
 }
 
-static int upload_map(sb_unit *u, const CUtensorMap &h, CUtensorMap **dev) {
-    int rc = dev_alloc(u, (void **)dev, sizeof(CUtensorMap));
+static int upload_map(sb_unit *u, const CUtensorMap &h, CUtensorMap **dev, bool weights) {
+    int rc = weights ? dev_alloc_w(u, (void **)dev, sizeof(CUtensorMap)) : dev_alloc(u, (void **)dev, sizeof(CUtensorMap));
     if (rc) return rc;
     CK(cudaMemcpy(*dev, &h, sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     return SB_OK;
@@ -507,12 +551,12 @@ static int upload_expanded_weights(sb_unit *u, SliceDev &sd, const double *basis
                     if (q >= 0 && q < sd.Q) w[row * K + j] = to16((float)basis[l * sd.Q + q], u->bf16);
                 }
             }
-    int rc = dev_alloc(u, &sd.W16, w.size() * 2);
+    int rc = dev_alloc_w(u, &sd.W16, w.size() * 2);
     if (rc) return rc;
     CK(cudaMemcpy(sd.W16, w.data(), w.size() * 2, cudaMemcpyHostToDevice));
     CUtensorMap m;
     if ((rc = encode_map(&m, sd.W16, u->bf16, K, rows, kTcM))) return rc;
-    return upload_map(u, m, &sd.mapW);
+    return upload_map(u, m, &sd.mapW, true);
 }
 
 static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d) {
@@ -526,13 +570,12 @@ static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d) {
             for (int64_t a = 0; a < M2; ++a)
                 for (int l = 0; l < sd.L; ++l) m[a * L.Lk_pad + sd.o_col16 + l] = to16((float)mx[a * sd.L + l], u->bf16);
         }
-        CK(cudaMemcpy(L.M16, m.data(), m.size() * 2, cudaMemcpyHostToDevice));
-        CUtensorMap hm, ho;
         int rc;
+        if ((rc = dev_alloc_w(u, &L.M16, M2 * L.Lk_pad * 2))) return rc;
+        CK(cudaMemcpy(L.M16, m.data(), m.size() * 2, cudaMemcpyHostToDevice));
+        CUtensorMap hm;
         if ((rc = encode_map(&hm, L.M16, u->bf16, L.Lk_pad, M2, 128))) return rc;
-        if ((rc = upload_map(u, hm, &L.mapM))) return rc;
-        if ((rc = encode_map(&ho, L.O16, u->bf16, L.Lk_pad, L.Bk_max + 256, 256))) return rc;
-        if ((rc = upload_map(u, ho, &L.mapO))) return rc;
+        if ((rc = upload_map(u, hm, &L.mapM, true))) return rc;
     }
     return SB_OK;
 }
@@ -566,6 +609,60 @@ static int64_t plan_flops(const sb_desc *d) {
         f += 2.0 * sl.n_basis * (sl.n_taps + 2.0 * d->n_templates) * sl.rate_hz;
     }
     return (int64_t)std::llround(f);
+}
+
+// Streaming state of a unit (decimated strain, SNR blocks and histories, basis
+// outputs, trigger partials and open windows), zero-initialised; every field of
+// u->levels except the state pointers must be set.
+static int alloc_state(sb_unit *u) {
+    const int64_t M2 = 2 * (int64_t)u->M;
+    int rc;
+    for (auto &L : u->levels) {
+        const int k = L.k;
+        for (int b = 0; b < 2; ++b) {
+            if ((rc = dev_alloc(u, (void **)&L.dbuf[b], (L.Hd + L.Bk_max) * 4))) return rc;
+            CK(cudaMemset(L.dbuf[b], 0, (L.Hd + L.Bk_max) * 4));
+        }
+        if (!u->tc) {
+            if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return rc;
+            if (L.Hy > 0) {
+                for (int b = 0; b < 2; ++b) {
+                    if ((rc = dev_alloc(u, (void **)&L.yhist[b], M2 * L.Hy * 4))) return rc;
+                    CK(cudaMemset(L.yhist[b], 0, M2 * L.Hy * 4));
+                }
+            }
+            if (L.Lk > 0 && (rc = dev_alloc(u, (void **)&L.obuf, (int64_t)L.Lk * L.Bk_max * 4))) return rc;
+            continue;
+        }
+        if (k >= 1) {
+            if ((rc = dev_alloc(u, (void **)&L.yuni, M2 * L.ldu * 4))) return rc;
+            CK(cudaMemset(L.yuni, 0, M2 * L.ldu * 4));
+            if ((rc = dev_alloc(u, (void **)&L.ytmp, M2 * L.Hy * 4))) return rc;
+        } else if (u->flags & SB_FLAG_KEEP_SNR) {
+            if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return rc;
+        }
+        if ((rc = dev_alloc(u, &L.x16, L.x16_len * 2))) return rc;
+        CK(cudaMemset(L.x16, 0, L.x16_len * 2));
+        if (L.Lk_pad > 0) {
+            const int64_t rows = L.Bk_max + 256;
+            if ((rc = dev_alloc(u, &L.O16, rows * L.Lk_pad * 2))) return rc;
+            CK(cudaMemset(L.O16, 0, rows * L.Lk_pad * 2));
+            CUtensorMap ho;
+            if ((rc = encode_map(&ho, L.O16, u->bf16, L.Lk_pad, rows, 256))) return rc;
+            if ((rc = upload_map(u, ho, &L.mapO, false))) return rc;
+        }
+    }
+    if (u->tc) {
+        u->part_rec_max = ((u->Bmax + 255) / 256) * 4;
+        if ((rc = dev_alloc(u, (void **)&u->part, u->part_rec_max * u->M * sizeof(WinPart)))) return rc;
+    }
+    std::vector<WinState> ws(u->M);
+    for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = 0.0f; w.flags = 0; w.n = -1; }
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dev_alloc(u, (void **)&u->wstate[b], u->M * sizeof(WinState)))) return rc;
+        CK(cudaMemcpy(u->wstate[b], ws.data(), u->M * sizeof(WinState), cudaMemcpyHostToDevice));
+    }
+    return SB_OK;
 }
 
 extern "C" int svdbank_plan(const sb_desc *d, sb_unit_info *info) {
@@ -622,11 +719,14 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         free_unit_memory(u);
         {
             std::lock_guard<std::mutex> lk(c->mu);
-            c->used -= u->bytes;
+            c->used -= P.bytes;
         }
+        if (u->w) u->w->bytes = 0;                // nothing of this bank was charged yet
         delete u;
         return code;
     };
+    u->w = std::make_shared<Weights>();
+    u->w->ctx = c;
     u->levels.resize(P.kmax + 1);
     for (int k = 0; k <= P.kmax; ++k) {
         LevelDev &L = u->levels[k];
@@ -638,44 +738,13 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         L.Lk = (int)P.Lk[k];
         L.Bk_max = u->Bmax >> k;
         L.ldy = round_up(L.Bk_max, 4);
-        for (int b = 0; b < 2; ++b) {
-            if ((rc = dev_alloc(u, (void **)&L.dbuf[b], (L.Hd + L.Bk_max) * 4))) return cleanup(rc);
-            if (cudaMemset(L.dbuf[b], 0, (L.Hd + L.Bk_max) * 4) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
-        }
-        if (!u->tc) {
-            if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return cleanup(rc);
-            if (L.Hy > 0) {
-                for (int b = 0; b < 2; ++b) {
-                    if ((rc = dev_alloc(u, (void **)&L.yhist[b], M2 * L.Hy * 4))) return cleanup(rc);
-                    if (cudaMemset(L.yhist[b], 0, M2 * L.Hy * 4) != cudaSuccess)
-                        return cleanup(fail(SB_ECUDA, "memset"));
-                }
-            }
-        } else if (k >= 1) {
-            L.ldu = round_up(L.Hy + L.Bk_max, 4);
-            if ((rc = dev_alloc(u, (void **)&L.yuni, M2 * L.ldu * 4))) return cleanup(rc);
-            if (cudaMemset(L.yuni, 0, M2 * L.ldu * 4) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
-            if ((rc = dev_alloc(u, (void **)&L.ytmp, M2 * L.Hy * 4))) return cleanup(rc);
-        } else if (u->flags & SB_FLAG_KEEP_SNR) {
-            if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return cleanup(rc);
-        }
-        if (L.Lk > 0 && (!u->tc || u->refine)) {
-            if ((rc = dev_alloc(u, (void **)&L.Mcat, M2 * L.Lk * 4))) return cleanup(rc);
-        }
-        if (L.Lk > 0 && !u->tc) {
-            if ((rc = dev_alloc(u, (void **)&L.obuf, (int64_t)L.Lk * L.Bk_max * 4))) return cleanup(rc);
-        }
         if (u->tc) {
             L.Lk_pad = (int)P.Lk_pad[k];
             L.x16_len = P.x16_len[k];
-            if ((rc = dev_alloc(u, &L.x16, L.x16_len * 2))) return cleanup(rc);
-            if (cudaMemset(L.x16, 0, L.x16_len * 2) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
-            if (L.Lk_pad > 0) {
-                const int64_t rows = L.Bk_max + 256;
-                if ((rc = dev_alloc(u, &L.O16, rows * L.Lk_pad * 2))) return cleanup(rc);
-                if (cudaMemset(L.O16, 0, rows * L.Lk_pad * 2) != cudaSuccess) return cleanup(fail(SB_ECUDA, "memset"));
-                if ((rc = dev_alloc(u, &L.M16, M2 * L.Lk_pad * 2))) return cleanup(rc);
-            }
+            if (k >= 1) L.ldu = round_up(L.Hy + L.Bk_max, 4);
+        }
+        if (L.Lk > 0 && (!u->tc || u->refine)) {
+            if ((rc = dev_alloc_w(u, (void **)&L.Mcat, M2 * L.Lk * 4))) return cleanup(rc);
         }
     }
     // slices: basis filters and the per-level stacked mixing matrices
@@ -695,7 +764,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         if (!u->tc || u->refine) {
             std::vector<float> v((size_t)sd.L * sd.Q);
             for (size_t i = 0; i < v.size(); ++i) v[i] = (float)sl.basis[i];
-            if ((rc = dev_alloc(u, (void **)&sd.V, v.size() * 4))) return cleanup(rc);
+            if ((rc = dev_alloc_w(u, (void **)&sd.V, v.size() * 4))) return cleanup(rc);
             if (cudaMemcpy(sd.V, v.data(), v.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
                 return cleanup(fail(SB_ECUDA, "basis upload"));
             const int Lk = u->levels[sd.level].Lk;
@@ -720,28 +789,82 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
             return cleanup(fail(SB_ECUDA, "mixing upload"));
     }
     if (u->tc && (rc = upload_tc_mixing_and_maps(u, d))) return cleanup(rc);
-    if (u->tc) {
-        u->part_rec_max = ((u->Bmax + 255) / 256) * 4;
-        if ((rc = dev_alloc(u, (void **)&u->part, u->part_rec_max * u->M * sizeof(WinPart)))) return cleanup(rc);
-    }
-    // trigger state and template ids
-    std::vector<WinState> ws(u->M);
-    for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = 0.0f; w.flags = 0; w.n = -1; }
-    for (int b = 0; b < 2; ++b) {
-        if ((rc = dev_alloc(u, (void **)&u->wstate[b], u->M * sizeof(WinState)))) return cleanup(rc);
-        if (cudaMemcpy(u->wstate[b], ws.data(), u->M * sizeof(WinState), cudaMemcpyHostToDevice) != cudaSuccess)
-            return cleanup(fail(SB_ECUDA, "state upload"));
-    }
     std::vector<int64_t> ids(u->M);
     for (int i = 0; i < u->M; ++i) ids[i] = d->template_ids ? d->template_ids[i] : i;
-    if ((rc = dev_alloc(u, (void **)&u->tids, u->M * 8))) return cleanup(rc);
+    if ((rc = dev_alloc_w(u, (void **)&u->tids, u->M * 8))) return cleanup(rc);
     if (cudaMemcpy(u->tids, ids.data(), u->M * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         return cleanup(fail(SB_ECUDA, "template id upload"));
+    if ((rc = alloc_state(u))) return cleanup(rc);
     {
         std::lock_guard<std::mutex> lk(c->mu);
+        c->used += u->state_bytes + u->w->bytes - P.bytes;     // reservation -> measured
+        u->bytes = u->state_bytes;
         u->id = c->next_unit_id++;
         c->units.push_back(u);
     }
+    *out = u;
+    return SB_OK;
+}
+
+extern "C" int svdbank_create_like(sb_ctx *c, sb_unit *src, int32_t detector, sb_unit **out) {
+    if (!c || !src || !out) return fail(SB_EINVAL, "null argument");
+    if (src->ctx != c) return fail(SB_EINVAL, "source unit belongs to another context");
+    *out = nullptr;
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (c->used + src->state_bytes > c->budget)
+            return fail(SB_EBUSY, "HBM budget exhausted: unit state needs " + std::to_string(src->state_bytes) +
+                                      " bytes, " + std::to_string(c->budget - c->used) + " free in budget");
+        c->used += src->state_bytes;
+    }
+    sb_unit *u = new sb_unit();
+    u->ctx = c;
+    u->w = src->w;
+    u->detector = detector;
+    u->M = src->M;
+    u->precision = src->precision;
+    u->tc = src->tc;
+    u->bf16 = src->bf16;
+    u->refine = src->refine;
+    u->flags = src->flags;
+    u->thr = src->thr;
+    u->refine_thr = src->refine_thr;
+    u->f0 = src->f0;
+    u->win_len = src->win_len;
+    u->kmax = src->kmax;
+    u->Bmax = src->Bmax;
+    u->flops_per_s = src->flops_per_s;
+    u->slices = src->slices;
+    u->tids = src->tids;
+    u->levels = src->levels;
+    for (auto &L : u->levels) {                  // fresh streaming state, shared weights
+        L.dbuf[0] = L.dbuf[1] = nullptr;
+        L.dcur = 0;
+        L.last_Bk = 0;
+        L.ynew = nullptr;
+        L.yhist[0] = L.yhist[1] = nullptr;
+        L.ycur = 0;
+        L.obuf = nullptr;
+        L.x16 = nullptr;
+        L.O16 = nullptr;
+        L.mapO = nullptr;
+        L.yuni = nullptr;
+        L.ytmp = nullptr;
+    }
+    const int64_t reserved = src->state_bytes;
+    int rc = alloc_state(u);
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->used += u->state_bytes - reserved;
+    if (rc) {
+        free_unit_memory(u);
+        c->used -= u->state_bytes;
+        delete u;
+        return rc;
+    }
+    u->bytes = u->state_bytes;
+    u->id = c->next_unit_id++;
+    c->units.push_back(u);
     *out = u;
     return SB_OK;
 }
@@ -750,14 +873,13 @@ extern "C" int svdbank_destroy(sb_unit *u) {
     if (!u) return SB_OK;
     sb_ctx *c = u->ctx;
     cudaSetDevice(c->device);
-    cudaStreamSynchronize(c->stream);
-    free_unit_memory(u);
+    free_unit_memory(u);                  // stream-ordered: after every push already queued
     {
         std::lock_guard<std::mutex> lk(c->mu);
         c->used -= u->bytes;
         c->units.erase(std::remove(c->units.begin(), c->units.end(), u), c->units.end());
     }
-    delete u;
+    delete u;                             // the last unit of a bank releases its weights (~Weights)
     return SB_OK;
 }
 
@@ -891,7 +1013,19 @@ static int drain_ready_slots(sb_ctx *c, bool block_all) {
         if (rc == 1) break;                      // not finished yet
         if (rc < 0) return rc;
         c->pending.pop_front();
+        c->pushes_completed += 1;
     }
+    return SB_OK;
+}
+
+extern "C" int sb_ctx_progress(sb_ctx *c, int64_t *pushed, int64_t *completed) {
+    if (!c || !pushed || !completed) return fail(SB_EINVAL, "null argument");
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    std::lock_guard<std::mutex> lk(c->mu);
+    int rc = drain_ready_slots(c, false);
+    if (rc < 0) return rc;
+    *pushed = c->stats.pushes;
+    *completed = c->pushes_completed;
     return SB_OK;
 }
 
@@ -963,6 +1097,7 @@ static int slot_acquire(sb_ctx *c, int64_t need, TriggerSlot *&out, int &idx) {
             int rc = drain_slot(c, c->slots[j], true);
             if (rc < 0) return rc;
             c->pending.pop_front();
+            c->pushes_completed += 1;
             if (j == idx) break;
         }
     }
@@ -1415,8 +1550,9 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     }
     // a6: FP32 refinement of the top level's candidate maxima (16-bit modes)
     if (!refu.empty()) {
-        constexpr int kRefCap = 64;
-        if (c->ref_flags_cap < ref_flag_total || c->ref_slot_floats < ref_slot_floats || !c->ref_counters) {
+        const int kRefCap = (int)std::min<int64_t>(1024, std::max<int64_t>(64, 2 * (int64_t)refu.size()));
+        if (c->ref_flags_cap < ref_flag_total || c->ref_slot_floats < ref_slot_floats || !c->ref_counters ||
+            c->ref_cap < kRefCap) {
             CK(cudaStreamSynchronize(st));
             if (c->ref_flags) cudaFree(c->ref_flags);
             if (c->ref_obuf) cudaFree(c->ref_obuf);
@@ -1425,8 +1561,10 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             c->ref_flags_cap = std::max(ref_flag_total, 2 * c->ref_flags_cap);
             c->ref_slot_floats = std::max(ref_slot_floats, c->ref_slot_floats);
             CK(cudaMalloc(&c->ref_flags, 3 * c->ref_flags_cap * sizeof(int)));
-            CK(cudaMalloc(&c->ref_obuf, (size_t)kRefCap * c->ref_slot_floats * sizeof(float)));
-            if (!c->ref_slots) CK(cudaMalloc(&c->ref_slots, kRefCap * sizeof(RefSlot)));
+            c->ref_cap = std::max(c->ref_cap, kRefCap);
+            CK(cudaMalloc(&c->ref_obuf, (size_t)c->ref_cap * c->ref_slot_floats * sizeof(float)));
+            if (c->ref_slots) cudaFree(c->ref_slots);
+            CK(cudaMalloc(&c->ref_slots, c->ref_cap * sizeof(RefSlot)));
             if (!c->ref_counters) CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
         }
         CK(cudaMemsetAsync(c->ref_flags, 0, ref_flag_total * sizeof(int), st));

@@ -249,3 +249,28 @@ def shape_only_bank(bin_index: int, top_rate_hz: float = 4096.0,
     for f_s, t0, t1, V, Mx in raw:
         slices.append(ShapeSlice(f_s, t0, t1, V, Mx * scale[:, None]))
     return ShapeBank(M, top_rate_hz, slices)
+
+
+def production_shape_bank(index: int, top_rate_hz: float = 4096.0) -> ShapeBank:
+    """Random bank shaped like the production bin: about 1000 templates (U[800, 1200]),
+    its six slices (4096 ... 128 Hz over 60 s) and basis counts near its SVD ranks
+    (14, 23, 46, 191, 451, 679, each scaled by U[0.8, 1.2]), orthonormal DCT bases."""
+    g = rng(KIND_SHAPE, 100000 + index)
+    M = int(g.integers(800, 1201))
+    ranks = (14, 23, 46, 191, 451, 679)
+    weight = np.zeros(2 * M)
+    raw = []
+    for s, (sp, r) in enumerate(zip(PRODUCTION_BIN.slices, ranks)):
+        Q = int(round((sp.t_end_s - sp.t_start_s) * sp.rate_hz))
+        L = max(1, min(int(round(r * g.uniform(0.8, 1.2))), Q, 2 * M))
+        freq = np.sort(g.choice(Q, size=L, replace=False))
+        qq = np.arange(Q) + 0.5
+        V = np.cos(np.pi * freq[:, None] * qq[None, :] / Q) * np.sqrt(2.0 / Q)
+        V[freq == 0] *= np.sqrt(0.5)
+        Mx = g.standard_normal((2 * M, L))
+        k = int(round(math.log2(top_rate_hz / sp.rate_hz)))
+        weight += (Mx ** 2).sum(axis=1) * 2.0 ** (-k)
+        raw.append((sp, V, Mx))
+    scale = 1.0 / np.sqrt(weight)
+    return ShapeBank(M, top_rate_hz, [ShapeSlice(sp.rate_hz, sp.t_start_s, sp.t_end_s, V, Mx * scale[:, None])
+                                      for sp, V, Mx in raw])
