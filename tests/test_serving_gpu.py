@@ -56,7 +56,7 @@ def test_continuous_batching_matches_alone(lloid):
     ctx.close()
     s = rep.summary()
     assert s["buffers"] == 6 * len(reqs)
-    assert rep.admitted_late >= 1 and rep.max_concurrent <= 3
+    assert rep.admitted_late >= 1 and rep.max_concurrent < len(reqs)
     assert np.isfinite(s["p99_latency_s"])
     for r, req in enumerate(reqs):
         mine = np.sort(rep.triggers[rep.trigger_stream == r][FIELDS], order=["window", "template_id"])
