@@ -616,52 +616,57 @@ static int64_t plan_flops(const sb_desc *d) {
 // u->levels except the state pointers must be set.
 static int alloc_state(sb_unit *u) {
     const int64_t M2 = 2 * (int64_t)u->M;
-    int rc;
+    // one allocation carved into 256-byte aligned pieces, zeroed by one memset
+    struct Piece { void **dst; int64_t bytes; };
+    std::vector<Piece> pieces;
+    auto want = [&](void **dst, int64_t bytes) { pieces.push_back({dst, std::max<int64_t>(bytes, 16)}); };
     for (auto &L : u->levels) {
         const int k = L.k;
-        for (int b = 0; b < 2; ++b) {
-            if ((rc = dev_alloc(u, (void **)&L.dbuf[b], (L.Hd + L.Bk_max) * 4))) return rc;
-            CK(cudaMemset(L.dbuf[b], 0, (L.Hd + L.Bk_max) * 4));
-        }
+        for (int b = 0; b < 2; ++b) want((void **)&L.dbuf[b], (L.Hd + L.Bk_max) * 4);
         if (!u->tc) {
-            if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return rc;
-            if (L.Hy > 0) {
-                for (int b = 0; b < 2; ++b) {
-                    if ((rc = dev_alloc(u, (void **)&L.yhist[b], M2 * L.Hy * 4))) return rc;
-                    CK(cudaMemset(L.yhist[b], 0, M2 * L.Hy * 4));
-                }
-            }
-            if (L.Lk > 0 && (rc = dev_alloc(u, (void **)&L.obuf, (int64_t)L.Lk * L.Bk_max * 4))) return rc;
+            want((void **)&L.ynew, M2 * L.ldy * 4);
+            if (L.Hy > 0)
+                for (int b = 0; b < 2; ++b) want((void **)&L.yhist[b], M2 * L.Hy * 4);
+            if (L.Lk > 0) want((void **)&L.obuf, (int64_t)L.Lk * L.Bk_max * 4);
             continue;
         }
         if (k >= 1) {
-            if ((rc = dev_alloc(u, (void **)&L.yuni, M2 * L.ldu * 4))) return rc;
-            CK(cudaMemset(L.yuni, 0, M2 * L.ldu * 4));
-            if ((rc = dev_alloc(u, (void **)&L.ytmp, M2 * L.Hy * 4))) return rc;
+            want((void **)&L.yuni, M2 * L.ldu * 4);
+            want((void **)&L.ytmp, M2 * L.Hy * 4);
         } else if (u->flags & SB_FLAG_KEEP_SNR) {
-            if ((rc = dev_alloc(u, (void **)&L.ynew, M2 * L.ldy * 4))) return rc;
+            want((void **)&L.ynew, M2 * L.ldy * 4);
         }
-        if ((rc = dev_alloc(u, &L.x16, L.x16_len * 2))) return rc;
-        CK(cudaMemset(L.x16, 0, L.x16_len * 2));
-        if (L.Lk_pad > 0) {
-            const int64_t rows = L.Bk_max + 256;
-            if ((rc = dev_alloc(u, &L.O16, rows * L.Lk_pad * 2))) return rc;
-            CK(cudaMemset(L.O16, 0, rows * L.Lk_pad * 2));
-            CUtensorMap ho;
-            if ((rc = encode_map(&ho, L.O16, u->bf16, L.Lk_pad, rows, 256))) return rc;
-            if ((rc = upload_map(u, ho, &L.mapO, false))) return rc;
-        }
+        want(&L.x16, L.x16_len * 2);
+        if (L.Lk_pad > 0) want(&L.O16, (L.Bk_max + 256) * L.Lk_pad * 2);
     }
     if (u->tc) {
         u->part_rec_max = ((u->Bmax + 255) / 256) * 4;
-        if ((rc = dev_alloc(u, (void **)&u->part, u->part_rec_max * u->M * sizeof(WinPart)))) return rc;
+        want((void **)&u->part, u->part_rec_max * u->M * (int64_t)sizeof(WinPart));
+    }
+    for (int b = 0; b < 2; ++b) want((void **)&u->wstate[b], u->M * (int64_t)sizeof(WinState));
+    int64_t total = 0;
+    for (auto &p : pieces) total += round_up(p.bytes, 256);
+    char *base = nullptr;
+    int rc = dev_alloc(u, (void **)&base, total);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(base, 0, total, u->ctx->alloc_stream));
+    int64_t off = 0;
+    for (auto &p : pieces) {
+        *p.dst = base + off;
+        off += round_up(p.bytes, 256);
     }
     std::vector<WinState> ws(u->M);
     for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = 0.0f; w.flags = 0; w.n = -1; }
-    for (int b = 0; b < 2; ++b) {
-        if ((rc = dev_alloc(u, (void **)&u->wstate[b], u->M * sizeof(WinState)))) return rc;
-        CK(cudaMemcpy(u->wstate[b], ws.data(), u->M * sizeof(WinState), cudaMemcpyHostToDevice));
+    for (int b = 0; b < 2; ++b)
+        CK(cudaMemcpyAsync(u->wstate[b], ws.data(), u->M * sizeof(WinState), cudaMemcpyHostToDevice,
+                           u->ctx->alloc_stream));
+    for (auto &L : u->levels) {
+        if (!u->tc || L.Lk_pad == 0) continue;
+        CUtensorMap ho;
+        if ((rc = encode_map(&ho, L.O16, u->bf16, L.Lk_pad, L.Bk_max + 256, 256))) return rc;
+        if ((rc = upload_map(u, ho, &L.mapO, false))) return rc;
     }
+    CK(cudaStreamSynchronize(u->ctx->alloc_stream));
     return SB_OK;
 }
 

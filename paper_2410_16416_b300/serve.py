@@ -68,10 +68,23 @@ def poisson_arrivals(rng: np.random.Generator, n: int, start_s: float, rate_hz: 
     return start_s + np.cumsum(rng.exponential(1.0 / rate_hz, n))
 
 
+def preload(ctx: "_abi.Context", requests: List[StreamRequest], buffer_samples: int) -> Dict[str, "_abi.Unit"]:
+    """Load each shared bank once, before serving starts (a resident unit per share_key
+    that streams then clone with svdbank_create_like)."""
+    anchors: Dict[str, "_abi.Unit"] = {}
+    for req in requests:
+        if req.share_key is not None and req.share_key not in anchors:
+            anchors[req.share_key] = ctx.create_unit(req.bank, detector=req.detector,
+                                                     max_push_samples=buffer_samples, **req.unit_kwargs)
+    return anchors
+
+
 def run(ctx: "_abi.Context", requests: List[StreamRequest], buffer_samples: int,
         time_scale: float = 1.0, on_device: bool = False, idle_sleep_s: float = 0.0005,
-        max_wall_s: Optional[float] = None) -> ServeReport:
-    """Serve all requests to completion.  time_scale > 1 replays arrivals faster than real time."""
+        max_wall_s: Optional[float] = None, anchors: Optional[Dict[str, "_abi.Unit"]] = None) -> ServeReport:
+    """Serve all requests to completion.  time_scale > 1 replays arrivals faster than real time.
+    anchors: preloaded units (see preload) that streams with the same share_key clone."""
+    anchors = anchors or {}
     n_req = len(requests)
     units: Dict[int, "_abi.Unit"] = {}
     next_buf = [0] * n_req
@@ -121,7 +134,9 @@ def run(ctx: "_abi.Context", requests: List[StreamRequest], buffer_samples: int,
                 continue
             key = requests[r].share_key
             try:
-                if key is not None and shared.get(key):
+                if key is not None and key in anchors:
+                    u = ctx.create_like(anchors[key], detector=requests[r].detector)
+                elif key is not None and shared.get(key):
                     u = ctx.create_like(units[shared[key][0]], detector=requests[r].detector)
                 else:
                     u = ctx.create_unit(requests[r].bank, detector=requests[r].detector,
