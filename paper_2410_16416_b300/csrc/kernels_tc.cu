@@ -18,6 +18,7 @@
 // all four warps drain TMEM (each warp owns 32 TMEM lanes).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "lloid_internal.h"
 #include "tc_ptx.cuh"
@@ -26,18 +27,41 @@ namespace lloid {
 
 using namespace tc;
 
-template <bool BF16>
-struct Half;
+// Operand modes: element type, bytes, the Hankel block (phases = 16 bytes of
+// samples), K per MMA instruction (32 bytes) and the instruction kind.
+template <int MODE>
+struct Op;
 template <>
-struct Half<true> {
+struct Op<kModeF16> {
+    using T = __half;
+    static constexpr int kBytes = 2, kPhases = 8, kMmaK = 16;
+    static constexpr uint32_t kFmt = 0;
+    static __device__ __forceinline__ T cvt(float v) { return __float2half_rn(v); }
+};
+template <>
+struct Op<kModeBF16> {
     using T = __nv_bfloat16;
+    static constexpr int kBytes = 2, kPhases = 8, kMmaK = 16;
+    static constexpr uint32_t kFmt = 1;
     static __device__ __forceinline__ T cvt(float v) { return __float2bfloat16_rn(v); }
 };
 template <>
-struct Half<false> {
-    using T = __half;
-    static __device__ __forceinline__ T cvt(float v) { return __float2half_rn(v); }
+struct Op<kModeE4M3> {
+    using T = __nv_fp8_e4m3;
+    static constexpr int kBytes = 1, kPhases = 16, kMmaK = 32;
+    static constexpr uint32_t kFmt = 0;
+    static __device__ __forceinline__ T cvt(float v) { return __nv_fp8_e4m3(v); }   // saturating
 };
+template <int MODE>
+__device__ __forceinline__ void mma_op(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (MODE == kModeE4M3) mma_f8(d, a, b, idesc, acc);
+    else mma_f16(d, a, b, idesc, acc);
+}
+template <int MODE>
+__host__ __device__ constexpr uint32_t idesc_op(int M, int N) {
+    return (1u << 4) | (Op<MODE>::kFmt << 7) | (Op<MODE>::kFmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
 
 template <class Task>
 __device__ __forceinline__ int find_tile(const Task *tasks, int n, int tile) {
@@ -56,13 +80,30 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 // ---------------------------------------------------------------------------
 // FP32 -> 16-bit copies of the decimated strain (FIR data operand)
 // ---------------------------------------------------------------------------
-template <bool BF16>
+template <int MODE>
 __global__ void __launch_bounds__(256) to_half_kernel(const HalfConvTask *__restrict__ tasks) {
     const HalfConvTask t = tasks[blockIdx.y];
-    using T = typename Half<BF16>::T;
+    using T = typename Op<MODE>::T;
     T *dst = reinterpret_cast<T *>(t.dst);
+    float mul = 1.0f;
+    if (MODE == kModeE4M3) {                  // per-buffer absmax scaling: samples map to [-448, 448]
+        const float amax = t.amax[0];
+        mul = amax > 0.0f ? 448.0f / amax : 1.0f;
+        if (blockIdx.x == 0 && threadIdx.x == 0) t.amax_next[0] = 0.0f;   // reset for the next push
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = Half<BF16>::cvt(t.src[i]);
+        dst[i] = Op<MODE>::cvt(t.src[i] * mul);
+}
+
+// |x| maximum of each task's source (E4M3 mode), as the bits of a non-negative float.
+__global__ void __launch_bounds__(256) absmax_kernel(const HalfConvTask *__restrict__ tasks) {
+    const HalfConvTask t = tasks[blockIdx.y];
+    float m = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(t.src[i]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(t.amax), __float_as_int(m));
 }
 
 // ---------------------------------------------------------------------------
@@ -72,10 +113,11 @@ constexpr int kFirStages = 4;
 constexpr int kFirStageBytes = kTcM * 64 * 2;             // 128 rows x 64 K x 2 B
 constexpr int kTmemCols = 256;
 
-template <bool BF16>
+template <int MODE>
 __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restrict__ tasks, int n_tasks,
                                                         int *err) {
-    using H = Half<BF16>;
+    using H = Op<MODE>;
+    constexpr int kPh = H::kPhases, kB = H::kBytes, kKC = 128 / kB;   // K elements per 128-byte row
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -109,22 +151,22 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const int nk = t.Kpad / 64;
+    const int nk = t.Kpad / kKC;
 
     if (warp == 0 && lane == 0) {
         prefetch_tmap(t.mapW);
-        const uint32_t wbytes = (uint32_t)(kTcN * 8 + t.Kpad) * 2;
+        const uint32_t wbytes = (uint32_t)(kTcN * kPh + t.Kpad) * kB;
         mbar_expect_tx(winb, wbytes);
-        bulk_load(win, reinterpret_cast<const uint8_t *>(t.x) + 2 * (t.X0 + (int64_t)8 * kTcN * nt), wbytes, winb);
+        bulk_load(win, reinterpret_cast<const uint8_t *>(t.x) + kB * (t.X0 + (int64_t)kPh * kTcN * nt), wbytes, winb);
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % kFirStages;
             if (kc >= kFirStages && !mbar_wait(&empty[s], ((kc / kFirStages) - 1) & 1, err, 1)) break;
             mbar_expect_tx(&full[s], kFirStageBytes);
-            tma_load_2d(a_st + s * kFirStageBytes, t.mapW, kc * 64, mt * kTcM, &full[s]);
+            tma_load_2d(a_st + s * kFirStageBytes, t.mapW, kc * kKC, mt * kTcM, &full[s]);
         }
     } else if (warp == 1 && lane == 0) {
         if (mbar_wait(winb, 0, err, 2)) {
-            const uint32_t idesc = idesc_f16(kTcM, kTcN, BF16);
+            const uint32_t idesc = idesc_op<MODE>(kTcM, kTcN);
             const uint32_t wa = smem_u32(win);
             bool ok = true;
             for (int kc = 0; kc < nk && ok; ++kc) {
@@ -134,8 +176,8 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
                 const uint32_t aa = smem_u32(a_st + s * kFirStageBytes);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
-                    mma_f16(tmem, desc_k_sw128(aa + kk * 32), desc_hankel(wa + (kc * 64 + kk * 16) * 2), idesc,
-                            (kc | kk) != 0);
+                    mma_op<MODE>(tmem, desc_k_sw128(aa + kk * 32), desc_hankel(wa + kc * 128 + kk * 32), idesc,
+                                 (kc | kk) != 0);
                 mma_commit(&empty[s]);
             }
             if (ok) mma_commit(accb);
@@ -145,12 +187,15 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
     const bool have = mbar_wait(accb, 0, err, 4);
     tc_fence_after();
     if (have) {
-        // TMEM lane R = 16 r + l_loc (row of W in this tile), column c = block b - 256 nt
+        // TMEM lane R = lpt r + l_loc (row of W in this tile), column c = block b - 256 nt
+        constexpr int lpt = kTcM / kPh;                      // basis vectors per tile
         const int R = warp * 32 + lane;
-        const int r = R >> 4;
-        const int col = t.o_col + mt * 16 + (R & 15);
+        const int r = R / lpt;
+        const int col = t.o_col + mt * lpt + (R % lpt);
         typename H::T *O = reinterpret_cast<typename H::T *>(t.O);
-        const int64_t m_base = (int64_t)8 * kTcN * nt + r;
+        const int64_t m_base = (int64_t)kPh * kTcN * nt + r;
+        float oscale = 1.0f;                                 // E4M3: strain scale x basis/output scales
+        if (MODE == kModeE4M3) oscale = t.xamax[0] * (1.0f / 448.0f) * t.colscale[col];
 #pragma unroll 1
         for (int c0 = 0; c0 < kTcN; c0 += 32) {
             uint32_t v[32];
@@ -158,8 +203,8 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
             tmem_ld_wait();
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const int64_t m = m_base + 8 * (c0 + j);
-                if (m < t.Bk) O[m * t.ldo + col] = H::cvt(__uint_as_float(v[j]));
+                const int64_t m = m_base + kPh * (c0 + j);
+                if (m < t.Bk) O[m * t.ldo + col] = H::cvt(__uint_as_float(v[j]) * oscale);
             }
         }
     }
@@ -226,9 +271,10 @@ struct SegBest {
     int64_t n;
 };
 
-template <bool BF16>
+template <int MODE>
 __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
                                                           Halfband g, int *err) {
+    constexpr int kKC = 128 / Op<MODE>::kBytes, kMK = Op<MODE>::kMmaK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -241,7 +287,7 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
     const int local = blockIdx.x - t.tile_begin;
     const int tt = local / t.tiles_a, at = local % t.tiles_a;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (t.Lk_pad + 63) / 64;
+    const int nk = (t.Lk_pad + kKC - 1) / kKC;
     // coarser-level window of chunk c0 starts at position A0 - 16 + c0/2 (A0: position of
     // relative column 0 halved); loads start 16-byte aligned at xs0 + c0/2, REM floats earlier
     const int64_t rel0 = (int64_t)kMixCols * tt - t.lam;
@@ -274,21 +320,21 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
             if (kc >= kMixStages && !mbar_wait(&empty[s], ((kc / kMixStages) - 1) & 1, err, 5)) break;
             uint8_t *sa = st + s * kMixStageBytes;
             mbar_expect_tx(&full[s], kMixStageBytes);
-            tma_load_2d(sa, t.mapM, kc * 64, at * kMixRows, &full[s]);
-            tma_load_2d(sa + kMixABytes, t.mapO, kc * 64, tt * kMixCols, &full[s]);
+            tma_load_2d(sa, t.mapM, kc * kKC, at * kMixRows, &full[s]);
+            tma_load_2d(sa + kMixABytes, t.mapO, kc * kKC, tt * kMixCols, &full[s]);
         }
     } else if (warp == 1 && lane == 0 && nk > 0) {
-        const uint32_t idesc = idesc_f16(kMixRows, kMixCols, BF16);
+        const uint32_t idesc = idesc_op<MODE>(kMixRows, kMixCols);
         bool ok = true;
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % kMixStages;
             if (!mbar_wait(&full[s], (kc / kMixStages) & 1, err, 6)) { ok = false; break; }
             tc_fence_after();
             const uint32_t sa = smem_u32(st + s * kMixStageBytes);
-            const int nmma = min(4, (t.Lk_pad - kc * 64) / 16);
+            const int nmma = min(4, (t.Lk_pad - kc * kKC) / kMK);
             for (int kk = 0; kk < nmma; ++kk)
-                mma_f16(tmem, desc_k_sw128(sa + kk * 32), desc_k_sw128(sa + kMixABytes + kk * 32), idesc,
-                        (kc | kk) != 0);
+                mma_op<MODE>(tmem, desc_k_sw128(sa + kk * 32), desc_k_sw128(sa + kMixABytes + kk * 32), idesc,
+                             (kc | kk) != 0);
             mma_commit(&empty[s]);
         }
         if (ok) mma_commit(accb);
@@ -302,6 +348,7 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
         const int a = kMixRows * at + R;
         const bool row_ok = a < t.M2;
         const float *src = t.Ysrc ? t.Ysrc + (int64_t)(row_ok ? a : 0) * t.ld_src : nullptr;
+        const float rsc = (MODE == kModeE4M3 && row_ok) ? t.rscale[a] : 1.0f;   // E4M3: mixing-row scale
         const bool top = t.part != nullptr;
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
@@ -326,7 +373,7 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
                     tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + c0, v);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
+                    for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]) * rsc;
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) x[j] = 0.0f;
@@ -401,49 +448,63 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-size_t tc_fir_smem_bytes(int kpad_max) { return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * 8 + kpad_max) * 2; }
+size_t tc_fir_smem_bytes(int kpad_max, int mode) {
+    const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2;
+    return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * ph + kpad_max) * by;
+}
 size_t tc_mixup_smem_bytes() { return 1024 + 1024 + kMixStages * kMixStageBytes; }
 
-cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, bool bf16, cudaStream_t s) {
+template <class K>
+static cudaError_t set_smem(K kernel, size_t smem) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s) {
     if (n_tasks == 0) return cudaSuccess;
     dim3 grid(64, n_tasks);
-    if (bf16) to_half_kernel<true><<<grid, 256, 0, s>>>(d_tasks);
-    else to_half_kernel<false><<<grid, 256, 0, s>>>(d_tasks);
+    if (mode == kModeBF16) to_half_kernel<kModeBF16><<<grid, 256, 0, s>>>(d_tasks);
+    else if (mode == kModeF16) to_half_kernel<kModeF16><<<grid, 256, 0, s>>>(d_tasks);
+    else {
+        absmax_kernel<<<grid, 256, 0, s>>>(d_tasks);
+        to_half_kernel<kModeE4M3><<<grid, 256, 0, s>>>(d_tasks);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, bool bf16, int *err,
+template <int MODE>
+static cudaError_t fir_launch(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int *err,
+                              cudaStream_t s) {
+    const size_t smem = tc_fir_smem_bytes(kpad_max, MODE);
+    cudaError_t e = set_smem(tc_fir_kernel<MODE>, smem);
+    if (e != cudaSuccess) return e;
+    tc_fir_kernel<MODE><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    const size_t smem = tc_fir_smem_bytes(kpad_max);
-    cudaError_t e;
-    if (bf16) {
-        e = cudaFuncSetAttribute(tc_fir_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        tc_fir_kernel<true><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
-    } else {
-        e = cudaFuncSetAttribute(tc_fir_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        tc_fir_kernel<false><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
-    }
+    if (mode == kModeBF16) return fir_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, kpad_max, err, s);
+    if (mode == kModeF16) return fir_launch<kModeF16>(d_tasks, n_tasks, total_tiles, kpad_max, err, s);
+    return fir_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, kpad_max, err, s);
+}
+
+template <int MODE>
+static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g,
+                                int *err, cudaStream_t s) {
+    const size_t smem = tc_mixup_smem_bytes();
+    cudaError_t e = set_smem(tc_mixup_kernel<MODE>, smem);
+    if (e != cudaSuccess) return e;
+    tc_mixup_kernel<MODE><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, g, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g, bool bf16,
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g, int mode,
                             int *err, cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    const size_t smem = tc_mixup_smem_bytes();
-    cudaError_t e;
-    if (bf16) {
-        e = cudaFuncSetAttribute(tc_mixup_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        tc_mixup_kernel<true><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, g, err);
-    } else {
-        e = cudaFuncSetAttribute(tc_mixup_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        tc_mixup_kernel<false><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, g, err);
-    }
-    return cudaGetLastError();
+    if (mode == kModeBF16) return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, g, err, s);
+    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, g, err, s);
+    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, g, err, s);
 }
 
 }  // namespace lloid

@@ -29,6 +29,7 @@
 
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_fp16.h>
 
 #include "lloid.h"
@@ -92,7 +93,7 @@ struct SliceDev {
     float *V = nullptr;       // [L x Q] (FP32 mode)
     int o_row = 0;            // first row in the level's basis-output block
     // tensor-core modes: 8-phase expanded weights and their TMA map
-    void *W16 = nullptr;      // [8 L16 x Kpad] 16-bit
+    void *W16 = nullptr;      // [phases x L16 x Kpad] 16- or 8-bit expanded weights
     CUtensorMap *mapW = nullptr;   // device address
     int L16 = 0, Kpad = 0, o_col16 = 0;
     int64_t X0 = 0, phi = 0;
@@ -113,7 +114,10 @@ struct LevelDev {
     float *obuf = nullptr;    // [Lk x Bk_max]
     std::vector<int> slices;
     // tensor-core modes
-    int Lk_pad = 0;           // sum of the level's L16
+    int Lk_pad = 0;           // padded width of the level's basis-output block
+    float *colscale = nullptr;   // E4M3: per output column, basis scale / output scale
+    float *rscale = nullptr;     // E4M3: per mixing row scale
+    float *amax = nullptr;       // E4M3: |strain| maximum accumulators [2] (state)
     void *x16 = nullptr;      // 16-bit copy of the decimated strain (+ window slack)
     int64_t x16_len = 0;
     void *O16 = nullptr;      // basis outputs [Bk_max x Lk_pad], time-major
@@ -198,6 +202,8 @@ struct sb_unit {
     int32_t detector = 0;
     int M = 0, precision = 0, flags = 0;
     bool tc = false, bf16 = false;
+    int mode = 0;                 // tensor-core operand mode (kModeF16 / kModeBF16 / kModeE4M3)
+    int amax_cur = 0;
     bool refine = false;           // 16-bit modes with a refine threshold: FP32 copies kept for a6
     float thr = 0.f, refine_thr = 0.f;
     double f0 = 0.0;
@@ -283,7 +289,15 @@ struct Plan {
     int64_t bytes = 0;
 };
 
-static bool is_tc(int precision) { return precision == SB_BF16 || precision == SB_FP16; }
+static bool is_tc(int precision) { return precision == SB_BF16 || precision == SB_FP16 || precision == SB_FP8; }
+static int tc_mode(int precision) {
+    return precision == SB_FP8 ? kModeE4M3 : precision == SB_BF16 ? kModeBF16 : kModeF16;
+}
+static int mode_phases(int mode) { return mode == kModeE4M3 ? 16 : 8; }    // 16 bytes of samples
+static int mode_bytes(int mode) { return mode == kModeE4M3 ? 1 : 2; }
+// E4M3 static scale of level-k basis outputs: white noise gives o_l ~ N(0, 2^-k); the
+// scaled values have standard deviation 4, leaving 112 sigma below the E4M3 maximum.
+static float e4m3_out_scale(int k) { return std::ldexp(1.0f, -k) > 0 ? std::sqrt(std::ldexp(1.0f, -k)) / 4.0f : 1.0f; }
 
 static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &P) {
     const int S = d->n_slices;
@@ -348,21 +362,25 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
     P.L16.assign(S, 0);
     P.o_col16.assign(S, 0);
     std::vector<int64_t> kpad_max(NL, 0);
+    const int mode = tc_mode(d->precision), ph = mode_phases(mode), by = mode_bytes(mode);
+    const int lpt = kTcM / ph;                       // basis vectors per 128-row weight tile
     for (int s = 0; s < S; ++s) {
         const int k = levels_of_slice[s];
         const int64_t D = std::llround(d->slices[s].t_start_s * d->slices[s].rate_hz);
         const int64_t Q = d->slices[s].n_taps;
         const int64_t start = P.Hd[k] + P.e[k] - P.lam[k] - D - (Q - 1);    // >= 0 by the choice of Hd
-        P.X0[s] = start & ~int64_t(7);
+        P.X0[s] = start / ph * ph;                     // window starts on 16 bytes
         P.phi[s] = start - P.X0[s];
-        P.Kpad[s] = round_up(Q + 7 + P.phi[s], 64);
-        P.L16[s] = round_up(d->slices[s].n_basis, 16);
+        P.Kpad[s] = round_up(Q + ph - 1 + P.phi[s], 128 / by);
+        P.L16[s] = round_up(d->slices[s].n_basis, lpt);
         P.o_col16[s] = P.Lk_pad[k];
         P.Lk_pad[k] += P.L16[s];
         kpad_max[k] = std::max(kpad_max[k], P.Kpad[s]);
     }
-    for (int k = 0; k < NL; ++k)
-        P.x16_len[k] = P.Hd[k] + (d->max_push_samples >> k) + 8 * kTcN + kpad_max[k] + 64;
+    for (int k = 0; k < NL; ++k) {
+        if (mode == kModeE4M3) P.Lk_pad[k] = round_up(P.Lk_pad[k], 32);   // K per 8-bit MMA
+        P.x16_len[k] = P.Hd[k] + (d->max_push_samples >> k) + (int64_t)ph * kTcN + kpad_max[k] + 64;
+    }
     // bytes
     const int64_t M2 = 2 * (int64_t)d->n_templates;
     int64_t b = 0;
@@ -376,13 +394,15 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
             b -= M2 * ldy * 4 + 2 * M2 * P.Hy[k] * 4;   // replaced by the unified level buffer
             if (k >= 1) b += M2 * round_up(P.Hy[k] + Bk, 4) * 4 + M2 * P.Hy[k] * 4 + 128;
             else if (d->flags & SB_FLAG_KEEP_SNR) b += M2 * ldy * 4;
-            b += P.x16_len[k] * 2 + (Bk + 256) * P.Lk_pad[k] * 2 + M2 * P.Lk_pad[k] * 2 + 2 * 128;
+            b += (P.x16_len[k] + (Bk + 256) * P.Lk_pad[k] + M2 * P.Lk_pad[k]) * by + 2 * 128;
+            if (mode == kModeE4M3) b += (P.Lk_pad[k] + M2 + 2) * 4;
         } else {
             b += M2 * P.Lk[k] * 4 + P.Lk[k] * Bk * 4;    // mixing + basis outputs
         }
     }
     for (int s = 0; s < S; ++s)
-        b += P.tc ? 8 * P.L16[s] * P.Kpad[s] * 2 + 128 : (int64_t)d->slices[s].n_basis * d->slices[s].n_taps * 4;
+        b += P.tc ? (int64_t)ph * P.L16[s] * P.Kpad[s] * by + 128
+                  : (int64_t)d->slices[s].n_basis * d->slices[s].n_taps * 4;
     b += 2 * (int64_t)d->n_templates * sizeof(WinState) + d->n_templates * 8;
     if (P.tc) b += ((d->max_push_samples + 255) / 256) * 4 * (int64_t)d->n_templates * sizeof(WinPart);
     if (P.tc && d->refine_threshold > 0.0f)            // FP32 basis and mixing for the refinement
@@ -513,14 +533,27 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-static int encode_map(CUtensorMap *out, void *base, bool bf16, uint64_t inner, uint64_t outer, uint32_t box_outer) {
+static void put_elem(std::vector<uint8_t> &buf, size_t i, float v, int mode) {
+    if (mode == kModeE4M3) {
+        __nv_fp8_e4m3 q(v);
+        buf[i] = *reinterpret_cast<uint8_t *>(&q);
+    } else {
+        const uint16_t h = to16(v, mode == kModeBF16);
+        std::memcpy(&buf[2 * i], &h, 2);
+    }
+}
+
+static int encode_map(CUtensorMap *out, void *base, int mode, uint64_t inner, uint64_t outer, uint32_t box_outer) {
     auto encode = tensor_map_encoder();
     if (!encode) return fail(SB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int by = mode_bytes(mode);
     cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {inner * 2};
-    cuuint32_t box[2] = {64, box_outer};
+    cuuint64_t strides[1] = {inner * by};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / by), box_outer};          // 128-byte rows
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(out, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+    CUresult r = encode(out, mode == kModeE4M3   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                             : mode == kModeBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                                         2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -536,46 +569,81 @@ static int upload_map(sb_unit *u, const CUtensorMap &h, CUtensorMap **dev, bool 
 }
 
 // W[(l, r)][j] = v[l][r + Q - 1 + phi - j] (zero outside 0 <= q < Q), rows
-// ordered per 128-row tile t as 16 r + l_loc with l = 16 t + l_loc.
-static int upload_expanded_weights(sb_unit *u, SliceDev &sd, const double *basis) {
-    const int64_t rows = 8 * (int64_t)sd.L16, K = sd.Kpad;
-    std::vector<uint16_t> w((size_t)(rows * K), to16(0.0f, u->bf16));
-    for (int64_t t = 0; t < sd.L16 / 16; ++t)
-        for (int r = 0; r < 8; ++r)
-            for (int ll = 0; ll < 16; ++ll) {
-                const int64_t l = 16 * t + ll;
+// ordered per 128-row tile t as lpt r + l_loc with l = lpt t + l_loc (lpt = 16
+// basis vectors x 8 phases in the 16-bit modes, 8 x 16 in E4M3).  E4M3 rows are
+// scaled by 448 / max|v_l| (per-basis-vector absmax scaling).
+static int upload_expanded_weights(sb_unit *u, SliceDev &sd, const double *basis, std::vector<float> &vscale) {
+    const int ph = mode_phases(u->mode), by = mode_bytes(u->mode), lpt = kTcM / ph;
+    const int64_t rows = (int64_t)ph * sd.L16, K = sd.Kpad;
+    vscale.assign(sd.L, 1.0f);
+    if (u->mode == kModeE4M3)
+        for (int l = 0; l < sd.L; ++l) {
+            double m = 0.0;
+            for (int q = 0; q < sd.Q; ++q) m = std::max(m, std::fabs(basis[(int64_t)l * sd.Q + q]));
+            vscale[l] = m > 0.0 ? (float)(m / 448.0) : 1.0f;
+        }
+    std::vector<uint8_t> w((size_t)(rows * K * by), 0);
+    for (int64_t t = 0; t < sd.L16 / lpt; ++t)
+        for (int r = 0; r < ph; ++r)
+            for (int ll = 0; ll < lpt; ++ll) {
+                const int64_t l = lpt * t + ll;
                 if (l >= sd.L) continue;
-                const int64_t row = 128 * t + 16 * r + ll;
+                const int64_t row = kTcM * t + lpt * r + ll;
                 for (int64_t j = 0; j < K; ++j) {
                     const int64_t q = r + sd.Q - 1 + sd.phi - j;
-                    if (q >= 0 && q < sd.Q) w[row * K + j] = to16((float)basis[l * sd.Q + q], u->bf16);
+                    if (q >= 0 && q < sd.Q) put_elem(w, row * K + j, (float)(basis[l * sd.Q + q] / vscale[l]), u->mode);
                 }
             }
-    int rc = dev_alloc_w(u, &sd.W16, w.size() * 2);
+    int rc = dev_alloc_w(u, &sd.W16, w.size());
     if (rc) return rc;
-    CK(cudaMemcpy(sd.W16, w.data(), w.size() * 2, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sd.W16, w.data(), w.size(), cudaMemcpyHostToDevice));
     CUtensorMap m;
-    if ((rc = encode_map(&m, sd.W16, u->bf16, K, rows, kTcM))) return rc;
+    if ((rc = encode_map(&m, sd.W16, u->mode, K, rows, kTcM))) return rc;
     return upload_map(u, m, &sd.mapW, true);
 }
 
-static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d) {
+// Stacked mixing matrix of every level in the operand type.  E4M3: the basis
+// outputs are stored divided by a static per-level scale s_o, so the mixing
+// columns carry s_o, and each row is scaled by 448 / its absmax (kept in rscale
+// for the epilogue); colscale = basis scale / s_o for the basis FIR epilogue.
+static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d, const std::vector<std::vector<float>> &vscale) {
     const int64_t M2 = 2 * (int64_t)u->M;
+    const int by = mode_bytes(u->mode);
     for (auto &L : u->levels) {
         if (L.Lk_pad == 0) continue;
-        std::vector<uint16_t> m((size_t)(M2 * L.Lk_pad), to16(0.0f, u->bf16));
+        const float so = u->mode == kModeE4M3 ? e4m3_out_scale(L.k) : 1.0f;
+        std::vector<float> rs(M2, 1.0f), cs(L.Lk_pad, 0.0f);
+        if (u->mode == kModeE4M3) {
+            for (int64_t a = 0; a < M2; ++a) {
+                double m = 0.0;
+                for (int s : L.slices)
+                    for (int l = 0; l < u->slices[s].L; ++l)
+                        m = std::max(m, std::fabs(d->slices[s].mixing[a * u->slices[s].L + l]) * so);
+                rs[a] = m > 0.0 ? (float)(m / 448.0) : 1.0f;
+            }
+            for (int s : L.slices)
+                for (int l = 0; l < u->slices[s].L; ++l) cs[u->slices[s].o_col16 + l] = vscale[s][l] / so;
+        }
+        std::vector<uint8_t> m((size_t)(M2 * L.Lk_pad * by), 0);
         for (int s : L.slices) {
             const SliceDev &sd = u->slices[s];
             const double *mx = d->slices[s].mixing;
             for (int64_t a = 0; a < M2; ++a)
-                for (int l = 0; l < sd.L; ++l) m[a * L.Lk_pad + sd.o_col16 + l] = to16((float)mx[a * sd.L + l], u->bf16);
+                for (int l = 0; l < sd.L; ++l)
+                    put_elem(m, a * L.Lk_pad + sd.o_col16 + l, (float)(mx[a * sd.L + l] * so / rs[a]), u->mode);
         }
         int rc;
-        if ((rc = dev_alloc_w(u, &L.M16, M2 * L.Lk_pad * 2))) return rc;
-        CK(cudaMemcpy(L.M16, m.data(), m.size() * 2, cudaMemcpyHostToDevice));
+        if ((rc = dev_alloc_w(u, &L.M16, m.size()))) return rc;
+        CK(cudaMemcpy(L.M16, m.data(), m.size(), cudaMemcpyHostToDevice));
         CUtensorMap hm;
-        if ((rc = encode_map(&hm, L.M16, u->bf16, L.Lk_pad, M2, 128))) return rc;
+        if ((rc = encode_map(&hm, L.M16, u->mode, L.Lk_pad, M2, 128))) return rc;
         if ((rc = upload_map(u, hm, &L.mapM, true))) return rc;
+        if (u->mode == kModeE4M3) {
+            if ((rc = dev_alloc_w(u, (void **)&L.rscale, M2 * 4))) return rc;
+            CK(cudaMemcpy(L.rscale, rs.data(), M2 * 4, cudaMemcpyHostToDevice));
+            if ((rc = dev_alloc_w(u, (void **)&L.colscale, L.Lk_pad * 4))) return rc;
+            CK(cudaMemcpy(L.colscale, cs.data(), L.Lk_pad * 4, cudaMemcpyHostToDevice));
+        }
     }
     return SB_OK;
 }
@@ -636,8 +704,9 @@ static int alloc_state(sb_unit *u) {
         } else if (u->flags & SB_FLAG_KEEP_SNR) {
             want((void **)&L.ynew, M2 * L.ldy * 4);
         }
-        want(&L.x16, L.x16_len * 2);
-        if (L.Lk_pad > 0) want(&L.O16, (L.Bk_max + 256) * L.Lk_pad * 2);
+        want(&L.x16, L.x16_len * mode_bytes(u->mode));
+        if (L.Lk_pad > 0) want(&L.O16, (L.Bk_max + 256) * L.Lk_pad * mode_bytes(u->mode));
+        if (u->mode == kModeE4M3) want((void **)&L.amax, 2 * 4);
     }
     if (u->tc) {
         u->part_rec_max = ((u->Bmax + 255) / 256) * 4;
@@ -663,7 +732,7 @@ static int alloc_state(sb_unit *u) {
     for (auto &L : u->levels) {
         if (!u->tc || L.Lk_pad == 0) continue;
         CUtensorMap ho;
-        if ((rc = encode_map(&ho, L.O16, u->bf16, L.Lk_pad, L.Bk_max + 256, 256))) return rc;
+        if ((rc = encode_map(&ho, L.O16, u->mode, L.Lk_pad, L.Bk_max + 256, 256))) return rc;
         if ((rc = upload_map(u, ho, &L.mapO, false))) return rc;
     }
     CK(cudaStreamSynchronize(u->ctx->alloc_stream));
@@ -710,6 +779,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
     u->precision = d->precision;
     u->tc = is_tc(d->precision);
     u->bf16 = d->precision == SB_BF16;
+    u->mode = tc_mode(d->precision);
     u->refine = u->tc && d->refine_threshold > 0.0f;
     u->flags = d->flags;
     u->thr = d->threshold;
@@ -756,6 +826,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
     std::vector<std::vector<float>> mcat(P.kmax + 1);
     for (int k = 0; k <= P.kmax; ++k) mcat[k].assign(M2 * u->levels[k].Lk, 0.0f);
     std::vector<int> row_of_level(P.kmax + 1, 0);
+    std::vector<std::vector<float>> vscale(d->n_slices);
     u->flops_per_s = plan_flops(d);
     for (int s = 0; s < d->n_slices; ++s) {
         const sb_slice &sl = d->slices[s];
@@ -782,7 +853,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
             sd.o_col16 = (int)P.o_col16[s];
             sd.X0 = P.X0[s];
             sd.phi = P.phi[s];
-            if ((rc = upload_expanded_weights(u, sd, sl.basis))) return cleanup(rc);
+            if ((rc = upload_expanded_weights(u, sd, sl.basis, vscale[s]))) return cleanup(rc);
         }
         u->levels[sd.level].slices.push_back(s);
         u->slices.push_back(sd);
@@ -793,7 +864,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         if (cudaMemcpy(L.Mcat, mcat[k].data(), mcat[k].size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(fail(SB_ECUDA, "mixing upload"));
     }
-    if (u->tc && (rc = upload_tc_mixing_and_maps(u, d))) return cleanup(rc);
+    if (u->tc && (rc = upload_tc_mixing_and_maps(u, d, vscale))) return cleanup(rc);
     std::vector<int64_t> ids(u->M);
     for (int i = 0; i < u->M; ++i) ids[i] = d->template_ids ? d->template_ids[i] : i;
     if ((rc = dev_alloc_w(u, (void **)&u->tids, u->M * 8))) return cleanup(rc);
@@ -831,6 +902,7 @@ extern "C" int svdbank_create_like(sb_ctx *c, sb_unit *src, int32_t detector, sb
     u->precision = src->precision;
     u->tc = src->tc;
     u->bf16 = src->bf16;
+    u->mode = src->mode;
     u->refine = src->refine;
     u->flags = src->flags;
     u->thr = src->thr;
@@ -844,6 +916,7 @@ extern "C" int svdbank_create_like(sb_ctx *c, sb_unit *src, int32_t detector, sb
     u->tids = src->tids;
     u->levels = src->levels;
     for (auto &L : u->levels) {                  // fresh streaming state, shared weights
+        L.amax = nullptr;
         L.dbuf[0] = L.dbuf[1] = nullptr;
         L.dcur = 0;
         L.last_Bk = 0;
@@ -1149,17 +1222,19 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     std::vector<std::vector<UpTask>> ups(kall + 1);
     std::vector<std::vector<GemmTask>> recon(kall + 1);
     std::vector<WinTask> win;
-    // tensor-core modes, indexed [bf16 ? 1 : 0]
-    std::vector<HalfConvTask> conv[2];
-    std::vector<TcFirTask> tfir[2];
-    std::vector<std::vector<TcMixUpTask>> tmix[2] = {std::vector<std::vector<TcMixUpTask>>(kall + 1),
-                                                     std::vector<std::vector<TcMixUpTask>>(kall + 1)};
+    // tensor-core modes, indexed by operand mode (kModeF16, kModeBF16, kModeE4M3)
+    constexpr int NM = 3;
+    std::vector<HalfConvTask> conv[NM];
+    std::vector<TcFirTask> tfir[NM];
+    std::vector<std::vector<TcMixUpTask>> tmix[NM] = {std::vector<std::vector<TcMixUpTask>>(kall + 1),
+                                                      std::vector<std::vector<TcMixUpTask>>(kall + 1),
+                                                      std::vector<std::vector<TcMixUpTask>>(kall + 1)};
     std::vector<WinFinTask> wfin;
     std::vector<RefUnit> refu;
     int64_t ref_flag_total = 0, ref_slot_floats = 0, ref_max_records = 0;
     int ref_max_tiles = 0, ref_max_items = 0;
     std::vector<CopyTask> yshift1, yshift2;
-    int kpad_max[2] = {0, 0};
+    int kpad_max[NM] = {0, 0, 0};
     int max_hd = 0, max_hy = 0, max_rows = 0;
     int64_t trig_need = 0;
 
@@ -1191,8 +1266,10 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 decim[k].push_back(dt);
             }
             if (u->tc) {
-                const int h = u->bf16 ? 1 : 0;
-                conv[h].push_back(HalfConvTask{L.dbuf[nb], L.x16, L.Hd + Bk});
+                const int h = u->mode;
+                float *am = L.amax ? L.amax + u->amax_cur : nullptr;
+                float *am_next = L.amax ? L.amax + (1 - u->amax_cur) : nullptr;
+                conv[h].push_back(HalfConvTask{L.dbuf[nb], L.x16, L.Hd + Bk, am, am_next});
                 for (int s : L.slices) {
                     const SliceDev &sd = u->slices[s];
                     TcFirTask f{};
@@ -1205,7 +1282,9 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     f.Kpad = sd.Kpad;
                     f.Bk = (int32_t)Bk;
                     f.tiles_n = (int32_t)(((Bk + 7) / 8 + kTcN - 1) / kTcN);
-                    f.tiles_m = sd.L16 / 16;
+                    f.tiles_m = sd.L16 / (kTcM / mode_phases(u->mode));
+                    f.xamax = am;
+                    f.colscale = L.colscale;
                     tfir[h].push_back(f);
                     kpad_max[h] = std::max(kpad_max[h], sd.Kpad);
                 }
@@ -1233,6 +1312,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     mt.tiles_t = (int32_t)((Bk + 255) / 256);
                     mt.tiles_a = (M2 + 127) / 128;
                     mt.n_rec = mt.tiles_t * 4;
+                    mt.rscale = L.rscale;
                     tmix[h][k].push_back(mt);
                 }
                 if (k >= 1) {           // next push's interpolation history: columns [Bk, Bk + Hy) -> [0, Hy)
@@ -1419,9 +1499,10 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     const int fir_tiles = assign_tiles(fir);
     std::vector<int> recon_tiles(kall + 1);
     for (int k = 0; k <= kall; ++k) recon_tiles[k] = assign_tiles(recon[k]);
-    int tfir_tiles[2] = {0, 0};
-    std::vector<int> tmix_tiles[2] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0)};
-    for (int h = 0; h < 2; ++h) {
+    int tfir_tiles[NM] = {0, 0, 0};
+    std::vector<int> tmix_tiles[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
+                                       std::vector<int>(kall + 1, 0)};
+    for (int h = 0; h < NM; ++h) {
         for (auto &f : tfir[h]) {
             f.tile_begin = tfir_tiles[h];
             tfir_tiles[h] += f.tiles_m * f.tiles_n;
@@ -1454,9 +1535,10 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         o_recon[k] = pk.add(recon[k].data(), recon[k].size() * sizeof(GemmTask));
     }
     const size_t o_win = pk.add(win.data(), win.size() * sizeof(WinTask));
-    size_t o_conv[2], o_tfir[2];
-    std::vector<size_t> o_tmix[2] = {std::vector<size_t>(kall + 1), std::vector<size_t>(kall + 1)};
-    for (int h = 0; h < 2; ++h) {
+    size_t o_conv[NM], o_tfir[NM];
+    std::vector<size_t> o_tmix[NM] = {std::vector<size_t>(kall + 1), std::vector<size_t>(kall + 1),
+                                      std::vector<size_t>(kall + 1)};
+    for (int h = 0; h < NM; ++h) {
         o_conv[h] = pk.add(conv[h].data(), conv[h].size() * sizeof(HalfConvTask));
         o_tfir[h] = pk.add(tfir[h].data(), tfir[h].size() * sizeof(TcFirTask));
         for (int k = 0; k <= kall; ++k) o_tmix[h][k] = pk.add(tmix[h][k].data(), tmix[h][k].size() * sizeof(TcMixUpTask));
@@ -1509,11 +1591,11 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
              })))
             return rc;
     // 16-bit copies of the decimated strain for the tensor-core FIR
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < NM; ++h)
         if (!conv[h].empty() && (rc = run_stage(c, SB_STAGE_DECIMATE, [&](int *n) {
                                      *n = 1;
                                      return launch_to_half((HalfConvTask *)(D + o_conv[h]), (int)conv[h].size(),
-                                                           h == 1, st);
+                                                           h, st);
                                  })))
             return rc;
     // 4. a2 basis FIR, all slices of all units at once
@@ -1522,11 +1604,11 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                              return launch_gemm_fp32((GemmTask *)(D + o_fir), (int)fir.size(), fir_tiles, st);
                          })))
         return rc;
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < NM; ++h)
         if (!tfir[h].empty() && (rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
                                      *n = 1;
                                      return launch_tc_fir((TcFirTask *)(D + o_tfir[h]), (int)tfir[h].size(),
-                                                          tfir_tiles[h], kpad_max[h], h == 1, derr, st);
+                                                          tfir_tiles[h], kpad_max[h], h, derr, st);
                                  })))
             return rc;
     // 5. a4 + a3 from the lowest rate up
@@ -1544,12 +1626,12 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                  return launch_gemm_fp32((GemmTask *)(D + o_recon[k]), (int)recon[k].size(), recon_tiles[k], st);
              })))
             return rc;
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < NM; ++h)
             if (!tmix[h][k].empty() &&
                 (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
                      *n = 1;
                      return launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
-                                            tmix_tiles[h][k], c->g, h == 1, derr, st);
+                                            tmix_tiles[h][k], c->g, h, derr, st);
                  })))
                 return rc;
     }
@@ -1628,6 +1710,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         if (first_n + B > std::max<int64_t>(first_n, 0)) u->wcur = 1 - u->wcur;
         u->T += B;
         u->last_B = B;
+        u->amax_cur = 1 - u->amax_cur;
     }
     return SB_OK;
 }

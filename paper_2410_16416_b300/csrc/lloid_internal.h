@@ -118,12 +118,15 @@ struct TrigOut {
 
 // ---- tensor-core path (kernels_tc.cu) ---------------------------------------
 constexpr int kTcM = 128;   // MMA M (rows of the A operand per tile)
+constexpr int kModeF16 = 0, kModeBF16 = 1, kModeE4M3 = 2;   // tensor-core operand modes
 constexpr int kTcN = 256;   // MMA N (columns of the accumulator per tile)
 
-struct HalfConvTask {       // dst[i] = 16-bit(src[i]), i < n
+struct HalfConvTask {       // dst[i] = narrow(src[i]), i < n (E4M3: scaled by 448 / absmax)
     const float *src;
     void *dst;
     int64_t n;
+    float *amax;               // E4M3: this push's |src| maximum (accumulated by absmax_kernel)
+    float *amax_next;          // E4M3: the next push's accumulator, zeroed here
 };
 
 // a2 on tensor cores.  Tile (mt, nt): W rows [128 mt, 128 mt + 128) (16 basis
@@ -137,9 +140,11 @@ struct TcFirTask {
     int32_t o_col;             // column of this slice's first basis vector in O
     int32_t Kpad;              // multiple of 64
     int32_t Bk;                // outputs m' < Bk are written
-    int32_t tiles_m;           // L16 / 16
+    int32_t tiles_m;           // padded basis vectors / basis vectors per tile
     int32_t tiles_n;
     int32_t tile_begin;
+    const float *xamax;        // E4M3: |strain| maximum of this push at this level
+    const float *colscale;     // E4M3: per output column, basis scale / output scale
 };
 
 // Partial window maximum of one template over one column run of one tile.
@@ -166,6 +171,7 @@ struct TcMixUpTask {
     int32_t lam;               // Lambda of this level
     int32_t in_off;            // Lambda_{k+1} + Hy_{k+1}: coarser position of (relative index 0) / 2
     int32_t tiles_t, tiles_a, tile_begin, n_rec;
+    const float *rscale;       // E4M3: per mixing row (filter) scale
 };
 
 // Window bookkeeping after the top-level partial maxima: one warp per
@@ -187,12 +193,12 @@ struct WinFinTask {
     int32_t pad;
 };
 
-size_t tc_fir_smem_bytes(int kpad_max);
+size_t tc_fir_smem_bytes(int kpad_max, int mode);
 size_t tc_mixup_smem_bytes();
-cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, bool bf16, cudaStream_t s);
-cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, bool bf16, int *err,
+cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
+cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s);
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g, bool bf16,
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g, int mode,
                             int *err, cudaStream_t s);
 cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                                 cudaStream_t s);

@@ -106,6 +106,16 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// Same with 8-bit operands (kind::f8f6f4; A and B both E4M3 here), FP32 accumulate.
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // Arrive on `bar` once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -150,9 +160,9 @@ __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) { return smem_d
 // 8-row groups 128 bytes apart; no swizzle.
 __device__ __forceinline__ uint64_t desc_hankel(uint32_t saddr) { return smem_desc(saddr, 16, 128, 0); }
 
-// Instruction descriptor, kind::f16: D format F32 (bits 4-5 = 1), A/B format
-// (bits 7-9 / 10-12: 0 = F16, 1 = BF16), both K-major, N >> 3 at bit 17,
-// M >> 4 at bit 24.
+// Instruction descriptor: D format F32 (bits 4-5 = 1), A/B format (bits 7-9 /
+// 10-12; kind::f16: 0 = F16, 1 = BF16; kind::f8f6f4: 0 = E4M3), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
     return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);

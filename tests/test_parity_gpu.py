@@ -312,3 +312,54 @@ def test_refined_production_injection(lloid):
     print("refined", hit["snr"][0], "oracle", amax[0, 0], "samples", hit["sample"][0], n_star[0, 0])
     assert abs(hit["snr"][0] - amax[0, 0]) <= 1e-3
     assert hit["sample"][0] == n_star[0, 0]
+
+
+# ---------------------------------------------------------------- E4M3 mode (config 4)
+def test_fp8_small_bin_error_distribution_and_refinement(lloid, small_case):
+    """E4M3 basis FIR and mixing (per-vector / per-buffer absmax scales, FP32 accumulate):
+    the unrefined SNR error distribution is reported and bounded loosely; every trigger
+    (window maximum above 5.5) is refined in FP32 and matches the oracle within 1e-3."""
+    spec, h, bank, d, x = small_case
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, precision="fp8", threshold=6.0, refine_threshold=5.5, max_push_samples=4096,
+                        keep_snr=True)
+    (xg,) = push_and_collect(ctx, [u], [d], [4096] * 8)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    ctx.close()
+    n = xg.shape[1]
+    rg = xg[0::2].astype(np.float64) + 1j * xg[1::2]
+    ro = x[0::2, :n] + 1j * x[1::2, :n]
+    err = np.abs(rg - ro)
+    rel = err / np.maximum(1.0, np.abs(ro))
+    q = np.percentile(err, [50, 99, 100])
+    print(f"fp8 unrefined |rho| error p50 {q[0]:.4f} p99 {q[1]:.4f} max {q[2]:.4f}; max rel {rel.max():.4f}")
+    assert rel.max() <= 0.25
+    assert len(trig) >= 1 and np.all(trig["flags"] & lloid.SB_TRIG_REFINED)
+    assert check_triggers(trig, x, 2048, 6.0, n, 1e-3, absolute=True) >= 1
+
+
+def test_fp8_production_refined_injection(lloid):
+    spec = synth.PRODUCTION_BIN
+    h, _ = synth.template_bank(spec.n_templates, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 2, 0, 0)
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    n = 96 * 4096
+    d = synth.white_noise(n, 2, 0, 1)
+    synth.inject(d, h, 500, 80 * 4096 + 99, 30.0, -0.8)
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, precision="fp8", threshold=6.0, refine_threshold=5.5, max_push_samples=16 * 4096)
+    for t in range(0, n, 16 * 4096):
+        u.push(d[t:t + 16 * 4096], t)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    ctx.close()
+    hit = trig[(trig["template_id"] == 500) & (trig["window"] == 80)]
+    assert len(hit) == 1 and hit["flags"][0] & lloid.SB_TRIG_REFINED
+    rows = np.array([1000, 1001])
+    sub = oracle.OracleBank(1, bank.top_rate_hz,
+                            [oracle.OracleSlice(s.rate_hz, s.t_start_s, s.t_end_s, s.level, s.delay, s.basis,
+                                                s.mixing[rows], s.sigma) for s in bank.slices])
+    xo = oracle.lloid_snr(sub, d)
+    wins, n_star, amax, ph = oracle.window_maxima(xo, 4096, 81 * 4096, 80 * 4096)
+    print("fp8 refined", hit["snr"][0], "oracle", amax[0, 0])
+    assert abs(hit["snr"][0] - amax[0, 0]) <= 1e-3 and hit["sample"][0] == n_star[0, 0]
