@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
         const int a = kMixRows * at + R;
         const bool row_ok = a < t.M2;
         const float *src = t.Ysrc ? t.Ysrc + (int64_t)(row_ok ? a : 0) * t.ld_src : nullptr;
-        const float rsc = (MODE == kModeE4M3 && row_ok) ? t.rscale[a] : 1.0f;   // E4M3: mixing-row scale
+        // E4M3: mixing-row scale (levels without slices have no mixing and no scale)
+        const float rsc = (MODE == kModeE4M3 && row_ok && t.rscale) ? t.rscale[a] : 1.0f;
         const bool top = t.part != nullptr;
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {

@@ -1281,7 +1281,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     f.o_col = sd.o_col16;
                     f.Kpad = sd.Kpad;
                     f.Bk = (int32_t)Bk;
-                    f.tiles_n = (int32_t)(((Bk + 7) / 8 + kTcN - 1) / kTcN);
+                    const int64_t ph = mode_phases(u->mode);       // samples per Hankel block
+                    f.tiles_n = (int32_t)(((Bk + ph - 1) / ph + kTcN - 1) / kTcN);
                     f.tiles_m = sd.L16 / (kTcM / mode_phases(u->mode));
                     f.xamax = am;
                     f.colscale = L.colscale;
