@@ -248,12 +248,14 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU arm
 def roofline_of(stages, flops, bytes_, precision, steps, peaks):
-    """Bound, achieved and fraction of the stage that takes the most device time."""
+    """Bound, achieved and fraction of the stage that takes the most device time among the stages
+    with an algorithmic model (the refinement's work depends on how many candidates the data
+    produce, so it has none and is reported through its time share only)."""
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12            # FP32 FFMA lanes x 2 FLOP x max clock
     tensor_peak = peaks.get("bf16_tflops", 1800.0)             # dense BF16 = FP16 rate, burst (short steps)
-    busy = {k: v[0] for k, v in stages.items() if v[1] > 0}
+    busy = {k: v[0] for k, v in stages.items() if v[1] > 0 and (flops.get(k, 0.0) > 0 or bytes_.get(k, 0.0) > 0)}
     dom = max(busy, key=busy.get)
     dom_ms, _ = stages[dom]
     on_tensor = precision in ("bf16", "fp16") and dom in ("fir", "mix")

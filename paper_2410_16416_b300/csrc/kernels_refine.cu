@@ -37,7 +37,8 @@ __device__ __forceinline__ void tile_ranges(const RefUnit &u, int tt, const int 
 // range to cover R samples on either side of the candidate's maximum.
 __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restrict__ units, int n_units,
                                                           int *__restrict__ flags, int *__restrict__ tlo,
-                                                          int *__restrict__ thi) {
+                                                          int *__restrict__ thi, RefCand *__restrict__ cands,
+                                                          int *__restrict__ counters, int cand_cap) {
     const RefUnit &u = units[blockIdx.y];
     const int64_t total = (int64_t)u.M * u.n_rec;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -50,6 +51,9 @@ __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restr
         flags[u.flag_off + tt] = 1;
         atomicMin(&tlo[u.flag_off + tt], max(c - kRefR, c0));
         atomicMax(&thi[u.flag_off + tt], min(c + kRefR, c1));
+        const int slot = atomicAdd(&counters[1], 1);
+        if (slot < cand_cap) cands[slot] = RefCand{(int)blockIdx.y, idx};
+        else atomicExch(&counters[2], 1);
     }
 }
 
@@ -116,18 +120,18 @@ __global__ void __launch_bounds__(128) refine_candidate_kernel(const RefUnit *__
                                                                const int *__restrict__ flags,
                                                                const int *__restrict__ tlo, const int *__restrict__ thi,
                                                                const int *__restrict__ counters,
+                                                               const RefCand *__restrict__ cands, int cand_cap,
                                                                const float *__restrict__ obuf, int64_t slot_floats,
-                                                               Halfband g, int cand_cap) {
+                                                               Halfband g) {
     __shared__ float ya[2][kRefRange(0)], yb[2][kRefRange(0)];
     __shared__ float red_m[128];
     __shared__ int red_c[128];
-    // candidate = (unit, template, record) enumerated over all records above threshold
-    const int u_idx = blockIdx.y;
-    const RefUnit &u = units[u_idx];
-    const int64_t total = (int64_t)u.M * u.n_rec;
-    for (int64_t idx = blockIdx.x; idx < total; idx += gridDim.x) {
+    const int n_cand = min(counters[1], cand_cap);
+    for (int ci = blockIdx.x; ci < n_cand; ci += gridDim.x) {
+        const RefCand cand = cands[ci];
+        const RefUnit &u = units[cand.unit];
+        const int64_t idx = cand.idx;
         WinPart rec = u.part[idx];
-        if (!(rec.mag2 > u.thr2)) continue;
         const int i = (int)(idx / u.n_rec), r = (int)(idx % u.n_rec);
         const int tt = r / 4;
         const int slot = flags[u.flag_off + tt];
@@ -217,12 +221,16 @@ cudaError_t launch_refine(const RefUnit *d_units, int n_units, int max_tiles, in
     if (n_units == 0) return cudaSuccess;
     const int fb = (int)std::min<int64_t>(1024, (max_records + 255) / 256);
     int *tlo = flags + max_tiles_total, *thi = tlo + max_tiles_total;
-    refine_flag_kernel<<<dim3(fb, n_units), 256, 0, s>>>(d_units, n_units, flags, tlo, thi);
+    // candidate list after the three int arrays, 16-byte aligned (the allocation has 16 bytes of slack)
+    RefCand *cands = reinterpret_cast<RefCand *>((reinterpret_cast<uintptr_t>(thi + max_tiles_total) + 15) &
+                                                 ~uintptr_t(15));
+    refine_flag_kernel<<<dim3(fb, n_units), 256, 0, s>>>(d_units, n_units, flags, tlo, thi, cands, counters,
+                                                         kRefCandCap);
     refine_slot_kernel<<<dim3((max_tiles + 255) / 256, n_units), 256, 0, s>>>(d_units, n_units, flags, slots,
                                                                                counters, cap);
     refine_fir_kernel<<<dim3(cap, max_items), 256, 0, s>>>(d_units, slots, counters, tlo, thi, obuf, slot_floats);
-    refine_candidate_kernel<<<dim3(148, n_units), 128, 0, s>>>(d_units, n_units, flags, tlo, thi, counters, obuf,
-                                                               slot_floats, g, cap);
+    refine_candidate_kernel<<<4 * 148, 128, 0, s>>>(d_units, n_units, flags, tlo, thi, counters, cands,
+                                                    kRefCandCap, obuf, slot_floats, g);
     return cudaGetLastError();
 }
 

@@ -1648,7 +1648,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             c->ref_obuf = nullptr;
             c->ref_flags_cap = std::max(ref_flag_total, 2 * c->ref_flags_cap);
             c->ref_slot_floats = std::max(ref_slot_floats, c->ref_slot_floats);
-            CK(cudaMalloc(&c->ref_flags, 3 * c->ref_flags_cap * sizeof(int)));
+            CK(cudaMalloc(&c->ref_flags, 3 * c->ref_flags_cap * sizeof(int) + kRefCandCap * sizeof(RefCand) + 16));
             c->ref_cap = std::max(c->ref_cap, kRefCap);
             CK(cudaMalloc(&c->ref_obuf, (size_t)c->ref_cap * c->ref_slot_floats * sizeof(float)));
             if (c->ref_slots) cudaFree(c->ref_slots);

@@ -228,7 +228,13 @@ struct RefUnit {                         // one unit of a push with refinement o
 struct RefSlot {
     int32_t unit, tt;
 };
-// flags: 3 x max_tiles_total ints: flag/slot, then the first and last refined column per tile
+struct RefCand {                         // one partial record to refine
+    int32_t unit;
+    int64_t idx;                         // i * n_rec + record
+};
+constexpr int kRefCandCap = 1 << 16;
+// flags: 3 x max_tiles_total ints (flag/slot, first and last refined column per tile), then
+// kRefCandCap RefCand entries
 cudaError_t launch_refine(const RefUnit *d_units, int n_units, int max_tiles, int64_t max_tiles_total,
                           int64_t max_records, int *flags, RefSlot *slots, int *counters, int cap, float *obuf,
                           int64_t slot_floats, int max_items, const Halfband &g, cudaStream_t s);
