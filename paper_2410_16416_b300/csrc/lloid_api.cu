@@ -91,6 +91,8 @@ struct SliceDev {
     int level = 0, L = 0, Q = 0;
     int64_t D = 0;
     float *V = nullptr;       // [L x Q] (FP32 mode)
+    float *H = nullptr;       // [2M x ldh] reconstructed FP32 slice filters (refinement in the 16/8-bit modes)
+    int ldh = 0;
     int o_row = 0;            // first row in the level's basis-output block
     // tensor-core modes: 8-phase expanded weights and their TMA map
     void *W16 = nullptr;      // [phases x L16 x Kpad] 16- or 8-bit expanded weights
@@ -170,14 +172,9 @@ struct sb_ctx {
     int timeout_code = 0;      // first bounded device wait that expired (0: none)
     std::mutex mu;
     sb_ctx_stats stats{};
-    // FP32 refinement scratch (grown on demand, shared by the pushes of this context)
-    int *ref_flags = nullptr;
-    int64_t ref_flags_cap = 0;
-    RefSlot *ref_slots = nullptr;
+    // FP32 refinement scratch (allocated on the first refined push, shared by later pushes)
+    RefCand *ref_cands = nullptr;
     int *ref_counters = nullptr;
-    float *ref_obuf = nullptr;
-    int64_t ref_slot_floats = 0;
-    int ref_cap = 0;
     // profiling: event pairs around each launch, summed per stage on query
     bool prof = false;
     struct Mark { int stage; cudaEvent_t a, b; };
@@ -405,9 +402,8 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
                   : (int64_t)d->slices[s].n_basis * d->slices[s].n_taps * 4;
     b += 2 * (int64_t)d->n_templates * sizeof(WinState) + d->n_templates * 8;
     if (P.tc) b += ((d->max_push_samples + 255) / 256) * 4 * (int64_t)d->n_templates * sizeof(WinPart);
-    if (P.tc && d->refine_threshold > 0.0f)            // FP32 basis and mixing for the refinement
-        for (int s = 0; s < S; ++s)
-            b += (int64_t)d->slices[s].n_basis * (d->slices[s].n_taps + M2) * 4;
+    if (P.tc && d->refine_threshold > 0.0f)            // FP32 reconstructed slice filters for the refinement
+        for (int s = 0; s < S; ++s) b += M2 * round_up(d->slices[s].n_taps, 4) * 4;
     P.bytes = b;
     return SB_OK;
 }
@@ -481,10 +477,8 @@ extern "C" int sb_ctx_destroy(sb_ctx *c) {
     }
     release_marks(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-    if (c->ref_flags) cudaFree(c->ref_flags);
-    if (c->ref_slots) cudaFree(c->ref_slots);
+    if (c->ref_cands) cudaFree(c->ref_cands);
     if (c->ref_counters) cudaFree(c->ref_counters);
-    if (c->ref_obuf) cudaFree(c->ref_obuf);
     if (c->stream) cudaStreamSynchronize(c->stream);      // unit memory returned on the work stream
     if (c->pop_stream) cudaStreamDestroy(c->pop_stream);
     if (c->alloc_stream) cudaStreamDestroy(c->alloc_stream);
@@ -565,6 +559,53 @@ static int upload_map(sb_unit *u, const CUtensorMap &h, CUtensorMap **dev, bool 
     int rc = weights ? dev_alloc_w(u, (void **)dev, sizeof(CUtensorMap)) : dev_alloc(u, (void **)dev, sizeof(CUtensorMap));
     if (rc) return rc;
     CK(cudaMemcpy(*dev, &h, sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    return SB_OK;
+}
+
+// The refinement's filters: H_s = M_s V_s, each template's two real FP32
+// filters of slice s (Eq. 4 summed over the basis), one FP32 GEMM on the device
+// at create time; [2M][ldh] rows, ldh = Q rounded up to 4.
+static int build_refine_filters(sb_unit *u, SliceDev &sd, const sb_slice &sl) {
+    const int64_t M2 = 2 * (int64_t)u->M;
+    sd.ldh = (int)round_up(sd.Q, 4);
+    int rc = dev_alloc_w(u, (void **)&sd.H, M2 * sd.ldh * 4);
+    if (rc) return rc;
+    std::vector<float> a((size_t)M2 * sd.L), v((size_t)sd.L * sd.Q);
+    for (size_t i = 0; i < a.size(); ++i) a[i] = (float)sl.mixing[i];
+    for (size_t i = 0; i < v.size(); ++i) v[i] = (float)sl.basis[i];
+    cudaStream_t st = u->ctx->alloc_stream;
+    float *dA = nullptr, *dV = nullptr;
+    GemmTask *dT = nullptr;
+    GemmTask t{};
+    t.lda = sd.L;
+    t.ldb = sd.Q;
+    t.ldc = sd.ldh;
+    t.M = (int32_t)M2;
+    t.N = sd.Q;
+    t.K = sd.L;
+    t.tiles_n = (sd.Q + kGemmTN - 1) / kGemmTN;
+    const int tiles = (int)((M2 + kGemmTM - 1) / kGemmTM) * t.tiles_n;
+    cudaError_t e = cudaMallocAsync(&dA, a.size() * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dV, v.size() * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dT, sizeof(GemmTask), st);
+    if (e == cudaSuccess) {
+        t.A = dA;
+        t.B = dV;
+        t.C = sd.H;
+        e = cudaMemcpyAsync(dA, a.data(), a.size() * 4, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dV, v.data(), v.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dT, &t, sizeof(GemmTask), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_gemm_fp32(dT, 1, tiles, st);
+    if (dA) cudaFreeAsync(dA, st);
+    if (dV) cudaFreeAsync(dV, st);
+    if (dT) cudaFreeAsync(dT, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SB_ECUDA, std::string("refinement filters: ") + cudaGetErrorString(e));
+    }
     return SB_OK;
 }
 
@@ -818,7 +859,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
             L.x16_len = P.x16_len[k];
             if (k >= 1) L.ldu = round_up(L.Hy + L.Bk_max, 4);
         }
-        if (L.Lk > 0 && (!u->tc || u->refine)) {
+        if (L.Lk > 0 && !u->tc) {
             if ((rc = dev_alloc_w(u, (void **)&L.Mcat, M2 * L.Lk * 4))) return cleanup(rc);
         }
     }
@@ -837,7 +878,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         sd.D = std::llround(sl.t_start_s * sl.rate_hz);
         sd.o_row = row_of_level[sd.level];
         row_of_level[sd.level] += sd.L;
-        if (!u->tc || u->refine) {
+        if (!u->tc) {
             std::vector<float> v((size_t)sd.L * sd.Q);
             for (size_t i = 0; i < v.size(); ++i) v[i] = (float)sl.basis[i];
             if ((rc = dev_alloc_w(u, (void **)&sd.V, v.size() * 4))) return cleanup(rc);
@@ -854,11 +895,12 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
             sd.X0 = P.X0[s];
             sd.phi = P.phi[s];
             if ((rc = upload_expanded_weights(u, sd, sl.basis, vscale[s]))) return cleanup(rc);
+            if (u->refine && (rc = build_refine_filters(u, sd, sl))) return cleanup(rc);
         }
         u->levels[sd.level].slices.push_back(s);
         u->slices.push_back(sd);
     }
-    for (int k = 0; k <= P.kmax && (!u->tc || u->refine); ++k) {
+    for (int k = 0; k <= P.kmax && !u->tc; ++k) {
         LevelDev &L = u->levels[k];
         if (L.Lk == 0) continue;
         if (cudaMemcpy(L.Mcat, mcat[k].data(), mcat[k].size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1231,8 +1273,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                                                       std::vector<std::vector<TcMixUpTask>>(kall + 1)};
     std::vector<WinFinTask> wfin;
     std::vector<RefUnit> refu;
-    int64_t ref_flag_total = 0, ref_slot_floats = 0, ref_max_records = 0;
-    int ref_max_tiles = 0, ref_max_items = 0;
+    int64_t ref_max_records = 0;
     std::vector<CopyTask> yshift1, yshift2;
     int kpad_max[NM] = {0, 0, 0};
     int max_hd = 0, max_hy = 0, max_rows = 0;
@@ -1416,38 +1457,24 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             r.thr2 = u->refine_thr * u->refine_thr;
             r.kmax = u->kmax;
             r.M = u->M;
-            r.tiles_t = (int32_t)((B + kRefTile - 1) / kRefTile);
-            r.n_rec = r.tiles_t * 4;
+            r.n_rec = (int32_t)((B + kRefTile - 1) / kRefTile) * 4;
             r.B = (int32_t)B;
-            r.flag_off = (int32_t)ref_flag_total;
             r.n_slices = (int32_t)u->slices.size();
-            int64_t off = 0;
             for (int k = 0; k <= u->kmax; ++k) {
                 LevelDev &L = u->levels[k];
                 r.lv_d[k] = L.dbuf[1 - L.dcur];
                 r.lv_origin[k] = (Tp >> k) - L.e - L.Hd;
                 r.lv_len[k] = L.Hd + (B >> k);
-                r.lv_M[k] = L.Mcat;
-                r.lv_Lk[k] = L.Lk;
-                r.lv_off[k] = off;
-                off += (int64_t)L.Lk * kRefRange(k);
             }
-            int items = 0;
             for (size_t si = 0; si < u->slices.size(); ++si) {
                 const SliceDev &sd = u->slices[si];
-                r.sl_V[si] = sd.V;
+                r.sl_H[si] = sd.H;
+                r.sl_ldh[si] = sd.ldh;
                 r.sl_D[si] = sd.D;
-                r.sl_L[si] = sd.L;
                 r.sl_Q[si] = sd.Q;
-                r.sl_row[si] = sd.o_row;
                 r.sl_level[si] = sd.level;
-                items += ((sd.L + kGemmTM - 1) / kGemmTM) * ((kRefRange(sd.level) + kGemmTN - 1) / kGemmTN);
             }
-            ref_flag_total += r.tiles_t;
-            ref_slot_floats = std::max(ref_slot_floats, off);
             ref_max_records = std::max<int64_t>(ref_max_records, (int64_t)r.M * r.n_rec);
-            ref_max_tiles = std::max(ref_max_tiles, (int)r.tiles_t);
-            ref_max_items = std::max(ref_max_items, items);
             refu.push_back(r);
         }
         if (end > start && u->tc) {
@@ -1638,32 +1665,15 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     }
     // a6: FP32 refinement of the top level's candidate maxima (16-bit modes)
     if (!refu.empty()) {
-        const int kRefCap = (int)std::min<int64_t>(1024, std::max<int64_t>(64, 2 * (int64_t)refu.size()));
-        if (c->ref_flags_cap < ref_flag_total || c->ref_slot_floats < ref_slot_floats || !c->ref_counters ||
-            c->ref_cap < kRefCap) {
-            CK(cudaStreamSynchronize(st));
-            if (c->ref_flags) cudaFree(c->ref_flags);
-            if (c->ref_obuf) cudaFree(c->ref_obuf);
-            c->ref_flags = nullptr;
-            c->ref_obuf = nullptr;
-            c->ref_flags_cap = std::max(ref_flag_total, 2 * c->ref_flags_cap);
-            c->ref_slot_floats = std::max(ref_slot_floats, c->ref_slot_floats);
-            CK(cudaMalloc(&c->ref_flags, 3 * c->ref_flags_cap * sizeof(int) + kRefCandCap * sizeof(RefCand) + 16));
-            c->ref_cap = std::max(c->ref_cap, kRefCap);
-            CK(cudaMalloc(&c->ref_obuf, (size_t)c->ref_cap * c->ref_slot_floats * sizeof(float)));
-            if (c->ref_slots) cudaFree(c->ref_slots);
-            CK(cudaMalloc(&c->ref_slots, c->ref_cap * sizeof(RefSlot)));
-            if (!c->ref_counters) CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
+        if (!c->ref_cands) {
+            CK(cudaMalloc(&c->ref_cands, kRefCandCap * sizeof(RefCand)));
+            CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
         }
-        CK(cudaMemsetAsync(c->ref_flags, 0, ref_flag_total * sizeof(int), st));
-        CK(cudaMemsetAsync(c->ref_flags + c->ref_flags_cap, 0x7f, c->ref_flags_cap * sizeof(int), st));  // first column
-        CK(cudaMemsetAsync(c->ref_flags + 2 * c->ref_flags_cap, 0x80, c->ref_flags_cap * sizeof(int), st)); // last
         CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
         if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
-                 *n = 4;
-                 return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_tiles, c->ref_flags_cap,
-                                      ref_max_records, c->ref_flags, c->ref_slots, c->ref_counters, kRefCap,
-                                      c->ref_obuf, c->ref_slot_floats, std::max(1, ref_max_items), c->g, st);
+                 *n = 2;
+                 return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_records, c->ref_cands,
+                                      c->ref_counters, c->g, st);
              })))
             return rc;
     }

@@ -204,40 +204,32 @@ cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int tota
                                 cudaStream_t s);
 
 // ---- FP32 refinement of candidate maxima (kernels_refine.cu) ----------------
-constexpr int kRefTile = 256;            // top-level samples per refinement tile (= mixing tile)
+constexpr int kRefTile = 256;            // top-level samples per record tile (= mixing tile)
 constexpr int kRefR = 8;                 // refined samples on either side of a candidate maximum
 constexpr int kRefMaxLevels = 8;
 constexpr int kRefMaxSlices = 12;
-__host__ __device__ constexpr int kRefRange(int k) { return (kRefTile >> k) + 66; }   // samples of a tile at level k
+constexpr int kRefSpan = 64;             // level-k samples one candidate needs (<= 63 for R = 8)
+constexpr int kRefCandCap = 1 << 16;     // candidates one push refines at most
 
 struct RefUnit {                         // one unit of a push with refinement on
     WinPart *part;                       // [M][n_rec] top-level partial maxima (refined in place)
     int64_t first_n;                     // absolute top-level index of push column 0
     int64_t win_len;
     float thr2;                          // refine threshold squared
-    int32_t kmax, M, n_rec, tiles_t, B, flag_off, n_slices, pad;
+    int32_t kmax, M, n_rec, B, n_slices, pad;
     const float *lv_d[kRefMaxLevels];    // FP32 decimated strain of this push, position 0 = absolute lv_origin
     int64_t lv_origin[kRefMaxLevels], lv_len[kRefMaxLevels];
-    const float *lv_M[kRefMaxLevels];    // FP32 stacked mixing [2M][Lk]
-    int32_t lv_Lk[kRefMaxLevels];
-    int64_t lv_off[kRefMaxLevels];       // float offset of level k's [Lk][kRefRange(k)] block in a slot
-    const float *sl_V[kRefMaxSlices];    // FP32 basis [L][Q]
+    const float *sl_H[kRefMaxSlices];    // FP32 reconstructed slice filters [2M][ldh] (mixing x basis)
     int64_t sl_D[kRefMaxSlices];
-    int32_t sl_L[kRefMaxSlices], sl_Q[kRefMaxSlices], sl_row[kRefMaxSlices], sl_level[kRefMaxSlices];
-};
-struct RefSlot {
-    int32_t unit, tt;
+    int32_t sl_Q[kRefMaxSlices], sl_ldh[kRefMaxSlices], sl_level[kRefMaxSlices];
 };
 struct RefCand {                         // one partial record to refine
     int32_t unit;
     int64_t idx;                         // i * n_rec + record
 };
-constexpr int kRefCandCap = 1 << 16;
-// flags: 3 x max_tiles_total ints (flag/slot, first and last refined column per tile), then
-// kRefCandCap RefCand entries
-cudaError_t launch_refine(const RefUnit *d_units, int n_units, int max_tiles, int64_t max_tiles_total,
-                          int64_t max_records, int *flags, RefSlot *slots, int *counters, int cap, float *obuf,
-                          int64_t slot_floats, int max_items, const Halfband &g, cudaStream_t s);
+// cands: kRefCandCap entries; counters[1] = candidates found, counters[2] = 1 when some were dropped
+cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_records, RefCand *cands, int *counters,
+                          const Halfband &g, cudaStream_t s);
 
 // ---- launchers (kernels_simt.cu) -------------------------------------------
 cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,
