@@ -221,16 +221,28 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
 // interpolation of the coarser level fused into its epilogue.
 //   D[a][m] = sum_l M[a][l] O[m][l]   (TMEM lanes = filters, columns = time)
 //   y_k[a][m] = D[a][m] + sum_j 2 g[j] y_{k+1}[a][(m - j)/2]
-// Each thread owns one filter row: it reads the coarser level's row segment
-// (52 samples per 32 outputs, through L1) and interpolates from registers.  At the top level the epilogue does not store the SNR: it
-// reduces |rho|^2 over its columns into per-window partial maxima.
+// Tile = 128 filters x 256 samples.  Persistent CTAs (one per SM), warp roles:
+//   warp 0   TMA producer: per tile, the K chunks of M and O into a ring of
+//            n_stages stage buffers, then the coarser level's window for each
+//            half tile (128 filters x 100 samples, FP32) into a ring of n_win
+//            window buffers;
+//   warp 1   MMA issuer into one of two TMEM accumulators (256 columns each),
+//            so the next tile's GEMM runs while this tile's epilogue drains;
+//   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) (its 32 filters)
+//            for half tile (w / 4 - 1), takes each filter's 52 coarser samples
+//            per 32 outputs from shared memory and interpolates from registers.
+// At the top level the epilogue does not store the SNR: it reduces |rho|^2
+// over its columns into per-window partial maxima.
 // ---------------------------------------------------------------------------
-constexpr int kMixStages = 2;
 constexpr int kMixRows = 128;                            // filters per tile (MMA M)
 constexpr int kMixCols = 256;                            // time samples per tile (MMA N)
-constexpr int kMixABytes = kMixRows * 64 * 2;            // mixing tile: 128 filters x 64 l
-constexpr int kMixBBytes = kMixCols * 64 * 2;            // basis-output tile: 256 time x 64 l
+constexpr int kMixABytes = kMixRows * 128;               // mixing tile: 128 filters x 128 bytes of K
+constexpr int kMixBBytes = kMixCols * 128;               // basis-output tile: 256 time x 128 bytes of K
 constexpr int kMixStageBytes = kMixABytes + kMixBBytes;
+constexpr int kMixWinCols = 100;                         // coarser samples of a half tile: 64 + 32 taps + 4
+constexpr int kMixWinBytes = kMixRows * kMixWinCols * 4;
+constexpr int kMixThreads = 384;
+constexpr int kMixMaxStages = 2, kMixMaxWin = 3;
 
 // x[j] += interpolated coarser level at column c0 + j.  w[i] holds the staged
 // coarser sample at register index i; PAR = parity of the first column's
@@ -271,41 +283,67 @@ struct SegBest {
     int64_t n;
 };
 
+// Geometry of one tile, identical for every role.
+struct MixTile {
+    const TcMixUpTask *t;
+    int tt, at, nk;
+    int64_t xs0;        // first coarser position of the tile's window (16-byte aligned)
+    int rem, par;
+};
+__device__ __forceinline__ MixTile mix_tile(const TcMixUpTask *tasks, int n_tasks, int tile, int kc_elems) {
+    MixTile m;
+    m.t = &tasks[find_tile(tasks, n_tasks, tile)];
+    const int local = tile - m.t->tile_begin;
+    m.tt = local / m.t->tiles_a;
+    m.at = local % m.t->tiles_a;
+    m.nk = (m.t->Lk_pad + kc_elems - 1) / kc_elems;
+    // coarser-level window of column c0 starts at position A0 - 16 + c0/2 (A0: position of
+    // relative column 0 halved); loads start 16-byte aligned at xs0 + c0/2, rem floats earlier
+    const int64_t rel0 = (int64_t)kMixCols * m.tt - m.t->lam;
+    const int64_t A0 = (rel0 >> 1) + m.t->in_off;
+    m.xs0 = (A0 - 16) & ~int64_t(3);
+    m.rem = (int)((A0 - 16) - m.xs0);
+    m.par = (int)(rel0 & 1);
+    return m;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
-                                                          Halfband g, int *err) {
+__global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
+                                                                   int total_tiles, int n_stages, int n_win,
+                                                                   Halfband g, int *err) {
     constexpr int kKC = 128 / Op<MODE>::kBytes, kMK = Op<MODE>::kMmaK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + kMixStages;
-    uint64_t *accb = empty + kMixStages;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
-    uint8_t *st = smem + 1024;
-
-    const TcMixUpTask &t = tasks[find_tile(tasks, n_tasks, blockIdx.x)];
-    const int local = blockIdx.x - t.tile_begin;
-    const int tt = local / t.tiles_a, at = local % t.tiles_a;
+    uint64_t *empty = full + kMixMaxStages;
+    uint64_t *wfull = empty + kMixMaxStages;
+    uint64_t *wempty = wfull + kMixMaxWin;
+    uint64_t *afull = wempty + kMixMaxWin;
+    uint64_t *aempty = afull + 2;
+    uint64_t *mdrain = aempty + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mdrain + 1);
+    uint8_t *stage = smem + 1024;
+    float *win = reinterpret_cast<float *>(stage + n_stages * kMixStageBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (t.Lk_pad + kKC - 1) / kKC;
-    // coarser-level window of chunk c0 starts at position A0 - 16 + c0/2 (A0: position of
-    // relative column 0 halved); loads start 16-byte aligned at xs0 + c0/2, REM floats earlier
-    const int64_t rel0 = (int64_t)kMixCols * tt - t.lam;
-    const int64_t A0 = (rel0 >> 1) + t.in_off;
-    const int64_t xs0 = (A0 - 16) & ~int64_t(3);
-    const int rem = (int)((A0 - 16) - xs0);
-    const int par = (int)(rel0 & 1);
 
     if (warp == 0) {
-        tmem_alloc(tslot, kTmemCols);
+        tmem_alloc(tslot, 2 * kMixCols);
         tmem_relinquish();
     }
     if (threadIdx.x == 32) {
-        for (int s = 0; s < kMixStages; ++s) {
+        for (int s = 0; s < kMixMaxStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        for (int s = 0; s < kMixMaxWin; ++s) {
+            mbar_init(&wfull[s], 1);
+            mbar_init(&wempty[s], 4);                        // the 4 warps of one half
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&afull[b], 1);
+            mbar_init(&aempty[b], 8);                        // all 8 epilogue warps
+        }
+        mbar_init(mdrain, 1);
         fence_barrier_init();
         fence_proxy_async();
     }
@@ -315,50 +353,115 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
     const uint32_t tmem = *tslot;
 
     if (warp == 0 && lane == 0) {
-        for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % kMixStages;
-            if (kc >= kMixStages && !mbar_wait(&empty[s], ((kc / kMixStages) - 1) & 1, err, 5)) break;
-            uint8_t *sa = st + s * kMixStageBytes;
-            mbar_expect_tx(&full[s], kMixStageBytes);
-            tma_load_2d(sa, t.mapM, kc * kKC, at * kMixRows, &full[s]);
-            tma_load_2d(sa + kMixABytes, t.mapO, kc * kKC, tt * kMixCols, &full[s]);
-        }
-    } else if (warp == 1 && lane == 0 && nk > 0) {
-        const uint32_t idesc = idesc_op<MODE>(kMixRows, kMixCols);
+        // ---- TMA producer ----
+        uint32_t su = 0, wu = 0;
         bool ok = true;
-        for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % kMixStages;
-            if (!mbar_wait(&full[s], (kc / kMixStages) & 1, err, 6)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t sa = smem_u32(st + s * kMixStageBytes);
-            const int nmma = min(4, (t.Lk_pad - kc * kKC) / kMK);
-            for (int kk = 0; kk < nmma; ++kk)
-                mma_op<MODE>(tmem, desc_k_sw128(sa + kk * 32), desc_k_sw128(sa + kMixABytes + kk * 32), idesc,
-                             (kc | kk) != 0);
-            mma_commit(&empty[s]);
+        for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
+            const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
+            const TcMixUpTask &t = *m.t;
+            for (int kc = 0; kc < m.nk; ++kc) {
+                const int s = su % n_stages;
+                if (su >= (uint32_t)n_stages && !mbar_wait(&empty[s], ((su / n_stages) - 1) & 1, err, 5)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *sa = stage + s * kMixStageBytes;
+                mbar_expect_tx(&full[s], kMixStageBytes);
+                tma_load_2d(sa, t.mapM, kc * kKC, m.at * kMixRows, &full[s]);
+                tma_load_2d(sa + kMixABytes, t.mapO, kc * kKC, m.tt * kMixCols, &full[s]);
+                ++su;
+            }
+            if (!ok || !t.mapY) continue;
+            for (int h = 0; h < 2; ++h) {
+                const int ws = wu % n_win;
+                if (wu >= (uint32_t)n_win && !mbar_wait(&wempty[ws], ((wu / n_win) - 1) & 1, err, 8)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&wfull[ws], kMixWinBytes);
+                tma_load_2d(win + ws * (kMixWinBytes / 4), t.mapY, (int)(m.xs0 + 64 * h), m.at * kMixRows,
+                            &wfull[ws]);
+                ++wu;
+            }
         }
-        if (ok) mma_commit(accb);
-    }
-    __syncwarp();
-    bool have = true;
-    if (nk > 0) have = mbar_wait(accb, 0, err, 7);
-    tc_fence_after();
-    if (have) {
-        const int R = warp * 32 + lane;                  // TMEM lane = filter row in the tile
-        const int a = kMixRows * at + R;
-        const bool row_ok = a < t.M2;
-        const float *src = t.Ysrc ? t.Ysrc + (int64_t)(row_ok ? a : 0) * t.ld_src : nullptr;
-        // E4M3: mixing-row scale (levels without slices have no mixing and no scale)
-        const float rsc = (MODE == kModeE4M3 && row_ok && t.rscale) ? t.rscale[a] : 1.0f;
-        const bool top = t.part != nullptr;
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
+        if (!ok) {
+            // copies still in flight land before the CTA leaves: wait for the last load of each buffer
+            // (the last use of slot s is use s + n ((used - 1 - s) / n); its phase parity is that quotient's)
+            for (int s = 0; s < n_stages && s < (int)su; ++s)
+                mbar_wait_bounded(&full[s], ((su - 1 - s) / n_stages) & 1);
+            for (int s = 0; s < n_win && s < (int)wu; ++s)
+                mbar_wait_bounded(&wfull[s], ((wu - 1 - s) / n_win) & 1);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        uint32_t su = 0, au = 0;
+        bool issued = false;
+        const uint32_t idesc = idesc_op<MODE>(kMixRows, kMixCols);
+        for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+            const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
+            if (m.nk == 0) continue;
+            const int b = au & 1;
+            if (au >= 2 && !mbar_wait(&aempty[b], ((au >> 1) - 1) & 1, err, 9)) break;
+            tc_fence_after();
+            const uint32_t d = tmem + b * kMixCols;
+            bool ok = true;
+            for (int kc = 0; kc < m.nk; ++kc) {
+                const int s = su % n_stages;
+                if (!mbar_wait(&full[s], (su / n_stages) & 1, err, 6)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(stage + s * kMixStageBytes);
+                const int nmma = min(128 / (kMK * Op<MODE>::kBytes), (m.t->Lk_pad - kc * kKC) / kMK);
+                for (int kk = 0; kk < nmma; ++kk)
+                    mma_op<MODE>(d, desc_k_sw128(sa + kk * 32), desc_k_sw128(sa + kMixABytes + kk * 32), idesc,
+                                 (kc | kk) != 0);
+                issued = true;
+                mma_commit(&empty[s]);
+                ++su;
+            }
+            if (!ok) break;
+            mma_commit(&afull[b]);
+            ++au;
+        }
+        if (issued) {                                        // every MMA has completed before TMEM is freed
+            mma_commit(mdrain);
+            mbar_wait_bounded(mdrain, 0);
+        }
+    } else if (warp >= 4) {
+        // ---- epilogue ----
+        const int q = warp & 3, h = (warp >> 2) - 1;
+        const int R = 32 * q + lane;                         // TMEM lane = filter row in the tile
+        uint32_t au = 0, wu = 0;
+        for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+            const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
+            const TcMixUpTask &t = *m.t;
+            const int b = au & 1;
+            bool ok = true;
+            if (m.nk > 0) {
+                ok = mbar_wait(&afull[b], (au >> 1) & 1, err, 7);
+                tc_fence_after();
+            }
+            int ws = 0;
+            if (ok && t.mapY) {
+                const uint32_t idx = wu + h;
+                ws = idx % n_win;
+                ok = mbar_wait(&wfull[ws], (idx / n_win) & 1, err, 10);
+            }
+            if (!ok) break;
+            const int a = kMixRows * m.at + R;
+            const bool row_ok = a < t.M2;
+            // E4M3: mixing-row scale (levels without slices have no mixing and no scale)
+            const float rsc = (MODE == kModeE4M3 && row_ok && t.rscale) ? t.rscale[a] : 1.0f;
+            const bool top = t.part != nullptr;
+            const float *wrow = win + ws * (kMixWinBytes / 4) + R * kMixWinCols;
             SegBest b0{-1.0f, 0.0f, 0.0f, -1}, b1{-1.0f, 0.0f, 0.0f, -1};
             // top level: columns [vlo, vhi) of this half are real samples (n >= 0, inside the push);
             // columns >= cb belong to the next window (window length >= 128 columns)
             int vlo = 0, vhi = 0, cb = 1 << 30;
             if (top) {
-                const int64_t hcol0 = (int64_t)kMixCols * tt + 128 * h;
+                const int64_t hcol0 = (int64_t)kMixCols * m.tt + 128 * h;
                 const int64_t half_first = t.first_n + hcol0;
                 vlo = half_first < 0 ? (int)min((int64_t)128, -half_first) : 0;
                 vhi = (int)min((int64_t)128, (int64_t)t.Bk - hcol0);
@@ -367,11 +470,12 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
                 cb = (int)min((int64_t)(1 << 30), wend - half_first);
             }
 #pragma unroll 1
-            for (int c0 = 128 * h; c0 < 128 * h + 128; c0 += 32) {
+            for (int c = 0; c < 4; ++c) {
+                const int c0 = 128 * h + 32 * c;
                 float x[32];
-                if (nk > 0) {
+                if (m.nk > 0) {
                     uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + c0, v);
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * kMixCols + c0, v);
                     tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]) * rsc;
@@ -379,26 +483,17 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
 #pragma unroll
                     for (int j = 0; j < 32; ++j) x[j] = 0.0f;
                 }
-                if (src) {
+                if (t.mapY) {
                     float w[52];
-                    const int64_t p0 = xs0 + (c0 >> 1);
-                    if (p0 >= 0 && p0 + 52 <= t.n_src) {
-                        const float4 *s4 = reinterpret_cast<const float4 *>(src + p0);
+                    const float4 *s4 = reinterpret_cast<const float4 *>(wrow + 16 * c);
 #pragma unroll
-                        for (int i = 0; i < 13; ++i) {
-                            const float4 f = __ldg(s4 + i);
-                            w[4 * i] = f.x; w[4 * i + 1] = f.y; w[4 * i + 2] = f.z; w[4 * i + 3] = f.w;
-                        }
-                    } else {                                    // row edge: positions outside read as 0
-#pragma unroll
-                        for (int i = 0; i < 52; ++i) {
-                            const int64_t p = p0 + i;
-                            w[i] = (p >= 0 && p < t.n_src) ? __ldg(src + p) : 0.0f;
-                        }
+                    for (int i = 0; i < 13; ++i) {
+                        const float4 f = s4[i];
+                        w[4 * i] = f.x; w[4 * i + 1] = f.y; w[4 * i + 2] = f.z; w[4 * i + 3] = f.w;
                     }
-                    add_interp_dispatch(par * 4 + rem, x, w, g);
+                    add_interp_dispatch(m.par * 4 + m.rem, x, w, g);
                 }
-                const int64_t col0 = (int64_t)kMixCols * tt + c0;
+                const int64_t col0 = (int64_t)kMixCols * m.tt + c0;
                 const int64_t n0 = t.first_n + col0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
@@ -420,10 +515,10 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const float p = __shfl_xor_sync(0xffffffffu, x[j], 1);   // other phase of the template
-                        const int c = cl + j;
-                        if (c < vlo || c >= vhi) continue;
+                        const int cc = cl + j;
+                        if (cc < vlo || cc >= vhi) continue;
                         const float m2 = fmaf(p, p, x[j] * x[j]);
-                        if (c < cb) {
+                        if (cc < cb) {
                             if (m2 > b0.mag2) { b0.mag2 = m2; b0.re = x[j]; b0.im = p; b0.n = n0 + j; }
                         } else {
                             if (m2 > b1.mag2) { b1.mag2 = m2; b1.re = x[j]; b1.im = p; b1.n = n0 + j; }
@@ -432,17 +527,26 @@ __global__ void __launch_bounds__(128, 2) tc_mixup_kernel(const TcMixUpTask *__r
                 }
             }
             if (top && (a & 1) == 0 && row_ok) {
-                WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (tt * 2 + h) * 2;
+                WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (m.tt * 2 + h) * 2;
                 base[0] = WinPart{b0.mag2, b0.re, b0.im, 0, b0.n};
                 base[1] = WinPart{b1.mag2, b1.re, b1.im, 0, b1.n};
             }
+            // release the accumulator and the window buffer (TMEM reads and shared loads are done)
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (m.nk > 0) mbar_arrive(&aempty[b]);
+                if (t.mapY) mbar_arrive(&wempty[ws]);
+            }
+            if (m.nk > 0) ++au;
+            if (t.mapY) wu += 2;
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, kTmemCols);
+        tmem_dealloc(tmem, 2 * kMixCols);
     }
 }
 
@@ -453,7 +557,9 @@ size_t tc_fir_smem_bytes(int kpad_max, int mode) {
     const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2;
     return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * ph + kpad_max) * by;
 }
-size_t tc_mixup_smem_bytes() { return 1024 + 1024 + kMixStages * kMixStageBytes; }
+size_t tc_mixup_smem_bytes(int n_stages, int n_win) {
+    return 1024 + 1024 + (size_t)n_stages * kMixStageBytes + (size_t)n_win * kMixWinBytes;
+}
 
 template <class K>
 static cudaError_t set_smem(K kernel, size_t smem) {
@@ -490,22 +596,34 @@ cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles
     return fir_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, kpad_max, err, s);
 }
 
+static int sm_count() {
+    static int count[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (count[dev] == 0 && cudaDeviceGetAttribute(&count[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        count[dev] = 148;
+    return count[dev];
+}
+
 template <int MODE>
-static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g,
-                                int *err, cudaStream_t s) {
-    const size_t smem = tc_mixup_smem_bytes();
+static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk,
+                                const Halfband &g, int *err, cudaStream_t s) {
+    // one K chunk per tile: a single stage buffer and three window buffers; else two and two
+    const int n_stages = max_nk >= 2 ? 2 : 1, n_win = n_stages == 1 ? 3 : 2;
+    const size_t smem = tc_mixup_smem_bytes(n_stages, n_win);
     cudaError_t e = set_smem(tc_mixup_kernel<MODE>, smem);
     if (e != cudaSuccess) return e;
-    tc_mixup_kernel<MODE><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, g, err);
+    const int grid = std::min(total_tiles, sm_count());
+    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_stages, n_win, g, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g, int mode,
-                            int *err, cudaStream_t s) {
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, const Halfband &g,
+                            int mode, int *err, cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    if (mode == kModeBF16) return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, g, err, s);
-    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, g, err, s);
-    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, g, err, s);
+    if (mode == kModeBF16) return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, max_nk, g, err, s);
+    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, max_nk, g, err, s);
+    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, max_nk, g, err, s);
 }
 
 }  // namespace lloid

@@ -125,6 +125,7 @@ struct LevelDev {
     void *O16 = nullptr;      // basis outputs [Bk_max x Lk_pad], time-major
     void *M16 = nullptr;      // stacked mixing [2M x Lk_pad]
     CUtensorMap *mapO = nullptr, *mapM = nullptr;   // device addresses (box 64 x 256 time rows, 64 x 128 filters)
+    CUtensorMap *mapY = nullptr;  // yuni as the finer level's interpolation source (FP32, box 100 x 128)
     // 16-bit modes, levels k >= 1: SNR rows [history (Hy) | new (B_k)] in one buffer, so the
     // next finer level's epilogue can stage a row segment with one TMA load
     float *yuni = nullptr;    // [2M x ldu]
@@ -555,6 +556,23 @@ static int encode_map(CUtensorMap *out, void *base, int mode, uint64_t inner, ui
     return SB_OK;
 }
 
+// FP32 [outer][inner] row-major map (rows inner*4 bytes apart), no swizzle;
+// positions outside the tensor read as 0.
+static int encode_map_f32(CUtensorMap *out, void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                          uint32_t box_outer) {
+    auto encode = tensor_map_encoder();
+    if (!encode) return fail(SB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 4};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SB_ECUDA, "cuTensorMapEncodeTiled (f32) failed (" + std::to_string((int)r) + ")");
+    return SB_OK;
+}
+
 static int upload_map(sb_unit *u, const CUtensorMap &h, CUtensorMap **dev, bool weights) {
     int rc = weights ? dev_alloc_w(u, (void **)dev, sizeof(CUtensorMap)) : dev_alloc(u, (void **)dev, sizeof(CUtensorMap));
     if (rc) return rc;
@@ -771,7 +789,13 @@ static int alloc_state(sb_unit *u) {
         CK(cudaMemcpyAsync(u->wstate[b], ws.data(), u->M * sizeof(WinState), cudaMemcpyHostToDevice,
                            u->ctx->alloc_stream));
     for (auto &L : u->levels) {
-        if (!u->tc || L.Lk_pad == 0) continue;
+        if (!u->tc) continue;
+        if (L.k >= 1) {                          // interpolation source of level k - 1 (box: 100 samples x 128 filters)
+            CUtensorMap hy;
+            if ((rc = encode_map_f32(&hy, L.yuni, L.ldu, M2, 100, 128))) return rc;
+            if ((rc = upload_map(u, hy, &L.mapY, false))) return rc;
+        }
+        if (L.Lk_pad == 0) continue;
         CUtensorMap ho;
         if ((rc = encode_map(&ho, L.O16, u->mode, L.Lk_pad, L.Bk_max + 256, 256))) return rc;
         if ((rc = upload_map(u, ho, &L.mapO, false))) return rc;
@@ -969,6 +993,7 @@ extern "C" int svdbank_create_like(sb_ctx *c, sb_unit *src, int32_t detector, sb
         L.x16 = nullptr;
         L.O16 = nullptr;
         L.mapO = nullptr;
+        L.mapY = nullptr;
         L.yuni = nullptr;
         L.ytmp = nullptr;
     }
@@ -1336,6 +1361,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     mt.mapO = L.mapO;
                     if (k < u->kmax) {
                         const LevelDev &N = u->levels[k + 1];
+                        mt.mapY = N.mapY;
                         mt.Ysrc = N.yuni;
                         mt.ld_src = N.ldu;
                         mt.n_src = N.Hy + (B >> (k + 1));
@@ -1530,6 +1556,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     int tfir_tiles[NM] = {0, 0, 0};
     std::vector<int> tmix_tiles[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
                                        std::vector<int>(kall + 1, 0)};
+    std::vector<int> tmix_maxnk[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
+                                       std::vector<int>(kall + 1, 0)};
     for (int h = 0; h < NM; ++h) {
         for (auto &f : tfir[h]) {
             f.tile_begin = tfir_tiles[h];
@@ -1539,6 +1567,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             for (auto &m : tmix[h][k]) {
                 m.tile_begin = tmix_tiles[h][k];
                 tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
+                const int kc = 128 / mode_bytes(h);                  // K elements per 128-byte chunk
+                tmix_maxnk[h][k] = std::max(tmix_maxnk[h][k], (m.Lk_pad + kc - 1) / kc);
             }
     }
     int wfin_warps = 0;
@@ -1659,7 +1689,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
                      *n = 1;
                      return launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
-                                            tmix_tiles[h][k], c->g, h, derr, st);
+                                            tmix_tiles[h][k], tmix_maxnk[h][k], c->g, h, derr, st);
                  })))
                 return rc;
     }

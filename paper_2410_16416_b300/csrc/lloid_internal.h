@@ -160,6 +160,7 @@ struct WinPart {
 struct TcMixUpTask {
     const CUtensorMap *mapM;   // A: mixing [2M x Lk_pad] 16-bit, box 64 x 128 (unused when Lk_pad = 0)
     const CUtensorMap *mapO;   // B: basis outputs [rows x Lk_pad] 16-bit, box 64 x 256
+    const CUtensorMap *mapY;   // coarser level y_{k+1} [2M x ld_src] FP32, box 100 x 128; null at the deepest level
     const float *Ysrc;         // coarser level y_{k+1}: row a at Ysrc + a ld_src (n_src columns); null at the deepest level
     int64_t ld_src, n_src;
     float *Y;                  // this level's first new column (row a at Y + a ldy); null: not stored
@@ -194,12 +195,12 @@ struct WinFinTask {
 };
 
 size_t tc_fir_smem_bytes(int kpad_max, int mode);
-size_t tc_mixup_smem_bytes();
+size_t tc_mixup_smem_bytes(int n_stages, int n_win);
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s);
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const Halfband &g, int mode,
-                            int *err, cudaStream_t s);
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, const Halfband &g,
+                            int mode, int *err, cudaStream_t s);
 cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                                 cudaStream_t s);
 
