@@ -246,35 +246,35 @@ constexpr int kMixMaxStages = 2, kMixMaxWin = 3;
 
 // x[j] += interpolated coarser level at column c0 + j.  w[i] holds the staged
 // coarser sample at register index i; PAR = parity of the first column's
-// relative index, REM = offset of the first needed sample inside w.
+// relative index, REM = offset of the first needed sample inside w; g2 holds
+// the doubled odd taps 2 g[2t+1].  Even outputs add the coarser sample itself
+// (2 g[0] = 1); odd outputs add 16 symmetric tap pairs, taps outermost so the
+// 16 odd outputs of the chunk are independent multiply-add chains.
 template <int PAR, int REM>
-__device__ __forceinline__ void add_interp(float (&x)[32], const float (&w)[52], const Halfband &g) {
+__device__ __forceinline__ void add_interp(float (&x)[32], const float (&w)[52], const Halfband &g2) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int base = REM + 16 + ((j + PAR) >> 1);
-        if (((j + PAR) & 1) == 0) {
-            x[j] += w[base];
-        } else {
-            float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};      // four independent chains
+    for (int j = PAR; j < 32; j += 2) x[j] += w[REM + 16 + ((j + PAR) >> 1)];
 #pragma unroll
-            for (int t = 0; t < kOddTaps; ++t)
-                v[t & 3] = fmaf(2.0f * g.odd[t], w[base - t] + w[base + 1 + t], v[t & 3]);
-            x[j] += (v[0] + v[1]) + (v[2] + v[3]);
+    for (int t = 0; t < kOddTaps; ++t) {
+#pragma unroll
+        for (int j = 1 - PAR; j < 32; j += 2) {
+            const int base = REM + 16 + ((j + PAR) >> 1);
+            x[j] = fmaf(g2.odd[t], w[base - t] + w[base + 1 + t], x[j]);
         }
     }
 }
 
 __device__ __forceinline__ void add_interp_dispatch(int sel, float (&x)[32], const float (&w)[52],
-                                                    const Halfband &g) {
+                                                    const Halfband &g2) {
     switch (sel) {
-        case 0: add_interp<0, 0>(x, w, g); break;
-        case 1: add_interp<0, 1>(x, w, g); break;
-        case 2: add_interp<0, 2>(x, w, g); break;
-        case 3: add_interp<0, 3>(x, w, g); break;
-        case 4: add_interp<1, 0>(x, w, g); break;
-        case 5: add_interp<1, 1>(x, w, g); break;
-        case 6: add_interp<1, 2>(x, w, g); break;
-        default: add_interp<1, 3>(x, w, g); break;
+        case 0: add_interp<0, 0>(x, w, g2); break;
+        case 1: add_interp<0, 1>(x, w, g2); break;
+        case 2: add_interp<0, 2>(x, w, g2); break;
+        case 3: add_interp<0, 3>(x, w, g2); break;
+        case 4: add_interp<1, 0>(x, w, g2); break;
+        case 5: add_interp<1, 1>(x, w, g2); break;
+        case 6: add_interp<1, 2>(x, w, g2); break;
+        default: add_interp<1, 3>(x, w, g2); break;
     }
 }
 
@@ -282,6 +282,27 @@ struct SegBest {
     float mag2, re, im;
     int64_t n;
 };
+__device__ __forceinline__ void seg_update(SegBest &b, float m2, float re, float im, int64_t n) {
+    if (m2 > b.mag2) {
+        b.mag2 = m2;
+        b.re = re;
+        b.im = im;
+        b.n = n;
+    }
+}
+// Takes the other lane's maximum of the same segment when larger (the earlier sample on ties).
+__device__ __forceinline__ void seg_merge_pair(SegBest &b) {
+    const float om = __shfl_xor_sync(0xffffffffu, b.mag2, 1);
+    const float ore = __shfl_xor_sync(0xffffffffu, b.re, 1);
+    const float oim = __shfl_xor_sync(0xffffffffu, b.im, 1);
+    const long long on = __shfl_xor_sync(0xffffffffu, (long long)b.n, 1);
+    if (om > b.mag2 || (om == b.mag2 && om >= 0.0f && on < b.n)) {
+        b.mag2 = om;
+        b.re = ore;
+        b.im = oim;
+        b.n = on;
+    }
+}
 
 // Geometry of one tile, identical for every role.
 struct MixTile {
@@ -310,7 +331,7 @@ __device__ __forceinline__ MixTile mix_tile(const TcMixUpTask *tasks, int n_task
 template <int MODE>
 __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
                                                                    int total_tiles, int n_stages, int n_win,
-                                                                   Halfband g, int *err) {
+                                                                   Halfband g2, int *err) {
     constexpr int kKC = 128 / Op<MODE>::kBytes, kMK = Op<MODE>::kMmaK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
@@ -491,13 +512,15 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                         const float4 f = s4[i];
                         w[4 * i] = f.x; w[4 * i + 1] = f.y; w[4 * i + 2] = f.z; w[4 * i + 3] = f.w;
                     }
-                    add_interp_dispatch(m.par * 4 + m.rem, x, w, g);
+                    add_interp_dispatch(m.par * 4 + m.rem, x, w, g2);
                 }
                 const int64_t col0 = (int64_t)kMixCols * m.tt + c0;
                 const int64_t n0 = t.first_n + col0;
+                if (n0 < 0) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (n0 + j < 0) x[j] = 0.0f;             // every rate starts at index 0
+                    for (int j = 0; j < 32; ++j)
+                        if (n0 + j < 0) x[j] = 0.0f;         // every rate starts at index 0
+                }
                 if (t.Y && row_ok) {
                     float *dst = t.Y + (int64_t)a * t.ldy + col0;
                     if (col0 + 32 <= t.Bk) {
@@ -511,25 +534,60 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     }
                 }
                 if (top) {
+                    // lanes 2i, 2i+1 hold the two phases (re, im) of template i
                     const int cl = c0 - 128 * h;
+                    const bool odd = lane & 1;
+                    if (cl >= vlo && cl + 32 <= vhi && (cl + 32 <= cb || cl >= cb)) {
+                        // whole chunk valid and in one window: the even lane takes columns 0-15, the
+                        // odd lane 16-31; one exchange gives each lane the other phase of its columns
+                        float own[16], oth[16], m2[16];
+                        int id[16];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float p = __shfl_xor_sync(0xffffffffu, x[j], 1);   // other phase of the template
-                        const int cc = cl + j;
-                        if (cc < vlo || cc >= vhi) continue;
-                        const float m2 = fmaf(p, p, x[j] * x[j]);
-                        if (cc < cb) {
-                            if (m2 > b0.mag2) { b0.mag2 = m2; b0.re = x[j]; b0.im = p; b0.n = n0 + j; }
-                        } else {
-                            if (m2 > b1.mag2) { b1.mag2 = m2; b1.re = x[j]; b1.im = p; b1.n = n0 + j; }
+                        for (int j = 0; j < 16; ++j) {
+                            const float lo = x[j], hi = x[j + 16];
+                            own[j] = odd ? hi : lo;
+                            oth[j] = __shfl_xor_sync(0xffffffffu, odd ? lo : hi, 1);
+                            m2[j] = fmaf(oth[j], oth[j], own[j] * own[j]);
+                            id[j] = j;
+                        }
+                        // maximum by a tree, the lower column on ties
+#pragma unroll
+                        for (int st = 1; st < 16; st *= 2)
+#pragma unroll
+                            for (int j = 0; j < 16; j += 2 * st)
+                                if (m2[j + st] > m2[j]) {
+                                    m2[j] = m2[j + st];
+                                    id[j] = id[j + st];
+                                    own[j] = own[j + st];
+                                    oth[j] = oth[j + st];
+                                }
+                        const float re = odd ? oth[0] : own[0], im = odd ? own[0] : oth[0];
+                        const int64_t nb = n0 + id[0] + (odd ? 16 : 0);
+                        if (cl >= cb) seg_update(b1, m2[0], re, im, nb);
+                        else seg_update(b0, m2[0], re, im, nb);
+                    } else {
+                        // chunk at a push edge or a window boundary: both lanes scan every column
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float p = __shfl_xor_sync(0xffffffffu, x[j], 1);   // other phase
+                            const int cc = cl + j;
+                            if (cc < vlo || cc >= vhi) continue;
+                            const float mm = fmaf(p, p, x[j] * x[j]);
+                            const float re = odd ? p : x[j], im = odd ? x[j] : p;
+                            if (cc < cb) seg_update(b0, mm, re, im, n0 + j);
+                            else seg_update(b1, mm, re, im, n0 + j);
                         }
                     }
                 }
             }
-            if (top && (a & 1) == 0 && row_ok) {
-                WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (m.tt * 2 + h) * 2;
-                base[0] = WinPart{b0.mag2, b0.re, b0.im, 0, b0.n};
-                base[1] = WinPart{b1.mag2, b1.re, b1.im, 0, b1.n};
+            if (top) {
+                seg_merge_pair(b0);                  // the two lanes' maxima of each segment
+                seg_merge_pair(b1);
+                if ((a & 1) == 0 && row_ok) {
+                    WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (m.tt * 2 + h) * 2;
+                    base[0] = WinPart{b0.mag2, b0.re, b0.im, 0, b0.n};
+                    base[1] = WinPart{b1.mag2, b1.re, b1.im, 0, b1.n};
+                }
             }
             // release the accumulator and the window buffer (TMEM reads and shared loads are done)
             tc_fence_before();
@@ -614,7 +672,9 @@ static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int tot
     cudaError_t e = set_smem(tc_mixup_kernel<MODE>, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total_tiles, sm_count());
-    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_stages, n_win, g, err);
+    Halfband g2;                                     // doubled odd taps 2 g[2t+1] (exact)
+    for (int t = 0; t < kOddTaps; ++t) g2.odd[t] = 2.0f * g.odd[t];
+    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_stages, n_win, g2, err);
     return cudaGetLastError();
 }
 
