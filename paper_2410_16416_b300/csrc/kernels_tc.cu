@@ -242,6 +242,7 @@ constexpr int kMixStageBytes = kMixABytes + kMixBBytes;
 constexpr int kMixWinCols = 100;                         // coarser samples of a half tile: 64 + 32 taps + 4
 constexpr int kMixWinBytes = kMixRows * kMixWinCols * 4;
 constexpr int kMixThreads = 384;
+constexpr int kMixStBytes = 32 * 32 * 4;                 // store staging: 32 filters x 32 samples, 128-byte swizzle
 constexpr int kMixMaxStages = 2, kMixMaxWin = 3;
 
 // x[j] += interpolated coarser level at column c0 + j.  w[i] holds the staged
@@ -331,7 +332,7 @@ __device__ __forceinline__ MixTile mix_tile(const TcMixUpTask *tasks, int n_task
 template <int MODE>
 __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
                                                                    int total_tiles, int n_stages, int n_win,
-                                                                   Halfband g2, int *err) {
+                                                                   int n_stbuf, Halfband g2, int *err) {
     constexpr int kKC = 128 / Op<MODE>::kBytes, kMK = Op<MODE>::kMmaK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mdrain + 1);
     uint8_t *stage = smem + 1024;
     float *win = reinterpret_cast<float *>(stage + n_stages * kMixStageBytes);
+    float *stbuf = win + n_win * (kMixWinBytes / 4);      // 1024-byte aligned: n_stbuf per epilogue warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) {
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         // ---- epilogue ----
         const int q = warp & 3, h = (warp >> 2) - 1;
         const int R = 32 * q + lane;                         // TMEM lane = filter row in the tile
-        uint32_t au = 0, wu = 0;
+        uint32_t au = 0, wu = 0, stu = 0;                    // stu: staged stores issued by this warp
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
             const TcMixUpTask &t = *m.t;
@@ -521,7 +523,26 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     for (int j = 0; j < 32; ++j)
                         if (n0 + j < 0) x[j] = 0.0f;         // every rate starts at index 0
                 }
-                if (t.Y && row_ok) {
+                if (t.mapYst && n_stbuf > 0) {
+                    // staged store: row `lane` of a 32 x 32 tile with 128-byte swizzle (16-byte chunk
+                    // i of row r at chunk i ^ (r & 7)), then one TMA store of the whole tile
+                    float *sb = stbuf + ((warp - 4) * n_stbuf + (stu & 1)) * (kMixStBytes / 4);
+                    if (stu >= 2) {
+                        if (lane == 0) bulk_wait_read_1();           // this buffer's previous store has read it
+                        __syncwarp();
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        *reinterpret_cast<float4 *>(sb + lane * 32 + ((i ^ (lane & 7)) * 4)) =
+                            make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(t.mapYst, sb, (int)(t.yst_col0 + col0), kMixRows * m.at + 32 * q);
+                        bulk_commit();
+                    }
+                    ++stu;
+                } else if (t.Y && row_ok) {
                     float *dst = t.Y + (int64_t)a * t.ldy + col0;
                     if (col0 + 32 <= t.Bk) {
 #pragma unroll
@@ -599,6 +620,8 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
             if (m.nk > 0) ++au;
             if (t.mapY) wu += 2;
         }
+        if (stu > 0 && lane == 0) bulk_wait_all();           // stores done before shared memory is released
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -615,8 +638,9 @@ size_t tc_fir_smem_bytes(int kpad_max, int mode) {
     const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2;
     return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * ph + kpad_max) * by;
 }
-size_t tc_mixup_smem_bytes(int n_stages, int n_win) {
-    return 1024 + 1024 + (size_t)n_stages * kMixStageBytes + (size_t)n_win * kMixWinBytes;
+size_t tc_mixup_smem_bytes(int n_stages, int n_win, int n_stbuf) {
+    return 1024 + 1024 + (size_t)n_stages * kMixStageBytes + (size_t)n_win * kMixWinBytes +
+           (size_t)8 * n_stbuf * kMixStBytes;
 }
 
 template <class K>
@@ -665,25 +689,30 @@ static int sm_count() {
 
 template <int MODE>
 static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk,
-                                const Halfband &g, int *err, cudaStream_t s) {
-    // one K chunk per tile: a single stage buffer and three window buffers; else two and two
-    const int n_stages = max_nk >= 2 ? 2 : 1, n_win = n_stages == 1 ? 3 : 2;
-    const size_t smem = tc_mixup_smem_bytes(n_stages, n_win);
+                                bool tma_store, const Halfband &g, int *err, cudaStream_t s) {
+    // shared memory (<= 227 KB): stage, window and store-staging buffers.  Several K chunks per
+    // tile: 2 stages, 2 windows, plain stores; one K chunk and stored y: 1, 2 and two staging
+    // buffers per epilogue warp; one K chunk at the top level (nothing stored): 1, 3, none
+    int n_stages = 1, n_win = 3, n_stbuf = 0;
+    if (max_nk >= 2) n_stages = 2, n_win = 2;
+    else if (tma_store) n_win = 2, n_stbuf = 2;
+    const size_t smem = tc_mixup_smem_bytes(n_stages, n_win, n_stbuf);
     cudaError_t e = set_smem(tc_mixup_kernel<MODE>, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total_tiles, sm_count());
     Halfband g2;                                     // doubled odd taps 2 g[2t+1] (exact)
     for (int t = 0; t < kOddTaps; ++t) g2.odd[t] = 2.0f * g.odd[t];
-    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_stages, n_win, g2, err);
+    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_stages, n_win, n_stbuf,
+                                                          g2, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, const Halfband &g,
-                            int mode, int *err, cudaStream_t s) {
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool tma_store,
+                            const Halfband &g, int mode, int *err, cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    if (mode == kModeBF16) return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, max_nk, g, err, s);
-    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, max_nk, g, err, s);
-    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, max_nk, g, err, s);
+    if (mode == kModeBF16) return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, max_nk, tma_store, g, err, s);
+    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, max_nk, tma_store, g, err, s);
+    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, max_nk, tma_store, g, err, s);
 }
 
 }  // namespace lloid

@@ -126,6 +126,7 @@ struct LevelDev {
     void *M16 = nullptr;      // stacked mixing [2M x Lk_pad]
     CUtensorMap *mapO = nullptr, *mapM = nullptr;   // device addresses (box 64 x 256 time rows, 64 x 128 filters)
     CUtensorMap *mapY = nullptr;  // yuni as the finer level's interpolation source (FP32, box 100 x 128)
+    CUtensorMap *mapYst = nullptr;   // yuni as this level's store target (FP32, box 32 x 32, 128-byte swizzle)
     // 16-bit modes, levels k >= 1: SNR rows [history (Hy) | new (B_k)] in one buffer, so the
     // next finer level's epilogue can stage a row segment with one TMA load
     float *yuni = nullptr;    // [2M x ldu]
@@ -559,7 +560,7 @@ static int encode_map(CUtensorMap *out, void *base, int mode, uint64_t inner, ui
 // FP32 [outer][inner] row-major map (rows inner*4 bytes apart), no swizzle;
 // positions outside the tensor read as 0.
 static int encode_map_f32(CUtensorMap *out, void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                          uint32_t box_outer) {
+                          uint32_t box_outer, bool swizzle128 = false) {
     auto encode = tensor_map_encoder();
     if (!encode) return fail(SB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     cuuint64_t dims[2] = {inner, outer};
@@ -567,7 +568,9 @@ static int encode_map_f32(CUtensorMap *out, void *base, uint64_t inner, uint64_t
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SB_ECUDA, "cuTensorMapEncodeTiled (f32) failed (" + std::to_string((int)r) + ")");
     return SB_OK;
@@ -794,6 +797,9 @@ static int alloc_state(sb_unit *u) {
             CUtensorMap hy;
             if ((rc = encode_map_f32(&hy, L.yuni, L.ldu, M2, 100, 128))) return rc;
             if ((rc = upload_map(u, hy, &L.mapY, false))) return rc;
+            CUtensorMap hs;                      // this level's own stores (box: 32 samples x 32 filters)
+            if ((rc = encode_map_f32(&hs, L.yuni, L.ldu, M2, 32, 32, true))) return rc;
+            if ((rc = upload_map(u, hs, &L.mapYst, false))) return rc;
         }
         if (L.Lk_pad == 0) continue;
         CUtensorMap ho;
@@ -994,6 +1000,7 @@ extern "C" int svdbank_create_like(sb_ctx *c, sb_unit *src, int32_t detector, sb
         L.O16 = nullptr;
         L.mapO = nullptr;
         L.mapY = nullptr;
+        L.mapYst = nullptr;
         L.yuni = nullptr;
         L.ytmp = nullptr;
     }
@@ -1368,6 +1375,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     }
                     mt.Y = k >= 1 ? L.yuni + L.Hy : L.ynew;
                     mt.ldy = k >= 1 ? L.ldu : L.ldy;
+                    mt.mapYst = k >= 1 ? L.mapYst : nullptr;
+                    mt.yst_col0 = L.Hy;
                     mt.part = k == 0 ? u->part : nullptr;
                     mt.first_n = (Tp >> k) - L.lam;
                     mt.win_len = u->win_len;
@@ -1558,6 +1567,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                                        std::vector<int>(kall + 1, 0)};
     std::vector<int> tmix_maxnk[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
                                        std::vector<int>(kall + 1, 0)};
+    std::vector<int> tmix_tstore[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
+                                        std::vector<int>(kall + 1, 0)};
     for (int h = 0; h < NM; ++h) {
         for (auto &f : tfir[h]) {
             f.tile_begin = tfir_tiles[h];
@@ -1569,6 +1580,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
                 const int kc = 128 / mode_bytes(h);                  // K elements per 128-byte chunk
                 tmix_maxnk[h][k] = std::max(tmix_maxnk[h][k], (m.Lk_pad + kc - 1) / kc);
+                if (m.mapYst) tmix_tstore[h][k] = 1;
             }
     }
     int wfin_warps = 0;
@@ -1689,7 +1701,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
                      *n = 1;
                      return launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
-                                            tmix_tiles[h][k], tmix_maxnk[h][k], c->g, h, derr, st);
+                                            tmix_tiles[h][k], tmix_maxnk[h][k], tmix_tstore[h][k] != 0, c->g, h,
+                                            derr, st);
                  })))
                 return rc;
     }

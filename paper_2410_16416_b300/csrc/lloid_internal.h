@@ -164,6 +164,8 @@ struct TcMixUpTask {
     const float *Ysrc;         // coarser level y_{k+1}: row a at Ysrc + a ld_src (n_src columns); null at the deepest level
     int64_t ld_src, n_src;
     float *Y;                  // this level's first new column (row a at Y + a ldy); null: not stored
+    const CUtensorMap *mapYst; // this level's y [2M x ldu] FP32, box 32 x 32, 128-byte swizzle (null: plain stores)
+    int64_t yst_col0;          // column of Y inside the mapYst tensor
     int64_t ldy;
     WinPart *part;             // top level: partials [i][n_rec], record (tt*2 + half)*2 + seg; null below
     int64_t first_n;           // absolute index (this level's rate) of column 0
@@ -195,12 +197,12 @@ struct WinFinTask {
 };
 
 size_t tc_fir_smem_bytes(int kpad_max, int mode);
-size_t tc_mixup_smem_bytes(int n_stages, int n_win);
+size_t tc_mixup_smem_bytes(int n_stages, int n_win, int n_stbuf);
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s);
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, const Halfband &g,
-                            int mode, int *err, cudaStream_t s);
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool tma_store,
+                            const Halfband &g, int mode, int *err, cudaStream_t s);
 cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                                 cudaStream_t s);
 
