@@ -79,6 +79,16 @@ __global__ void __launch_bounds__(256) copy_kernel(const CopyTask *__restrict__ 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= t.rows || i >= t.n) return;
     const int64_t pos = (int64_t)t.off + i;
+    if (t.elem16) {
+        const uint16_t *hist = reinterpret_cast<const uint16_t *>(t.hist);
+        const uint16_t *cur = reinterpret_cast<const uint16_t *>(t.cur);
+        uint16_t *dst = reinterpret_cast<uint16_t *>(t.dst);
+        for (int part = 0; part < 2; ++part) {
+            const int64_t r = row + (int64_t)part * t.rows;
+            dst[r * t.ld_dst + i] = pos < t.n_hist ? hist[r * t.ld_hist + pos] : cur[r * t.ld_cur + (pos - t.n_hist)];
+        }
+        return;
+    }
     const float v = pos < t.n_hist ? t.hist[row * t.ld_hist + pos] : t.cur[row * t.ld_cur + (pos - t.n_hist)];
     t.dst[row * t.ld_dst + i] = v;
 }

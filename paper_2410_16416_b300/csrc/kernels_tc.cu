@@ -16,6 +16,9 @@
 //
 // One CTA = 4 warps: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, then
 // all four warps drain TMEM (each warp owns 32 TMEM lanes).
+#include <cstring>
+#include <vector>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -217,65 +220,91 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
 }
 
 // ---------------------------------------------------------------------------
-// a3 + a4 (+ a5 partials at the top level): mixing GEMM with the x2
-// interpolation of the coarser level fused into its epilogue.
-//   D[a][m] = sum_l M[a][l] O[m][l]   (TMEM lanes = filters, columns = time)
-//   y_k[a][m] = D[a][m] + sum_j 2 g[j] y_{k+1}[a][(m - j)/2]
-// Tile = 128 filters x 256 samples.  Persistent CTAs (one per SM), warp roles:
-//   warp 0   TMA producer: per tile, the K chunks of M and O into a ring of
-//            n_stages stage buffers, then the coarser level's window for each
-//            half tile (128 filters x 100 samples, FP32) into a ring of n_win
-//            window buffers;
-//   warp 1   MMA issuer into one of two TMEM accumulators (256 columns each),
-//            so the next tile's GEMM runs while this tile's epilogue drains;
-//   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) (its 32 filters)
-//            for half tile (w / 4 - 1), takes each filter's 52 coarser samples
-//            per 32 outputs from shared memory and interpolates from registers.
-// At the top level the epilogue does not store the SNR: it reduces |rho|^2
-// over its columns into per-window partial maxima.
+// a3 + a4 (+ a5 partials at the top level): mixing GEMM and the x2
+// interpolation of the coarser level, both on the tensor cores, accumulated
+// into one TMEM tile:
+//   D[a][m] = sum_l M[a][l] O[m][l] + sum_i y_{k+1}[a][i] U[m][i]
+// (TMEM lanes = filters, columns = time; U[m][i] = 2 g[m - 2i] is the banded
+// halfband interpolator, Eq. 6).  The interpolation operands keep FP32
+// accuracy by a two-term BF16 split: y = y_hi + y_lo and U = U_hi + U_lo, and
+// D takes y_hi U_hi + y_hi U_lo + y_lo U_hi (the y_lo U_lo term is below 2^-16
+// of the result).  Every level stores its y in that split form for the next
+// finer level, so no conversion happens on the read side.
+//
+// Tile = 128 filters x 256 samples, cut into four 64-sample blocks; block j
+// reads coarser samples [32 j, 32 j + 80) of the tile's window, and U is the
+// same 64 x 80 matrix for every block (one of 16 variants: the parity of the
+// tile's first sample and the window's offset inside its 16-byte-aligned
+// start).  Persistent CTAs (one per SM), warp roles:
+//   warp 0      TMA producer: mixing chunks (stage buffer), the tile's U
+//               variant (bulk copy, ring of 2) and its three window chunks of
+//               64 coarser samples, hi and lo (ring of n_win);
+//   warp 1      MMA issuer into one of two TMEM accumulators (256 columns each);
+//   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) for half tile
+//               (w / 4 - 1); at the top level it reduces |rho|^2 into
+//               per-window partial maxima, below it stores y (hi / lo) by TMA.
 // ---------------------------------------------------------------------------
 constexpr int kMixRows = 128;                            // filters per tile (MMA M)
 constexpr int kMixCols = 256;                            // time samples per tile (MMA N)
 constexpr int kMixABytes = kMixRows * 128;               // mixing tile: 128 filters x 128 bytes of K
 constexpr int kMixBBytes = kMixCols * 128;               // basis-output tile: 256 time x 128 bytes of K
 constexpr int kMixStageBytes = kMixABytes + kMixBBytes;
-constexpr int kMixWinCols = 100;                         // coarser samples of a half tile: 64 + 32 taps + 4
-constexpr int kMixWinBytes = kMixRows * kMixWinCols * 4;
+constexpr int kWinHalfBytes = kMixRows * 128;            // 64 coarser samples (BF16) x 128 filters
+constexpr int kWinChunkBytes = 2 * kWinHalfBytes;        // hi + lo
+constexpr int kWinChunks = 3;                            // 192 >= 7 + 176 coarser samples per tile
+constexpr int kUBlk = 64;                                // outputs per interpolation block (MMA N)
+constexpr int kUK = 80;                                  // coarser samples per block (5 MMA K steps)
+constexpr int kUBytes = kUBlk * kUK * 2;                 // one BF16 term, no-swizzle K-major core matrices
+constexpr int kUVarBytes = 2 * kUBytes;                  // hi + lo
+constexpr int kUVariants = 16;                           // (parity, offset 0..7)
+constexpr int kMixStBytes = 2 * 32 * 64;                 // store staging: hi + lo, 32 filters x 32 samples
 constexpr int kMixThreads = 384;
-constexpr int kMixStBytes = 32 * 32 * 4;                 // store staging: 32 filters x 32 samples, 128-byte swizzle
-constexpr int kMixMaxStages = 2, kMixMaxWin = 3;
+constexpr int kMixMaxWin = 4;
 
-// x[j] += interpolated coarser level at column c0 + j.  w[i] holds the staged
-// coarser sample at register index i; PAR = parity of the first column's
-// relative index, REM = offset of the first needed sample inside w; g2 holds
-// the doubled odd taps 2 g[2t+1].  Even outputs add the coarser sample itself
-// (2 g[0] = 1); odd outputs add 16 symmetric tap pairs, taps outermost so the
-// 16 odd outputs of the chunk are independent multiply-add chains.
-template <int PAR, int REM>
-__device__ __forceinline__ void add_interp(float (&x)[32], const float (&w)[52], const Halfband &g2) {
-#pragma unroll
-    for (int j = PAR; j < 32; j += 2) x[j] += w[REM + 16 + ((j + PAR) >> 1)];
-#pragma unroll
-    for (int t = 0; t < kOddTaps; ++t) {
-#pragma unroll
-        for (int j = 1 - PAR; j < 32; j += 2) {
-            const int base = REM + 16 + ((j + PAR) >> 1);
-            x[j] = fmaf(g2.odd[t], w[base - t] + w[base + 1 + t], x[j]);
+size_t tc_interp_table_bytes() { return (size_t)kUVariants * kUVarBytes; }
+
+// U for variant (par, rem): output c (0..63) of a block takes coarser sample
+// i = rem + 16 + ((c + par) >> 1) (even c + par: weight 1 = 2 g[0]) or the
+// pairs i - t, i + 1 + t with weight 2 g[2t+1] (odd c + par).  Stored as BF16
+// hi and lo terms in the no-swizzle K-major layout: element (c, i) at byte
+// ((c / 8) * 10 + i / 8) * 128 + (c % 8) * 16 + (i % 8) * 2.
+void tc_interp_table(const Halfband &g, void *host_out) {
+    uint16_t *out = static_cast<uint16_t *>(host_out);
+    auto bf16_bits = [](float v) {                       // round to nearest even
+        uint32_t u;
+        std::memcpy(&u, &v, 4);
+        u += 0x7fffu + ((u >> 16) & 1u);
+        return (uint16_t)(u >> 16);
+    };
+    auto bf16_val = [](uint16_t h) {
+        const uint32_t u = (uint32_t)h << 16;
+        float v;
+        std::memcpy(&v, &u, 4);
+        return v;
+    };
+    for (int var = 0; var < kUVariants; ++var) {
+        const int par = var / 8, rem = var % 8;
+        uint16_t *hi = out + (size_t)var * (kUVarBytes / 2), *lo = hi + kUBytes / 2;
+        std::vector<float> U((size_t)kUBlk * kUK, 0.0f);
+        for (int c = 0; c < kUBlk; ++c) {
+            const int i = rem + 16 + ((c + par) >> 1);
+            if (((c + par) & 1) == 0) {
+                U[(size_t)c * kUK + i] = 1.0f;
+            } else {
+                for (int t = 0; t < kOddTaps; ++t) {
+                    U[(size_t)c * kUK + i - t] = 2.0f * g.odd[t];
+                    U[(size_t)c * kUK + i + 1 + t] = 2.0f * g.odd[t];
+                }
+            }
         }
-    }
-}
-
-__device__ __forceinline__ void add_interp_dispatch(int sel, float (&x)[32], const float (&w)[52],
-                                                    const Halfband &g2) {
-    switch (sel) {
-        case 0: add_interp<0, 0>(x, w, g2); break;
-        case 1: add_interp<0, 1>(x, w, g2); break;
-        case 2: add_interp<0, 2>(x, w, g2); break;
-        case 3: add_interp<0, 3>(x, w, g2); break;
-        case 4: add_interp<1, 0>(x, w, g2); break;
-        case 5: add_interp<1, 1>(x, w, g2); break;
-        case 6: add_interp<1, 2>(x, w, g2); break;
-        default: add_interp<1, 3>(x, w, g2); break;
+        for (int c = 0; c < kUBlk; ++c)
+            for (int i = 0; i < kUK; ++i) {
+                const size_t at = ((size_t)(c / 8) * (kUK / 8) + i / 8) * 64 + (c % 8) * 8 + (i % 8);
+                const float u = U[(size_t)c * kUK + i];
+                const uint16_t h = bf16_bits(u);
+                hi[at] = h;
+                lo[at] = bf16_bits(u - bf16_val(h));
+            }
     }
 }
 
@@ -308,9 +337,8 @@ __device__ __forceinline__ void seg_merge_pair(SegBest &b) {
 // Geometry of one tile, identical for every role.
 struct MixTile {
     const TcMixUpTask *t;
-    int tt, at, nk;
+    int tt, at, nk, var;
     int64_t xs0;        // first coarser position of the tile's window (16-byte aligned)
-    int rem, par;
 };
 __device__ __forceinline__ MixTile mix_tile(const TcMixUpTask *tasks, int n_tasks, int tile, int kc_elems) {
     MixTile m;
@@ -319,34 +347,39 @@ __device__ __forceinline__ MixTile mix_tile(const TcMixUpTask *tasks, int n_task
     m.tt = local / m.t->tiles_a;
     m.at = local % m.t->tiles_a;
     m.nk = (m.t->Lk_pad + kc_elems - 1) / kc_elems;
-    // coarser-level window of column c0 starts at position A0 - 16 + c0/2 (A0: position of
-    // relative column 0 halved); loads start 16-byte aligned at xs0 + c0/2, rem floats earlier
+    // output column c of the tile interpolates around coarser position A0 + (c + par) / 2
+    // (A0: position of relative column 0 halved); the window starts 16-byte aligned at xs0
     const int64_t rel0 = (int64_t)kMixCols * m.tt - m.t->lam;
     const int64_t A0 = (rel0 >> 1) + m.t->in_off;
-    m.xs0 = (A0 - 16) & ~int64_t(3);
-    m.rem = (int)((A0 - 16) - m.xs0);
-    m.par = (int)(rel0 & 1);
+    m.xs0 = (A0 - 16) & ~int64_t(7);
+    m.var = (int)(rel0 & 1) * 8 + (int)((A0 - 16) - m.xs0);
     return m;
 }
 
+// no-swizzle K-major descriptor of U (core matrices 128 B apart along K, 1280 B along N)
+__device__ __forceinline__ uint64_t desc_u(uint32_t saddr) { return smem_desc(saddr, 128, (kUK / 8) * 128, 0); }
+
 template <int MODE>
 __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
-                                                                   int total_tiles, int n_stages, int n_win,
-                                                                   int n_stbuf, Halfband g2, int *err) {
+                                                                   int total_tiles, int n_win, int n_stbuf,
+                                                                   const uint8_t *__restrict__ utab, int *err) {
     constexpr int kKC = 128 / Op<MODE>::kBytes, kMK = Op<MODE>::kMmaK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + kMixMaxStages;
-    uint64_t *wfull = empty + kMixMaxStages;
+    uint64_t *empty = full + 1;
+    uint64_t *wfull = empty + 1;
     uint64_t *wempty = wfull + kMixMaxWin;
-    uint64_t *afull = wempty + kMixMaxWin;
+    uint64_t *ufull = wempty + kMixMaxWin;
+    uint64_t *uempty = ufull + 2;
+    uint64_t *afull = uempty + 2;
     uint64_t *aempty = afull + 2;
     uint64_t *mdrain = aempty + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mdrain + 1);
-    uint8_t *stage = smem + 1024;
-    float *win = reinterpret_cast<float *>(stage + n_stages * kMixStageBytes);
-    float *stbuf = win + n_win * (kMixWinBytes / 4);      // 1024-byte aligned: n_stbuf per epilogue warp
+    uint8_t *stage = smem + 1024;                                  // one mixing stage
+    uint8_t *win = stage + kMixStageBytes;                         // n_win window chunks
+    uint8_t *ubuf = win + n_win * kWinChunkBytes;                  // 2 U variants
+    uint8_t *stbuf = ubuf + 2 * kUVarBytes;                        // n_stbuf per epilogue warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) {
@@ -354,15 +387,15 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         tmem_relinquish();
     }
     if (threadIdx.x == 32) {
-        for (int s = 0; s < kMixMaxStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
+        mbar_init(full, 1);
+        mbar_init(empty, 1);
         for (int s = 0; s < kMixMaxWin; ++s) {
             mbar_init(&wfull[s], 1);
-            mbar_init(&wempty[s], 4);                        // the 4 warps of one half
+            mbar_init(&wempty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
+            mbar_init(&ufull[b], 1);
+            mbar_init(&uempty[b], 1);
             mbar_init(&afull[b], 1);
             mbar_init(&aempty[b], 8);                        // all 8 epilogue warps
         }
@@ -377,74 +410,116 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
 
     if (warp == 0 && lane == 0) {
         // ---- TMA producer ----
-        uint32_t su = 0, wu = 0;
+        uint32_t su = 0, wu = 0, uu = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
             const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
             const TcMixUpTask &t = *m.t;
             for (int kc = 0; kc < m.nk; ++kc) {
-                const int s = su % n_stages;
-                if (su >= (uint32_t)n_stages && !mbar_wait(&empty[s], ((su / n_stages) - 1) & 1, err, 5)) {
+                if (su >= 1 && !mbar_wait(empty, (su - 1) & 1, err, 5)) {
                     ok = false;
                     break;
                 }
-                uint8_t *sa = stage + s * kMixStageBytes;
-                mbar_expect_tx(&full[s], kMixStageBytes);
-                tma_load_2d(sa, t.mapM, kc * kKC, m.at * kMixRows, &full[s]);
-                tma_load_2d(sa + kMixABytes, t.mapO, kc * kKC, m.tt * kMixCols, &full[s]);
+                mbar_expect_tx(full, kMixStageBytes);
+                tma_load_2d(stage, t.mapM, kc * kKC, m.at * kMixRows, full);
+                tma_load_2d(stage + kMixABytes, t.mapO, kc * kKC, m.tt * kMixCols, full);
                 ++su;
             }
             if (!ok || !t.mapY) continue;
-            for (int h = 0; h < 2; ++h) {
+            const int us = uu & 1;
+            if (uu >= 2 && !mbar_wait(&uempty[us], ((uu >> 1) - 1) & 1, err, 11)) {
+                ok = false;
+                break;
+            }
+            mbar_expect_tx(&ufull[us], kUVarBytes);
+            bulk_load(ubuf + us * kUVarBytes, utab + (size_t)m.var * kUVarBytes, kUVarBytes, &ufull[us]);
+            ++uu;
+            for (int wc = 0; wc < kWinChunks; ++wc) {
                 const int ws = wu % n_win;
                 if (wu >= (uint32_t)n_win && !mbar_wait(&wempty[ws], ((wu / n_win) - 1) & 1, err, 8)) {
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(&wfull[ws], kMixWinBytes);
-                tma_load_2d(win + ws * (kMixWinBytes / 4), t.mapY, (int)(m.xs0 + 64 * h), m.at * kMixRows,
-                            &wfull[ws]);
+                uint8_t *dst = win + ws * kWinChunkBytes;
+                mbar_expect_tx(&wfull[ws], kWinChunkBytes);
+                const int x = (int)(m.xs0 + 64 * wc);
+                tma_load_2d(dst, t.mapY, x, m.at * kMixRows, &wfull[ws]);                     // hi
+                tma_load_2d(dst + kWinHalfBytes, t.mapY, x, t.M2 + m.at * kMixRows, &wfull[ws]);  // lo
                 ++wu;
             }
         }
         if (!ok) {
             // copies still in flight land before the CTA leaves: wait for the last load of each buffer
-            // (the last use of slot s is use s + n ((used - 1 - s) / n); its phase parity is that quotient's)
-            for (int s = 0; s < n_stages && s < (int)su; ++s)
-                mbar_wait_bounded(&full[s], ((su - 1 - s) / n_stages) & 1);
+            // (the last use of slot s of a ring of n is use s + n ((used - 1 - s) / n))
+            if (su > 0) mbar_wait_bounded(full, (su - 1) & 1);
+            for (int s = 0; s < 2 && s < (int)uu; ++s) mbar_wait_bounded(&ufull[s], ((uu - 1 - s) / 2) & 1);
             for (int s = 0; s < n_win && s < (int)wu; ++s)
                 mbar_wait_bounded(&wfull[s], ((wu - 1 - s) / n_win) & 1);
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
-        uint32_t su = 0, au = 0;
+        uint32_t su = 0, wu = 0, uu = 0, au = 0;
         bool issued = false;
         const uint32_t idesc = idesc_op<MODE>(kMixRows, kMixCols);
+        const uint32_t idesc_u = idesc_op<kModeBF16>(kMixRows, kUBlk);
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
-            if (m.nk == 0) continue;
+            const bool has_src = m.t->mapY != nullptr;
             const int b = au & 1;
             if (au >= 2 && !mbar_wait(&aempty[b], ((au >> 1) - 1) & 1, err, 9)) break;
             tc_fence_after();
             const uint32_t d = tmem + b * kMixCols;
             bool ok = true;
             for (int kc = 0; kc < m.nk; ++kc) {
-                const int s = su % n_stages;
-                if (!mbar_wait(&full[s], (su / n_stages) & 1, err, 6)) {
+                if (!mbar_wait(full, su & 1, err, 6)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(stage + s * kMixStageBytes);
+                const uint32_t sa = smem_u32(stage);
                 const int nmma = min(128 / (kMK * Op<MODE>::kBytes), (m.t->Lk_pad - kc * kKC) / kMK);
                 for (int kk = 0; kk < nmma; ++kk)
                     mma_op<MODE>(d, desc_k_sw128(sa + kk * 32), desc_k_sw128(sa + kMixABytes + kk * 32), idesc,
                                  (kc | kk) != 0);
                 issued = true;
-                mma_commit(&empty[s]);
+                mma_commit(empty);
                 ++su;
             }
             if (!ok) break;
+            if (has_src) {
+                const int us = uu & 1;
+                if (!mbar_wait(&ufull[us], (uu >> 1) & 1, err, 12)) break;
+                tc_fence_after();
+                const uint32_t uhi = smem_u32(ubuf + us * kUVarBytes), ulo = uhi + kUBytes;
+                // block j reads window samples [32 j, 32 j + 80): K step (j, s) sits at sample 32 j + 16 s,
+                // in window chunk (32 j + 16 s) / 64
+                for (int wc = 0; wc < kWinChunks; ++wc) {
+                    const int ws = wu % n_win;
+                    if (!mbar_wait(&wfull[ws], (wu / n_win) & 1, err, 13)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t whi = smem_u32(win + ws * kWinChunkBytes), wlo = whi + kWinHalfBytes;
+                    for (int j = 0; j < 4; ++j)
+                        for (int st = 0; st < kUK / 16; ++st) {
+                            const int kap = 32 * j + 16 * st;
+                            if (kap / 64 != wc) continue;
+                            const uint32_t off = (uint32_t)(kap % 64) * 2;
+                            const uint32_t dj = d + kUBlk * j;
+                            const uint32_t acc0 = (m.nk > 0 || kap > 32 * j) ? 1u : 0u;
+                            mma_f16(dj, desc_k_sw128(whi + off), desc_u(uhi + 256 * st), idesc_u, acc0);
+                            mma_f16(dj, desc_k_sw128(whi + off), desc_u(ulo + 256 * st), idesc_u, 1u);
+                            mma_f16(dj, desc_k_sw128(wlo + off), desc_u(uhi + 256 * st), idesc_u, 1u);
+                        }
+                    issued = true;
+                    mma_commit(&wempty[ws]);
+                    ++wu;
+                }
+                if (!ok) break;
+                mma_commit(&uempty[us]);
+                ++uu;
+            }
             mma_commit(&afull[b]);
             ++au;
         }
@@ -454,40 +529,39 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         }
     } else if (warp >= 4) {
         // ---- epilogue ----
-        const int q = warp & 3, h = (warp >> 2) - 1;
+        const int q = warp & 3, h = (warp >> 2) - 1;            // TMEM lane quarter (warp % 4), half tile
         const int R = 32 * q + lane;                         // TMEM lane = filter row in the tile
-        uint32_t au = 0, wu = 0, stu = 0;                    // stu: staged stores issued by this warp
+        uint8_t *sbuf = stbuf + (warp - 4) * kMixStBytes;
+        uint32_t au = 0, stu = 0;                            // stu: staged stores issued by this warp
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
             const TcMixUpTask &t = *m.t;
             const int b = au & 1;
-            bool ok = true;
-            if (m.nk > 0) {
-                ok = mbar_wait(&afull[b], (au >> 1) & 1, err, 7);
-                tc_fence_after();
-            }
-            int ws = 0;
-            if (ok && t.mapY) {
-                const uint32_t idx = wu + h;
-                ws = idx % n_win;
-                ok = mbar_wait(&wfull[ws], (idx / n_win) & 1, err, 10);
-            }
-            if (!ok) break;
+            if (!mbar_wait(&afull[b], (au >> 1) & 1, err, 7)) break;
+            tc_fence_after();
+            // task fields used per chunk, read once per tile
+            const int64_t first_n = t.first_n, Bk = t.Bk, ldy = t.ldy, yst_col0 = t.yst_col0;
+            float *const Y = t.Y;
+            const CUtensorMap *const mapYst = t.mapYst;
+            const int M2 = t.M2;
             const int a = kMixRows * m.at + R;
-            const bool row_ok = a < t.M2;
-            // E4M3: mixing-row scale (levels without slices have no mixing and no scale)
-            const float rsc = (MODE == kModeE4M3 && row_ok && t.rscale) ? t.rscale[a] : 1.0f;
+            const bool row_ok = a < M2;
+            // E4M3: mixing-row scale of this level; the stored y is divided by the finer level's
+            float rsc = 1.0f, inv_next = 1.0f;
+            if (MODE == kModeE4M3 && row_ok) {
+                if (t.rscale) rsc = t.rscale[a];
+                if (t.rsc_next) inv_next = 1.0f / t.rsc_next[a];
+            }
             const bool top = t.part != nullptr;
-            const float *wrow = win + ws * (kMixWinBytes / 4) + R * kMixWinCols;
             SegBest b0{-1.0f, 0.0f, 0.0f, -1}, b1{-1.0f, 0.0f, 0.0f, -1};
             // top level: columns [vlo, vhi) of this half are real samples (n >= 0, inside the push);
             // columns >= cb belong to the next window (window length >= 128 columns)
             int vlo = 0, vhi = 0, cb = 1 << 30;
             if (top) {
                 const int64_t hcol0 = (int64_t)kMixCols * m.tt + 128 * h;
-                const int64_t half_first = t.first_n + hcol0;
+                const int64_t half_first = first_n + hcol0;
                 vlo = half_first < 0 ? (int)min((int64_t)128, -half_first) : 0;
-                vhi = (int)min((int64_t)128, (int64_t)t.Bk - hcol0);
+                vhi = (int)min((int64_t)128, Bk - hcol0);
                 const int64_t a0 = half_first + vlo;
                 const int64_t wend = (a0 >= 0 ? a0 / t.win_len + 1 : 1) * t.win_len;
                 cb = (int)min((int64_t)(1 << 30), wend - half_first);
@@ -496,62 +570,64 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
             for (int c = 0; c < 4; ++c) {
                 const int c0 = 128 * h + 32 * c;
                 float x[32];
-                if (m.nk > 0) {
+                {
                     uint32_t v[32];
                     tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * kMixCols + c0, v);
                     tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]) * rsc;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) x[j] = 0.0f;
-                }
-                if (t.mapY) {
-                    float w[52];
-                    const float4 *s4 = reinterpret_cast<const float4 *>(wrow + 16 * c);
-#pragma unroll
-                    for (int i = 0; i < 13; ++i) {
-                        const float4 f = s4[i];
-                        w[4 * i] = f.x; w[4 * i + 1] = f.y; w[4 * i + 2] = f.z; w[4 * i + 3] = f.w;
-                    }
-                    add_interp_dispatch(m.par * 4 + m.rem, x, w, g2);
                 }
                 const int64_t col0 = (int64_t)kMixCols * m.tt + c0;
-                const int64_t n0 = t.first_n + col0;
+                const int64_t n0 = first_n + col0;
                 if (n0 < 0) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         if (n0 + j < 0) x[j] = 0.0f;         // every rate starts at index 0
                 }
-                if (t.mapYst && n_stbuf > 0) {
-                    // staged store: row `lane` of a 32 x 32 tile with 128-byte swizzle (16-byte chunk
-                    // i of row r at chunk i ^ (r & 7)), then one TMA store of the whole tile
-                    float *sb = stbuf + ((warp - 4) * n_stbuf + (stu & 1)) * (kMixStBytes / 4);
-                    if (stu >= 2) {
-                        if (lane == 0) bulk_wait_read_1();           // this buffer's previous store has read it
+                if (mapYst && n_stbuf > 0) {
+                    // staged store of y as BF16 hi / lo: row `lane` of two 32 x 32 tiles with 64-byte
+                    // swizzle (16-byte chunk i of row r at chunk i ^ ((r >> 1) & 3)), then two TMA stores
+                    if (stu >= 1) {
+                        if (lane == 0) bulk_wait_read_0();           // the previous store has read the buffer
                         __syncwarp();
                     }
+                    uint32_t hw[16], lw[16];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        *reinterpret_cast<float4 *>(sb + lane * 32 + ((i ^ (lane & 7)) * 4)) =
-                            make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
+                    for (int j = 0; j < 16; ++j) {
+                        const float y0 = x[2 * j] * inv_next, y1 = x[2 * j + 1] * inv_next;
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(y0), h1 = __float2bfloat16_rn(y1);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(y0 - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(y1 - __bfloat162float(h1));
+                        hw[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                        lw[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                    }
+                    const int sw = (lane >> 1) & 3;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        *reinterpret_cast<uint4 *>(sbuf + lane * 64 + ((i ^ sw) * 16)) =
+                            make_uint4(hw[4 * i], hw[4 * i + 1], hw[4 * i + 2], hw[4 * i + 3]);
+                        *reinterpret_cast<uint4 *>(sbuf + 2048 + lane * 64 + ((i ^ sw) * 16)) =
+                            make_uint4(lw[4 * i], lw[4 * i + 1], lw[4 * i + 2], lw[4 * i + 3]);
+                    }
                     fence_proxy_async();
                     __syncwarp();
                     if (lane == 0) {
-                        tma_store_2d(t.mapYst, sb, (int)(t.yst_col0 + col0), kMixRows * m.at + 32 * q);
+                        const int xs = (int)(yst_col0 + col0), ys = kMixRows * m.at + 32 * q;
+                        tma_store_3d(mapYst, sbuf, xs, ys, 0);           // hi
+                        tma_store_3d(mapYst, sbuf + 2048, xs, ys, 1);    // lo
                         bulk_commit();
                     }
                     ++stu;
-                } else if (t.Y && row_ok) {
-                    float *dst = t.Y + (int64_t)a * t.ldy + col0;
-                    if (col0 + 32 <= t.Bk) {
+                } else if (Y && row_ok) {
+                    float *dst = Y + (int64_t)a * ldy + col0;
+                    if (col0 + 32 <= Bk) {
 #pragma unroll
                         for (int j = 0; j < 32; j += 4)
                             *reinterpret_cast<float4 *>(dst + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
-                            if (col0 + j < t.Bk) dst[j] = x[j];
+                            if (col0 + j < Bk) dst[j] = x[j];
                     }
                 }
                 if (top) {
@@ -610,15 +686,11 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     base[1] = WinPart{b1.mag2, b1.re, b1.im, 0, b1.n};
                 }
             }
-            // release the accumulator and the window buffer (TMEM reads and shared loads are done)
+            // release the accumulator (TMEM reads are done)
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                if (m.nk > 0) mbar_arrive(&aempty[b]);
-                if (t.mapY) mbar_arrive(&wempty[ws]);
-            }
-            if (m.nk > 0) ++au;
-            if (t.mapY) wu += 2;
+            if (lane == 0) mbar_arrive(&aempty[b]);
+            ++au;
         }
         if (stu > 0 && lane == 0) bulk_wait_all();           // stores done before shared memory is released
         __syncwarp();
@@ -638,11 +710,10 @@ size_t tc_fir_smem_bytes(int kpad_max, int mode) {
     const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2;
     return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * ph + kpad_max) * by;
 }
-size_t tc_mixup_smem_bytes(int n_stages, int n_win, int n_stbuf) {
-    return 1024 + 1024 + (size_t)n_stages * kMixStageBytes + (size_t)n_win * kMixWinBytes +
+size_t tc_mixup_smem_bytes(int n_win, int n_stbuf) {
+    return 1024 + 1024 + (size_t)kMixStageBytes + (size_t)n_win * kWinChunkBytes + 2 * (size_t)kUVarBytes +
            (size_t)8 * n_stbuf * kMixStBytes;
 }
-
 template <class K>
 static cudaError_t set_smem(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -688,31 +759,26 @@ static int sm_count() {
 }
 
 template <int MODE>
-static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk,
-                                bool tma_store, const Halfband &g, int *err, cudaStream_t s) {
-    // shared memory (<= 227 KB): stage, window and store-staging buffers.  Several K chunks per
-    // tile: 2 stages, 2 windows, plain stores; one K chunk and stored y: 1, 2 and two staging
-    // buffers per epilogue warp; one K chunk at the top level (nothing stored): 1, 3, none
-    int n_stages = 1, n_win = 3, n_stbuf = 0;
-    if (max_nk >= 2) n_stages = 2, n_win = 2;
-    else if (tma_store) n_win = 2, n_stbuf = 2;
-    const size_t smem = tc_mixup_smem_bytes(n_stages, n_win, n_stbuf);
+static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, bool tma_store,
+                                const void *utab, int *err, cudaStream_t s) {
+    // shared memory (<= 227 KB): one mixing stage, the window ring, two U variants and, when the
+    // level's y is stored, one staging buffer per epilogue warp
+    const int n_win = tma_store ? 3 : 4, n_stbuf = tma_store ? 1 : 0;
+    const size_t smem = tc_mixup_smem_bytes(n_win, n_stbuf);
     cudaError_t e = set_smem(tc_mixup_kernel<MODE>, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total_tiles, sm_count());
-    Halfband g2;                                     // doubled odd taps 2 g[2t+1] (exact)
-    for (int t = 0; t < kOddTaps; ++t) g2.odd[t] = 2.0f * g.odd[t];
-    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_stages, n_win, n_stbuf,
-                                                          g2, err);
+    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_win, n_stbuf,
+                                                          static_cast<const uint8_t *>(utab), err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool tma_store,
-                            const Halfband &g, int mode, int *err, cudaStream_t s) {
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, bool tma_store,
+                            const void *utab, int mode, int *err, cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    if (mode == kModeBF16) return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, max_nk, tma_store, g, err, s);
-    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, max_nk, tma_store, g, err, s);
-    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, max_nk, tma_store, g, err, s);
+    if (mode == kModeBF16) return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, tma_store, utab, err, s);
+    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, tma_store, utab, err, s);
+    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, tma_store, utab, err, s);
 }
 
 }  // namespace lloid

@@ -125,13 +125,13 @@ struct LevelDev {
     void *O16 = nullptr;      // basis outputs [Bk_max x Lk_pad], time-major
     void *M16 = nullptr;      // stacked mixing [2M x Lk_pad]
     CUtensorMap *mapO = nullptr, *mapM = nullptr;   // device addresses (box 64 x 256 time rows, 64 x 128 filters)
-    CUtensorMap *mapY = nullptr;  // yuni as the finer level's interpolation source (FP32, box 100 x 128)
-    CUtensorMap *mapYst = nullptr;   // yuni as this level's store target (FP32, box 32 x 32, 128-byte swizzle)
+    CUtensorMap *mapY = nullptr;     // yuni as the finer level's interpolation operand (box 64 x 128, 128-byte swizzle)
+    CUtensorMap *mapYst = nullptr;   // yuni as this level's store target (box 32 x 32, 64-byte swizzle)
     // 16-bit modes, levels k >= 1: SNR rows [history (Hy) | new (B_k)] in one buffer, so the
     // next finer level's epilogue can stage a row segment with one TMA load
-    float *yuni = nullptr;    // [2M x ldu]
+    float *yuni = nullptr;    // FP32 mode: unused; 16/8-bit modes: y as BF16 hi rows [0, 2M), lo rows [2M, 4M), ld ldu
     int64_t ldu = 0;
-    float *ytmp = nullptr;    // [2M x Hy] history shift staging
+    float *ytmp = nullptr;    // history shift staging, same layout with ld Hy
 };
 
 struct TriggerSlot {
@@ -176,6 +176,7 @@ struct sb_ctx {
     sb_ctx_stats stats{};
     // FP32 refinement scratch (allocated on the first refined push, shared by later pushes)
     RefCand *ref_cands = nullptr;
+    void *utab = nullptr;      // tensor-core interpolation operand table (16 variants of U, BF16 hi / lo)
     int *ref_counters = nullptr;
     // profiling: event pairs around each launch, summed per stage on query
     bool prof = false;
@@ -348,7 +349,7 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
             hd = std::max(hd, P.lam[k] - P.e[k] + D + d->slices[s].n_taps - 1 + (is_tc(d->precision) ? 128 : 0));
         }
         P.Hd[k] = round_up(std::max<int64_t>(hd, 1), 32);
-        if (k >= 1) P.Hy[k] = round_up((P.lam[k - 1] + 2 * kHalfK) / 2 + 1 - P.lam[k], 4);
+        if (k >= 1) P.Hy[k] = round_up((P.lam[k - 1] + 2 * kHalfK) / 2 + 1 - P.lam[k], 8);   // 16 bytes of BF16
     }
     // tensor-core layout: every slice's 16-bit window start X0 is a multiple of 8
     // samples (16 bytes, the TMA/descriptor alignment); phi zero columns pad W.
@@ -391,7 +392,7 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
         b += 2 * M2 * P.Hy[k] * 4;                   // SNR history ping-pong
         if (P.tc) {
             b -= M2 * ldy * 4 + 2 * M2 * P.Hy[k] * 4;   // replaced by the unified level buffer
-            if (k >= 1) b += M2 * round_up(P.Hy[k] + Bk, 4) * 4 + M2 * P.Hy[k] * 4 + 128;
+            if (k >= 1) b += M2 * round_up(P.Hy[k] + Bk, 8) * 4 + M2 * P.Hy[k] * 4 + 128;
             else if (d->flags & SB_FLAG_KEEP_SNR) b += M2 * ldy * 4;
             b += (P.x16_len[k] + (Bk + 256) * P.Lk_pad[k] + M2 * P.Lk_pad[k]) * by + 2 * 128;
             if (mode == kModeE4M3) b += (P.Lk_pad[k] + M2 + 2) * 4;
@@ -456,6 +457,15 @@ extern "C" int sb_ctx_create(int32_t device, void *stream, int64_t hbm_budget_by
             return fail(SB_ECUDA, "event creation failed");
         }
     }
+    {   // interpolation operands of the tensor-core mixing kernel (constant per context)
+        std::vector<uint8_t> ut(tc_interp_table_bytes());
+        tc_interp_table(c->g, ut.data());
+        if (cudaMalloc(&c->utab, ut.size()) != cudaSuccess ||
+            cudaMemcpy(c->utab, ut.data(), ut.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            sb_ctx_destroy(c);
+            return fail(SB_ENOMEM, "interpolation table allocation failed");
+        }
+    }
     *out = c;
     return SB_OK;
 }
@@ -480,6 +490,7 @@ extern "C" int sb_ctx_destroy(sb_ctx *c) {
     release_marks(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->ref_cands) cudaFree(c->ref_cands);
+    if (c->utab) cudaFree(c->utab);
     if (c->ref_counters) cudaFree(c->ref_counters);
     if (c->stream) cudaStreamSynchronize(c->stream);      // unit memory returned on the work stream
     if (c->pop_stream) cudaStreamDestroy(c->pop_stream);
@@ -557,22 +568,19 @@ static int encode_map(CUtensorMap *out, void *base, int mode, uint64_t inner, ui
     return SB_OK;
 }
 
-// FP32 [outer][inner] row-major map (rows inner*4 bytes apart), no swizzle;
-// positions outside the tensor read as 0.
-static int encode_map_f32(CUtensorMap *out, void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                          uint32_t box_outer, bool swizzle128 = false) {
+// y as BF16 [2][rows][inner] (hi, lo) for tile stores: box 32 samples x 32 rows x 1, 64-byte
+// swizzle; the row dimension clips each half at its own bound.
+static int encode_map_y_store(CUtensorMap *out, void *base, uint64_t inner, uint64_t rows) {
     auto encode = tensor_map_encoder();
     if (!encode) return fail(SB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {inner * 4};
-    cuuint32_t box[2] = {box_inner, box_outer};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    cuuint64_t dims[3] = {inner, rows, 2};
+    cuuint64_t strides[2] = {inner * 2, rows * inner * 2};
+    cuuint32_t box[3] = {32, 32, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(SB_ECUDA, "cuTensorMapEncodeTiled (f32) failed (" + std::to_string((int)r) + ")");
+    if (r != CUDA_SUCCESS) return fail(SB_ECUDA, "cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")");
     return SB_OK;
 }
 
@@ -793,12 +801,12 @@ static int alloc_state(sb_unit *u) {
                            u->ctx->alloc_stream));
     for (auto &L : u->levels) {
         if (!u->tc) continue;
-        if (L.k >= 1) {                          // interpolation source of level k - 1 (box: 100 samples x 128 filters)
-            CUtensorMap hy;
-            if ((rc = encode_map_f32(&hy, L.yuni, L.ldu, M2, 100, 128))) return rc;
+        if (L.k >= 1) {                          // y as BF16 hi / lo rows [4M x ldu]
+            CUtensorMap hy;                      // level k - 1's interpolation operand (64 samples x 128 filters)
+            if ((rc = encode_map(&hy, L.yuni, kModeBF16, L.ldu, 2 * M2, 128))) return rc;
             if ((rc = upload_map(u, hy, &L.mapY, false))) return rc;
-            CUtensorMap hs;                      // this level's own stores (box: 32 samples x 32 filters)
-            if ((rc = encode_map_f32(&hs, L.yuni, L.ldu, M2, 32, 32, true))) return rc;
+            CUtensorMap hs;                      // this level's own stores (32 samples x 32 filters)
+            if ((rc = encode_map_y_store(&hs, L.yuni, L.ldu, M2))) return rc;
             if ((rc = upload_map(u, hs, &L.mapYst, false))) return rc;
         }
         if (L.Lk_pad == 0) continue;
@@ -887,7 +895,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
         if (u->tc) {
             L.Lk_pad = (int)P.Lk_pad[k];
             L.x16_len = P.x16_len[k];
-            if (k >= 1) L.ldu = round_up(L.Hy + L.Bk_max, 4);
+            if (k >= 1) L.ldu = round_up(L.Hy + L.Bk_max, 8);
         }
         if (L.Lk > 0 && !u->tc) {
             if ((rc = dev_alloc_w(u, (void **)&L.Mcat, M2 * L.Lk * 4))) return cleanup(rc);
@@ -1366,17 +1374,12 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     TcMixUpTask mt{};
                     mt.mapM = L.mapM;
                     mt.mapO = L.mapO;
-                    if (k < u->kmax) {
-                        const LevelDev &N = u->levels[k + 1];
-                        mt.mapY = N.mapY;
-                        mt.Ysrc = N.yuni;
-                        mt.ld_src = N.ldu;
-                        mt.n_src = N.Hy + (B >> (k + 1));
-                    }
-                    mt.Y = k >= 1 ? L.yuni + L.Hy : L.ynew;
-                    mt.ldy = k >= 1 ? L.ldu : L.ldy;
+                    if (k < u->kmax) mt.mapY = u->levels[k + 1].mapY;
+                    mt.Y = k == 0 ? L.ynew : nullptr;             // SB_FLAG_KEEP_SNR
+                    mt.ldy = L.ldy;
                     mt.mapYst = k >= 1 ? L.mapYst : nullptr;
                     mt.yst_col0 = L.Hy;
+                    mt.rsc_next = k >= 1 ? u->levels[k - 1].rscale : nullptr;
                     mt.part = k == 0 ? u->part : nullptr;
                     mt.first_n = (Tp >> k) - L.lam;
                     mt.win_len = u->win_len;
@@ -1401,6 +1404,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     a.rows = M2;
                     a.n = (int32_t)L.Hy;
                     a.off = (int32_t)Bk;
+                    a.elem16 = 1;
                     yshift1.push_back(a);
                     CopyTask bt{};
                     bt.cur = L.ytmp;
@@ -1410,6 +1414,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     bt.rows = M2;
                     bt.n = (int32_t)L.Hy;
                     bt.off = 0;
+                    bt.elem16 = 1;
                     yshift2.push_back(bt);
                     max_hy = std::max<int>(max_hy, (int)L.Hy);
                 }
@@ -1565,8 +1570,6 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     int tfir_tiles[NM] = {0, 0, 0};
     std::vector<int> tmix_tiles[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
                                        std::vector<int>(kall + 1, 0)};
-    std::vector<int> tmix_maxnk[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
-                                       std::vector<int>(kall + 1, 0)};
     std::vector<int> tmix_tstore[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
                                         std::vector<int>(kall + 1, 0)};
     for (int h = 0; h < NM; ++h) {
@@ -1578,8 +1581,6 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             for (auto &m : tmix[h][k]) {
                 m.tile_begin = tmix_tiles[h][k];
                 tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
-                const int kc = 128 / mode_bytes(h);                  // K elements per 128-byte chunk
-                tmix_maxnk[h][k] = std::max(tmix_maxnk[h][k], (m.Lk_pad + kc - 1) / kc);
                 if (m.mapYst) tmix_tstore[h][k] = 1;
             }
     }
@@ -1701,8 +1702,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
                      *n = 1;
                      return launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
-                                            tmix_tiles[h][k], tmix_maxnk[h][k], tmix_tstore[h][k] != 0, c->g, h,
-                                            derr, st);
+                                            tmix_tiles[h][k], tmix_tstore[h][k] != 0, c->utab, h, derr, st);
                  })))
                 return rc;
     }

@@ -59,6 +59,8 @@ struct CopyTask {
     int32_t rows;
     int32_t n;           // columns to copy
     int32_t off;         // first virtual column
+    int32_t elem16;      // 1: 16-bit elements, rows r and r + rows (the hi and lo halves) both copied
+    int32_t pad;
 };
 
 // ---- GEMM-shaped steps (a2 basis FIR as a Toeplitz GEMM, a3 mixing GEMM) --
@@ -160,13 +162,13 @@ struct WinPart {
 struct TcMixUpTask {
     const CUtensorMap *mapM;   // A: mixing [2M x Lk_pad] 16-bit, box 64 x 128 (unused when Lk_pad = 0)
     const CUtensorMap *mapO;   // B: basis outputs [rows x Lk_pad] 16-bit, box 64 x 256
-    const CUtensorMap *mapY;   // coarser level y_{k+1} [2M x ld_src] FP32, box 100 x 128; null at the deepest level
-    const float *Ysrc;         // coarser level y_{k+1}: row a at Ysrc + a ld_src (n_src columns); null at the deepest level
-    int64_t ld_src, n_src;
-    float *Y;                  // this level's first new column (row a at Y + a ldy); null: not stored
-    const CUtensorMap *mapYst; // this level's y [2M x ldu] FP32, box 32 x 32, 128-byte swizzle (null: plain stores)
-    int64_t yst_col0;          // column of Y inside the mapYst tensor
+    const CUtensorMap *mapY;   // coarser level y_{k+1} as BF16 hi rows [0, 2M) and lo rows [2M, 4M),
+                               // box 64 x 128, 128-byte swizzle; null at the deepest level
+    float *Y;                  // top level with SB_FLAG_KEEP_SNR: FP32 SNR (row a at Y + a ldy); else null
     int64_t ldy;
+    const CUtensorMap *mapYst; // this level's y as BF16 [hi / lo][2M][ldu], box 32 x 32 x 1, 64-byte swizzle;
+                               // null at the top
+    int64_t yst_col0;          // column of this push's first sample inside mapYst
     WinPart *part;             // top level: partials [i][n_rec], record (tt*2 + half)*2 + seg; null below
     int64_t first_n;           // absolute index (this level's rate) of column 0
     int64_t win_len;           // top level: window length in samples (>= 128)
@@ -174,7 +176,8 @@ struct TcMixUpTask {
     int32_t lam;               // Lambda of this level
     int32_t in_off;            // Lambda_{k+1} + Hy_{k+1}: coarser position of (relative index 0) / 2
     int32_t tiles_t, tiles_a, tile_begin, n_rec;
-    const float *rscale;       // E4M3: per mixing row (filter) scale
+    const float *rscale;       // E4M3: per mixing row (filter) scale of this level (null: 1)
+    const float *rsc_next;     // E4M3: row scale of the finer level, which reads this level's y (null: 1)
 };
 
 // Window bookkeeping after the top-level partial maxima: one warp per
@@ -197,12 +200,15 @@ struct WinFinTask {
 };
 
 size_t tc_fir_smem_bytes(int kpad_max, int mode);
-size_t tc_mixup_smem_bytes(int n_stages, int n_win, int n_stbuf);
+size_t tc_mixup_smem_bytes(int n_win, int n_stbuf);
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s);
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool tma_store,
-                            const Halfband &g, int mode, int *err, cudaStream_t s);
+// utab: the interpolation operand table (tc_interp_table_bytes(), built by tc_interp_table)
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, bool tma_store,
+                            const void *utab, int mode, int *err, cudaStream_t s);
+size_t tc_interp_table_bytes();
+void tc_interp_table(const Halfband &g, void *host_out);
 cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                                 cudaStream_t s);
 
