@@ -260,6 +260,7 @@ constexpr int kUVariants = 16;                           // (parity, offset 0..7
 constexpr int kMixStBytes = 2 * 32 * 64;                 // store staging: hi + lo, 32 filters x 32 samples
 constexpr int kMixThreads = 384;
 constexpr int kMixMaxWin = 4;
+constexpr size_t kMixSmemMax = 227 * 1024;               // dynamic shared memory per CTA (opt-in maximum)
 
 size_t tc_interp_table_bytes() { return (size_t)kUVariants * kUVarBytes; }
 
@@ -361,14 +362,15 @@ __device__ __forceinline__ uint64_t desc_u(uint32_t saddr) { return smem_desc(sa
 
 template <int MODE>
 __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
-                                                                   int total_tiles, int n_win, int n_stbuf,
+                                                                   int total_tiles, int n_st, int n_win, int n_u,
+                                                                   int n_stbuf,
                                                                    const uint8_t *__restrict__ utab, int *err) {
     constexpr int kKC = 128 / Op<MODE>::kBytes, kMK = Op<MODE>::kMmaK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + 1;
-    uint64_t *wfull = empty + 1;
+    uint64_t *empty = full + 2;
+    uint64_t *wfull = empty + 2;
     uint64_t *wempty = wfull + kMixMaxWin;
     uint64_t *ufull = wempty + kMixMaxWin;
     uint64_t *uempty = ufull + 2;
@@ -376,10 +378,10 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     uint64_t *aempty = afull + 2;
     uint64_t *mdrain = aempty + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mdrain + 1);
-    uint8_t *stage = smem + 1024;                                  // one mixing stage
-    uint8_t *win = stage + kMixStageBytes;                         // n_win window chunks
-    uint8_t *ubuf = win + n_win * kWinChunkBytes;                  // 2 U variants
-    uint8_t *stbuf = ubuf + 2 * kUVarBytes;                        // n_stbuf per epilogue warp
+    uint8_t *stage = smem + 1024;                                  // n_st mixing stages
+    uint8_t *win = stage + n_st * kMixStageBytes;                  // n_win window chunks
+    uint8_t *ubuf = win + n_win * kWinChunkBytes;                  // n_u U variants
+    uint8_t *stbuf = ubuf + n_u * kUVarBytes;                      // n_stbuf per epilogue warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) {
@@ -387,8 +389,10 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         tmem_relinquish();
     }
     if (threadIdx.x == 32) {
-        mbar_init(full, 1);
-        mbar_init(empty, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
         for (int s = 0; s < kMixMaxWin; ++s) {
             mbar_init(&wfull[s], 1);
             mbar_init(&wempty[s], 1);
@@ -411,29 +415,35 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     if (warp == 0 && lane == 0) {
         // ---- TMA producer ----
         uint32_t su = 0, wu = 0, uu = 0;
+        int uvar = -1;                                       // U variant in the newest U buffer
         bool ok = true;
         for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
             const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
             const TcMixUpTask &t = *m.t;
             for (int kc = 0; kc < m.nk; ++kc) {
-                if (su >= 1 && !mbar_wait(empty, (su - 1) & 1, err, 5)) {
+                const int s = su % n_st;
+                if (su >= (uint32_t)n_st && !mbar_wait(&empty[s], ((su / n_st) - 1) & 1, err, 5)) {
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(full, kMixStageBytes);
-                tma_load_2d(stage, t.mapM, kc * kKC, m.at * kMixRows, full);
-                tma_load_2d(stage + kMixABytes, t.mapO, kc * kKC, m.tt * kMixCols, full);
+                uint8_t *sa = stage + s * kMixStageBytes;
+                mbar_expect_tx(&full[s], 3 * kMixRows * t.kbytes);
+                tma_load_2d(sa, t.mapM, kc * kKC, m.at * kMixRows, &full[s]);
+                tma_load_2d(sa + kMixRows * t.kbytes, t.mapO, kc * kKC, m.tt * kMixCols, &full[s]);
                 ++su;
             }
             if (!ok || !t.mapY) continue;
-            const int us = uu & 1;
-            if (uu >= 2 && !mbar_wait(&uempty[us], ((uu >> 1) - 1) & 1, err, 11)) {
-                ok = false;
-                break;
+            if (m.var != uvar) {                             // a new U variant (tiles of one task share it)
+                const int us = uu % n_u;
+                if (uu >= (uint32_t)n_u && !mbar_wait(&uempty[us], ((uu / n_u) - 1) & 1, err, 11)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&ufull[us], kUVarBytes);
+                bulk_load(ubuf + us * kUVarBytes, utab + (size_t)m.var * kUVarBytes, kUVarBytes, &ufull[us]);
+                ++uu;
+                uvar = m.var;
             }
-            mbar_expect_tx(&ufull[us], kUVarBytes);
-            bulk_load(ubuf + us * kUVarBytes, utab + (size_t)m.var * kUVarBytes, kUVarBytes, &ufull[us]);
-            ++uu;
             for (int wc = 0; wc < kWinChunks; ++wc) {
                 const int ws = wu % n_win;
                 if (wu >= (uint32_t)n_win && !mbar_wait(&wempty[ws], ((wu / n_win) - 1) & 1, err, 8)) {
@@ -451,14 +461,15 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         if (!ok) {
             // copies still in flight land before the CTA leaves: wait for the last load of each buffer
             // (the last use of slot s of a ring of n is use s + n ((used - 1 - s) / n))
-            if (su > 0) mbar_wait_bounded(full, (su - 1) & 1);
-            for (int s = 0; s < 2 && s < (int)uu; ++s) mbar_wait_bounded(&ufull[s], ((uu - 1 - s) / 2) & 1);
+            for (int s = 0; s < n_st && s < (int)su; ++s) mbar_wait_bounded(&full[s], ((su - 1 - s) / n_st) & 1);
+            for (int s = 0; s < n_u && s < (int)uu; ++s) mbar_wait_bounded(&ufull[s], ((uu - 1 - s) / n_u) & 1);
             for (int s = 0; s < n_win && s < (int)wu; ++s)
                 mbar_wait_bounded(&wfull[s], ((wu - 1 - s) / n_win) & 1);
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
         uint32_t su = 0, wu = 0, uu = 0, au = 0;
+        int uvar = -1;
         bool issued = false;
         const uint32_t idesc = idesc_op<MODE>(kMixRows, kMixCols);
         const uint32_t idesc_u = idesc_op<kModeBF16>(kMixRows, kUBlk);
@@ -471,28 +482,40 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
             const uint32_t d = tmem + b * kMixCols;
             bool ok = true;
             for (int kc = 0; kc < m.nk; ++kc) {
-                if (!mbar_wait(full, su & 1, err, 6)) {
+                const int s = su % n_st;
+                if (!mbar_wait(&full[s], (su / n_st) & 1, err, 6)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(stage);
-                const int nmma = min(128 / (kMK * Op<MODE>::kBytes), (m.t->Lk_pad - kc * kKC) / kMK);
+                const int kb = m.t->kbytes;
+                // descriptors differ only in the start address field (address >> 4, no carry)
+                const uint32_t sa = smem_u32(stage + s * kMixStageBytes);
+                const uint64_t da = desc_k_sw(sa, kb), db = desc_k_sw(sa + kMixRows * kb, kb);
+                const int nmma = min(kb / 32, (m.t->Lk_pad - kc * kKC) / kMK);     // 32 bytes of K per MMA
                 for (int kk = 0; kk < nmma; ++kk)
-                    mma_op<MODE>(d, desc_k_sw128(sa + kk * 32), desc_k_sw128(sa + kMixABytes + kk * 32), idesc,
-                                 (kc | kk) != 0);
+                    mma_op<MODE>(d, da + 2 * kk, db + 2 * kk, idesc, (kc | kk) != 0);
                 issued = true;
-                mma_commit(empty);
+                mma_commit(&empty[s]);
                 ++su;
             }
             if (!ok) break;
             if (has_src) {
-                const int us = uu & 1;
-                if (!mbar_wait(&ufull[us], (uu >> 1) & 1, err, 12)) break;
+                if (m.var != uvar) {                         // switch to the next U buffer
+                    if (uvar >= 0) {
+                        mma_commit(&uempty[(uu - 1) % n_u]);   // released once the previous variant's MMAs complete
+                    }
+                    if (!mbar_wait(&ufull[uu % n_u], (uu / n_u) & 1, err, 12)) break;
+                    ++uu;
+                    uvar = m.var;
+                }
+                const int us = (uu - 1) % n_u;
                 tc_fence_after();
-                const uint32_t uhi = smem_u32(ubuf + us * kUVarBytes), ulo = uhi + kUBytes;
+                const uint64_t du_hi = desc_u(smem_u32(ubuf + us * kUVarBytes)), du_lo = du_hi + (kUBytes >> 4);
+                const uint32_t first = m.nk > 0 ? 1u : 0u;           // no mixing: each block starts afresh
                 // block j reads window samples [32 j, 32 j + 80): K step (j, s) sits at sample 32 j + 16 s,
-                // in window chunk (32 j + 16 s) / 64
+                // in window chunk (32 j + 16 s) / 64; fully unrolled, so the schedule is fixed at compile time
+#pragma unroll
                 for (int wc = 0; wc < kWinChunks; ++wc) {
                     const int ws = wu % n_win;
                     if (!mbar_wait(&wfull[ws], (wu / n_win) & 1, err, 13)) {
@@ -500,25 +523,25 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t whi = smem_u32(win + ws * kWinChunkBytes), wlo = whi + kWinHalfBytes;
+                    const uint64_t da_hi = desc_k_sw128(smem_u32(win + ws * kWinChunkBytes));
+                    const uint64_t da_lo = da_hi + (kWinHalfBytes >> 4);
+#pragma unroll
                     for (int j = 0; j < 4; ++j)
+#pragma unroll
                         for (int st = 0; st < kUK / 16; ++st) {
                             const int kap = 32 * j + 16 * st;
                             if (kap / 64 != wc) continue;
-                            const uint32_t off = (uint32_t)(kap % 64) * 2;
+                            const uint64_t ao = (uint64_t)((kap % 64) * 2 / 16), bo = (uint64_t)(256 * st / 16);
                             const uint32_t dj = d + kUBlk * j;
-                            const uint32_t acc0 = (m.nk > 0 || kap > 32 * j) ? 1u : 0u;
-                            mma_f16(dj, desc_k_sw128(whi + off), desc_u(uhi + 256 * st), idesc_u, acc0);
-                            mma_f16(dj, desc_k_sw128(whi + off), desc_u(ulo + 256 * st), idesc_u, 1u);
-                            mma_f16(dj, desc_k_sw128(wlo + off), desc_u(uhi + 256 * st), idesc_u, 1u);
+                            mma_f16(dj, da_hi + ao, du_hi + bo, idesc_u, kap > 32 * j ? 1u : first);
+                            mma_f16(dj, da_hi + ao, du_lo + bo, idesc_u, 1u);
+                            mma_f16(dj, da_lo + ao, du_hi + bo, idesc_u, 1u);
                         }
                     issued = true;
                     mma_commit(&wempty[ws]);
                     ++wu;
                 }
                 if (!ok) break;
-                mma_commit(&uempty[us]);
-                ++uu;
             }
             mma_commit(&afull[b]);
             ++au;
@@ -532,7 +555,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         const int q = warp & 3, h = (warp >> 2) - 1;            // TMEM lane quarter (warp % 4), half tile
         const int R = 32 * q + lane;                         // TMEM lane = filter row in the tile
         uint8_t *sbuf = stbuf + (warp - 4) * kMixStBytes;
-        uint32_t au = 0, stu = 0;                            // stu: staged stores issued by this warp
+        uint32_t au = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
             const TcMixUpTask &t = *m.t;
@@ -540,9 +563,9 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
             if (!mbar_wait(&afull[b], (au >> 1) & 1, err, 7)) break;
             tc_fence_after();
             // task fields used per chunk, read once per tile
-            const int64_t first_n = t.first_n, Bk = t.Bk, ldy = t.ldy, yst_col0 = t.yst_col0;
+            const int64_t first_n = t.first_n, Bk = t.Bk, ldy = t.ldy, yst_col0 = t.yst_col0, ldu = t.ldu;
             float *const Y = t.Y;
-            const CUtensorMap *const mapYst = t.mapYst;
+            uint16_t *const Yh = t.Yh;
             const int M2 = t.M2;
             const int a = kMixRows * m.at + R;
             const bool row_ok = a < M2;
@@ -584,23 +607,21 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     for (int j = 0; j < 32; ++j)
                         if (n0 + j < 0) x[j] = 0.0f;         // every rate starts at index 0
                 }
-                if (mapYst && n_stbuf > 0) {
-                    // staged store of y as BF16 hi / lo: row `lane` of two 32 x 32 tiles with 64-byte
-                    // swizzle (16-byte chunk i of row r at chunk i ^ ((r >> 1) & 3)), then two TMA stores
-                    if (stu >= 1) {
-                        if (lane == 0) bulk_wait_read_0();           // the previous store has read the buffer
-                        __syncwarp();
-                    }
+                if (Yh && n_stbuf > 0) {
+                    // y as BF16 hi / lo through a per-warp staging buffer: row `lane` of two 32 x 32 tiles
+                    // (64-byte rows, 16-byte chunk i at chunk i ^ ((r >> 1) & 3): no bank conflicts),
+                    // then each store instruction writes 8 whole 64-byte row segments
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float y0 = x[2 * j] * inv_next, y1 = x[2 * j + 1] * inv_next;
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(y0), h1 = __float2bfloat16_rn(y1);
-                        const __nv_bfloat16 l0 = __float2bfloat16_rn(y0 - __bfloat162float(h0));
-                        const __nv_bfloat16 l1 = __float2bfloat16_rn(y1 - __bfloat162float(h1));
-                        hw[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                        lw[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                        const __nv_bfloat162 hv = __floats2bfloat162_rn(y0, y1);       // hi: one packed convert
+                        const float2 hf = __bfloat1622float2(hv);
+                        const __nv_bfloat162 lv = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
+                        hw[j] = *reinterpret_cast<const uint32_t *>(&hv);
+                        lw[j] = *reinterpret_cast<const uint32_t *>(&lv);
                     }
+                    __syncwarp();                                   // the previous chunk's reads are done
                     const int sw = (lane >> 1) & 3;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -609,15 +630,21 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                         *reinterpret_cast<uint4 *>(sbuf + 2048 + lane * 64 + ((i ^ sw) * 16)) =
                             make_uint4(lw[4 * i], lw[4 * i + 1], lw[4 * i + 2], lw[4 * i + 3]);
                     }
-                    fence_proxy_async();
                     __syncwarp();
-                    if (lane == 0) {
-                        const int xs = (int)(yst_col0 + col0), ys = kMixRows * m.at + 32 * q;
-                        tma_store_3d(mapYst, sbuf, xs, ys, 0);           // hi
-                        tma_store_3d(mapYst, sbuf + 2048, xs, ys, 1);    // lo
-                        bulk_commit();
+                    const int ch = lane & 3;
+                    const int64_t col = yst_col0 + col0 + 8 * ch;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = (lane >> 2) + 8 * i;          // row of the warp's 32
+                        const int arow = kMixRows * m.at + 32 * q + r;
+                        const int pc = ch ^ ((r >> 1) & 3);
+                        const uint4 vh = *reinterpret_cast<const uint4 *>(sbuf + r * 64 + pc * 16);
+                        const uint4 vl = *reinterpret_cast<const uint4 *>(sbuf + 2048 + r * 64 + pc * 16);
+                        if (arow < M2 && col + 8 <= ldu) {
+                            *reinterpret_cast<uint4 *>(Yh + (int64_t)arow * ldu + col) = vh;
+                            *reinterpret_cast<uint4 *>(Yh + ((int64_t)M2 + arow) * ldu + col) = vl;
+                        }
                     }
-                    ++stu;
                 } else if (Y && row_ok) {
                     float *dst = Y + (int64_t)a * ldy + col0;
                     if (col0 + 32 <= Bk) {
@@ -692,8 +719,6 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
             if (lane == 0) mbar_arrive(&aempty[b]);
             ++au;
         }
-        if (stu > 0 && lane == 0) bulk_wait_all();           // stores done before shared memory is released
-        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -710,8 +735,8 @@ size_t tc_fir_smem_bytes(int kpad_max, int mode) {
     const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2;
     return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * ph + kpad_max) * by;
 }
-size_t tc_mixup_smem_bytes(int n_win, int n_stbuf) {
-    return 1024 + 1024 + (size_t)kMixStageBytes + (size_t)n_win * kWinChunkBytes + 2 * (size_t)kUVarBytes +
+size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf) {
+    return 1024 + 1024 + (size_t)n_st * kMixStageBytes + (size_t)n_win * kWinChunkBytes + (size_t)n_u * kUVarBytes +
            (size_t)8 * n_stbuf * kMixStBytes;
 }
 template <class K>
@@ -759,26 +784,30 @@ static int sm_count() {
 }
 
 template <int MODE>
-static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, bool tma_store,
+static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
                                 const void *utab, int *err, cudaStream_t s) {
-    // shared memory (<= 227 KB): one mixing stage, the window ring, two U variants and, when the
-    // level's y is stored, one staging buffer per epilogue warp
-    const int n_win = tma_store ? 3 : 4, n_stbuf = tma_store ? 1 : 0;
-    const size_t smem = tc_mixup_smem_bytes(n_win, n_stbuf);
+    // shared memory (<= 227 KB): several K chunks per tile take two mixing stages and one U
+    // buffer (U changes only between tasks), one chunk takes one stage and two U buffers; one
+    // staging buffer per epilogue warp when the level's y is stored; the window ring gets the rest
+    const int n_st = max_nk >= 2 ? 2 : 1, n_u = n_st == 2 ? 1 : 2, n_stbuf = store_y ? 1 : 0;
+    const size_t fixed = tc_mixup_smem_bytes(n_st, 0, n_u, n_stbuf);
+    const int n_win = (int)std::min<size_t>(kMixMaxWin, (kMixSmemMax - fixed) / kWinChunkBytes);
+    const size_t smem = tc_mixup_smem_bytes(n_st, n_win, n_u, n_stbuf);
     cudaError_t e = set_smem(tc_mixup_kernel<MODE>, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total_tiles, sm_count());
-    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_win, n_stbuf,
+    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_st, n_win, n_u, n_stbuf,
                                                           static_cast<const uint8_t *>(utab), err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, bool tma_store,
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
                             const void *utab, int mode, int *err, cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    if (mode == kModeBF16) return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, tma_store, utab, err, s);
-    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, tma_store, utab, err, s);
-    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, tma_store, utab, err, s);
+    if (mode == kModeBF16)
+        return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, s);
+    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, s);
+    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, s);
 }
 
 }  // namespace lloid

@@ -126,7 +126,6 @@ struct LevelDev {
     void *M16 = nullptr;      // stacked mixing [2M x Lk_pad]
     CUtensorMap *mapO = nullptr, *mapM = nullptr;   // device addresses (box 64 x 256 time rows, 64 x 128 filters)
     CUtensorMap *mapY = nullptr;     // yuni as the finer level's interpolation operand (box 64 x 128, 128-byte swizzle)
-    CUtensorMap *mapYst = nullptr;   // yuni as this level's store target (box 32 x 32, 64-byte swizzle)
     // 16-bit modes, levels k >= 1: SNR rows [history (Hy) | new (B_k)] in one buffer, so the
     // next finer level's epilogue can stage a row segment with one TMA load
     float *yuni = nullptr;    // FP32 mode: unused; 16/8-bit modes: y as BF16 hi rows [0, 2M), lo rows [2M, 4M), ld ldu
@@ -550,37 +549,32 @@ static void put_elem(std::vector<uint8_t> &buf, size_t i, float v, int mode) {
     }
 }
 
-static int encode_map(CUtensorMap *out, void *base, int mode, uint64_t inner, uint64_t outer, uint32_t box_outer) {
+// Bytes of K per row of a mixing-operand chunk: the padded K when it fits 32 or 64 bytes, else
+// 128-byte chunks (the swizzle span matches, so small-K levels move no padding).
+static int mix_kbytes(int64_t Lk_pad, int mode) {
+    const int64_t b = Lk_pad * mode_bytes(mode);
+    return b <= 32 ? 32 : b <= 64 ? 64 : 128;
+}
+
+static int encode_map(CUtensorMap *out, void *base, int mode, uint64_t inner, uint64_t outer, uint32_t box_outer,
+                      int row_bytes = 128) {
     auto encode = tensor_map_encoder();
     if (!encode) return fail(SB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const int by = mode_bytes(mode);
     cuuint64_t dims[2] = {inner, outer};
     cuuint64_t strides[1] = {inner * by};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / by), box_outer};          // 128-byte rows
+    cuuint32_t box[2] = {(cuuint32_t)(row_bytes / by), box_outer};    // row_bytes-byte rows
     cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(out, mode == kModeE4M3   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                              : mode == kModeBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                                         2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        row_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                        : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                          : CU_TENSOR_MAP_SWIZZLE_32B,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-    return SB_OK;
-}
-
-// y as BF16 [2][rows][inner] (hi, lo) for tile stores: box 32 samples x 32 rows x 1, 64-byte
-// swizzle; the row dimension clips each half at its own bound.
-static int encode_map_y_store(CUtensorMap *out, void *base, uint64_t inner, uint64_t rows) {
-    auto encode = tensor_map_encoder();
-    if (!encode) return fail(SB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    cuuint64_t dims[3] = {inner, rows, 2};
-    cuuint64_t strides[2] = {inner * 2, rows * inner * 2};
-    cuuint32_t box[3] = {32, 32, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(SB_ECUDA, "cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")");
     return SB_OK;
 }
 
@@ -706,7 +700,7 @@ static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d, const std::ve
         if ((rc = dev_alloc_w(u, &L.M16, m.size()))) return rc;
         CK(cudaMemcpy(L.M16, m.data(), m.size(), cudaMemcpyHostToDevice));
         CUtensorMap hm;
-        if ((rc = encode_map(&hm, L.M16, u->mode, L.Lk_pad, M2, 128))) return rc;
+        if ((rc = encode_map(&hm, L.M16, u->mode, L.Lk_pad, M2, 128, mix_kbytes(L.Lk_pad, u->mode)))) return rc;
         if ((rc = upload_map(u, hm, &L.mapM, true))) return rc;
         if (u->mode == kModeE4M3) {
             if ((rc = dev_alloc_w(u, (void **)&L.rscale, M2 * 4))) return rc;
@@ -805,13 +799,11 @@ static int alloc_state(sb_unit *u) {
             CUtensorMap hy;                      // level k - 1's interpolation operand (64 samples x 128 filters)
             if ((rc = encode_map(&hy, L.yuni, kModeBF16, L.ldu, 2 * M2, 128))) return rc;
             if ((rc = upload_map(u, hy, &L.mapY, false))) return rc;
-            CUtensorMap hs;                      // this level's own stores (32 samples x 32 filters)
-            if ((rc = encode_map_y_store(&hs, L.yuni, L.ldu, M2))) return rc;
-            if ((rc = upload_map(u, hs, &L.mapYst, false))) return rc;
         }
         if (L.Lk_pad == 0) continue;
         CUtensorMap ho;
-        if ((rc = encode_map(&ho, L.O16, u->mode, L.Lk_pad, L.Bk_max + 256, 256))) return rc;
+        if ((rc = encode_map(&ho, L.O16, u->mode, L.Lk_pad, L.Bk_max + 256, 256, mix_kbytes(L.Lk_pad, u->mode))))
+            return rc;
         if ((rc = upload_map(u, ho, &L.mapO, false))) return rc;
     }
     CK(cudaStreamSynchronize(u->ctx->alloc_stream));
@@ -1008,7 +1000,6 @@ extern "C" int svdbank_create_like(sb_ctx *c, sb_unit *src, int32_t detector, sb
         L.O16 = nullptr;
         L.mapO = nullptr;
         L.mapY = nullptr;
-        L.mapYst = nullptr;
         L.yuni = nullptr;
         L.ytmp = nullptr;
     }
@@ -1377,8 +1368,10 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     if (k < u->kmax) mt.mapY = u->levels[k + 1].mapY;
                     mt.Y = k == 0 ? L.ynew : nullptr;             // SB_FLAG_KEEP_SNR
                     mt.ldy = L.ldy;
-                    mt.mapYst = k >= 1 ? L.mapYst : nullptr;
+                    mt.Yh = k >= 1 ? reinterpret_cast<uint16_t *>(L.yuni) : nullptr;
+                    mt.ldu = L.ldu;
                     mt.yst_col0 = L.Hy;
+                    mt.kbytes = mix_kbytes(L.Lk_pad, u->mode);
                     mt.rsc_next = k >= 1 ? u->levels[k - 1].rscale : nullptr;
                     mt.part = k == 0 ? u->part : nullptr;
                     mt.first_n = (Tp >> k) - L.lam;
@@ -1570,6 +1563,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     int tfir_tiles[NM] = {0, 0, 0};
     std::vector<int> tmix_tiles[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
                                        std::vector<int>(kall + 1, 0)};
+    std::vector<int> tmix_maxnk[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
+                                       std::vector<int>(kall + 1, 0)};
     std::vector<int> tmix_tstore[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
                                         std::vector<int>(kall + 1, 0)};
     for (int h = 0; h < NM; ++h) {
@@ -1581,7 +1576,9 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             for (auto &m : tmix[h][k]) {
                 m.tile_begin = tmix_tiles[h][k];
                 tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
-                if (m.mapYst) tmix_tstore[h][k] = 1;
+                if (m.Yh) tmix_tstore[h][k] = 1;
+                const int kc = 128 / mode_bytes(h);                  // K elements per 128-byte chunk
+                tmix_maxnk[h][k] = std::max(tmix_maxnk[h][k], (m.Lk_pad + kc - 1) / kc);
             }
     }
     int wfin_warps = 0;
@@ -1702,7 +1699,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
                      *n = 1;
                      return launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
-                                            tmix_tiles[h][k], tmix_tstore[h][k] != 0, c->utab, h, derr, st);
+                                            tmix_tiles[h][k], tmix_maxnk[h][k], tmix_tstore[h][k] != 0, c->utab, h,
+                                            derr, st);
                  })))
                 return rc;
     }

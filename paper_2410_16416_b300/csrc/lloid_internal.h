@@ -166,13 +166,14 @@ struct TcMixUpTask {
                                // box 64 x 128, 128-byte swizzle; null at the deepest level
     float *Y;                  // top level with SB_FLAG_KEEP_SNR: FP32 SNR (row a at Y + a ldy); else null
     int64_t ldy;
-    const CUtensorMap *mapYst; // this level's y as BF16 [hi / lo][2M][ldu], box 32 x 32 x 1, 64-byte swizzle;
-                               // null at the top
-    int64_t yst_col0;          // column of this push's first sample inside mapYst
+    uint16_t *Yh;              // this level's y as BF16 hi rows [0, 2M), lo rows [2M, 4M) (ld ldu); null at the top
+    int64_t ldu;
+    int64_t yst_col0;          // column of this push's first sample in Yh
     WinPart *part;             // top level: partials [i][n_rec], record (tt*2 + half)*2 + seg; null below
     int64_t first_n;           // absolute index (this level's rate) of column 0
     int64_t win_len;           // top level: window length in samples (>= 128)
     int32_t Lk_pad, M2, M, Bk;
+    int32_t kbytes;            // bytes of K per mixing-operand row in one chunk: 32, 64 or 128 (the swizzle span)
     int32_t lam;               // Lambda of this level
     int32_t in_off;            // Lambda_{k+1} + Hy_{k+1}: coarser position of (relative index 0) / 2
     int32_t tiles_t, tiles_a, tile_begin, n_rec;
@@ -200,12 +201,12 @@ struct WinFinTask {
 };
 
 size_t tc_fir_smem_bytes(int kpad_max, int mode);
-size_t tc_mixup_smem_bytes(int n_win, int n_stbuf);
+size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf);
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s);
 // utab: the interpolation operand table (tc_interp_table_bytes(), built by tc_interp_table)
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, bool tma_store,
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
                             const void *utab, int mode, int *err, cudaStream_t s);
 size_t tc_interp_table_bytes();
 void tc_interp_table(const Halfband &g, void *host_out);

@@ -86,26 +86,6 @@ __device__ __forceinline__ void bulk_load(void *smem_dst, const void *gsrc, uint
                  "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-// Tile store shared -> global (bulk async group; the tensor map clips at its bounds).
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *smem_src, int x, int y) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y), "r"(smem_u32(smem_src))
-                 : "memory");
-}
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *smem_src, int x, int y, int z) {
-    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(smem_src))
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// No committed store group is still reading shared memory.
-__device__ __forceinline__ void bulk_wait_read_0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// At most one committed store group may still be reading shared memory.
-__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-// Every committed store group has completed.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -187,6 +167,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes
 // K-major operand tile written by TMA with 128-byte swizzle (rows of 64 16-bit
 // elements, 8-row groups 1024 bytes apart).
 __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) { return smem_desc(saddr, 16, 1024, 2); }
+// K-major tile with rows of `row_bytes` (32, 64 or 128) swizzled over the same span
+// (layout type 6, 4 or 2); 8-row groups 8 * row_bytes apart.
+__device__ __forceinline__ uint64_t desc_k_sw(uint32_t saddr, int row_bytes) {
+    const uint32_t layout = row_bytes == 128 ? 2u : row_bytes == 64 ? 4u : 6u;
+    return smem_desc(saddr, 16, 8 * row_bytes, layout);
+}
 // Hankel operand read straight from a strain window: row n starts 8 elements
 // (16 bytes) after row n-1, so core matrices are 16 bytes apart along K and
 // 8-row groups 128 bytes apart; no swizzle.
