@@ -1,10 +1,12 @@
 // a6: FP32 refinement of candidate window maxima in the 16-bit and 8-bit modes.
 //
 // After the top level's partial maxima are known, every partial record whose
-// |rho| exceeds the refine threshold is recomputed in FP32 over the top-level
-// samples within R = 8 of its maximum (clipped to the record's half tile and
-// window).  The SVD factorisation pays off when all M templates are filtered;
-// for a handful of candidates it does not, so the refinement filters the
+// |rho| exceeds the refine threshold and comes within a margin of its window's
+// 16-bit maximum (so that it may be that window's maximum once refined) is
+// recomputed in FP32 over the top-level samples within R = 8 of its maximum
+// (clipped to the record's half tile and window).  The SVD factorisation pays
+// off when all M templates are filtered; for a handful of candidates it does
+// not, so the refinement filters the
 // strain directly with each template's reconstructed slice filters
 // H_s = M_s V_s (Eq. 4 summed over the basis, FP32, built once per bank):
 //   z_k[row][m] = sum_{slices s at level k} sum_q H_s[2i+row][q] d_k[m - D_s - q]
@@ -24,7 +26,21 @@ namespace lloid {
 __device__ __forceinline__ int64_t floor_div2(int64_t v) { return v >> 1; }
 __device__ __forceinline__ int64_t ceil_div2(int64_t v) { return -((-v) >> 1); }
 
-// R1: every record above the refine threshold becomes a candidate.
+// R1a: 16-bit maximum of |rho|^2 over each (template, window) among records above the threshold
+// (non-negative floats order as their bit patterns).
+__global__ void __launch_bounds__(256) refine_wmax_kernel(const RefUnit *__restrict__ units) {
+    const RefUnit &u = units[blockIdx.y];
+    const int64_t total = (int64_t)u.M * u.n_rec;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const WinPart p = u.part[idx];
+        if (!(p.mag2 > u.thr2)) continue;
+        const int i = (int)(idx / u.n_rec);
+        atomicMax(&u.wmax[(int64_t)i * u.n_wslot + (p.n / u.win_len - u.win0)], __float_as_uint(p.mag2));
+    }
+}
+
+// R1b: records above the threshold and within the margin of their window's maximum become candidates.
 __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restrict__ units,
                                                           RefCand *__restrict__ cands, int *__restrict__ counters,
                                                           int cand_cap) {
@@ -32,7 +48,11 @@ __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restr
     const int64_t total = (int64_t)u.M * u.n_rec;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        if (!(u.part[idx].mag2 > u.thr2)) continue;
+        const WinPart p = u.part[idx];
+        if (!(p.mag2 > u.thr2)) continue;
+        const int i = (int)(idx / u.n_rec);
+        const float wm = __uint_as_float(u.wmax[(int64_t)i * u.n_wslot + (p.n / u.win_len - u.win0)]);
+        if (p.mag2 < u.keep2 * wm) continue;
         const int slot = atomicAdd(&counters[1], 1);
         if (slot < cand_cap) cands[slot] = RefCand{(int)blockIdx.y, idx};
         else atomicExch(&counters[2], 1);          // not every candidate could be refined
@@ -41,7 +61,7 @@ __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restr
 
 // R2: one block (8 warps) per candidate.  At each level every warp takes a
 // contiguous share of each slice's taps; lane l accumulates both rows for
-// m = lo + l and m = lo + 32 + l; the warps' partial sums are added in a fixed
+// m = lo + 2l and m = lo + 2l + 1; the warps' partial sums are added in a fixed
 // order, then the interpolated coarser level is added.
 constexpr int kRefWarps = 8;
 
@@ -72,6 +92,8 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
         }
         int cur = 0;                                    // z[cur]: level k + 1
         for (int k = u.kmax; k >= 0; --k) {
+            // lane l takes outputs m = lo + 2l and lo + 2l + 1: as q steps by one, the strain
+            // sample of the second output is the first's previous one, so one load per tap
             float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
             const float *d = u.lv_d[k];
             const int64_t dlen = u.lv_len[k];
@@ -80,26 +102,44 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
                 const int Q = u.sl_Q[s];
                 const float *H0 = u.sl_H[s] + (int64_t)(2 * i) * u.sl_ldh[s];
                 const float *H1 = H0 + u.sl_ldh[s];
-                const int64_t pa = lo[k] + lane - u.sl_D[s] - u.lv_origin[k];   // d position of m_a at q = 0
-                const int64_t pb = pa + 32;
-                const int qc = (Q + kRefWarps - 1) / kRefWarps;
+                const int64_t pa = lo[k] + 2 * lane - u.sl_D[s] - u.lv_origin[k];   // d position of m_a at q = 0
+                const int qc = ((Q + kRefWarps - 1) / kRefWarps + 3) & ~3;          // taps per warp, multiple of 4
                 const int q0 = warp * qc, q1 = min(Q, q0 + qc);
-#pragma unroll 4
-                for (int q = q0; q < q1; ++q) {
-                    const float h0 = __ldg(H0 + q), h1 = __ldg(H1 + q);
-                    const int64_t ia = pa - q, ib = pb - q;
-                    const float xa = (ia >= 0 && ia < dlen) ? __ldg(d + ia) : 0.0f;
-                    const float xb = (ib >= 0 && ib < dlen) ? __ldg(d + ib) : 0.0f;
-                    a0 = fmaf(h0, xa, a0);
-                    a1 = fmaf(h1, xa, a1);
-                    b0 = fmaf(h0, xb, b0);
-                    b1 = fmaf(h1, xb, b1);
+                if (q0 >= q1) continue;
+                float xb = (pa + 1 - q0 >= 0 && pa + 1 - q0 < dlen) ? __ldg(d + pa + 1 - q0) : 0.0f;
+                if (pa - (q1 - 1) >= 0 && pa + 1 - q0 < dlen) {                    // whole range inside the buffer
+                    int q = q0;
+                    for (; q + 4 <= q1; q += 4) {
+                        const float4 h0 = __ldg(reinterpret_cast<const float4 *>(H0 + q));
+                        const float4 h1 = __ldg(reinterpret_cast<const float4 *>(H1 + q));
+                        const float x0 = __ldg(d + pa - q), x1 = __ldg(d + pa - q - 1);
+                        const float x2 = __ldg(d + pa - q - 2), x3 = __ldg(d + pa - q - 3);
+                        a0 = fmaf(h0.x, x0, a0); a1 = fmaf(h1.x, x0, a1); b0 = fmaf(h0.x, xb, b0); b1 = fmaf(h1.x, xb, b1);
+                        a0 = fmaf(h0.y, x1, a0); a1 = fmaf(h1.y, x1, a1); b0 = fmaf(h0.y, x0, b0); b1 = fmaf(h1.y, x0, b1);
+                        a0 = fmaf(h0.z, x2, a0); a1 = fmaf(h1.z, x2, a1); b0 = fmaf(h0.z, x1, b0); b1 = fmaf(h1.z, x1, b1);
+                        a0 = fmaf(h0.w, x3, a0); a1 = fmaf(h1.w, x3, a1); b0 = fmaf(h0.w, x2, b0); b1 = fmaf(h1.w, x2, b1);
+                        xb = x3;
+                    }
+                    for (; q < q1; ++q) {
+                        const float h0 = __ldg(H0 + q), h1 = __ldg(H1 + q);
+                        const float xa = __ldg(d + pa - q);
+                        a0 = fmaf(h0, xa, a0); a1 = fmaf(h1, xa, a1); b0 = fmaf(h0, xb, b0); b1 = fmaf(h1, xb, b1);
+                        xb = xa;
+                    }
+                } else {                                                             // buffer edge: guarded
+                    for (int q = q0; q < q1; ++q) {
+                        const float h0 = __ldg(H0 + q), h1 = __ldg(H1 + q);
+                        const int64_t ia = pa - q;
+                        const float xa = (ia >= 0 && ia < dlen) ? __ldg(d + ia) : 0.0f;
+                        a0 = fmaf(h0, xa, a0); a1 = fmaf(h1, xa, a1); b0 = fmaf(h0, xb, b0); b1 = fmaf(h1, xb, b1);
+                        xb = xa;
+                    }
                 }
             }
-            part[warp][0][lane] = a0;
-            part[warp][1][lane] = a1;
-            part[warp][0][lane + 32] = b0;
-            part[warp][1][lane + 32] = b1;
+            part[warp][0][2 * lane] = a0;
+            part[warp][1][2 * lane] = a1;
+            part[warp][0][2 * lane + 1] = b0;
+            part[warp][1][2 * lane + 1] = b1;
             __syncthreads();
             if (threadIdx.x < 2 * kRefSpan) {
                 const int row = threadIdx.x / kRefSpan, mi = threadIdx.x % kRefSpan;
@@ -162,6 +202,7 @@ cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_recor
                           const Halfband &g, cudaStream_t s) {
     if (n_units == 0) return cudaSuccess;
     const int fb = (int)std::min<int64_t>(1024, (max_records + 255) / 256);
+    refine_wmax_kernel<<<dim3(fb, n_units), 256, 0, s>>>(d_units);
     refine_flag_kernel<<<dim3(fb, n_units), 256, 0, s>>>(d_units, cands, counters, kRefCandCap);
     refine_candidate_kernel<<<8 * 148, kRefWarps * 32, 0, s>>>(d_units, counters, cands, kRefCandCap, g);
     return cudaGetLastError();

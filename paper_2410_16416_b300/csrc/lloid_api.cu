@@ -175,6 +175,8 @@ struct sb_ctx {
     sb_ctx_stats stats{};
     // FP32 refinement scratch (allocated on the first refined push, shared by later pushes)
     RefCand *ref_cands = nullptr;
+    uint32_t *ref_wmax = nullptr;     // per (unit, template, window) 16-bit maxima of one push
+    int64_t ref_wmax_cap = 0;
     void *utab = nullptr;      // tensor-core interpolation operand table (16 variants of U, BF16 hi / lo)
     int *ref_counters = nullptr;
     // profiling: event pairs around each launch, summed per stage on query
@@ -489,6 +491,7 @@ extern "C" int sb_ctx_destroy(sb_ctx *c) {
     release_marks(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->ref_cands) cudaFree(c->ref_cands);
+    if (c->ref_wmax) cudaFree(c->ref_wmax);
     if (c->utab) cudaFree(c->utab);
     if (c->ref_counters) cudaFree(c->ref_counters);
     if (c->stream) cudaStreamSynchronize(c->stream);      // unit memory returned on the work stream
@@ -1304,7 +1307,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                                                       std::vector<std::vector<TcMixUpTask>>(kall + 1)};
     std::vector<WinFinTask> wfin;
     std::vector<RefUnit> refu;
-    int64_t ref_max_records = 0;
+    int64_t ref_max_records = 0, ref_wmax_total = 0;
     std::vector<CopyTask> yshift1, yshift2;
     int kpad_max[NM] = {0, 0, 0};
     int max_hd = 0, max_hy = 0, max_rows = 0;
@@ -1488,6 +1491,11 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             r.first_n = first_n;
             r.win_len = u->win_len;
             r.thr2 = u->refine_thr * u->refine_thr;
+            r.keep2 = u->mode == kModeE4M3 ? kRefKeep8 : kRefKeep16;
+            r.win0 = start / u->win_len;
+            r.n_wslot = (int32_t)((end - 1) / u->win_len - r.win0 + 1);
+            r.wmax = reinterpret_cast<uint32_t *>(ref_wmax_total);   // offset; the base is added before packing
+            ref_wmax_total += (int64_t)u->M * r.n_wslot;
             r.kmax = u->kmax;
             r.M = u->M;
             r.n_rec = (int32_t)((B + kRefTile - 1) / kRefTile) * 4;
@@ -1613,6 +1621,16 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     }
     const size_t o_ycopy = pk.add(ycopy.data(), ycopy.size() * sizeof(CopyTask));
     const size_t o_wfin = pk.add(wfin.data(), wfin.size() * sizeof(WinFinTask));
+    if (!refu.empty()) {                       // window-maxima scratch of the refinement (grown on demand)
+        if (c->ref_wmax_cap < ref_wmax_total) {
+            CK(cudaStreamSynchronize(st));
+            if (c->ref_wmax) cudaFree(c->ref_wmax);
+            c->ref_wmax = nullptr;
+            c->ref_wmax_cap = std::max(ref_wmax_total, 2 * c->ref_wmax_cap);
+            CK(cudaMalloc(&c->ref_wmax, c->ref_wmax_cap * sizeof(uint32_t)));
+        }
+        for (auto &r : refu) r.wmax = c->ref_wmax + reinterpret_cast<intptr_t>(r.wmax);   // offset -> address
+    }
     const size_t o_refu = pk.add(refu.data(), refu.size() * sizeof(RefUnit));
     const size_t o_ys1 = pk.add(yshift1.data(), yshift1.size() * sizeof(CopyTask));
     const size_t o_ys2 = pk.add(yshift2.data(), yshift2.size() * sizeof(CopyTask));
@@ -1711,6 +1729,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
         }
         CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
+        CK(cudaMemsetAsync(c->ref_wmax, 0, ref_wmax_total * sizeof(uint32_t), st));
         if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
                  *n = 2;
                  return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_records, c->ref_cands,

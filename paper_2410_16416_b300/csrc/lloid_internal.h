@@ -226,7 +226,11 @@ struct RefUnit {                         // one unit of a push with refinement o
     int64_t first_n;                     // absolute top-level index of push column 0
     int64_t win_len;
     float thr2;                          // refine threshold squared
-    int32_t kmax, M, n_rec, B, n_slices, pad;
+    float keep2;                         // a record is refined when mag2 >= keep2 x its window's 16-bit maximum
+    uint32_t *wmax;                      // [M][n_wslot] 16-bit window maxima of this push (mag2 bits)
+    int64_t win0;                        // window of slot 0
+    int32_t n_wslot;
+    int32_t kmax, M, n_rec, B, n_slices;
     const float *lv_d[kRefMaxLevels];    // FP32 decimated strain of this push, position 0 = absolute lv_origin
     int64_t lv_origin[kRefMaxLevels], lv_len[kRefMaxLevels];
     const float *sl_H[kRefMaxSlices];    // FP32 reconstructed slice filters [2M][ldh] (mixing x basis)
@@ -240,6 +244,10 @@ struct RefCand {                         // one partial record to refine
 // cands: kRefCandCap entries; counters[1] = candidates found, counters[2] = 1 when some were dropped
 cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_records, RefCand *cands, int *counters,
                           const Halfband &g, cudaStream_t s);
+// Margin of the candidate rule per operand mode: records within (1 - margin) of their window's
+// 16-bit maximum are refined (the 16-bit error stays well inside it).
+constexpr float kRefKeep16 = 0.81f;      // (1 - 0.1)^2, BF16 / FP16
+constexpr float kRefKeep8 = 0.25f;       // (1 - 0.5)^2, E4M3
 
 // ---- launchers (kernels_simt.cu) -------------------------------------------
 cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,
