@@ -81,8 +81,15 @@ def algorithmic_model(bank, units: int, B_s: float, precision: str = "fp32"):
     """Per-stage algorithmic FLOPs and HBM bytes of one push (all units).
 
     Weights and basis outputs move in the operand width (4 bytes in FP32 mode,
-    2 in the 16-bit modes); SNR series are FP32."""
-    w = 4.0 if precision == "fp32" else 2.0
+    2 in the 16-bit modes, 1 in E4M3).  FP32 mode: SNR series are FP32, each
+    level's is written once and read once by the interpolation stage.  16-bit
+    and 8-bit modes: mixing and interpolation are one stage ("mix"); each level
+    k >= 1 writes its y once and the next finer level reads it once (4 bytes per
+    sample, BF16 hi + lo); the top level writes only per-window partial maxima
+    (two 24-byte records per template and 128 samples).  Interpolation FLOPs are
+    the halfband filter's own (about 17 per output), however it is executed."""
+    w = {"fp32": 4.0, "bf16": 2.0, "fp16": 2.0, "fp8": 1.0}[precision]
+    fused = precision != "fp32"
     f0 = bank.top_rate_hz
     M2 = 2 * bank.n_templates
     levels = {}
@@ -101,11 +108,19 @@ def algorithmic_model(bank, units: int, B_s: float, precision: str = "fp32"):
         Lk = sum(s.basis.shape[0] for s in ss)
         N = B_s * f0 / 2 ** k
         fl["mix"] += 2.0 * M2 * Lk * N
-        by["mix"] += w * (M2 * Lk + Lk * N) + 4.0 * M2 * N * (2 if k < kmax else 1)
+        if fused:
+            by["mix"] += w * (M2 * Lk + Lk * N) + (8.0 * M2 * N if k >= 1 else 0.0)
+        else:
+            by["mix"] += w * (M2 * Lk + Lk * N) + 4.0 * M2 * N * (2 if k < kmax else 1)
+    if fused:
+        by["mix"] += (M2 / 2) * (B_s * f0 / 128) * 2 * 24.0          # top-level window records
     for k in range(1, kmax + 1):
         N = B_s * f0 / 2 ** k
-        fl["upsample"] += M2 * (2 * N) * 17
-        by["upsample"] += 4.0 * M2 * (N + 2 * N)
+        if fused:
+            fl["mix"] += M2 * (2 * N) * 17                            # the halfband filter's own work
+        else:
+            fl["upsample"] += M2 * (2 * N) * 17
+            by["upsample"] += 4.0 * M2 * (N + 2 * N)
         fl["decimate"] += 2 * N * 17
         by["decimate"] += 4.0 * (3 * N)
     fl["trigger"] = 3.0 * M2 / 2 * B_s * f0
@@ -247,7 +262,22 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def roofline_of(stages, flops, bytes_, precision, steps, peaks):
+def measured_traffic(stage: str, workload: str, precision: str):
+    """DRAM bytes per step of a stage from a committed ncu capture (profiles/), or None when
+    there is none or the kernel source changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{stage}_{workload}_{precision}.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["kernel_source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except (OSError, KeyError, ValueError):
+        return None
+    return float(rec["dram_bytes_per_step"]) if sha == rec.get("kernel_source_sha256_16") else None
+
+
+def roofline_of(stages, flops, bytes_, precision, steps, peaks, workload="production"):
     """Bound, achieved and fraction of the stage that takes the most device time among the stages
     with an algorithmic model (the refinement's work depends on how many candidates the data
     produce, so it has none and is reported through its time share only)."""
@@ -271,7 +301,8 @@ def roofline_of(stages, flops, bytes_, precision, steps, peaks):
                      "derived: 148 SM x 128 FP32 lanes x 2 FLOP x max SM clock"}
     ach = bytes_[dom] * steps / secs / 1e9
     return dom, {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                 "traffic": None, "kernel": dom, "peak_source": "measured hbm_gbs"}
+                 "traffic": measured_traffic(dom, workload, precision), "algorithmic_bytes": bytes_[dom],
+                 "kernel": dom, "peak_source": "measured hbm_gbs"}
 
 
 def run_serve(args):
@@ -466,7 +497,7 @@ def main():
             flops[k] = flops.get(k, 0.0) + f1[k]
             bytes_[k] = bytes_.get(k, 0.0) + b1[k]
     flops["refine"], bytes_["refine"] = 0.0, 0.0          # data-dependent: no fixed algorithmic work
-    dom, roof = roofline_of(prim["stages"], flops, bytes_, args.precision, args.steps, peaks)
+    dom, roof = roofline_of(prim["stages"], flops, bytes_, args.precision, args.steps, peaks, args.workload)
     busy = {k: v[0] for k, v in prim["stages"].items() if v[1] > 0}
     total_stage_ms = sum(busy.values())
     line = {"metric": METRIC, "value": prim["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
