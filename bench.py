@@ -262,6 +262,25 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def shard_bins(n_bins: int, rank: int, world: int):
+    """Bins of one rank: rank, rank + world, ...  Units never cross ranks, so the data path
+    needs no collective."""
+    return list(range(rank, n_bins, world))
+
+
+def job_rate(tpl_s_rank: float, secs_rank: float, dist, device):
+    """Whole-job throughput: every rank's template-seconds over the slowest rank's time
+    (returns the rate and that time).  dist is torch.distributed or None (one process)."""
+    if dist is None:
+        return tpl_s_rank / secs_rank, secs_rank
+    import torch
+    t = torch.tensor([tpl_s_rank], dtype=torch.float64, device=device)
+    s = torch.tensor([secs_rank], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(t.item()) / float(s.item()), float(s.item())
+
+
 def measured_traffic(stage: str, workload: str, precision: str):
     """DRAM bytes per step of a stage from a committed ncu capture (profiles/), or None when
     there is none or the kernel source changed since it was taken."""
@@ -312,11 +331,16 @@ def run_serve(args):
     from paper_2410_16416_b300 import serve
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:                                     # ranks serve disjoint bins; only the report is reduced
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     banks = [synth.production_shape_bank(i) for i in range(args.distinct_banks)]
     g = np.random.default_rng(20241016 + rank)
     reqs = []
-    for b in range(rank, args.bins, world):
+    for b in shard_bins(args.bins, rank, world):
         bank = banks[b % len(banks)]
         for det in (0, 1):
             reqs.append(serve.StreamRequest(
@@ -333,7 +357,13 @@ def run_serve(args):
     st = ctx.stats()
     ctx.close()
     s = rep.summary()
-    line = {"metric": METRIC, "value": s["template_seconds_per_s"], "unit": UNIT, "n_gpus": world,
+    value, wall = job_rate(rep.template_seconds, rep.wall_s, dist, "cuda")
+    p99 = s["p99_latency_s"] or 0.0
+    if dist is not None:                              # the slowest rank's p99 and max (a conservative merge)
+        lat = torch.tensor([p99, s["max_latency_s"] or 0.0], dtype=torch.float64, device="cuda")
+        dist.all_reduce(lat, op=dist.ReduceOp.MAX)
+        p99, s["max_latency_s"] = float(lat[0]), float(lat[1])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": s["pushes"], "warmup": 0, "ms_per_step": 1e3 * s["wall_s"] / max(1, s["pushes"]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision],
@@ -343,12 +373,14 @@ def run_serve(args):
                                    f"{len(banks)} production-shaped banks (~1000 templates, 6 slices)",
                        "time_scale": args.time_scale, "precision": args.precision,
                        "bank_load_s": load_s},
-            "latency": {"p50_s": s["p50_latency_s"], "p99_s": s["p99_latency_s"], "max_s": s["max_latency_s"],
+            "latency": {"p50_s": s["p50_latency_s"], "p99_s": p99, "max_s": s["max_latency_s"],
                         "buffers": s["buffers"], "definition": "buffer arrival -> its push finished and its "
                                                                "triggers host-visible"},
             "serving": s, "gpu_launches": st["kernel_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
@@ -382,7 +414,7 @@ def main():
         banks = [bank]
         f0 = int(spec.top_rate_hz)
     else:                       # uneven shape-only bins; rank r takes bins r, r + world, ...
-        banks = [synth.shape_only_bank(b) for b in range(rank, args.bins, world)]
+        banks = [synth.shape_only_bank(b) for b in shard_bins(args.bins, rank, world)]
         spec, h, bank = None, None, banks[0]
         f0 = int(banks[0].top_rate_hz)
     B = args.push_seconds * f0
@@ -438,14 +470,10 @@ def main():
         st1 = ctx.stats()
         stages = ctx.stage_times()
         ctx.profile(False)
-        dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-        if dist is not None:
-            tt = torch.tensor([dev_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dev_s = float(tt.item())
+        value, dev_s = job_rate(tpl_s_rank, sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, "cuda")
         trig = ctx.pop_triggers()
         ctx.close()
-        return {"value": world * tpl_s_rank / dev_s, "dev_s": dev_s, "wall": wall, "clocks": clk, "create_s": create_s,
+        return {"value": value, "dev_s": dev_s, "wall": wall, "clocks": clk, "create_s": create_s,
                 "stages": stages, "launches": st1["kernel_launches"] - st0["kernel_launches"],
                 "triggers": int(len(trig))}
 
@@ -476,11 +504,8 @@ def main():
     ctx2.pop_triggers()
     e2e_wall = time.perf_counter() - w1
     s1 = ctx2.stats()
-    if dist is not None:
-        tt = torch.tensor([e2e_wall], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_wall = float(tt.item())
-    e2e = {"value": world * tpl_s_rank / e2e_wall, "unit": UNIT,
+    e2e_value, e2e_wall = job_rate(tpl_s_rank, e2e_wall, dist, "cuda")
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": (s1["h2d_bytes"] - s0["h2d_bytes"]) // args.steps,
            "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // args.steps}
     ctx2.close()
