@@ -435,8 +435,13 @@ def main():
     tpl_s_rank = n_templates_all * args.push_seconds * args.steps
 
     def make_units(ctx, precision):
-        return [ctx.create_unit(b, detector=det, precision=precision, threshold=6.0, refine_threshold=5.5,
-                                window_s=1.0, max_push_samples=B) for b, det in unit_specs]
+        # the two detectors of a bin share one copy of the bank's device data (svdbank_create_like)
+        units = []
+        for b in banks:
+            u0 = ctx.create_unit(b, detector=0, precision=precision, threshold=6.0, refine_threshold=5.5,
+                                 window_s=1.0, max_push_samples=B)
+            units += [u0, ctx.create_like(u0, detector=1)]
+        return units
 
     def device_arm(precision):
         ctx = lloid.Context(local, stream=stream.cuda_stream)
