@@ -252,25 +252,34 @@ constexpr int kMixStageBytes = kMixABytes + kMixBBytes;
 constexpr int kWinHalfBytes = kMixRows * 128;            // 64 coarser samples (BF16) x 128 filters
 constexpr int kWinChunkBytes = 2 * kWinHalfBytes;        // hi + lo
 constexpr int kWinChunks = 3;                            // 192 >= 7 + 176 coarser samples per tile
-constexpr int kUBlk = 64;                                // outputs per interpolation block (MMA N)
-constexpr int kUK = 80;                                  // coarser samples per block (5 MMA K steps)
-constexpr int kUBytes = kUBlk * kUK * 2;                 // one BF16 term, no-swizzle K-major core matrices
-constexpr int kUVarBytes = 2 * kUBytes;                  // hi + lo
+// Interpolation block geometry: UB outputs per block (MMA N); a block reads UB/2 + 48 coarser
+// samples (its own UB/2, 16 + 16 taps and up to 7 + 1 of alignment), rounded to whole MMA K steps.
+template <int UB>
+struct UGeo {
+    static constexpr int kBlk = UB;
+    static constexpr int kK = UB == 64 ? 80 : 112;
+    static constexpr int kBytes = kBlk * kK * 2;         // one BF16 term, no-swizzle K-major core matrices
+    static constexpr int kVarBytes = 2 * kBytes;         // hi + lo
+    static constexpr int kBlocks = 256 / UB;
+};
 constexpr int kUVariants = 16;                           // (parity, offset 0..7)
+// operand table: the 16 variants of the 64-wide blocks, then those of the 128-wide blocks
+constexpr size_t kUTab128 = (size_t)kUVariants * UGeo<64>::kVarBytes;
 constexpr int kMixStBytes = 2 * 32 * 64;                 // store staging: hi + lo, 32 filters x 32 samples
 constexpr int kMixThreads = 384;
 constexpr int kMixMaxWin = 4;
 constexpr size_t kMixSmemMax = 227 * 1024;               // dynamic shared memory per CTA (opt-in maximum)
 
-size_t tc_interp_table_bytes() { return (size_t)kUVariants * kUVarBytes; }
+size_t tc_interp_table_bytes() { return kUTab128 + (size_t)kUVariants * UGeo<128>::kVarBytes; }
 
-// U for variant (par, rem): output c (0..63) of a block takes coarser sample
+// U for variant (par, rem): output c of a block takes coarser sample
 // i = rem + 16 + ((c + par) >> 1) (even c + par: weight 1 = 2 g[0]) or the
 // pairs i - t, i + 1 + t with weight 2 g[2t+1] (odd c + par).  Stored as BF16
 // hi and lo terms in the no-swizzle K-major layout: element (c, i) at byte
-// ((c / 8) * 10 + i / 8) * 128 + (c % 8) * 16 + (i % 8) * 2.
-void tc_interp_table(const Halfband &g, void *host_out) {
-    uint16_t *out = static_cast<uint16_t *>(host_out);
+// ((c / 8) * (K / 8) + i / 8) * 128 + (c % 8) * 16 + (i % 8) * 2.
+template <int UB>
+static void interp_table_part(const Halfband &g, uint16_t *out) {
+    using G = UGeo<UB>;
     auto bf16_bits = [](float v) {                       // round to nearest even
         uint32_t u;
         std::memcpy(&u, &v, 4);
@@ -285,28 +294,34 @@ void tc_interp_table(const Halfband &g, void *host_out) {
     };
     for (int var = 0; var < kUVariants; ++var) {
         const int par = var / 8, rem = var % 8;
-        uint16_t *hi = out + (size_t)var * (kUVarBytes / 2), *lo = hi + kUBytes / 2;
-        std::vector<float> U((size_t)kUBlk * kUK, 0.0f);
-        for (int c = 0; c < kUBlk; ++c) {
+        uint16_t *hi = out + (size_t)var * (G::kVarBytes / 2), *lo = hi + G::kBytes / 2;
+        std::vector<float> U((size_t)G::kBlk * G::kK, 0.0f);
+        for (int c = 0; c < G::kBlk; ++c) {
             const int i = rem + 16 + ((c + par) >> 1);
             if (((c + par) & 1) == 0) {
-                U[(size_t)c * kUK + i] = 1.0f;
+                U[(size_t)c * G::kK + i] = 1.0f;
             } else {
                 for (int t = 0; t < kOddTaps; ++t) {
-                    U[(size_t)c * kUK + i - t] = 2.0f * g.odd[t];
-                    U[(size_t)c * kUK + i + 1 + t] = 2.0f * g.odd[t];
+                    U[(size_t)c * G::kK + i - t] = 2.0f * g.odd[t];
+                    U[(size_t)c * G::kK + i + 1 + t] = 2.0f * g.odd[t];
                 }
             }
         }
-        for (int c = 0; c < kUBlk; ++c)
-            for (int i = 0; i < kUK; ++i) {
-                const size_t at = ((size_t)(c / 8) * (kUK / 8) + i / 8) * 64 + (c % 8) * 8 + (i % 8);
-                const float u = U[(size_t)c * kUK + i];
+        for (int c = 0; c < G::kBlk; ++c)
+            for (int i = 0; i < G::kK; ++i) {
+                const size_t at = ((size_t)(c / 8) * (G::kK / 8) + i / 8) * 64 + (c % 8) * 8 + (i % 8);
+                const float u = U[(size_t)c * G::kK + i];
                 const uint16_t h = bf16_bits(u);
                 hi[at] = h;
                 lo[at] = bf16_bits(u - bf16_val(h));
             }
     }
+}
+
+void tc_interp_table(const Halfband &g, void *host_out) {
+    uint8_t *out = static_cast<uint8_t *>(host_out);
+    interp_table_part<64>(g, reinterpret_cast<uint16_t *>(out));
+    interp_table_part<128>(g, reinterpret_cast<uint16_t *>(out + kUTab128));
 }
 
 struct SegBest {
@@ -357,15 +372,20 @@ __device__ __forceinline__ MixTile mix_tile(const TcMixUpTask *tasks, int n_task
     return m;
 }
 
-// no-swizzle K-major descriptor of U (core matrices 128 B apart along K, 1280 B along N)
-__device__ __forceinline__ uint64_t desc_u(uint32_t saddr) { return smem_desc(saddr, 128, (kUK / 8) * 128, 0); }
+// no-swizzle K-major descriptor of U (core matrices 128 B apart along K, (K / 8) 128 B along N)
+template <int UB>
+__device__ __forceinline__ uint64_t desc_u(uint32_t saddr) {
+    return smem_desc(saddr, 128, (UGeo<UB>::kK / 8) * 128, 0);
+}
 
-template <int MODE>
+template <int MODE, int UB>
 __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
                                                                    int total_tiles, int n_st, int n_win, int n_u,
                                                                    int n_stbuf,
                                                                    const uint8_t *__restrict__ utab, int *err) {
     constexpr int kKC = 128 / Op<MODE>::kBytes, kMK = Op<MODE>::kMmaK;
+    using G = UGeo<UB>;
+    utab += UB == 128 ? kUTab128 : 0;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -381,7 +401,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     uint8_t *stage = smem + 1024;                                  // n_st mixing stages
     uint8_t *win = stage + n_st * kMixStageBytes;                  // n_win window chunks
     uint8_t *ubuf = win + n_win * kWinChunkBytes;                  // n_u U variants
-    uint8_t *stbuf = ubuf + n_u * kUVarBytes;                      // n_stbuf per epilogue warp
+    uint8_t *stbuf = ubuf + n_u * G::kVarBytes;                    // n_stbuf per epilogue warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) {
@@ -439,8 +459,8 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(&ufull[us], kUVarBytes);
-                bulk_load(ubuf + us * kUVarBytes, utab + (size_t)m.var * kUVarBytes, kUVarBytes, &ufull[us]);
+                mbar_expect_tx(&ufull[us], G::kVarBytes);
+                bulk_load(ubuf + us * G::kVarBytes, utab + (size_t)m.var * G::kVarBytes, G::kVarBytes, &ufull[us]);
                 ++uu;
                 uvar = m.var;
             }
@@ -472,7 +492,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         int uvar = -1;
         bool issued = false;
         const uint32_t idesc = idesc_op<MODE>(kMixRows, kMixCols);
-        const uint32_t idesc_u = idesc_op<kModeBF16>(kMixRows, kUBlk);
+        const uint32_t idesc_u = idesc_op<kModeBF16>(kMixRows, G::kBlk);
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
             const bool has_src = m.t->mapY != nullptr;
@@ -511,10 +531,11 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                 }
                 const int us = (uu - 1) % n_u;
                 tc_fence_after();
-                const uint64_t du_hi = desc_u(smem_u32(ubuf + us * kUVarBytes)), du_lo = du_hi + (kUBytes >> 4);
+                const uint64_t du_hi = desc_u<UB>(smem_u32(ubuf + us * G::kVarBytes)), du_lo = du_hi + (G::kBytes >> 4);
                 const uint32_t first = m.nk > 0 ? 1u : 0u;           // no mixing: each block starts afresh
-                // block j reads window samples [32 j, 32 j + 80): K step (j, s) sits at sample 32 j + 16 s,
-                // in window chunk (32 j + 16 s) / 64; fully unrolled, so the schedule is fixed at compile time
+                // block j reads window samples [(UB/2) j, (UB/2) j + K): K step (j, s) sits at sample
+                // (UB/2) j + 16 s, in window chunk ((UB/2) j + 16 s) / 64; fully unrolled, so the schedule
+                // is fixed at compile time
 #pragma unroll
                 for (int wc = 0; wc < kWinChunks; ++wc) {
                     const int ws = wu % n_win;
@@ -526,14 +547,14 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     const uint64_t da_hi = desc_k_sw128(smem_u32(win + ws * kWinChunkBytes));
                     const uint64_t da_lo = da_hi + (kWinHalfBytes >> 4);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
+                    for (int j = 0; j < G::kBlocks; ++j)
 #pragma unroll
-                        for (int st = 0; st < kUK / 16; ++st) {
-                            const int kap = 32 * j + 16 * st;
+                        for (int st = 0; st < G::kK / 16; ++st) {
+                            const int kap = (UB / 2) * j + 16 * st;
                             if (kap / 64 != wc) continue;
                             const uint64_t ao = (uint64_t)((kap % 64) * 2 / 16), bo = (uint64_t)(256 * st / 16);
-                            const uint32_t dj = d + kUBlk * j;
-                            mma_f16(dj, da_hi + ao, du_hi + bo, idesc_u, kap > 32 * j ? 1u : first);
+                            const uint32_t dj = d + UB * j;
+                            mma_f16(dj, da_hi + ao, du_hi + bo, idesc_u, kap > (UB / 2) * j ? 1u : first);
                             mma_f16(dj, da_hi + ao, du_lo + bo, idesc_u, 1u);
                             mma_f16(dj, da_lo + ao, du_hi + bo, idesc_u, 1u);
                         }
@@ -735,8 +756,9 @@ size_t tc_fir_smem_bytes(int kpad_max, int mode) {
     const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2;
     return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * ph + kpad_max) * by;
 }
-size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf) {
-    return 1024 + 1024 + (size_t)n_st * kMixStageBytes + (size_t)n_win * kWinChunkBytes + (size_t)n_u * kUVarBytes +
+size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk) {
+    const size_t uvar = ublk == 128 ? UGeo<128>::kVarBytes : UGeo<64>::kVarBytes;
+    return 1024 + 1024 + (size_t)n_st * kMixStageBytes + (size_t)n_win * kWinChunkBytes + (size_t)n_u * uvar +
            (size_t)8 * n_stbuf * kMixStBytes;
 }
 template <class K>
@@ -783,22 +805,31 @@ static int sm_count() {
     return count[dev];
 }
 
+template <int MODE, int UB>
+static cudaError_t mixup_launch_ub(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int n_st, int n_u,
+                                   int n_stbuf, const void *utab, int *err, cudaStream_t s) {
+    const size_t fixed = tc_mixup_smem_bytes(n_st, 0, n_u, n_stbuf, UB);
+    const int n_win = (int)std::min<size_t>(kMixMaxWin, (kMixSmemMax - fixed) / kWinChunkBytes);
+    const size_t smem = tc_mixup_smem_bytes(n_st, n_win, n_u, n_stbuf, UB);
+    cudaError_t e = set_smem(tc_mixup_kernel<MODE, UB>, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(total_tiles, sm_count());
+    tc_mixup_kernel<MODE, UB><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_st, n_win, n_u,
+                                                              n_stbuf, static_cast<const uint8_t *>(utab), err);
+    return cudaGetLastError();
+}
+
 template <int MODE>
 static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
                                 const void *utab, int *err, cudaStream_t s) {
     // shared memory (<= 227 KB): several K chunks per tile take two mixing stages and one U
     // buffer (U changes only between tasks), one chunk takes one stage and two U buffers; one
-    // staging buffer per epilogue warp when the level's y is stored; the window ring gets the rest
-    const int n_st = max_nk >= 2 ? 2 : 1, n_u = n_st == 2 ? 1 : 2, n_stbuf = store_y ? 1 : 0;
-    const size_t fixed = tc_mixup_smem_bytes(n_st, 0, n_u, n_stbuf);
-    const int n_win = (int)std::min<size_t>(kMixMaxWin, (kMixSmemMax - fixed) / kWinChunkBytes);
-    const size_t smem = tc_mixup_smem_bytes(n_st, n_win, n_u, n_stbuf);
-    cudaError_t e = set_smem(tc_mixup_kernel<MODE>, smem);
-    if (e != cudaSuccess) return e;
-    const int grid = std::min(total_tiles, sm_count());
-    tc_mixup_kernel<MODE><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_st, n_win, n_u, n_stbuf,
-                                                          static_cast<const uint8_t *>(utab), err);
-    return cudaGetLastError();
+    // staging buffer per epilogue warp when the level's y is stored; the window ring gets the rest.
+    // Levels that store nothing (the top) use 128-wide interpolation blocks (fewer, wider MMAs)
+    // with one U buffer.
+    const int n_st = max_nk >= 2 ? 2 : 1, n_stbuf = store_y ? 1 : 0;
+    if (!store_y) return mixup_launch_ub<MODE, 128>(d_tasks, n_tasks, total_tiles, n_st, 1, 0, utab, err, s);
+    return mixup_launch_ub<MODE, 64>(d_tasks, n_tasks, total_tiles, n_st, n_st == 2 ? 1 : 2, n_stbuf, utab, err, s);
 }
 
 cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,

@@ -201,7 +201,7 @@ struct WinFinTask {
 };
 
 size_t tc_fir_smem_bytes(int kpad_max, int mode);
-size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf);
+size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk);
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s);
