@@ -418,7 +418,8 @@ def main():
         spec, h, bank = None, None, banks[0]
         f0 = int(banks[0].top_rate_hz)
     B = args.push_seconds * f0
-    total_s = (args.warmup + args.steps) * args.push_seconds
+    n_prof = min(args.steps, 16)                       # profiled pushes after the timed ones (stage split)
+    total_s = (args.warmup + args.steps + n_prof) * args.push_seconds
     if spec is not None:
         strains = [make_strain(rank, det, total_s, f0, h, spec.n_templates) for det in (0, 1)]
     else:                       # every bank of a detector filters that detector's strain
@@ -455,7 +456,6 @@ def main():
             t += B
         ctx.pop_triggers()
         barrier()
-        ctx.profile(True)
         st0 = ctx.stats()
         clocks = ClockSampler(local)
         clocks.start()
@@ -473,6 +473,12 @@ def main():
         wall = time.perf_counter() - w0
         clk = clocks.stop()
         st1 = ctx.stats()
+        # stage split from separate pushes with every launch bracketed by events (not timed above)
+        ctx.profile(True)
+        for i in range(n_prof):
+            flush.zero_()
+            ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
+            t += B
         stages = ctx.stage_times()
         ctx.profile(False)
         value, dev_s = job_rate(tpl_s_rank, sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, "cuda")
@@ -480,6 +486,7 @@ def main():
         ctx.close()
         return {"value": value, "dev_s": dev_s, "wall": wall, "clocks": clk, "create_s": create_s,
                 "stages": stages, "launches": st1["kernel_launches"] - st0["kernel_launches"],
+                "refine_candidates": st1["refine_candidates"] - st0["refine_candidates"], "prof_steps": n_prof,
                 "triggers": int(len(trig))}
 
     prim = device_arm(args.precision)
@@ -527,7 +534,7 @@ def main():
             flops[k] = flops.get(k, 0.0) + f1[k]
             bytes_[k] = bytes_.get(k, 0.0) + b1[k]
     flops["refine"], bytes_["refine"] = 0.0, 0.0          # data-dependent: no fixed algorithmic work
-    dom, roof = roofline_of(prim["stages"], flops, bytes_, args.precision, args.steps, peaks, args.workload)
+    dom, roof = roofline_of(prim["stages"], flops, bytes_, args.precision, prim["prof_steps"], peaks, args.workload)
     busy = {k: v[0] for k, v in prim["stages"].items() if v[1] > 0}
     total_stage_ms = sum(busy.values())
     line = {"metric": METRIC, "value": prim["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -550,7 +557,8 @@ def main():
             "by_precision": {p: {"value": r["value"], "ms_per_step": 1e3 * r["dev_s"] / args.steps,
                                  "gain_vs_fp32": None}
                              for p, r in [(args.precision, prim), *others.items()]},
-            "wall_s": prim["wall"], "triggers": prim["triggers"]}
+            "wall_s": prim["wall"], "triggers": prim["triggers"],
+            "refine_candidates_per_step": prim["refine_candidates"] / args.steps}
     if "fp32" in line["by_precision"]:
         ref = line["by_precision"]["fp32"]["value"]
         for p in line["by_precision"]:

@@ -215,6 +215,8 @@ typedef struct sb_ctx_stats {
     int64_t h2d_bytes;       /* host -> device bytes copied by pushes          */
     int64_t d2h_bytes;       /* device -> host bytes copied for triggers       */
     int64_t triggers;        /* triggers delivered by triggers_pop             */
+    int64_t refine_candidates;  /* partial window maxima recomputed in FP32 (a6)  */
+    int64_t refine_dropped;     /* pushes whose candidates exceeded the list (65536); the rest kept 16-bit values */
 } sb_ctx_stats;
 int sb_ctx_get_stats(sb_ctx *ctx, sb_ctx_stats *out);
 

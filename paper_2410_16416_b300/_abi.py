@@ -48,7 +48,8 @@ class SbUnitInfo(C.Structure):
 
 class SbCtxStats(C.Structure):
     _fields_ = [("pushes", C.c_int64), ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64), ("triggers", C.c_int64)]
+                ("d2h_bytes", C.c_int64), ("triggers", C.c_int64), ("refine_candidates", C.c_int64),
+                ("refine_dropped", C.c_int64)]
 
 
 STAGES = ["history", "strain", "decimate", "fir", "upsample", "mix", "trigger", "snr_history", "refine"]

@@ -29,6 +29,7 @@ __device__ __forceinline__ int64_t ceil_div2(int64_t v) { return -((-v) >> 1); }
 // R1a: 16-bit maximum of |rho|^2 over each (template, window) among records above the threshold
 // (non-negative floats order as their bit patterns).
 __global__ void __launch_bounds__(256) refine_wmax_kernel(const RefUnit *__restrict__ units) {
+    griddep_wait();
     const RefUnit &u = units[blockIdx.y];
     const int64_t total = (int64_t)u.M * u.n_rec;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -44,6 +45,7 @@ __global__ void __launch_bounds__(256) refine_wmax_kernel(const RefUnit *__restr
 __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restrict__ units,
                                                           RefCand *__restrict__ cands, int *__restrict__ counters,
                                                           int cand_cap) {
+    griddep_wait();
     const RefUnit &u = units[blockIdx.y];
     const int64_t total = (int64_t)u.M * u.n_rec;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -64,15 +66,24 @@ __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restr
 // m = lo + 2l and m = lo + 2l + 1; the warps' partial sums are added in a fixed
 // order, then the interpolated coarser level is added.
 constexpr int kRefWarps = 8;
+constexpr int kRefQC = 2048;                             // filter taps staged per chunk
 
 __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const RefUnit *__restrict__ units,
                                                                           const int *__restrict__ counters,
                                                                           const RefCand *__restrict__ cands,
-                                                                          int cand_cap, Halfband g) {
+                                                                          int cand_cap, unsigned long long *cum,
+                                                                          Halfband g) {
     __shared__ float z[2][2][kRefSpan];                 // ping-pong levels [buf][row][m - lo_k]
     __shared__ float part[kRefWarps][2][kRefSpan];      // per-warp partial FIR sums
+    __shared__ __align__(16) float hs[2][kRefQC];       // staged filter rows (cos, sin)
+    __shared__ __align__(16) float xs[kRefQC + kRefSpan + 8];   // staged strain
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    griddep_wait();
     const int n_cand = min(counters[1], cand_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(&cum[0], (unsigned long long)n_cand);
+        if (counters[2]) atomicAdd(&cum[1], 1ull);
+    }
     for (int ci = blockIdx.x; ci < n_cand; ci += gridDim.x) {
         const RefCand cand = cands[ci];
         const RefUnit &u = units[cand.unit];
@@ -92,8 +103,11 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
         }
         int cur = 0;                                    // z[cur]: level k + 1
         for (int k = u.kmax; k >= 0; --k) {
-            // lane l takes outputs m = lo + 2l and lo + 2l + 1: as q steps by one, the strain
-            // sample of the second output is the first's previous one, so one load per tap
+            // The slice's two filter rows and the strain they meet are staged in shared memory,
+            // kRefQC taps at a time, by coalesced loads of the whole block (one candidate's taps
+            // are a few hundred kB spread over HBM; staging turns them into streaming reads).
+            // Lane l then takes outputs m = lo + 2l and lo + 2l + 1: as q steps by one, the strain
+            // sample of the second output is the first's previous one, so one read per tap.
             float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
             const float *d = u.lv_d[k];
             const int64_t dlen = u.lv_len[k];
@@ -102,37 +116,43 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
                 const int Q = u.sl_Q[s];
                 const float *H0 = u.sl_H[s] + (int64_t)(2 * i) * u.sl_ldh[s];
                 const float *H1 = H0 + u.sl_ldh[s];
-                const int64_t pa = lo[k] + 2 * lane - u.sl_D[s] - u.lv_origin[k];   // d position of m_a at q = 0
-                const int qc = ((Q + kRefWarps - 1) / kRefWarps + 3) & ~3;          // taps per warp, multiple of 4
-                const int q0 = warp * qc, q1 = min(Q, q0 + qc);
-                if (q0 >= q1) continue;
-                float xb = (pa + 1 - q0 >= 0 && pa + 1 - q0 < dlen) ? __ldg(d + pa + 1 - q0) : 0.0f;
-                if (pa - (q1 - 1) >= 0 && pa + 1 - q0 < dlen) {                    // whole range inside the buffer
-                    int q = q0;
-                    for (; q + 4 <= q1; q += 4) {
-                        const float4 h0 = __ldg(reinterpret_cast<const float4 *>(H0 + q));
-                        const float4 h1 = __ldg(reinterpret_cast<const float4 *>(H1 + q));
-                        const float x0 = __ldg(d + pa - q), x1 = __ldg(d + pa - q - 1);
-                        const float x2 = __ldg(d + pa - q - 2), x3 = __ldg(d + pa - q - 3);
-                        a0 = fmaf(h0.x, x0, a0); a1 = fmaf(h1.x, x0, a1); b0 = fmaf(h0.x, xb, b0); b1 = fmaf(h1.x, xb, b1);
-                        a0 = fmaf(h0.y, x1, a0); a1 = fmaf(h1.y, x1, a1); b0 = fmaf(h0.y, x0, b0); b1 = fmaf(h1.y, x0, b1);
-                        a0 = fmaf(h0.z, x2, a0); a1 = fmaf(h1.z, x2, a1); b0 = fmaf(h0.z, x1, b0); b1 = fmaf(h1.z, x1, b1);
-                        a0 = fmaf(h0.w, x3, a0); a1 = fmaf(h1.w, x3, a1); b0 = fmaf(h0.w, x2, b0); b1 = fmaf(h1.w, x2, b1);
-                        xb = x3;
+                const int64_t p0 = lo[k] - u.sl_D[s] - u.lv_origin[k];   // d position of output lo + mi at tap q: p0 + mi - q
+                for (int qb = 0; qb < Q; qb += kRefQC) {
+                    const int qn = min(kRefQC, Q - qb);
+                    // strain positions the chunk reads: [p0 - (qb + qn - 1), p0 + 63 - qb], from a 16-byte boundary
+                    const int64_t plo = p0 - (qb + qn - 1);
+                    const int64_t base = plo - (((plo % 4) + 4) % 4);
+                    const int nx = (int)(p0 + kRefSpan - qb - base);
+                    const int nx4 = (nx + 3) & ~3;
+                    __syncthreads();                                       // the previous chunk's readers are done
+                    for (int v = threadIdx.x; v < (qn + 3) / 4; v += blockDim.x) {   // rows padded to 4 floats
+                        reinterpret_cast<float4 *>(hs[0])[v] = __ldg(reinterpret_cast<const float4 *>(H0 + qb) + v);
+                        reinterpret_cast<float4 *>(hs[1])[v] = __ldg(reinterpret_cast<const float4 *>(H1 + qb) + v);
                     }
-                    for (; q < q1; ++q) {
-                        const float h0 = __ldg(H0 + q), h1 = __ldg(H1 + q);
-                        const float xa = __ldg(d + pa - q);
-                        a0 = fmaf(h0, xa, a0); a1 = fmaf(h1, xa, a1); b0 = fmaf(h0, xb, b0); b1 = fmaf(h1, xb, b1);
-                        xb = xa;
+                    if (base >= 0 && base + nx4 <= dlen) {
+                        for (int v = threadIdx.x; v < nx4 / 4; v += blockDim.x)
+                            reinterpret_cast<float4 *>(xs)[v] = __ldg(reinterpret_cast<const float4 *>(d + base) + v);
+                    } else {                                               // buffer edge: zero outside
+                        for (int v = threadIdx.x; v < nx4; v += blockDim.x) {
+                            const int64_t pp = base + v;
+                            xs[v] = (pp >= 0 && pp < dlen) ? d[pp] : 0.0f;
+                        }
                     }
-                } else {                                                             // buffer edge: guarded
-                    for (int q = q0; q < q1; ++q) {
-                        const float h0 = __ldg(H0 + q), h1 = __ldg(H1 + q);
-                        const int64_t ia = pa - q;
-                        const float xa = (ia >= 0 && ia < dlen) ? __ldg(d + ia) : 0.0f;
-                        a0 = fmaf(h0, xa, a0); a1 = fmaf(h1, xa, a1); b0 = fmaf(h0, xb, b0); b1 = fmaf(h1, xb, b1);
-                        xb = xa;
+                    __syncthreads();
+                    const int qcw = ((qn + kRefWarps - 1) / kRefWarps + 3) & ~3;   // taps per warp
+                    const int q0 = warp * qcw, q1 = min(qn, q0 + qcw);
+                    if (q0 < q1) {
+                        const int xa0 = (int)(p0 - base - qb) + 2 * lane;        // x index of output 2 lane at tap 0
+                        float xb = xs[xa0 + 1 - q0];
+                        for (int q = q0; q < q1; ++q) {
+                            const float h0 = hs[0][q], h1 = hs[1][q];
+                            const float xa = xs[xa0 - q];
+                            a0 = fmaf(h0, xa, a0);
+                            a1 = fmaf(h1, xa, a1);
+                            b0 = fmaf(h0, xb, b0);
+                            b1 = fmaf(h1, xb, b1);
+                            xb = xa;
+                        }
                     }
                 }
             }
@@ -199,13 +219,16 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
 }
 
 cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_records, RefCand *cands, int *counters,
-                          const Halfband &g, cudaStream_t s) {
+                          unsigned long long *cum, const Halfband &g, cudaStream_t s) {
     if (n_units == 0) return cudaSuccess;
     const int fb = (int)std::min<int64_t>(1024, (max_records + 255) / 256);
-    refine_wmax_kernel<<<dim3(fb, n_units), 256, 0, s>>>(d_units);
-    refine_flag_kernel<<<dim3(fb, n_units), 256, 0, s>>>(d_units, cands, counters, kRefCandCap);
-    refine_candidate_kernel<<<8 * 148, kRefWarps * 32, 0, s>>>(d_units, counters, cands, kRefCandCap, g);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(refine_wmax_kernel, dim3(fb, n_units), dim3(256), 0, s, d_units);
+    if (e == cudaSuccess)
+        e = launch_pdl(refine_flag_kernel, dim3(fb, n_units), dim3(256), 0, s, d_units, cands, counters, kRefCandCap);
+    if (e == cudaSuccess)
+        e = launch_pdl(refine_candidate_kernel, dim3(8 * 148), dim3(kRefWarps * 32), 0, s, d_units,
+                       (const int *)counters, (const RefCand *)cands, kRefCandCap, cum, g);
+    return e;
 }
 
 }  // namespace lloid

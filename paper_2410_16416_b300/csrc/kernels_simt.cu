@@ -12,6 +12,7 @@ namespace lloid {
 // a1: decimation by two with the halfband kernel (g[0] = 1/2, odd taps only).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) decimate_kernel(const DecimTask *__restrict__ tasks, Halfband g) {
+    griddep_wait();
     const DecimTask t = tasks[blockIdx.y];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= t.n_out) return;
@@ -33,6 +34,7 @@ __global__ void __launch_bounds__(256) decimate_kernel(const DecimTask *__restri
 // the chunk plus the 2K-1 tap halo on each side) is staged in shared memory with
 // coalesced loads, then every output is formed from shared memory.
 __global__ void __launch_bounds__(256) upsample_kernel(const UpTask *__restrict__ tasks, Halfband g) {
+    griddep_wait();
     constexpr int kSeg = kUpChunk / 2 + 2 * kHalfK + 2;
     __shared__ float seg[kSeg];
     const UpTask &t = tasks[blockIdx.z];
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(256) upsample_kernel(const UpTask *__restrict_
 // history shifts: dst[r][i] = [hist | cur][r][off + i]
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) copy_kernel(const CopyTask *__restrict__ tasks) {
+    griddep_wait();
     const CopyTask t = tasks[blockIdx.z];
     const int row = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -106,6 +109,7 @@ __device__ __forceinline__ int find_task_by_tile(const GemmTask *tasks, int n, i
 }
 
 __global__ void __launch_bounds__(256) gemm_fp32_kernel(const GemmTask *__restrict__ tasks, int n_tasks) {
+    griddep_wait();
     const int ti = find_task_by_tile(tasks, n_tasks, blockIdx.x);
     const GemmTask t = tasks[ti];
     const int local = blockIdx.x - t.tile_begin;
@@ -131,6 +135,7 @@ __device__ __forceinline__ int find_task_by_warp(const WinTask *tasks, int n, in
 
 __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restrict__ tasks, int n_tasks,
                                                          int total_warps, TrigOut out) {
+    griddep_wait();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (gw >= total_warps) return;
@@ -211,6 +216,7 @@ __device__ __forceinline__ int find_task_by_warp(const WinFinTask *tasks, int n,
 
 __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__restrict__ tasks, int n_tasks,
                                                            int total_warps, TrigOut out) {
+    griddep_wait();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (gw >= total_warps) return;
@@ -280,45 +286,40 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
 cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                                 cudaStream_t s) {
     if (n_tasks == 0 || total_warps == 0) return cudaSuccess;
-    win_finalize_kernel<<<(total_warps * 32 + 255) / 256, 256, 0, s>>>(d_tasks, n_tasks, total_warps, out);
-    return cudaGetLastError();
+    return launch_pdl(win_finalize_kernel, dim3((total_warps * 32 + 255) / 256), dim3(256), 0, s, d_tasks, n_tasks,
+                      total_warps, out);
 }
 
 cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,
                             cudaStream_t s) {
     if (n_tasks == 0 || max_out <= 0) return cudaSuccess;
     dim3 grid((max_out + 255) / 256, n_tasks);
-    decimate_kernel<<<grid, 256, 0, s>>>(d_tasks, g);
-    return cudaGetLastError();
+    return launch_pdl(decimate_kernel, grid, dim3(256), 0, s, d_tasks, g);
 }
 
 cudaError_t launch_upsample(const UpTask *d_tasks, int n_tasks, int max_rows, int max_out,
                             const Halfband &g, cudaStream_t s) {
     if (n_tasks == 0 || max_out <= 0 || max_rows <= 0) return cudaSuccess;
     dim3 grid((max_out + kUpChunk - 1) / kUpChunk, max_rows, n_tasks);
-    upsample_kernel<<<grid, 256, 0, s>>>(d_tasks, g);
-    return cudaGetLastError();
+    return launch_pdl(upsample_kernel, grid, dim3(256), 0, s, d_tasks, g);
 }
 
 cudaError_t launch_copy(const CopyTask *d_tasks, int n_tasks, int max_rows, int max_n, cudaStream_t s) {
     if (n_tasks == 0 || max_n <= 0 || max_rows <= 0) return cudaSuccess;
     dim3 grid((max_n + 255) / 256, max_rows, n_tasks);
-    copy_kernel<<<grid, 256, 0, s>>>(d_tasks);
-    return cudaGetLastError();
+    return launch_pdl(copy_kernel, grid, dim3(256), 0, s, d_tasks);
 }
 
 cudaError_t launch_gemm_fp32(const GemmTask *d_tasks, int n_tasks, int total_tiles, cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    gemm_fp32_kernel<<<total_tiles, 256, 0, s>>>(d_tasks, n_tasks);
-    return cudaGetLastError();
+    return launch_pdl(gemm_fp32_kernel, dim3(total_tiles), dim3(256), 0, s, d_tasks, n_tasks);
 }
 
 cudaError_t launch_window_max(const WinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                               cudaStream_t s) {
     if (n_tasks == 0 || total_warps == 0) return cudaSuccess;
     const int blocks = (total_warps * 32 + 255) / 256;
-    window_max_kernel<<<blocks, 256, 0, s>>>(d_tasks, n_tasks, total_warps, out);
-    return cudaGetLastError();
+    return launch_pdl(window_max_kernel, dim3(blocks), dim3(256), 0, s, d_tasks, n_tasks, total_warps, out);
 }
 
 }  // namespace lloid

@@ -85,6 +85,7 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(256) to_half_kernel(const HalfConvTask *__restrict__ tasks) {
+    griddep_wait();
     const HalfConvTask t = tasks[blockIdx.y];
     using T = typename Op<MODE>::T;
     T *dst = reinterpret_cast<T *>(t.dst);
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(256) to_half_kernel(const HalfConvTask *__rest
 
 // |x| maximum of each task's source (E4M3 mode), as the bits of a non-negative float.
 __global__ void __launch_bounds__(256) absmax_kernel(const HalfConvTask *__restrict__ tasks) {
+    griddep_wait();
     const HalfConvTask t = tasks[blockIdx.y];
     float m = 0.0f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n; i += (int64_t)gridDim.x * blockDim.x)
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    griddep_wait();                                  // the prologue above overlaps the previous kernel's tail
     const int nk = t.Kpad / kKC;
 
     if (warp == 0 && lane == 0) {
@@ -431,6 +434,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    griddep_wait();                                  // the prologue above overlaps the previous kernel's tail
 
     if (warp == 0 && lane == 0) {
         // ---- TMA producer ----
@@ -769,11 +773,12 @@ static cudaError_t set_smem(K kernel, size_t smem) {
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s) {
     if (n_tasks == 0) return cudaSuccess;
     dim3 grid(64, n_tasks);
-    if (mode == kModeBF16) to_half_kernel<kModeBF16><<<grid, 256, 0, s>>>(d_tasks);
-    else if (mode == kModeF16) to_half_kernel<kModeF16><<<grid, 256, 0, s>>>(d_tasks);
+    if (mode == kModeBF16) return launch_pdl(to_half_kernel<kModeBF16>, grid, dim3(256), 0, s, d_tasks);
+    if (mode == kModeF16) return launch_pdl(to_half_kernel<kModeF16>, grid, dim3(256), 0, s, d_tasks);
     else {
-        absmax_kernel<<<grid, 256, 0, s>>>(d_tasks);
-        to_half_kernel<kModeE4M3><<<grid, 256, 0, s>>>(d_tasks);
+        cudaError_t e = launch_pdl(absmax_kernel, grid, dim3(256), 0, s, d_tasks);
+        if (e == cudaSuccess) e = launch_pdl(to_half_kernel<kModeE4M3>, grid, dim3(256), 0, s, d_tasks);
+        return e;
     }
     return cudaGetLastError();
 }
@@ -784,8 +789,7 @@ static cudaError_t fir_launch(const TcFirTask *d_tasks, int n_tasks, int total_t
     const size_t smem = tc_fir_smem_bytes(kpad_max, MODE);
     cudaError_t e = set_smem(tc_fir_kernel<MODE>, smem);
     if (e != cudaSuccess) return e;
-    tc_fir_kernel<MODE><<<total_tiles, 128, smem, s>>>(d_tasks, n_tasks, err);
-    return cudaGetLastError();
+    return launch_pdl(tc_fir_kernel<MODE>, dim3(total_tiles), dim3(128), smem, s, d_tasks, n_tasks, err);
 }
 
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
@@ -814,9 +818,8 @@ static cudaError_t mixup_launch_ub(const TcMixUpTask *d_tasks, int n_tasks, int 
     cudaError_t e = set_smem(tc_mixup_kernel<MODE, UB>, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total_tiles, sm_count());
-    tc_mixup_kernel<MODE, UB><<<grid, kMixThreads, smem, s>>>(d_tasks, n_tasks, total_tiles, n_st, n_win, n_u,
-                                                              n_stbuf, static_cast<const uint8_t *>(utab), err);
-    return cudaGetLastError();
+    return launch_pdl(tc_mixup_kernel<MODE, UB>, dim3(grid), dim3(kMixThreads), smem, s, d_tasks, n_tasks,
+                      total_tiles, n_st, n_win, n_u, n_stbuf, static_cast<const uint8_t *>(utab), err);
 }
 
 template <int MODE>

@@ -176,6 +176,7 @@ struct sb_ctx {
     // FP32 refinement scratch (allocated on the first refined push, shared by later pushes)
     RefCand *ref_cands = nullptr;
     uint32_t *ref_wmax = nullptr;     // per (unit, template, window) 16-bit maxima of one push
+    unsigned long long *ref_cum = nullptr;   // running [candidates, pushes with dropped candidates]
     int64_t ref_wmax_cap = 0;
     void *utab = nullptr;      // tensor-core interpolation operand table (16 variants of U, BF16 hi / lo)
     int *ref_counters = nullptr;
@@ -492,6 +493,7 @@ extern "C" int sb_ctx_destroy(sb_ctx *c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->ref_cands) cudaFree(c->ref_cands);
     if (c->ref_wmax) cudaFree(c->ref_wmax);
+    if (c->ref_cum) cudaFree(c->ref_cum);
     if (c->utab) cudaFree(c->utab);
     if (c->ref_counters) cudaFree(c->ref_counters);
     if (c->stream) cudaStreamSynchronize(c->stream);      // unit memory returned on the work stream
@@ -1088,8 +1090,16 @@ static int run_stage(sb_ctx *c, int stage, F fn) {
 
 extern "C" int sb_ctx_get_stats(sb_ctx *c, sb_ctx_stats *out) {
     if (!c || !out) return fail(SB_EINVAL, "null argument");
+    unsigned long long cum[2] = {0, 0};
+    if (c->ref_cum) {                          // refinement totals live on the device
+        if (activate(c) != SB_OK) return SB_ECUDA;
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaMemcpy(cum, c->ref_cum, sizeof(cum), cudaMemcpyDeviceToHost));
+    }
     std::lock_guard<std::mutex> lk(c->mu);
     *out = c->stats;
+    out->refine_candidates = (int64_t)cum[0];
+    out->refine_dropped = (int64_t)cum[1];
     return SB_OK;
 }
 
@@ -1392,27 +1402,31 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     tmix[h][k].push_back(mt);
                 }
                 if (k >= 1) {           // next push's interpolation history: columns [Bk, Bk + Hy) -> [0, Hy)
+                    // (in place when the two ranges are disjoint, else through the staging buffer)
+                    const bool direct = Bk >= L.Hy;
                     CopyTask a{};
                     a.cur = L.yuni;
                     a.ld_cur = L.ldu;
-                    a.dst = L.ytmp;
-                    a.ld_dst = L.Hy;
+                    a.dst = direct ? L.yuni : L.ytmp;
+                    a.ld_dst = direct ? L.ldu : L.Hy;
                     a.rows = M2;
                     a.n = (int32_t)L.Hy;
                     a.off = (int32_t)Bk;
                     a.elem16 = 1;
                     yshift1.push_back(a);
-                    CopyTask bt{};
-                    bt.cur = L.ytmp;
-                    bt.ld_cur = L.Hy;
-                    bt.dst = L.yuni;
-                    bt.ld_dst = L.ldu;
-                    bt.rows = M2;
-                    bt.n = (int32_t)L.Hy;
-                    bt.off = 0;
-                    bt.elem16 = 1;
-                    yshift2.push_back(bt);
                     max_hy = std::max<int>(max_hy, (int)L.Hy);
+                    if (!direct) {
+                        CopyTask bt{};
+                        bt.cur = L.ytmp;
+                        bt.ld_cur = L.Hy;
+                        bt.dst = L.yuni;
+                        bt.ld_dst = L.ldu;
+                        bt.rows = M2;
+                        bt.n = (int32_t)L.Hy;
+                        bt.off = 0;
+                        bt.elem16 = 1;
+                        yshift2.push_back(bt);
+                    }
                 }
             }
             for (int s : L.slices) {
@@ -1727,13 +1741,15 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         if (!c->ref_cands) {
             CK(cudaMalloc(&c->ref_cands, kRefCandCap * sizeof(RefCand)));
             CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
+            CK(cudaMalloc(&c->ref_cum, 2 * sizeof(unsigned long long)));
+            CK(cudaMemsetAsync(c->ref_cum, 0, 2 * sizeof(unsigned long long), st));
         }
         CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
         CK(cudaMemsetAsync(c->ref_wmax, 0, ref_wmax_total * sizeof(uint32_t), st));
         if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
                  *n = 2;
                  return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_records, c->ref_cands,
-                                      c->ref_counters, c->g, st);
+                                      c->ref_counters, c->ref_cum, c->g, st);
              })))
             return rc;
     }
@@ -1748,7 +1764,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         return rc;
     // 7. SNR history for the interpolators of the next push
     if ((rc = run_stage(c, SB_STAGE_SNRHIST, [&](int *n) {
-             *n = (ycopy.empty() ? 0 : 1) + (yshift1.empty() ? 0 : 2);
+             *n = (ycopy.empty() ? 0 : 1) + (yshift1.empty() ? 0 : 1) + (yshift2.empty() ? 0 : 1);
              cudaError_t e = launch_copy((CopyTask *)(D + o_ycopy), (int)ycopy.size(), max_rows, max_hy, st);
              if (e != cudaSuccess) return e;
              e = launch_copy((CopyTask *)(D + o_ys1), (int)yshift1.size(), max_rows, max_hy, st);

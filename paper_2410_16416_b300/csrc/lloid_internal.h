@@ -9,6 +9,29 @@
 
 namespace lloid {
 
+// Programmatic dependent launch: every kernel of a push is launched with
+// programmatic stream serialization, so its CTAs may start (and run their
+// prologue) while the previous kernel's last CTAs finish; each kernel calls
+// griddep_wait() before it touches memory that earlier work in the stream
+// produces or still reads.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 constexpr int kHalfK = 16;              // halfband kernel spans |j| <= 2K (65 taps)
 constexpr int kOddTaps = kHalfK;        // g[2t+1], t = 0..K-1 (even taps are 0, g[0] = 1/2)
 
@@ -242,8 +265,9 @@ struct RefCand {                         // one partial record to refine
     int64_t idx;                         // i * n_rec + record
 };
 // cands: kRefCandCap entries; counters[1] = candidates found, counters[2] = 1 when some were dropped
+// cum: running totals [candidates, pushes with dropped candidates] (device, never reset)
 cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_records, RefCand *cands, int *counters,
-                          const Halfband &g, cudaStream_t s);
+                          unsigned long long *cum, const Halfband &g, cudaStream_t s);
 // Margin of the candidate rule per operand mode: records within (1 - margin) of their window's
 // 16-bit maximum are refined (the 16-bit error stays well inside it).
 constexpr float kRefKeep16 = 0.81f;      // (1 - 0.1)^2, BF16 / FP16
