@@ -55,6 +55,7 @@ extern "C" {
 
 /* ---- trigger flags --------------------------------------------------- */
 #define SB_TRIG_REFINED 1   /* SNR recomputed in FP32 around the peak           */
+#define SB_TRIG_SUBSAMPLE 2 /* snr_peak / dt_peak hold the sub-sample peak       */
 
 /* One time slice of an SVD bank (Sec. II.A "time slices ... SVD").
  * basis : [n_basis * n_taps] row-major; row l is v_l[q], q = 0 is the tap
@@ -99,6 +100,14 @@ typedef struct sb_desc {
  * sample = absolute top-rate index n* of the maximum (first one on ties),
  * window = n* / (window_s * f0), snr = |rho(n*)|,
  * phase = atan2(x_{2i+1}(n*), x_{2i}(n*)) in radians.                        */
+/* One trigger: the |SNR| maximum of one template in one window (Sec. II.A: a
+ * template, a time, an SNR and a phase).  With SB_TRIG_SUBSAMPLE set, the
+ * peak between samples (the future feature named in Sec. III for the SNR gap
+ * to GstLAL) is the vertex of the parabola through |rho|^2 at sample - 1,
+ * sample, sample + 1: |SNR| snr_peak at time sample + dt_peak (in samples,
+ * |dt_peak| <= 1/2).  It is set where both neighbours are computed in FP32 in
+ * the same pass (FP32 mode: inside one push; 16/8-bit modes: refined maxima)
+ * and the sample is a local maximum; otherwise snr_peak = snr, dt_peak = 0. */
 typedef struct sb_trigger {
     int64_t unit;
     int64_t template_id;
@@ -106,6 +115,8 @@ typedef struct sb_trigger {
     int64_t window;
     float snr;
     float phase;
+    float snr_peak;
+    float dt_peak;
     int32_t flags;
     int32_t reserved;
 } sb_trigger;
@@ -243,7 +254,7 @@ int sb_ctx_stage_times(sb_ctx *ctx, double *ms, int64_t *launches, int32_t n_sta
  * |rho| > threshold.  out_count: device int32[2] = {triggers, overflow flag},
  * zeroed by the call; at most cap triggers are stored.  Work is queued on
  * stream (a cudaStream_t; NULL = legacy default stream) and nothing blocks.
- * Scratch: a fixed device array of 2^18 partial records (6 MiB) that every
+ * Scratch: a fixed device array of 2^18 partial records (8 MiB) that every
  * GPU loading this library holds until the process exits; a call needs
  * 2 * M * ceil(n_samples / 256) records and returns SB_EINVAL (see
  * sb_last_error) beyond that, or when window_len < 256.  The first call on a

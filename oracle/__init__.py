@@ -11,9 +11,10 @@ force sums, SVD invariants (orthonormality, Eckart-Young), the reduction of
 the multirate path to the direct correlation for one untruncated full-rate
 slice, resampler closed forms, the noise-free injection recovering its
 amplitude and phase, white-noise statistics (E|rho|^2 = 2), tabulated values
-of I0, window-max brute force and shift invariance.
+of I0, window-max brute force, shift invariance, and for the sub-sample peak
+the exact parabola of numpy.polyfit and a fractional-delay injection.
 """
 from .resample import bessel_i0, decimate, halfband, kaiser, upsample
 from .svdbank import OracleBank, OracleSlice, bank_from_arrays, build_bank, slice_filters, truncated_svd
 from .lloid import (causal_correlate, complex_snr, decimation_cascade, direct_snr, lloid_levels,
-                    lloid_snr, triggers, window_maxima)
+                    lloid_snr, subsample_peak, triggers, window_maxima)

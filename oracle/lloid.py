@@ -142,3 +142,25 @@ def triggers(x: np.ndarray, window_len: int, threshold: float, n_valid: int,
         for i in np.nonzero(amax[wi] > threshold)[0]:
             out.append((int(i), int(n_star[wi, i]), int(w), float(amax[wi, i]), float(ph[wi, i])))
     return out
+
+
+def subsample_peak(x: np.ndarray, i: int, n: int):
+    """Sub-sample peak of template i around sample n.
+
+    Sec. III attributes the small SNR gap to GstLAL to its sub-sample
+    interpolation at peak finding (left as future work there); the method is
+    not given.  Reading: the vertex of the parabola through |rho|^2 at
+    n - 1, n, n + 1, taken only when n is a local maximum with both neighbours
+    inside the series.  Returns (|rho| at the vertex, vertex offset from n in
+    samples) or None.
+    """
+    if n < 1 or n + 1 >= x.shape[1]:
+        return None
+    rho2 = x[2 * i, n - 1:n + 2] ** 2 + x[2 * i + 1, n - 1:n + 2] ** 2
+    ym, y0, yp = (float(v) for v in rho2)
+    den = ym - 2.0 * y0 + yp
+    if not (y0 >= ym and y0 >= yp and den < 0.0):
+        return None
+    dt = 0.5 * (ym - yp) / den
+    return float(np.sqrt(y0 - 0.25 * (ym - yp) * dt)), dt
+

@@ -20,6 +20,7 @@ SB_OK, SB_EINVAL, SB_ENOMEM, SB_EBUSY, SB_EGAP, SB_ETIMEOUT, SB_ECUDA, SB_EOVERF
 PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3}
 SB_FLAG_KEEP_SNR = 1
 SB_TRIG_REFINED = 1
+SB_TRIG_SUBSAMPLE = 2
 
 
 class SbSlice(C.Structure):
@@ -37,7 +38,8 @@ class SbDesc(C.Structure):
 
 class SbTrigger(C.Structure):
     _fields_ = [("unit", C.c_int64), ("template_id", C.c_int64), ("sample", C.c_int64), ("window", C.c_int64),
-                ("snr", C.c_float), ("phase", C.c_float), ("flags", C.c_int32), ("reserved", C.c_int32)]
+                ("snr", C.c_float), ("phase", C.c_float), ("snr_peak", C.c_float), ("dt_peak", C.c_float),
+                ("flags", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SbUnitInfo(C.Structure):
@@ -55,7 +57,8 @@ class SbCtxStats(C.Structure):
 STAGES = ["history", "strain", "decimate", "fir", "upsample", "mix", "trigger", "snr_history", "refine"]
 
 TRIGGER_DTYPE = np.dtype([("unit", "<i8"), ("template_id", "<i8"), ("sample", "<i8"), ("window", "<i8"),
-                          ("snr", "<f4"), ("phase", "<f4"), ("flags", "<i4"), ("reserved", "<i4")])
+                          ("snr", "<f4"), ("phase", "<f4"), ("snr_peak", "<f4"), ("dt_peak", "<f4"),
+                          ("flags", "<i4"), ("reserved", "<i4")])
 assert TRIGGER_DTYPE.itemsize == C.sizeof(SbTrigger)
 
 # name -> (restype, argtypes): every entry point declared in include/lloid.h

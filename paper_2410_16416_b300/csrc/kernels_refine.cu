@@ -26,22 +26,9 @@ namespace lloid {
 __device__ __forceinline__ int64_t floor_div2(int64_t v) { return v >> 1; }
 __device__ __forceinline__ int64_t ceil_div2(int64_t v) { return -((-v) >> 1); }
 
-// R1a: 16-bit maximum of |rho|^2 over each (template, window) among records above the threshold
-// (non-negative floats order as their bit patterns).
-__global__ void __launch_bounds__(256) refine_wmax_kernel(const RefUnit *__restrict__ units) {
-    griddep_wait();
-    const RefUnit &u = units[blockIdx.y];
-    const int64_t total = (int64_t)u.M * u.n_rec;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const WinPart p = u.part[idx];
-        if (!(p.mag2 > u.thr2)) continue;
-        const int i = (int)(idx / u.n_rec);
-        atomicMax(&u.wmax[(int64_t)i * u.n_wslot + (p.n / u.win_len - u.win0)], __float_as_uint(p.mag2));
-    }
-}
-
-// R1b: records above the threshold and within the margin of their window's maximum become candidates.
+// R1: records above the threshold and within the margin of their window's maximum become
+// candidates.  The maxima (|rho|^2 bits, which order like the non-negative floats) are
+// gathered per (template, window) by the top level's mixing epilogue.
 __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restrict__ units,
                                                           RefCand *__restrict__ cands, int *__restrict__ counters,
                                                           int cand_cap) {
@@ -94,9 +81,13 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
         const int64_t w = rec.n / u.win_len;
         const int64_t half0 = u.first_n + (int64_t)kRefTile * tt + 128 * h;
         int64_t lo[kRefMaxLevels], hi[kRefMaxLevels];
-        lo[0] = max(rec.n - kRefR, max(half0, w * u.win_len));
-        hi[0] = min(min(rec.n + kRefR, half0 + 127), min((w + 1) * u.win_len, u.first_n + u.B) - 1);
-        if (hi[0] < lo[0]) continue;                    // block-uniform
+        // search range [slo, shi]; computed one sample wider on each side (the sub-sample peak's
+        // neighbours), inside the samples this push produces and n >= 0
+        const int64_t slo = max(rec.n - kRefR, max(half0, w * u.win_len));
+        const int64_t shi = min(min(rec.n + kRefR, half0 + 127), min((w + 1) * u.win_len, u.first_n + u.B) - 1);
+        if (shi < slo) continue;                        // block-uniform
+        lo[0] = max(slo - 1, (int64_t)0);
+        hi[0] = min(shi + 1, u.first_n + u.B - 1);
         for (int k = 0; k < u.kmax; ++k) {
             lo[k + 1] = ceil_div2(lo[k] - (2 * kHalfK - 1));
             hi[k + 1] = floor_div2(hi[k] + (2 * kHalfK - 1));
@@ -187,13 +178,16 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
             __syncthreads();
             cur ^= 1;
         }
-        // z[cur] holds level 0 over [lo_0, hi_0] (<= 2R + 1 samples): maximum, first on ties
+        // z[cur] holds level 0 over [lo_0, hi_0] (<= 2R + 3 samples): maximum over [slo, shi], first on
+        // ties, then the sub-sample peak from its neighbours
         if (warp == 0) {
-            const int len0 = (int)(hi[0] - lo[0] + 1);
+            const int len0 = (int)(hi[0] - lo[0] + 1), c0 = (int)(slo - lo[0]), c1 = (int)(shi - lo[0]);
+            const float m2l = lane < len0 ? fmaf(z[cur][1][lane], z[cur][1][lane], z[cur][0][lane] * z[cur][0][lane])
+                                          : -1.0f;
             float best = -1.0f;
             int bc = -1;
-            if (lane < len0) {
-                best = fmaf(z[cur][1][lane], z[cur][1][lane], z[cur][0][lane] * z[cur][0][lane]);
+            if (lane >= c0 && lane <= c1) {
+                best = m2l;
                 bc = lane;
             }
 #pragma unroll
@@ -205,12 +199,17 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
                     bc = oc;
                 }
             }
+            const float ym = __shfl_sync(0xffffffffu, m2l, max(bc - 1, 0));
+            const float yp = __shfl_sync(0xffffffffu, m2l, min(bc + 1, 31));
             if (lane == 0 && bc >= 0) {
                 rec.mag2 = best;
                 rec.re = z[cur][0][bc];
                 rec.im = z[cur][1][bc];
                 rec.n = lo[0] + bc;
                 rec.flags = SB_TRIG_REFINED_BIT;
+                rec.pk = rec.dt = 0.0f;
+                if (bc >= 1 && bc + 1 < len0 && subsample_peak(ym, best, yp, rec.pk, rec.dt))
+                    rec.flags |= SB_TRIG_SUBSAMPLE_BIT;
                 u.part[idx] = rec;
             }
         }
@@ -222,9 +221,9 @@ cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_recor
                           unsigned long long *cum, const Halfband &g, cudaStream_t s) {
     if (n_units == 0) return cudaSuccess;
     const int fb = (int)std::min<int64_t>(1024, (max_records + 255) / 256);
-    cudaError_t e = launch_pdl(refine_wmax_kernel, dim3(fb, n_units), dim3(256), 0, s, d_units);
-    if (e == cudaSuccess)
-        e = launch_pdl(refine_flag_kernel, dim3(fb, n_units), dim3(256), 0, s, d_units, cands, counters, kRefCandCap);
+    // the window maxima were gathered by the top level's mixing epilogue
+    cudaError_t e = launch_pdl(refine_flag_kernel, dim3(fb, n_units), dim3(256), 0, s, d_units, cands, counters,
+                               kRefCandCap);
     if (e == cudaSuccess)
         e = launch_pdl(refine_candidate_kernel, dim3(8 * 148), dim3(kRefWarps * 32), 0, s, d_units,
                        (const int *)counters, (const RefCand *)cands, kRefCandCap, cum, g);

@@ -165,11 +165,23 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
         if (better(ob, on, best, bn)) { best = ob; bn = on; }
     }
     if (lane != 0) return;
-    float re = 0.0f, im = 0.0f;
-    if (bn != INT64_MAX) { re = xc[bn - t.first_n]; im = xs[bn - t.first_n]; }
+    float re = 0.0f, im = 0.0f, pk = 0.0f, dt = 0.0f;
+    int fl = 0;
+    if (bn != INT64_MAX) {
+        const int64_t p = bn - t.first_n;
+        re = xc[p];
+        im = xs[p];
+        if (bn >= 1 && p >= 1 && p + 1 < t.n) {   // both neighbours in this push: sub-sample peak
+            const float ym = fmaf(xs[p - 1], xs[p - 1], xc[p - 1] * xc[p - 1]);
+            const float yp = fmaf(xs[p + 1], xs[p + 1], xc[p + 1] * xc[p + 1]);
+            if (subsample_peak(ym, best, yp, pk, dt)) fl = SB_TRIG_SUBSAMPLE_BIT;
+        }
+    }
     if (s == 0) {                          // the open window carried over from the last push
         const WinState st = t.state_in[i];
-        if (st.mag2 >= 0.0f && !(best > st.mag2)) { best = st.mag2; bn = st.n; re = st.re; im = st.im; }
+        if (st.mag2 >= 0.0f && !(best > st.mag2)) {
+            best = st.mag2; bn = st.n; re = st.re; im = st.im; pk = st.pk; dt = st.dt; fl = st.flags;
+        }
     }
     const bool complete = (w + 1) * t.win_len <= end_abs;
     if (complete) {
@@ -183,7 +195,9 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
                 r.window = w;
                 r.snr = sqrtf(best);
                 r.phase = atan2f(im, re);
-                r.flags = 0;
+                r.snr_peak = (fl & SB_TRIG_SUBSAMPLE_BIT) ? pk : r.snr;
+                r.dt_peak = (fl & SB_TRIG_SUBSAMPLE_BIT) ? dt : 0.0f;
+                r.flags = fl;
                 r.reserved = 0;
                 out.buf[slot] = r;
             } else {
@@ -193,9 +207,8 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
     }
     if (s == t.n_seg - 1) {
         WinState ns;
-        if (complete) { ns.mag2 = -1.0f; ns.re = ns.im = 0.0f; ns.n = -1; }
-        else { ns.mag2 = best; ns.re = re; ns.im = im; ns.n = bn; }
-        ns.flags = 0;
+        if (complete) { ns.mag2 = -1.0f; ns.re = ns.im = ns.pk = ns.dt = 0.0f; ns.n = -1; ns.flags = 0; }
+        else { ns.mag2 = best; ns.re = re; ns.im = im; ns.pk = pk; ns.dt = dt; ns.n = bn; ns.flags = fl; }
         t.state_out[i] = ns;
     }
 }
@@ -228,14 +241,14 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
     const int64_t hi = min((w + 1) * t.win_len, t.end_abs) - t.first_n;
     const int r0 = (int)(lo / 128) * 2, r1 = (int)((hi - 1) / 128) * 2 + 2;
     const WinPart *rec = t.part + (int64_t)i * t.n_rec;
-    float best = -1.0f, re = 0.0f, im = 0.0f;
+    float best = -1.0f, re = 0.0f, im = 0.0f, pk = 0.0f, dt = 0.0f;
     int64_t bn = INT64_MAX;
     int fl = 0;
     for (int r = r0 + lane; r < r1; r += 32) {
         const WinPart p = rec[r];
         if (p.mag2 < 0.0f || p.n / t.win_len != w) continue;
         if (p.mag2 > best || (p.mag2 == best && p.n < bn)) {
-            best = p.mag2; bn = p.n; re = p.re; im = p.im; fl = p.flags;
+            best = p.mag2; bn = p.n; re = p.re; im = p.im; pk = p.pk; dt = p.dt; fl = p.flags;
         }
     }
 #pragma unroll
@@ -244,14 +257,16 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
         const int64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
         const float ore = __shfl_xor_sync(0xffffffffu, re, off);
         const float oim = __shfl_xor_sync(0xffffffffu, im, off);
+        const float opk = __shfl_xor_sync(0xffffffffu, pk, off);
+        const float odt = __shfl_xor_sync(0xffffffffu, dt, off);
         const int ofl = __shfl_xor_sync(0xffffffffu, fl, off);
-        if (ob > best || (ob == best && on < bn)) { best = ob; bn = on; re = ore; im = oim; fl = ofl; }
+        if (ob > best || (ob == best && on < bn)) { best = ob; bn = on; re = ore; im = oim; pk = opk; dt = odt; fl = ofl; }
     }
     if (lane != 0) return;
     if (s == 0) {                          // the window left open by the previous push (earlier samples)
         const WinState st = t.state_in[i];
         if (st.mag2 >= 0.0f && !(best > st.mag2)) {
-            best = st.mag2; bn = st.n; re = st.re; im = st.im; fl = st.flags;
+            best = st.mag2; bn = st.n; re = st.re; im = st.im; pk = st.pk; dt = st.dt; fl = st.flags;
         }
     }
     const bool complete = (w + 1) * t.win_len <= t.end_abs;
@@ -265,6 +280,8 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
             r.window = w;
             r.snr = sqrtf(best);
             r.phase = atan2f(im, re);
+            r.snr_peak = (fl & SB_TRIG_SUBSAMPLE_BIT) ? pk : r.snr;
+            r.dt_peak = (fl & SB_TRIG_SUBSAMPLE_BIT) ? dt : 0.0f;
             r.flags = fl;
             r.reserved = 0;
             out.buf[slot] = r;
@@ -274,8 +291,11 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
     }
     if (s == t.n_win - 1) {
         WinState ns;
-        if (complete || bn == INT64_MAX) { ns.mag2 = -1.0f; ns.re = ns.im = 0.0f; ns.n = -1; ns.flags = 0; }
-        else { ns.mag2 = best; ns.re = re; ns.im = im; ns.n = bn; ns.flags = fl; }
+        if (complete || bn == INT64_MAX) {
+            ns.mag2 = -1.0f; ns.re = ns.im = ns.pk = ns.dt = 0.0f; ns.n = -1; ns.flags = 0;
+        } else {
+            ns.mag2 = best; ns.re = re; ns.im = im; ns.pk = pk; ns.dt = dt; ns.n = bn; ns.flags = fl;
+        }
         t.state_out[i] = ns;
     }
 }

@@ -794,7 +794,7 @@ static int alloc_state(sb_unit *u) {
         off += round_up(p.bytes, 256);
     }
     std::vector<WinState> ws(u->M);
-    for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = 0.0f; w.flags = 0; w.n = -1; }
+    for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = w.pk = w.dt = 0.0f; w.flags = 0; w.n = -1; }
     for (int b = 0; b < 2; ++b)
         CK(cudaMemcpyAsync(u->wstate[b], ws.data(), u->M * sizeof(WinState), cudaMemcpyHostToDevice,
                            u->ctx->alloc_stream));
@@ -1328,6 +1328,14 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         const int64_t Tp = u->T;
         const int M2 = 2 * u->M;
         max_rows = std::max(max_rows, M2);
+        // refinement: this unit's slice of the window-maxima scratch (offset; addresses set at packing)
+        const int64_t first_n0 = Tp - u->levels[0].lam;
+        const int64_t start0 = std::max<int64_t>(first_n0, 0), end0 = first_n0 + B;
+        const bool refine_here = end0 > start0 && u->refine;
+        const int64_t win0 = refine_here ? start0 / u->win_len : 0;
+        const int32_t n_wslot = refine_here ? (int32_t)((end0 - 1) / u->win_len - win0 + 1) : 0;
+        const int64_t wmax_off = ref_wmax_total;
+        if (refine_here) ref_wmax_total += (int64_t)u->M * n_wslot;
         for (int k = 0; k <= u->kmax; ++k) {
             LevelDev &L = u->levels[k];
             const int nb = 1 - L.dcur;
@@ -1387,6 +1395,12 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     mt.kbytes = mix_kbytes(L.Lk_pad, u->mode);
                     mt.rsc_next = k >= 1 ? u->levels[k - 1].rscale : nullptr;
                     mt.part = k == 0 ? u->part : nullptr;
+                    if (k == 0 && refine_here) {
+                        mt.wmax = reinterpret_cast<uint32_t *>(wmax_off + 1);   // offset + 1; address at packing
+                        mt.win0 = win0;
+                        mt.n_wslot = n_wslot;
+                        mt.thr2 = u->refine_thr * u->refine_thr;
+                    }
                     mt.first_n = (Tp >> k) - L.lam;
                     mt.win_len = u->win_len;
                     mt.Lk_pad = L.Lk_pad;
@@ -1506,10 +1520,9 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             r.win_len = u->win_len;
             r.thr2 = u->refine_thr * u->refine_thr;
             r.keep2 = u->mode == kModeE4M3 ? kRefKeep8 : kRefKeep16;
-            r.win0 = start / u->win_len;
-            r.n_wslot = (int32_t)((end - 1) / u->win_len - r.win0 + 1);
-            r.wmax = reinterpret_cast<uint32_t *>(ref_wmax_total);   // offset; the base is added before packing
-            ref_wmax_total += (int64_t)u->M * r.n_wslot;
+            r.win0 = win0;
+            r.n_wslot = n_wslot;
+            r.wmax = reinterpret_cast<uint32_t *>(wmax_off);         // offset; the base is added before packing
             r.kmax = u->kmax;
             r.M = u->M;
             r.n_rec = (int32_t)((B + kRefTile - 1) / kRefTile) * 4;
@@ -1625,6 +1638,20 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         o_recon[k] = pk.add(recon[k].data(), recon[k].size() * sizeof(GemmTask));
     }
     const size_t o_win = pk.add(win.data(), win.size() * sizeof(WinTask));
+    if (!refu.empty()) {                       // window-maxima scratch of the refinement (grown on demand)
+        if (c->ref_wmax_cap < ref_wmax_total) {
+            CK(cudaStreamSynchronize(st));
+            if (c->ref_wmax) cudaFree(c->ref_wmax);
+            c->ref_wmax = nullptr;
+            c->ref_wmax_cap = std::max(ref_wmax_total, 2 * c->ref_wmax_cap);
+            CK(cudaMalloc(&c->ref_wmax, c->ref_wmax_cap * sizeof(uint32_t)));
+        }
+        for (auto &r : refu) r.wmax = c->ref_wmax + reinterpret_cast<intptr_t>(r.wmax);   // offset -> address
+        for (int h = 0; h < NM; ++h)
+            for (auto &m : tmix[h][0])
+                if (m.wmax) m.wmax = c->ref_wmax + (reinterpret_cast<intptr_t>(m.wmax) - 1);
+        CK(cudaMemsetAsync(c->ref_wmax, 0, ref_wmax_total * sizeof(uint32_t), st));   // before this push's kernels
+    }
     size_t o_conv[NM], o_tfir[NM];
     std::vector<size_t> o_tmix[NM] = {std::vector<size_t>(kall + 1), std::vector<size_t>(kall + 1),
                                       std::vector<size_t>(kall + 1)};
@@ -1635,16 +1662,6 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     }
     const size_t o_ycopy = pk.add(ycopy.data(), ycopy.size() * sizeof(CopyTask));
     const size_t o_wfin = pk.add(wfin.data(), wfin.size() * sizeof(WinFinTask));
-    if (!refu.empty()) {                       // window-maxima scratch of the refinement (grown on demand)
-        if (c->ref_wmax_cap < ref_wmax_total) {
-            CK(cudaStreamSynchronize(st));
-            if (c->ref_wmax) cudaFree(c->ref_wmax);
-            c->ref_wmax = nullptr;
-            c->ref_wmax_cap = std::max(ref_wmax_total, 2 * c->ref_wmax_cap);
-            CK(cudaMalloc(&c->ref_wmax, c->ref_wmax_cap * sizeof(uint32_t)));
-        }
-        for (auto &r : refu) r.wmax = c->ref_wmax + reinterpret_cast<intptr_t>(r.wmax);   // offset -> address
-    }
     const size_t o_refu = pk.add(refu.data(), refu.size() * sizeof(RefUnit));
     const size_t o_ys1 = pk.add(yshift1.data(), yshift1.size() * sizeof(CopyTask));
     const size_t o_ys2 = pk.add(yshift2.data(), yshift2.size() * sizeof(CopyTask));
@@ -1745,7 +1762,6 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             CK(cudaMemsetAsync(c->ref_cum, 0, 2 * sizeof(unsigned long long), st));
         }
         CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
-        CK(cudaMemsetAsync(c->ref_wmax, 0, ref_wmax_total * sizeof(uint32_t), st));
         if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
                  *n = 2;
                  return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_records, c->ref_cands,

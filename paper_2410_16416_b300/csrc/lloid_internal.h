@@ -107,14 +107,26 @@ struct GemmTask {
 struct WinState {        // running maximum of one template in its open window
     float mag2;          // |rho|^2 (-1: empty)
     float re, im;
+    float pk, dt;        // sub-sample peak |rho| and offset (valid with SB_TRIG_SUBSAMPLE_BIT)
     int32_t flags;       // SB_TRIG_* bits of the maximum
     int64_t n;
 };
 constexpr int32_t SB_TRIG_REFINED_BIT = 1;
+constexpr int32_t SB_TRIG_SUBSAMPLE_BIT = 2;
+
+// Sub-sample peak: vertex of the parabola through |rho|^2 = ym, y0, yp at
+// n - 1, n, n + 1 when n is a local maximum: offset dt in [-1/2, 1/2] and |rho|.
+__host__ __device__ __forceinline__ bool subsample_peak(float ym, float y0, float yp, float &pk, float &dt) {
+    const float den = ym - 2.0f * y0 + yp;
+    if (!(y0 >= ym && y0 >= yp && den < 0.0f)) return false;
+    dt = 0.5f * (ym - yp) / den;
+    pk = sqrtf(y0 - 0.25f * (ym - yp) * dt);
+    return true;
+}
 
 struct DevTrigger {      // layout-identical to sb_trigger
     int64_t unit, template_id, sample, window;
-    float snr, phase;
+    float snr, phase, snr_peak, dt_peak;
     int32_t flags, reserved;
 };
 
@@ -176,7 +188,8 @@ struct TcFirTask {
 struct WinPart {
     float mag2;                // |rho|^2 (-1: no valid sample)
     float re, im;
-    int32_t flags;             // SB_TRIG_* bits (refined)
+    float pk, dt;              // sub-sample peak (refined records with SB_TRIG_SUBSAMPLE_BIT)
+    int32_t flags;             // SB_TRIG_* bits (refined, sub-sample)
     int64_t n;                 // absolute top-rate sample
 };
 
@@ -201,6 +214,10 @@ struct TcMixUpTask {
     int32_t in_off;            // Lambda_{k+1} + Hy_{k+1}: coarser position of (relative index 0) / 2
     int32_t tiles_t, tiles_a, tile_begin, n_rec;
     const float *rscale;       // E4M3: per mixing row (filter) scale of this level (null: 1)
+    uint32_t *wmax;            // top level with refinement: [M][n_wslot] 16-bit window maxima above thr2
+    int64_t win0;              //   (mag2 bits, atomicMax), window of slot 0
+    int32_t n_wslot;
+    float thr2;                //   refine threshold squared
     const float *rsc_next;     // E4M3: row scale of the finer level, which reads this level's y (null: 1)
 };
 

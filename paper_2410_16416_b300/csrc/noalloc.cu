@@ -18,7 +18,7 @@
 namespace lloid {
 
 // Maximum partial-maximum records one call may need: 2 per (template, 256-sample chunk).
-constexpr int64_t kNoAllocRecords = int64_t(1) << 18;      // 262144 records x 24 B = 6 MiB
+constexpr int64_t kNoAllocRecords = int64_t(1) << 18;      // 262144 records x 32 B = 8 MiB
 constexpr int kNoAllocChunk = 256;
 
 static __device__ __align__(256) WinPart g_noalloc_scratch[kNoAllocRecords];
@@ -60,10 +60,10 @@ __global__ void __launch_bounds__(256) noalloc_partials_kernel(const float *__re
     }
     if (lane == 0) {
         for (int s = 0; s < 2; ++s) {
-            WinPart r{-1.0f, 0.0f, 0.0f, 0, -1};
+            WinPart r{-1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, -1};
             if (bn[s] != INT64_MAX) {
                 const int64_t p = bn[s] - first;
-                r = WinPart{best[s], xc[p], xs[p], 0, bn[s]};
+                r = WinPart{best[s], xc[p], xs[p], 0.0f, 0.0f, 0, bn[s]};
             }
             scratch[((int64_t)c * 2 + s) * M + i] = r;
         }
@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(256) noalloc_merge_kernel(const WinPart *__res
         r.window = w;
         r.snr = sqrtf(bm);
         r.phase = atan2f(bim, bre);
+        r.snr_peak = r.snr;
+        r.dt_peak = 0.0f;
         r.flags = 0;
         r.reserved = 0;
         out[slot] = r;

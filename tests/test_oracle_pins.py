@@ -304,3 +304,47 @@ def test_p10_shift_by_rate_period_is_exact(cfg_small):
     skip = int(spec.duration_s * spec.top_rate_hz) + 8 * 2 * HALF_K * sh
     end = d.shape[0] - sh - 8 * 2 * HALF_K * sh          # the dropped tail reaches back this far
     assert np.abs(x2[:, skip + sh:end + sh] - x1[:, skip:end]).max() <= 1e-12 * np.abs(x1).max()
+
+
+# ---------------------------------------------------------------- P11 sub-sample peak
+def test_p11_subsample_vertex_is_the_exact_parabola():
+    """The vertex equals that of numpy.polyfit's degree-2 fit through the three samples of |rho|^2
+    (an exact interpolation), and non-maxima are refused."""
+    g = np.random.default_rng(11)
+    for _ in range(200):
+        x = g.standard_normal((2, 7))
+        n = 3
+        rho2 = x[0] ** 2 + x[1] ** 2
+        res = oracle.subsample_peak(x, 0, n)
+        is_max = rho2[n] >= rho2[n - 1] and rho2[n] >= rho2[n + 1] and rho2[n - 1] - 2 * rho2[n] + rho2[n + 1] < 0
+        if not is_max:
+            assert res is None
+            continue
+        a, b, c = np.polyfit([-1.0, 0.0, 1.0], rho2[n - 1:n + 2], 2)
+        t_v = -b / (2 * a)
+        assert abs(res[1] - t_v) <= 1e-12 and abs(t_v) <= 0.5
+        assert abs(res[0] ** 2 - (c - b * b / (4 * a))) <= 1e-12 * rho2[n]
+    edge = np.ones((2, 4))
+    assert oracle.subsample_peak(edge, 0, 0) is None and oracle.subsample_peak(edge, 0, 3) is None
+
+
+def test_p11_subsample_peak_recovers_a_fractional_delay(cfg_small):
+    """A noise-free injection delayed by a fraction tau of a sample (band-limited shift): the
+    on-grid maximum loses SNR, the sub-sample peak is closer to A and sits near n_c + tau."""
+    spec, h = cfg_small
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices, frac=1.0)
+    n = 12 * 2048
+    n_c, i, A = 10 * 2048 + 5, 7, 12.0
+    base = np.zeros(n)
+    synth.inject(base, h, i, n_c, A, 0.4)
+    spec_f = np.fft.rfft(base)
+    k = np.arange(spec_f.shape[0])
+    for tau in (-0.4, -0.15, 0.2, 0.35):
+        d = np.fft.irfft(spec_f * np.exp(-2j * np.pi * k * tau / n), n).astype(np.float32)
+        x = oracle.lloid_snr(bank, d)
+        mag = np.abs(oracle.complex_snr(x)[i, n_c - 4:n_c + 5])
+        n_star = n_c - 4 + int(np.argmax(mag))
+        grid = float(mag.max())
+        pk, dt = oracle.subsample_peak(x, i, n_star)
+        assert abs(pk - A) < abs(grid - A)
+        assert abs(n_star + dt - (n_c + tau)) <= 0.1

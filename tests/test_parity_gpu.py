@@ -73,6 +73,32 @@ def test_fp32_every_window_max_matches_oracle(lloid, small_case):
     ctx.close()
 
 
+def test_fp32_subsample_peaks_match_oracle(lloid, small_case):
+    """Every trigger whose sub-sample peak was taken (both neighbours inside one push, a local
+    maximum) matches the oracle's parabola vertex; most window maxima qualify."""
+    spec, h, bank, d, x = small_case
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, threshold=0.0, max_push_samples=8192)
+    for t in range(0, d.shape[0], 8192):
+        u.push(d[t:t + 8192], t)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    ctx.close()
+    sub = trig[(trig["flags"] & lloid.SB_TRIG_SUBSAMPLE) != 0]
+    assert len(sub) >= 0.8 * len(trig)
+    worst_pk, worst_dt = 0.0, 0.0
+    for t in sub:
+        ref = oracle.subsample_peak(x, int(t["template_id"]), int(t["sample"]))
+        assert ref is not None
+        worst_pk = max(worst_pk, abs(t["snr_peak"] - ref[0]) / max(1.0, ref[0]))
+        worst_dt = max(worst_dt, abs(t["dt_peak"] - ref[1]))
+    print(f"fp32 sub-sample peaks: {len(sub)} of {len(trig)}; max |snr_peak| error {worst_pk:.2e}, "
+          f"max |dt_peak| error {worst_dt:.2e} samples")
+    assert worst_pk <= 2 * TOL_FP32 and worst_dt <= 2e-3
+    plain = trig[(trig["flags"] & lloid.SB_TRIG_SUBSAMPLE) == 0]
+    assert np.all(plain["snr_peak"] == plain["snr"]) and np.all(plain["dt_peak"] == 0.0)
+
+
 def test_streaming_is_bitwise_independent_of_buffer_sizes(lloid, small_case):
     spec, h, bank, d, x = small_case
     runs = []
@@ -316,6 +342,10 @@ def test_refined_production_injection(lloid):
     print("refined", hit["snr"][0], "oracle", amax[0, 0], "samples", hit["sample"][0], n_star[0, 0])
     assert abs(hit["snr"][0] - amax[0, 0]) <= 1e-3
     assert hit["sample"][0] == n_star[0, 0]
+    ref = oracle.subsample_peak(xo, 0, int(n_star[0, 0]))
+    print("refined sub-sample peak", hit["snr_peak"][0], hit["dt_peak"][0], "oracle", ref)
+    assert hit["flags"][0] & lloid.SB_TRIG_SUBSAMPLE and ref is not None
+    assert abs(hit["snr_peak"][0] - ref[0]) <= 1e-3 and abs(hit["dt_peak"][0] - ref[1]) <= 5e-3
 
 
 # ---------------------------------------------------------------- E4M3 mode (config 4)

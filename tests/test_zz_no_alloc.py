@@ -23,7 +23,7 @@ TOL_FP32 = 1e-4
 
 
 def _noalloc(lloid, x_dev, first, win_len, threshold, M, cap=4096):
-    out = torch.zeros(cap * 48, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(cap * lloid.TRIGGER_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(2, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     rc = lloid.lib.sb_window_triggers_noalloc(x_dev.data_ptr(), x_dev.shape[1], M, x_dev.shape[1], first, win_len,
@@ -72,7 +72,7 @@ def test_noalloc_rejects_oversized_requests(has_gpu):
         pytest.skip("no CUDA device")
     import paper_2410_16416_b300 as lloid
     x = torch.zeros((2 * 1024, 1 << 17), dtype=torch.float32, device="cuda")      # 1024 templates x 131072 samples
-    out = torch.zeros(48, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(lloid.TRIGGER_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(2, dtype=torch.int32, device="cuda")
     rc = lloid.lib.sb_window_triggers_noalloc(x.data_ptr(), x.shape[1], 1024, x.shape[1], 0, 4096, 6.0, None,
                                               out.data_ptr(), cnt.data_ptr(), 1, None)
