@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--push-seconds", type=int, default=16)
     p.add_argument("--templates", type=int, default=1000)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--graphs", default="on", choices=["on", "off"],
+                   help="capture every push into a CUDA graph (reused per group shape)")
     p.add_argument("--cpu-seconds", type=float, default=8.0, help="strain seconds per oracle worker")
     p.add_argument("--workload", default="production", choices=["production", "batch", "serve"],
                    help="production: one 1000-template bin x 2 detectors; batch: --bins uneven bins x 2 detectors")
@@ -446,6 +448,7 @@ def main():
 
     def device_arm(precision):
         ctx = lloid.Context(local, stream=stream.cuda_stream)
+        ctx.graphs(args.graphs == "on")
         tc0 = time.perf_counter()
         units = make_units(ctx, precision)
         create_s = time.perf_counter() - tc0
@@ -498,6 +501,7 @@ def main():
 
     # e2e: host strain in, triggers out, through the C ABI
     ctx2 = lloid.Context(local, stream=stream.cuda_stream)
+    ctx2.graphs(args.graphs == "on")
     u2 = make_units(ctx2, args.precision)
     dets = [det for _, det in unit_specs]
     t2 = 0
@@ -550,7 +554,7 @@ def main():
                         f"L logU[50,600]), one grouped push per step, {args.push_seconds} s pushes"),
                        "templates": n_templates_all, "units_per_gpu": n_units, "setup_s": prim["create_s"],
                        "push_seconds": args.push_seconds, "precision": args.precision,
-                       "parallelism": f"units sharded, {world} GPU(s)",
+                       "parallelism": f"units sharded, {world} GPU(s)", "cuda_graphs": args.graphs,
                        "l2": "flushed between steps (256 MB write outside the step events)"},
             "roofline": roof, "e2e": e2e, "gpu_launches": prim["launches"], "clocks": prim["clocks"],
             "stages_ms_share": {k: round(v / total_stage_ms, 4) for k, v in busy.items()},

@@ -228,12 +228,21 @@ typedef struct sb_ctx_stats {
     int64_t triggers;        /* triggers delivered by triggers_pop             */
     int64_t refine_candidates;  /* partial window maxima recomputed in FP32 (a6)  */
     int64_t refine_dropped;     /* pushes whose candidates exceeded the list (65536); the rest kept 16-bit values */
+    int64_t graph_launches;     /* pushes launched as one CUDA graph (sb_ctx_graphs)  */
 } sb_ctx_stats;
 int sb_ctx_get_stats(sb_ctx *ctx, sb_ctx_stats *out);
 
 /* enable != 0: bracket every kernel launch with CUDA events on the context's
  * stream; enable == 0: stop.  Enabling clears previously collected times. */
 int sb_ctx_profile(sb_ctx *ctx, int32_t enable);
+/* enable != 0: every push (filter_push / filter_push_group) is stream-captured
+ * into a CUDA graph and launched as one graph; pushes with the same group
+ * (same units in the same order, same n_samples, host or device strain) reuse
+ * one executable graph, updated in place with the push's arguments
+ * (cudaGraphExecUpdate).  Pushes made while profiling is enabled are not
+ * captured.  enable == 0 (the default): kernels are launched one by one.
+ * Results are identical either way. */
+int sb_ctx_graphs(sb_ctx *ctx, int32_t enable);
 /* Blocks until queued work is done, then writes per stage the summed kernel
  * time (ms) and the number of launches since profiling was enabled
  * (arrays of n_stages entries; n_stages <= SB_N_STAGES). */

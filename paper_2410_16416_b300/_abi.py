@@ -51,7 +51,7 @@ class SbUnitInfo(C.Structure):
 class SbCtxStats(C.Structure):
     _fields_ = [("pushes", C.c_int64), ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("triggers", C.c_int64), ("refine_candidates", C.c_int64),
-                ("refine_dropped", C.c_int64)]
+                ("refine_dropped", C.c_int64), ("graph_launches", C.c_int64)]
 
 
 STAGES = ["history", "strain", "decimate", "fir", "upsample", "mix", "trigger", "snr_history", "refine"]
@@ -79,6 +79,7 @@ SIGNATURES = {
     "sb_unit_snr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sb_ctx_get_stats": (C.c_int, [C.c_void_p, C.POINTER(SbCtxStats)]),
     "sb_ctx_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sb_ctx_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
     "sb_ctx_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "sb_window_triggers_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                                              C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
@@ -196,6 +197,10 @@ class Context:
 
     def profile(self, enable: bool):
         _check(lib.sb_ctx_profile(self.handle, int(bool(enable))), "sb_ctx_profile")
+
+    def graphs(self, enable: bool):
+        """Capture every push into a CUDA graph (reused per group shape); results are unchanged."""
+        _check(lib.sb_ctx_graphs(self.handle, int(bool(enable))), "sb_ctx_graphs")
 
     def stage_times(self) -> dict:
         """{stage: (ms summed over launches, launches)} since profile(True); blocks."""

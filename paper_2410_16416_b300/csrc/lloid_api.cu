@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -180,6 +181,10 @@ struct sb_ctx {
     int64_t ref_wmax_cap = 0;
     void *utab = nullptr;      // tensor-core interpolation operand table (16 variants of U, BF16 hi / lo)
     int *ref_counters = nullptr;
+    // CUDA-graph pushes: one executable graph per group shape, updated in place
+    bool graphs = false;
+    std::map<std::string, cudaGraphExec_t> graph_execs;
+    int64_t graph_launches = 0;
     // profiling: event pairs around each launch, summed per stage on query
     bool prof = false;
     struct Mark { int stage; cudaEvent_t a, b; };
@@ -491,6 +496,8 @@ extern "C" int sb_ctx_destroy(sb_ctx *c) {
     }
     release_marks(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (auto &kv : c->graph_execs) cudaGraphExecDestroy(kv.second);
+    c->graph_execs.clear();
     if (c->ref_cands) cudaFree(c->ref_cands);
     if (c->ref_wmax) cudaFree(c->ref_wmax);
     if (c->ref_cum) cudaFree(c->ref_cum);
@@ -1080,7 +1087,7 @@ static int run_stage(sb_ctx *c, int stage, F fn) {
     int n = 0;
     cudaError_t e = fn(&n);
     if (e != cudaSuccess) return fail(SB_ECUDA, std::string("stage launch: ") + cudaGetErrorString(e));
-    c->stats.kernel_launches += (stage == SB_STAGE_STRAIN) ? 0 : n;
+    c->stats.kernel_launches += n;
     if (c->prof) {
         CK(cudaEventRecord(b, c->stream));
         c->marks.push_back({stage, a, b});
@@ -1100,6 +1107,7 @@ extern "C" int sb_ctx_get_stats(sb_ctx *c, sb_ctx_stats *out) {
     *out = c->stats;
     out->refine_candidates = (int64_t)cum[0];
     out->refine_dropped = (int64_t)cum[1];
+    out->graph_launches = c->graph_launches;
     return SB_OK;
 }
 
@@ -1109,6 +1117,13 @@ static void release_marks(sb_ctx *c) {
         c->ev_pool.push_back(m.b);
     }
     c->marks.clear();
+}
+
+extern "C" int sb_ctx_graphs(sb_ctx *c, int32_t enable) {
+    if (!c) return fail(SB_EINVAL, "ctx is null");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->graphs = enable != 0;
+    return SB_OK;
 }
 
 extern "C" int sb_ctx_profile(sb_ctx *c, int32_t enable) {
@@ -1229,6 +1244,64 @@ struct Packer {
         buf.resize(off + bytes);
         if (bytes) std::memcpy(buf.data() + off, p, bytes);
         return off;
+    }
+    size_t reserve(size_t bytes) {            // zeroed space, filled in later
+        size_t off = round_up((int64_t)buf.size(), 256);
+        buf.resize(off + bytes, 0);
+        return off;
+    }
+};
+
+// Graph mode: ends the push's stream capture and launches it, reusing (updating in place)
+// the executable graph of the same group shape when CUDA accepts the update.
+static int end_capture_and_launch(sb_ctx *c, const std::string &key, cudaStream_t st) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess || !g) {
+        cudaGetLastError();
+        return fail(SB_ECUDA, std::string("push capture: ") + cudaGetErrorString(e));
+    }
+    auto it = c->graph_execs.find(key);
+    if (it != c->graph_execs.end()) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(it->second, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(it->second);
+            c->graph_execs.erase(it);
+            it = c->graph_execs.end();
+        }
+    }
+    if (it == c->graph_execs.end()) {
+        if (c->graph_execs.size() >= 64) {        // many shapes (serving): start over
+            for (auto &kv : c->graph_execs) cudaGraphExecDestroy(kv.second);
+            c->graph_execs.clear();
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            cudaGetLastError();
+            return fail(SB_ECUDA, std::string("push graph instantiation: ") + cudaGetErrorString(e));
+        }
+        it = c->graph_execs.emplace(key, ex).first;
+    }
+    cudaGraphDestroy(g);
+    e = cudaGraphLaunch(it->second, st);
+    if (e != cudaSuccess) return fail(SB_ECUDA, std::string("push graph launch: ") + cudaGetErrorString(e));
+    c->graph_launches += 1;
+    return SB_OK;
+}
+
+// Ends a capture left open by an error inside a captured push.
+struct CaptureGuard {
+    cudaStream_t st = nullptr;
+    bool active = false;
+    ~CaptureGuard() {
+        if (!active) return;
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(st, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
     }
 };
 
@@ -1639,6 +1712,12 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     }
     const size_t o_win = pk.add(win.data(), win.size() * sizeof(WinTask));
     if (!refu.empty()) {                       // window-maxima scratch of the refinement (grown on demand)
+        if (!c->ref_cands) {                   // candidate list, counters and running totals
+            CK(cudaMalloc(&c->ref_cands, kRefCandCap * sizeof(RefCand)));
+            CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
+            CK(cudaMalloc(&c->ref_cum, 2 * sizeof(unsigned long long)));
+            CK(cudaMemsetAsync(c->ref_cum, 0, 2 * sizeof(unsigned long long), st));
+        }
         if (c->ref_wmax_cap < ref_wmax_total) {
             CK(cudaStreamSynchronize(st));
             if (c->ref_wmax) cudaFree(c->ref_wmax);
@@ -1668,17 +1747,44 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     std::vector<size_t> o_strain(n_units, 0);
     if (!on_device)
         for (int i = 0; i < n_units; ++i) o_strain[i] = pk.add(strains[i], B * sizeof(float));
+    // the new top-rate strain of every unit is copied by one task-driven kernel (its source
+    // pointers are data in the task block, not launch arguments)
+    const size_t o_scopy = pk.reserve(n_units * sizeof(CopyTask));
 
     TaskArena *ar = nullptr;
     int rc = arena_acquire(c, pk.buf.size(), ar);
     if (rc) return rc;
-    std::memcpy(ar->h, pk.buf.data(), pk.buf.size());
-    CK(cudaMemcpyAsync(ar->d, ar->h, pk.buf.size(), cudaMemcpyHostToDevice, st));
     char *D = ar->d;
-
+    {
+        CopyTask *sc = reinterpret_cast<CopyTask *>(pk.buf.data() + o_scopy);
+        for (int i = 0; i < n_units; ++i) {
+            LevelDev &L0 = units[i]->levels[0];
+            CopyTask t{};
+            t.cur = on_device ? strains[i] : reinterpret_cast<const float *>(D + o_strain[i]);
+            t.dst = L0.dbuf[1 - L0.dcur] + L0.Hd;
+            t.rows = 1;
+            t.n = (int32_t)B;
+            sc[i] = t;
+        }
+    }
     TriggerSlot *slot = nullptr;
     int slot_idx = 0;
     if ((rc = slot_acquire(c, trig_need, slot, slot_idx))) return rc;
+    std::memcpy(ar->h, pk.buf.data(), pk.buf.size());
+
+    // graph mode: everything from the task upload to the trigger read-back is one captured graph
+    const bool capture = c->graphs && !c->prof;
+    std::string gkey;
+    CaptureGuard guard;
+    if (capture) {
+        gkey = std::to_string(B) + (on_device ? "d" : "h") + std::to_string(slot_idx) + ":" +
+               std::to_string(c->next_arena);
+        for (int i = 0; i < n_units; ++i) gkey += "," + std::to_string(units[i]->id);
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+        guard.st = st;
+        guard.active = true;
+    }
+    CK(cudaMemcpyAsync(ar->d, ar->h, pk.buf.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(slot->dcount, 0, 3 * sizeof(int32_t), st));
     int *derr = slot->dcount + 2;
     // 1. history shifts of the decimated strain
@@ -1689,14 +1795,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         return rc;
     // 2. new top-rate strain
     if ((rc = run_stage(c, SB_STAGE_STRAIN, [&](int *n) {
-             for (int i = 0; i < n_units; ++i) {
-                 LevelDev &L0 = units[i]->levels[0];
-                 float *dst = L0.dbuf[1 - L0.dcur] + L0.Hd;
-                 const void *src = on_device ? (const void *)strains[i] : (const void *)(D + o_strain[i]);
-                 cudaError_t e = cudaMemcpyAsync(dst, src, B * sizeof(float), cudaMemcpyDeviceToDevice, st);
-                 if (e != cudaSuccess) return e;
-             }
-             return cudaSuccess;
+             *n = 1;
+             return launch_copy((CopyTask *)(D + o_scopy), n_units, 1, (int)B, st);
          })))
         return rc;
     // 3. a1 decimation cascade
@@ -1755,12 +1855,6 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     }
     // a6: FP32 refinement of the top level's candidate maxima (16-bit modes)
     if (!refu.empty()) {
-        if (!c->ref_cands) {
-            CK(cudaMalloc(&c->ref_cands, kRefCandCap * sizeof(RefCand)));
-            CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
-            CK(cudaMalloc(&c->ref_cum, 2 * sizeof(unsigned long long)));
-            CK(cudaMemsetAsync(c->ref_cum, 0, 2 * sizeof(unsigned long long), st));
-        }
         CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
         if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
                  *n = 2;
@@ -1791,6 +1885,10 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     // 8. triggers to the host (count plus an eager prefix; the rest on demand)
     CK(cudaMemcpyAsync(slot->hcount, slot->dcount, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(slot->hbuf, slot->dbuf, slot->eager * sizeof(DevTrigger), cudaMemcpyDeviceToHost, st));
+    if (capture) {
+        guard.active = false;
+        if ((rc = end_capture_and_launch(c, gkey, st))) return rc;
+    }
     CK(cudaEventRecord(slot->ev, st));
     slot->pending = true;
     c->pending.push_back(slot_idx);
