@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--graphs", default="on", choices=["on", "off"],
                    help="capture every push into a CUDA graph (reused per group shape)")
+    p.add_argument("--autotune", default="on", choices=["on", "off"],
+                   help="time the mixing kernel's pipeline shapes on the first push of each launch shape")
     p.add_argument("--cpu-seconds", type=float, default=8.0, help="strain seconds per oracle worker")
     p.add_argument("--workload", default="production", choices=["production", "batch", "serve"],
                    help="production: one 1000-template bin x 2 detectors; batch: --bins uneven bins x 2 detectors")
@@ -449,6 +451,7 @@ def main():
     def device_arm(precision):
         ctx = lloid.Context(local, stream=stream.cuda_stream)
         ctx.graphs(args.graphs == "on")
+        ctx.autotune(args.autotune == "on")
         tc0 = time.perf_counter()
         units = make_units(ctx, precision)
         create_s = time.perf_counter() - tc0
@@ -486,8 +489,10 @@ def main():
         ctx.profile(False)
         value, dev_s = job_rate(tpl_s_rank, sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, "cuda")
         trig = ctx.pop_triggers()
+        tuned = ctx.autotune_choices()
         ctx.close()
-        return {"value": value, "dev_s": dev_s, "wall": wall, "clocks": clk, "create_s": create_s,
+        return {"value": value, "autotune": {"choices": tuned, "timed_launches": st1["autotune_launches"],
+                                             "in_timed_region": st1["autotune_launches"] - st0["autotune_launches"]}, "dev_s": dev_s, "wall": wall, "clocks": clk, "create_s": create_s,
                 "stages": stages, "launches": st1["kernel_launches"] - st0["kernel_launches"],
                 "refine_candidates": st1["refine_candidates"] - st0["refine_candidates"], "prof_steps": n_prof,
                 "triggers": int(len(trig))}
@@ -502,6 +507,7 @@ def main():
     # e2e: host strain in, triggers out, through the C ABI
     ctx2 = lloid.Context(local, stream=stream.cuda_stream)
     ctx2.graphs(args.graphs == "on")
+    ctx2.autotune(args.autotune == "on")
     u2 = make_units(ctx2, args.precision)
     dets = [det for _, det in unit_specs]
     t2 = 0
@@ -555,12 +561,14 @@ def main():
                        "templates": n_templates_all, "units_per_gpu": n_units, "setup_s": prim["create_s"],
                        "push_seconds": args.push_seconds, "precision": args.precision,
                        "parallelism": f"units sharded, {world} GPU(s)", "cuda_graphs": args.graphs,
+                       "mix_autotune": args.autotune,
                        "l2": "flushed between steps (256 MB write outside the step events)"},
             "roofline": roof, "e2e": e2e, "gpu_launches": prim["launches"], "clocks": prim["clocks"],
             "stages_ms_share": {k: round(v / total_stage_ms, 4) for k, v in busy.items()},
             "by_precision": {p: {"value": r["value"], "ms_per_step": 1e3 * r["dev_s"] / args.steps,
                                  "gain_vs_fp32": None}
                              for p, r in [(args.precision, prim), *others.items()]},
+            "autotune": prim["autotune"],
             "wall_s": prim["wall"], "triggers": prim["triggers"],
             "refine_candidates_per_step": prim["refine_candidates"] / args.steps}
     if "fp32" in line["by_precision"]:

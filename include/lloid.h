@@ -229,6 +229,8 @@ typedef struct sb_ctx_stats {
     int64_t refine_candidates;  /* partial window maxima recomputed in FP32 (a6)  */
     int64_t refine_dropped;     /* pushes whose candidates exceeded the list (65536); the rest kept 16-bit values */
     int64_t graph_launches;     /* pushes launched as one CUDA graph (sb_ctx_graphs)  */
+    int64_t autotune_shapes;    /* mixing-kernel launch shapes timed by the autotuner  */
+    int64_t autotune_launches;  /* mixing-kernel launches spent timing candidates        */
 } sb_ctx_stats;
 int sb_ctx_get_stats(sb_ctx *ctx, sb_ctx_stats *out);
 
@@ -243,6 +245,22 @@ int sb_ctx_profile(sb_ctx *ctx, int32_t enable);
  * captured.  enable == 0 (the default): kernels are launched one by one.
  * Results are identical either way. */
 int sb_ctx_graphs(sb_ctx *ctx, int32_t enable);
+/* enable != 0 (the default): the first push that launches the mixing kernel
+ * (a3 + a4) with a new launch shape (precision, K chunks per tile, whether the
+ * level's SNR is stored, tile count rounded down to a power of two) times every
+ * pipeline shape that fits in shared memory (mixing stages 1-2, interpolation
+ * buffers 1-2, window-ring depth 2-4) on that push's own data and keeps the
+ * fastest for later pushes; that push is not graph-captured.  The pipeline
+ * shape changes no arithmetic: results are bitwise the same for every choice.
+ * enable == 0: later launches use the built-in shape for new launch shapes
+ * (tuned shapes are kept). */
+int sb_ctx_autotune(sb_ctx *ctx, int32_t enable);
+/* The tuned launch shapes: writes min(cap, number tuned) records of four int32
+ * {shape key, mixing stages, interpolation buffers, window-ring depth} into out
+ * (4 * cap entries) and returns the number of tuned shapes (>= 0), or a
+ * negative SB_E* code.  Shape key bits: 0-1 precision (0 FP16, 1 BF16,
+ * 2 E4M3), 2 SNR stored, 3-4 K chunks per tile (capped at 3), 5+ log2 tiles. */
+int sb_ctx_autotune_choices(sb_ctx *ctx, int32_t *out, int32_t cap);
 /* Blocks until queued work is done, then writes per stage the summed kernel
  * time (ms) and the number of launches since profiling was enabled
  * (arrays of n_stages entries; n_stages <= SB_N_STAGES). */

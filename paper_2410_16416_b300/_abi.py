@@ -51,7 +51,8 @@ class SbUnitInfo(C.Structure):
 class SbCtxStats(C.Structure):
     _fields_ = [("pushes", C.c_int64), ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("triggers", C.c_int64), ("refine_candidates", C.c_int64),
-                ("refine_dropped", C.c_int64), ("graph_launches", C.c_int64)]
+                ("refine_dropped", C.c_int64), ("graph_launches", C.c_int64),
+                ("autotune_shapes", C.c_int64), ("autotune_launches", C.c_int64)]
 
 
 STAGES = ["history", "strain", "decimate", "fir", "upsample", "mix", "trigger", "snr_history", "refine"]
@@ -80,6 +81,8 @@ SIGNATURES = {
     "sb_ctx_get_stats": (C.c_int, [C.c_void_p, C.POINTER(SbCtxStats)]),
     "sb_ctx_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "sb_ctx_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sb_ctx_autotune": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sb_ctx_autotune_choices": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]),
     "sb_ctx_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "sb_window_triggers_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                                              C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
@@ -201,6 +204,25 @@ class Context:
     def graphs(self, enable: bool):
         """Capture every push into a CUDA graph (reused per group shape); results are unchanged."""
         _check(lib.sb_ctx_graphs(self.handle, int(bool(enable))), "sb_ctx_graphs")
+
+    def autotune(self, enable: bool) -> None:
+        """Time the mixing kernel's pipeline shapes on new launch shapes (default on)."""
+        _check(lib.sb_ctx_autotune(self.handle, int(bool(enable))), "sb_ctx_autotune")
+
+    def autotune_choices(self) -> list:
+        """[{key, mode, store_y, k_chunks, log2_tiles, stages, u_buffers, window_ring}] tuned so far."""
+        n = lib.sb_ctx_autotune_choices(self.handle, None, 0)
+        _check(min(n, 0), "sb_ctx_autotune_choices")
+        buf = (C.c_int32 * (4 * max(n, 1)))()
+        n = lib.sb_ctx_autotune_choices(self.handle, buf, n)
+        _check(min(n, 0), "sb_ctx_autotune_choices")
+        out = []
+        for i in range(n):
+            k = buf[4 * i]
+            out.append({"key": k, "mode": ("fp16", "bf16", "e4m3")[k & 3], "store_y": bool(k & 4),
+                        "k_chunks": (k >> 3) & 3, "log2_tiles": k >> 5, "stages": buf[4 * i + 1],
+                        "u_buffers": buf[4 * i + 2], "window_ring": buf[4 * i + 3]})
+        return out
 
     def stage_times(self) -> dict:
         """{stage: (ms summed over launches, launches)} since profile(True); blocks."""

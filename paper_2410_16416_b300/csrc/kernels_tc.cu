@@ -815,38 +815,96 @@ static int sm_count() {
 }
 
 template <int MODE, int UB>
-static cudaError_t mixup_launch_ub(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int n_st, int n_u,
+static cudaError_t mixup_launch_ub(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixCfg &cfg,
                                    int n_stbuf, const void *utab, int *err, cudaStream_t s) {
-    const size_t fixed = tc_mixup_smem_bytes(n_st, 0, n_u, n_stbuf, UB);
-    const int n_win = (int)std::min<size_t>(kMixMaxWin, (kMixSmemMax - fixed) / kWinChunkBytes);
-    const size_t smem = tc_mixup_smem_bytes(n_st, n_win, n_u, n_stbuf, UB);
+    const size_t smem = tc_mixup_smem_bytes(cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, UB);
     cudaError_t e = set_smem(tc_mixup_kernel<MODE, UB>, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total_tiles, sm_count());
     return launch_pdl(tc_mixup_kernel<MODE, UB>, dim3(grid), dim3(kMixThreads), smem, s, d_tasks, n_tasks,
-                      total_tiles, n_st, n_win, n_u, n_stbuf, static_cast<const uint8_t *>(utab), err);
+                      total_tiles, cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, static_cast<const uint8_t *>(utab), err);
+}
+
+uint32_t tc_mixup_shape_key(int mode, int max_nk, bool store_y, int total_tiles) {
+    int lg = 0;
+    while ((1 << (lg + 1)) <= total_tiles && lg < 30) ++lg;
+    return (uint32_t)mode | (store_y ? 4u : 0u) | ((uint32_t)std::min(max_nk, 3) << 3) | ((uint32_t)lg << 5);
+}
+
+// Pipeline shapes that fit in shared memory (<= 227 KB).  Several K chunks per tile may take two
+// mixing stages; one staging buffer per epilogue warp when the level's y is stored; the window
+// ring takes 2 .. 4 chunks.  The default: two stages and one U buffer for several K chunks, else
+// one stage and two U buffers (one U buffer for the wider top-level blocks); the deepest ring.
+static std::vector<MixCfg> mix_candidates(int max_nk, bool store_y, int ub) {
+    std::vector<MixCfg> out;
+    const int n_stbuf = store_y ? 1 : 0;
+    for (int n_st = (max_nk >= 2 ? 2 : 1); n_st >= 1; --n_st)
+        for (int n_u = (ub == 128 ? 1 : 2); n_u >= 1; --n_u) {
+            const size_t fixed = tc_mixup_smem_bytes(n_st, 0, n_u, n_stbuf, ub);
+            const int n_max = (int)std::min<size_t>(kMixMaxWin, (kMixSmemMax - fixed) / kWinChunkBytes);
+            for (int n_win = n_max; n_win >= 2; --n_win) out.push_back(MixCfg{n_st, n_u, n_win});
+        }
+    return out;
+}
+
+template <int MODE, int UB>
+static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk,
+                                      bool store_y, const void *utab, int *err, MixTuner *tuner, bool may_tune,
+                                      cudaStream_t s) {
+    const int n_stbuf = store_y ? 1 : 0;
+    const std::vector<MixCfg> cands = mix_candidates(max_nk, store_y, UB);
+    MixCfg cfg = cands.front();
+    const uint32_t key = tc_mixup_shape_key(MODE, max_nk, store_y, total_tiles);
+    const MixCfg *known = tuner ? tuner->find(key) : nullptr;
+    if (known) cfg = *known;
+    if (tuner && !known && may_tune && cands.size() == 1) tuner->best.emplace_back(key, cfg);
+    if (tuner && !known && may_tune && cands.size() > 1) {
+        // time every candidate once on this push (each launch computes the same result)
+        std::vector<cudaEvent_t> ev(cands.size() + 1);
+        for (auto &x : ev) cudaEventCreate(&x);
+        cudaError_t e = cudaEventRecord(ev[0], s);
+        for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
+            e = mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cands[i], n_stbuf, utab, err, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[i + 1], s);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+        float best_ms = 1e30f;
+        for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
+            float ms = 0.0f;
+            e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            if (e == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                cfg = cands[i];
+            }
+        }
+        for (auto &x : ev) cudaEventDestroy(x);
+        if (e != cudaSuccess) return e;
+        tuner->best.emplace_back(key, cfg);
+        tuner->timed_launches += (int64_t)cands.size();
+        return cudaSuccess;
+    }
+    return mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cfg, n_stbuf, utab, err, s);
 }
 
 template <int MODE>
 static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
-                                const void *utab, int *err, cudaStream_t s) {
-    // shared memory (<= 227 KB): several K chunks per tile take two mixing stages and one U
-    // buffer (U changes only between tasks), one chunk takes one stage and two U buffers; one
-    // staging buffer per epilogue warp when the level's y is stored; the window ring gets the rest.
-    // Levels that store nothing (the top) use 128-wide interpolation blocks (fewer, wider MMAs)
-    // with one U buffer.
-    const int n_st = max_nk >= 2 ? 2 : 1, n_stbuf = store_y ? 1 : 0;
-    if (!store_y) return mixup_launch_ub<MODE, 128>(d_tasks, n_tasks, total_tiles, n_st, 1, 0, utab, err, s);
-    return mixup_launch_ub<MODE, 64>(d_tasks, n_tasks, total_tiles, n_st, n_st == 2 ? 1 : 2, n_stbuf, utab, err, s);
+                                const void *utab, int *err, MixTuner *tuner, bool may_tune, cudaStream_t s) {
+    // levels that store nothing (the top) use 128-wide interpolation blocks (fewer, wider MMAs)
+    if (!store_y)
+        return mixup_launch_tuned<MODE, 128>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner,
+                                             may_tune, s);
+    return mixup_launch_tuned<MODE, 64>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune,
+                                        s);
 }
 
 cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
-                            const void *utab, int mode, int *err, cudaStream_t s) {
+                            const void *utab, int mode, int *err, MixTuner *tuner, bool may_tune, cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
     if (mode == kModeBF16)
-        return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, s);
-    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, s);
-    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, s);
+        return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune, s);
+    if (mode == kModeF16)
+        return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune, s);
+    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune, s);
 }
 
 }  // namespace lloid

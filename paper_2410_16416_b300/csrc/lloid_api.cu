@@ -185,6 +185,9 @@ struct sb_ctx {
     bool graphs = false;
     std::map<std::string, cudaGraphExec_t> graph_execs;
     int64_t graph_launches = 0;
+    // mixing-kernel pipeline shapes chosen by timing (no effect on results)
+    bool autotune = true;
+    MixTuner tuner;
     // profiling: event pairs around each launch, summed per stage on query
     bool prof = false;
     struct Mark { int stage; cudaEvent_t a, b; };
@@ -1108,6 +1111,8 @@ extern "C" int sb_ctx_get_stats(sb_ctx *c, sb_ctx_stats *out) {
     out->refine_candidates = (int64_t)cum[0];
     out->refine_dropped = (int64_t)cum[1];
     out->graph_launches = c->graph_launches;
+    out->autotune_shapes = (int64_t)c->tuner.best.size();
+    out->autotune_launches = c->tuner.timed_launches;
     return SB_OK;
 }
 
@@ -1124,6 +1129,28 @@ extern "C" int sb_ctx_graphs(sb_ctx *c, int32_t enable) {
     std::lock_guard<std::mutex> lk(c->mu);
     c->graphs = enable != 0;
     return SB_OK;
+}
+
+extern "C" int sb_ctx_autotune(sb_ctx *c, int32_t enable) {
+    if (!c) return fail(SB_EINVAL, "ctx is null");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->autotune = enable != 0;
+    return SB_OK;
+}
+
+extern "C" int sb_ctx_autotune_choices(sb_ctx *c, int32_t *out, int32_t cap) {
+    if (!c) return fail(SB_EINVAL, "ctx is null");
+    if (cap < 0 || (cap > 0 && !out)) return fail(SB_EINVAL, "bad output buffer");
+    std::lock_guard<std::mutex> lk(c->mu);
+    const int n = (int)c->tuner.best.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        const auto &kv = c->tuner.best[i];
+        out[4 * i] = (int32_t)kv.first;
+        out[4 * i + 1] = kv.second.n_st;
+        out[4 * i + 2] = kv.second.n_u;
+        out[4 * i + 3] = kv.second.n_win;
+    }
+    return n;
 }
 
 extern "C" int sb_ctx_profile(sb_ctx *c, int32_t enable) {
@@ -1773,7 +1800,15 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     std::memcpy(ar->h, pk.buf.data(), pk.buf.size());
 
     // graph mode: everything from the task upload to the trigger read-back is one captured graph
-    const bool capture = c->graphs && !c->prof;
+    // a push that times a new mixing launch shape runs uncaptured (the tuner synchronises)
+    bool tune_now = false;
+    if (c->autotune)
+        for (int h = 0; h < NM; ++h)
+            for (int k = 0; k <= kall; ++k)
+                if (!tmix[h][k].empty() &&
+                    !c->tuner.find(tc_mixup_shape_key(h, tmix_maxnk[h][k], tmix_tstore[h][k] != 0, tmix_tiles[h][k])))
+                    tune_now = true;
+    const bool capture = c->graphs && !c->prof && !tune_now;
     std::string gkey;
     CaptureGuard guard;
     if (capture) {
@@ -1846,10 +1881,13 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         for (int h = 0; h < NM; ++h)
             if (!tmix[h][k].empty() &&
                 (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
-                     *n = 1;
-                     return launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
-                                            tmix_tiles[h][k], tmix_maxnk[h][k], tmix_tstore[h][k] != 0, c->utab, h,
-                                            derr, st);
+                     const int64_t timed0 = c->tuner.timed_launches;
+                     cudaError_t e = launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
+                                                     tmix_tiles[h][k], tmix_maxnk[h][k], tmix_tstore[h][k] != 0,
+                                                     c->utab, h, derr, c->autotune ? &c->tuner : nullptr, tune_now,
+                                                     st);
+                     *n = (int)std::max<int64_t>(1, c->tuner.timed_launches - timed0);
+                     return e;
                  })))
                 return rc;
     }

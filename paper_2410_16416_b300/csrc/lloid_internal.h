@@ -4,6 +4,8 @@
 // slices of several banks are filtered together).
 #pragma once
 #include <cstdint>
+#include <utility>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -245,9 +247,27 @@ size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk);
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s);
-// utab: the interpolation operand table (tc_interp_table_bytes(), built by tc_interp_table)
+// Pipeline shape of one tc_mixup launch: mixing stages, interpolation-operand buffers and the
+// depth of the window ring.  None of them changes the arithmetic, so results do not depend on
+// the choice; the autotuner times the candidates that fit in shared memory once per launch
+// shape (mode, K chunks, whether y is stored, tile count) and keeps the fastest.
+struct MixCfg {
+    int n_st, n_u, n_win;
+};
+struct MixTuner {
+    std::vector<std::pair<uint32_t, MixCfg>> best;    // launch shape -> fastest pipeline shape
+    int64_t timed_launches = 0;
+    const MixCfg *find(uint32_t key) const {
+        for (auto &kv : best)
+            if (kv.first == key) return &kv.second;
+        return nullptr;
+    }
+};
+uint32_t tc_mixup_shape_key(int mode, int max_nk, bool store_y, int total_tiles);
+// utab: the interpolation operand table (tc_interp_table_bytes(), built by tc_interp_table).
+// tuner: null, or the context's tuner; may_tune: the shape may be timed now (no capture running).
 cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
-                            const void *utab, int mode, int *err, cudaStream_t s);
+                            const void *utab, int mode, int *err, MixTuner *tuner, bool may_tune, cudaStream_t s);
 size_t tc_interp_table_bytes();
 void tc_interp_table(const Halfband &g, void *host_out);
 cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
