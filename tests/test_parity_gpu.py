@@ -155,7 +155,7 @@ def test_autotuned_pipeline_equals_default(lloid, small_case, precision):
     """The mixing kernel's pipeline shape, timed and chosen per launch shape, leaves every output
     bitwise unchanged (tuning on vs off, with the tuning pushes themselves included)."""
     spec, h, bank, d, x = small_case
-    sizes = [2048] * 3 + [4096] * 2 + [2048] * 2
+    sizes = [2048] * 3 + [4096] * 2 + [2048] * 5
     runs = []
     for tune in (False, True):
         ctx = lloid.Context(0)
