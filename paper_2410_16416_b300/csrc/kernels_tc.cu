@@ -770,9 +770,21 @@ size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk) 
     return 1024 + 1024 + (size_t)n_st * kMixStageBytes + (size_t)n_win * kWinChunkBytes + (size_t)n_u * uvar +
            (size_t)8 * n_stbuf * kMixStBytes;
 }
+// Opts a kernel into the full 227 KB of dynamic shared memory, once.  The attribute is a limit on
+// the launches of the function, kept by the function rather than by a launch: lowering it to one
+// launch's size would invalidate an earlier launch of the same function (a captured graph node,
+// or a profiler's replay of it) that needs more.  So it is raised to the maximum and never lowered.
 template <class K>
 static cudaError_t set_smem(K kernel, size_t smem) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool done[64] = {};                   // per kernel instantiation and device
+    if (smem > kMixSmemMax) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmemMax);
+    if (e == cudaSuccess && dev < 64) done[dev] = true;
+    return e;
 }
 
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s) {
