@@ -17,6 +17,8 @@
 // One CTA = 4 warps: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, then
 // all four warps drain TMEM (each warp owns 32 TMEM lanes).
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -776,14 +778,17 @@ size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk) 
 // or a profiler's replay of it) that needs more.  So it is raised to the maximum and never lowered.
 template <class K>
 static cudaError_t set_smem(K kernel, size_t smem) {
-    static bool done[64] = {};                   // per kernel instantiation and device
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;   // (kernel, device) pairs already raised
     if (smem > kMixSmemMax) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 64 && done[dev]) return cudaSuccess;
+    const std::pair<const void *, int> id(reinterpret_cast<const void *>(kernel), dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(id)) return cudaSuccess;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmemMax);
-    if (e == cudaSuccess && dev < 64) done[dev] = true;
+    if (e == cudaSuccess) done.insert(id);
     return e;
 }
 
