@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) copy_kernel(const CopyTask *__restrict__ 
         const uint16_t *hist = reinterpret_cast<const uint16_t *>(t.hist);
         const uint16_t *cur = reinterpret_cast<const uint16_t *>(t.cur);
         uint16_t *dst = reinterpret_cast<uint16_t *>(t.dst);
-        for (int part = 0; part < 2; ++part) {
+        for (int part = 0; part < t.elem16; ++part) {
             const int64_t r = row + (int64_t)part * t.rows;
             dst[r * t.ld_dst + i] = pos < t.n_hist ? hist[r * t.ld_hist + pos] : cur[r * t.ld_cur + (pos - t.n_hist)];
         }

@@ -254,8 +254,7 @@ constexpr int kMixCols = 256;                            // time samples per til
 constexpr int kMixABytes = kMixRows * 128;               // mixing tile: 128 filters x 128 bytes of K
 constexpr int kMixBBytes = kMixCols * 128;               // basis-output tile: 256 time x 128 bytes of K
 constexpr int kMixStageBytes = kMixABytes + kMixBBytes;
-constexpr int kWinHalfBytes = kMixRows * 128;            // 64 coarser samples (BF16) x 128 filters
-constexpr int kWinChunkBytes = 2 * kWinHalfBytes;        // hi + lo
+constexpr int kWinHalfBytes = kMixRows * 128;            // one plane: 64 coarser samples (16-bit) x 128 filters
 constexpr int kWinChunks = 3;                            // 192 >= 7 + 176 coarser samples per tile
 // Interpolation block geometry: UB outputs per block (MMA N); a block reads UB/2 + 48 coarser
 // samples (its own UB/2, 16 + 16 taps and up to 7 + 1 of alignment), rounded to whole MMA K steps.
@@ -268,22 +267,24 @@ struct UGeo {
     static constexpr int kBlocks = 256 / UB;
 };
 constexpr int kUVariants = 16;                           // (parity, offset 0..7)
-// operand table: the 16 variants of the 64-wide blocks, then those of the 128-wide blocks
+// operand table: BF16 hi / lo terms of the 16 variants of the 64-wide blocks, then of the 128-wide
+// blocks; then the same two parts as FP16 hi / lo terms (for the one-plane FP16 y)
 constexpr size_t kUTab128 = (size_t)kUVariants * UGeo<64>::kVarBytes;
-constexpr int kMixStBytes = 2 * 32 * 64;                 // store staging: hi + lo, 32 filters x 32 samples
+constexpr size_t kUTabPart = kUTab128 + (size_t)kUVariants * UGeo<128>::kVarBytes;
+constexpr int kMixStPlane = 32 * 64;                     // store staging per plane: 32 filters x 32 samples
 constexpr int kMixThreads = 384;
-constexpr int kMixMaxWin = 4;
+constexpr int kMixMaxWin = 6;
 constexpr size_t kMixSmemMax = 227 * 1024;               // dynamic shared memory per CTA (opt-in maximum)
 
-size_t tc_interp_table_bytes() { return kUTab128 + (size_t)kUVariants * UGeo<128>::kVarBytes; }
+size_t tc_interp_table_bytes() { return 2 * kUTabPart; }
 
 // U for variant (par, rem): output c of a block takes coarser sample
 // i = rem + 16 + ((c + par) >> 1) (even c + par: weight 1 = 2 g[0]) or the
-// pairs i - t, i + 1 + t with weight 2 g[2t+1] (odd c + par).  Stored as BF16
-// hi and lo terms in the no-swizzle K-major layout: element (c, i) at byte
-// ((c / 8) * (K / 8) + i / 8) * 128 + (c % 8) * 16 + (i % 8) * 2.
+// pairs i - t, i + 1 + t with weight 2 g[2t+1] (odd c + par).  Stored as hi and
+// lo terms (BF16, or FP16 with f16) in the no-swizzle K-major layout: element
+// (c, i) at byte ((c / 8) * (K / 8) + i / 8) * 128 + (c % 8) * 16 + (i % 8) * 2.
 template <int UB>
-static void interp_table_part(const Halfband &g, uint16_t *out) {
+static void interp_table_part(const Halfband &g, uint16_t *out, bool f16) {
     using G = UGeo<UB>;
     auto bf16_bits = [](float v) {                       // round to nearest even
         uint32_t u;
@@ -296,6 +297,17 @@ static void interp_table_part(const Halfband &g, uint16_t *out) {
         float v;
         std::memcpy(&v, &u, 4);
         return v;
+    };
+    auto bits = [&](float v) {
+        if (!f16) return bf16_bits(v);
+        const __half_raw r = __float2half_rn(v);
+        return (uint16_t)r.x;
+    };
+    auto val = [&](uint16_t h) {
+        if (!f16) return bf16_val(h);
+        __half_raw r;
+        r.x = h;
+        return __half2float(__half(r));
     };
     for (int var = 0; var < kUVariants; ++var) {
         const int par = var / 8, rem = var % 8;
@@ -316,17 +328,19 @@ static void interp_table_part(const Halfband &g, uint16_t *out) {
             for (int i = 0; i < G::kK; ++i) {
                 const size_t at = ((size_t)(c / 8) * (G::kK / 8) + i / 8) * 64 + (c % 8) * 8 + (i % 8);
                 const float u = U[(size_t)c * G::kK + i];
-                const uint16_t h = bf16_bits(u);
+                const uint16_t h = bits(u);
                 hi[at] = h;
-                lo[at] = bf16_bits(u - bf16_val(h));
+                lo[at] = bits(u - val(h));
             }
     }
 }
 
 void tc_interp_table(const Halfband &g, void *host_out) {
     uint8_t *out = static_cast<uint8_t *>(host_out);
-    interp_table_part<64>(g, reinterpret_cast<uint16_t *>(out));
-    interp_table_part<128>(g, reinterpret_cast<uint16_t *>(out + kUTab128));
+    for (int f = 0; f < 2; ++f) {
+        interp_table_part<64>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart), f == 1);
+        interp_table_part<128>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart + kUTab128), f == 1);
+    }
 }
 
 struct SegBest {
@@ -389,8 +403,10 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                                                                    int n_stbuf,
                                                                    const uint8_t *__restrict__ utab, int *err) {
     constexpr int kKC = 128 / Op<MODE>::kBytes, kMK = Op<MODE>::kMmaK;
+    constexpr int NP = y_planes(MODE);                   // 1: FP16 y; 2: BF16 hi + lo
+    constexpr int kWinBytes = NP * kWinHalfBytes;
     using G = UGeo<UB>;
-    utab += UB == 128 ? kUTab128 : 0;
+    utab += (NP == 1 ? kUTabPart : 0) + (UB == 128 ? kUTab128 : 0);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -405,7 +421,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mdrain + 1);
     uint8_t *stage = smem + 1024;                                  // n_st mixing stages
     uint8_t *win = stage + n_st * kMixStageBytes;                  // n_win window chunks
-    uint8_t *ubuf = win + n_win * kWinChunkBytes;                  // n_u U variants
+    uint8_t *ubuf = win + n_win * kWinBytes;                       // n_u U variants
     uint8_t *stbuf = ubuf + n_u * G::kVarBytes;                    // n_stbuf per epilogue warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -476,11 +492,11 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     ok = false;
                     break;
                 }
-                uint8_t *dst = win + ws * kWinChunkBytes;
-                mbar_expect_tx(&wfull[ws], kWinChunkBytes);
+                uint8_t *dst = win + ws * kWinBytes;
+                mbar_expect_tx(&wfull[ws], kWinBytes);
                 const int x = (int)(m.xs0 + 64 * wc);
-                tma_load_2d(dst, t.mapY, x, m.at * kMixRows, &wfull[ws]);                     // hi
-                tma_load_2d(dst + kWinHalfBytes, t.mapY, x, t.M2 + m.at * kMixRows, &wfull[ws]);  // lo
+                tma_load_2d(dst, t.mapY, x, m.at * kMixRows, &wfull[ws]);                         // (hi)
+                if (NP == 2) tma_load_2d(dst + kWinHalfBytes, t.mapY, x, t.M2 + m.at * kMixRows, &wfull[ws]);  // lo
                 ++wu;
             }
         }
@@ -498,7 +514,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         int uvar = -1;
         bool issued = false;
         const uint32_t idesc = idesc_op<MODE>(kMixRows, kMixCols);
-        const uint32_t idesc_u = idesc_op<kModeBF16>(kMixRows, G::kBlk);
+        const uint32_t idesc_u = idesc_op<NP == 1 ? kModeF16 : kModeBF16>(kMixRows, G::kBlk);
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
             const bool has_src = m.t->mapY != nullptr;
@@ -550,7 +566,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t da_hi = desc_k_sw128(smem_u32(win + ws * kWinChunkBytes));
+                    const uint64_t da_hi = desc_k_sw128(smem_u32(win + ws * kWinBytes));
                     const uint64_t da_lo = da_hi + (kWinHalfBytes >> 4);
 #pragma unroll
                     for (int j = 0; j < G::kBlocks; ++j)
@@ -562,7 +578,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                             const uint32_t dj = d + UB * j;
                             mma_f16(dj, da_hi + ao, du_hi + bo, idesc_u, kap > (UB / 2) * j ? 1u : first);
                             mma_f16(dj, da_hi + ao, du_lo + bo, idesc_u, 1u);
-                            mma_f16(dj, da_lo + ao, du_hi + bo, idesc_u, 1u);
+                            if (NP == 2) mma_f16(dj, da_lo + ao, du_hi + bo, idesc_u, 1u);
                         }
                     issued = true;
                     mma_commit(&wempty[ws]);
@@ -581,7 +597,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         // ---- epilogue ----
         const int q = warp & 3, h = (warp >> 2) - 1;            // TMEM lane quarter (warp % 4), half tile
         const int R = 32 * q + lane;                         // TMEM lane = filter row in the tile
-        uint8_t *sbuf = stbuf + (warp - 4) * kMixStBytes;
+        uint8_t *sbuf = stbuf + (warp - 4) * (NP * kMixStPlane);
         uint32_t au = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
@@ -635,18 +651,26 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                         if (n0 + j < 0) x[j] = 0.0f;         // every rate starts at index 0
                 }
                 if (Yh && n_stbuf > 0) {
-                    // y as BF16 hi / lo through a per-warp staging buffer: row `lane` of two 32 x 32 tiles
-                    // (64-byte rows, 16-byte chunk i at chunk i ^ ((r >> 1) & 3): no bank conflicts),
-                    // then each store instruction writes 8 whole 64-byte row segments
+                    // y (FP16, or BF16 hi / lo) through a per-warp staging buffer: row `lane` of one
+                    // 32 x 32 tile per plane (64-byte rows, 16-byte chunk i at chunk i ^ ((r >> 1) & 3):
+                    // no bank conflicts), then each store instruction writes 8 whole 64-byte row segments
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float y0 = x[2 * j] * inv_next, y1 = x[2 * j + 1] * inv_next;
-                        const __nv_bfloat162 hv = __floats2bfloat162_rn(y0, y1);       // hi: one packed convert
-                        const float2 hf = __bfloat1622float2(hv);
-                        const __nv_bfloat162 lv = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
-                        hw[j] = *reinterpret_cast<const uint32_t *>(&hv);
-                        lw[j] = *reinterpret_cast<const uint32_t *>(&lv);
+                        if constexpr (NP == 1) {
+                            // saturate instead of overflowing to infinity (|SNR| > 65504)
+                            const __half2 hv = __floats2half2_rn(fminf(fmaxf(y0, -65504.0f), 65504.0f),
+                                                                 fminf(fmaxf(y1, -65504.0f), 65504.0f));
+                            hw[j] = *reinterpret_cast<const uint32_t *>(&hv);
+                            lw[j] = 0u;
+                        } else {
+                            const __nv_bfloat162 hv = __floats2bfloat162_rn(y0, y1);   // hi: one packed convert
+                            const float2 hf = __bfloat1622float2(hv);
+                            const __nv_bfloat162 lv = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
+                            hw[j] = *reinterpret_cast<const uint32_t *>(&hv);
+                            lw[j] = *reinterpret_cast<const uint32_t *>(&lv);
+                        }
                     }
                     __syncwarp();                                   // the previous chunk's reads are done
                     const int sw = (lane >> 1) & 3;
@@ -654,8 +678,9 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     for (int i = 0; i < 4; ++i) {
                         *reinterpret_cast<uint4 *>(sbuf + lane * 64 + ((i ^ sw) * 16)) =
                             make_uint4(hw[4 * i], hw[4 * i + 1], hw[4 * i + 2], hw[4 * i + 3]);
-                        *reinterpret_cast<uint4 *>(sbuf + 2048 + lane * 64 + ((i ^ sw) * 16)) =
-                            make_uint4(lw[4 * i], lw[4 * i + 1], lw[4 * i + 2], lw[4 * i + 3]);
+                        if (NP == 2)
+                            *reinterpret_cast<uint4 *>(sbuf + kMixStPlane + lane * 64 + ((i ^ sw) * 16)) =
+                                make_uint4(lw[4 * i], lw[4 * i + 1], lw[4 * i + 2], lw[4 * i + 3]);
                     }
                     __syncwarp();
                     const int ch = lane & 3;
@@ -666,10 +691,11 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                         const int arow = kMixRows * m.at + 32 * q + r;
                         const int pc = ch ^ ((r >> 1) & 3);
                         const uint4 vh = *reinterpret_cast<const uint4 *>(sbuf + r * 64 + pc * 16);
-                        const uint4 vl = *reinterpret_cast<const uint4 *>(sbuf + 2048 + r * 64 + pc * 16);
                         if (arow < M2 && col + 8 <= ldu) {
                             *reinterpret_cast<uint4 *>(Yh + (int64_t)arow * ldu + col) = vh;
-                            *reinterpret_cast<uint4 *>(Yh + ((int64_t)M2 + arow) * ldu + col) = vl;
+                            if (NP == 2)
+                                *reinterpret_cast<uint4 *>(Yh + ((int64_t)M2 + arow) * ldu + col) =
+                                    *reinterpret_cast<const uint4 *>(sbuf + kMixStPlane + r * 64 + pc * 16);
                         }
                     }
                 } else if (Y && row_ok) {
@@ -767,10 +793,10 @@ size_t tc_fir_smem_bytes(int kpad_max, int mode) {
     const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2;
     return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * ph + kpad_max) * by;
 }
-size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk) {
+size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk, int np) {
     const size_t uvar = ublk == 128 ? UGeo<128>::kVarBytes : UGeo<64>::kVarBytes;
-    return 1024 + 1024 + (size_t)n_st * kMixStageBytes + (size_t)n_win * kWinChunkBytes + (size_t)n_u * uvar +
-           (size_t)8 * n_stbuf * kMixStBytes;
+    return 1024 + 1024 + (size_t)n_st * kMixStageBytes + (size_t)n_win * np * kWinHalfBytes +
+           (size_t)n_u * uvar + (size_t)8 * n_stbuf * np * kMixStPlane;
 }
 // Opts a kernel into the full 227 KB of dynamic shared memory, once.  The attribute is a limit on
 // the launches of the function, kept by the function rather than by a launch: lowering it to one
@@ -834,7 +860,7 @@ static int sm_count() {
 template <int MODE, int UB>
 static cudaError_t mixup_launch_ub(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixCfg &cfg,
                                    int n_stbuf, const void *utab, int *err, cudaStream_t s) {
-    const size_t smem = tc_mixup_smem_bytes(cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, UB);
+    const size_t smem = tc_mixup_smem_bytes(cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, UB, y_planes(MODE));
     cudaError_t e = set_smem(tc_mixup_kernel<MODE, UB>, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total_tiles, sm_count());
@@ -850,15 +876,16 @@ uint32_t tc_mixup_shape_key(int mode, int max_nk, bool store_y, int total_tiles)
 
 // Pipeline shapes that fit in shared memory (<= 227 KB).  Several K chunks per tile may take two
 // mixing stages; one staging buffer per epilogue warp when the level's y is stored; the window
-// ring takes 2 .. 4 chunks.  The default: two stages and one U buffer for several K chunks, else
-// one stage and two U buffers (one U buffer for the wider top-level blocks); the deepest ring.
-static std::vector<MixCfg> mix_candidates(int max_nk, bool store_y, int ub) {
+// ring takes 2 .. 6 chunks (np planes each).  The default: two stages and one U buffer for several
+// K chunks, else one stage and two U buffers (one U buffer for the wider top-level blocks); the
+// deepest ring that fits.
+static std::vector<MixCfg> mix_candidates(int max_nk, bool store_y, int ub, int np) {
     std::vector<MixCfg> out;
     const int n_stbuf = store_y ? 1 : 0;
     for (int n_st = (max_nk >= 2 ? 2 : 1); n_st >= 1; --n_st)
         for (int n_u = (ub == 128 ? 1 : 2); n_u >= 1; --n_u) {
-            const size_t fixed = tc_mixup_smem_bytes(n_st, 0, n_u, n_stbuf, ub);
-            const int n_max = (int)std::min<size_t>(kMixMaxWin, (kMixSmemMax - fixed) / kWinChunkBytes);
+            const size_t fixed = tc_mixup_smem_bytes(n_st, 0, n_u, n_stbuf, ub, np);
+            const int n_max = (int)std::min<size_t>(kMixMaxWin, (kMixSmemMax - fixed) / ((size_t)np * kWinHalfBytes));
             for (int n_win = n_max; n_win >= 2; --n_win) out.push_back(MixCfg{n_st, n_u, n_win});
         }
     return out;
@@ -869,7 +896,7 @@ static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, i
                                       bool store_y, const void *utab, int *err, MixTuner *tuner, bool may_tune,
                                       cudaStream_t s) {
     const int n_stbuf = store_y ? 1 : 0;
-    const std::vector<MixCfg> cands = mix_candidates(max_nk, store_y, UB);
+    const std::vector<MixCfg> cands = mix_candidates(max_nk, store_y, UB, y_planes(MODE));
     MixCfg cfg = cands.front();
     const uint32_t key = tc_mixup_shape_key(MODE, max_nk, store_y, total_tiles);
     const MixCfg *known = tuner ? tuner->find(key) : nullptr;

@@ -129,7 +129,8 @@ struct LevelDev {
     CUtensorMap *mapY = nullptr;     // yuni as the finer level's interpolation operand (box 64 x 128, 128-byte swizzle)
     // 16-bit modes, levels k >= 1: SNR rows [history (Hy) | new (B_k)] in one buffer, so the
     // next finer level's epilogue can stage a row segment with one TMA load
-    float *yuni = nullptr;    // FP32 mode: unused; 16/8-bit modes: y as BF16 hi rows [0, 2M), lo rows [2M, 4M), ld ldu
+    float *yuni = nullptr;    // FP32 mode: unused; BF16 mode: y as FP16 rows [0, 2M); FP16 / E4M3 modes: y as
+                              // BF16 hi rows [0, 2M), lo rows [2M, 4M); ld ldu
     int64_t ldu = 0;
     float *ytmp = nullptr;    // history shift staging, same layout with ld Hy
 };
@@ -402,7 +403,7 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
         b += 2 * M2 * P.Hy[k] * 4;                   // SNR history ping-pong
         if (P.tc) {
             b -= M2 * ldy * 4 + 2 * M2 * P.Hy[k] * 4;   // replaced by the unified level buffer
-            if (k >= 1) b += M2 * round_up(P.Hy[k] + Bk, 8) * 4 + M2 * P.Hy[k] * 4 + 128;
+            if (k >= 1) b += (M2 * round_up(P.Hy[k] + Bk, 8) + M2 * P.Hy[k]) * 2 * y_planes(mode) + 128;
             else if (d->flags & SB_FLAG_KEEP_SNR) b += M2 * ldy * 4;
             b += (P.x16_len[k] + (Bk + 256) * P.Lk_pad[k] + M2 * P.Lk_pad[k]) * by + 2 * 128;
             if (mode == kModeE4M3) b += (P.Lk_pad[k] + M2 + 2) * 4;
@@ -778,8 +779,8 @@ static int alloc_state(sb_unit *u) {
             continue;
         }
         if (k >= 1) {
-            want((void **)&L.yuni, M2 * L.ldu * 4);
-            want((void **)&L.ytmp, M2 * L.Hy * 4);
+            want((void **)&L.yuni, M2 * L.ldu * 2 * y_planes(u->mode));
+            want((void **)&L.ytmp, M2 * L.Hy * 2 * y_planes(u->mode));
         } else if (u->flags & SB_FLAG_KEEP_SNR) {
             want((void **)&L.ynew, M2 * L.ldy * 4);
         }
@@ -810,9 +811,10 @@ static int alloc_state(sb_unit *u) {
                            u->ctx->alloc_stream));
     for (auto &L : u->levels) {
         if (!u->tc) continue;
-        if (L.k >= 1) {                          // y as BF16 hi / lo rows [4M x ldu]
+        if (L.k >= 1) {                          // y as FP16 rows [2M x ldu], or BF16 hi / lo rows [4M x ldu]
             CUtensorMap hy;                      // level k - 1's interpolation operand (64 samples x 128 filters)
-            if ((rc = encode_map(&hy, L.yuni, kModeBF16, L.ldu, 2 * M2, 128))) return rc;
+            const int np = y_planes(u->mode);
+            if ((rc = encode_map(&hy, L.yuni, np == 1 ? kModeF16 : kModeBF16, L.ldu, np * M2, 128))) return rc;
             if ((rc = upload_map(u, hy, &L.mapY, false))) return rc;
         }
         if (L.Lk_pad == 0) continue;
@@ -1526,7 +1528,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     a.rows = M2;
                     a.n = (int32_t)L.Hy;
                     a.off = (int32_t)Bk;
-                    a.elem16 = 1;
+                    a.elem16 = y_planes(u->mode);
                     yshift1.push_back(a);
                     max_hy = std::max<int>(max_hy, (int)L.Hy);
                     if (!direct) {
@@ -1538,7 +1540,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                         bt.rows = M2;
                         bt.n = (int32_t)L.Hy;
                         bt.off = 0;
-                        bt.elem16 = 1;
+                        bt.elem16 = y_planes(u->mode);
                         yshift2.push_back(bt);
                     }
                 }

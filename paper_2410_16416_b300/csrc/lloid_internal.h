@@ -84,7 +84,7 @@ struct CopyTask {
     int32_t rows;
     int32_t n;           // columns to copy
     int32_t off;         // first virtual column
-    int32_t elem16;      // 1: 16-bit elements, rows r and r + rows (the hi and lo halves) both copied
+    int32_t elem16;      // 0: FP32 elements; p > 0: 16-bit elements in p planes (rows r + i rows, i < p)
     int32_t pad;
 };
 
@@ -159,6 +159,11 @@ struct TrigOut {
 constexpr int kTcM = 128;   // MMA M (rows of the A operand per tile)
 constexpr int kModeF16 = 0, kModeBF16 = 1, kModeE4M3 = 2;   // tensor-core operand modes
 constexpr int kTcN = 256;   // MMA N (columns of the accumulator per tile)
+// Planes of the stored per-level SNR y_k (levels k >= 1) in the tensor-core modes: BF16 mode keeps
+// y as one FP16 plane (11-bit significand; |y| is an SNR partial, far inside FP16's range); FP16
+// mode keeps BF16 hi + lo planes (about 16 significant bits) for its smaller error; E4M3 mode keeps
+// BF16 hi + lo too, since its stored y carries the finer level's row scale (1 / ~5e-4), beyond FP16.
+__host__ __device__ constexpr int y_planes(int mode) { return mode == kModeBF16 ? 1 : 2; }
 
 struct HalfConvTask {       // dst[i] = narrow(src[i]), i < n (E4M3: scaled by 448 / absmax)
     const float *src;
@@ -243,7 +248,7 @@ struct WinFinTask {
 };
 
 size_t tc_fir_smem_bytes(int kpad_max, int mode);
-size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk);
+size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk, int np);
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s);
