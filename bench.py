@@ -88,12 +88,14 @@ def algorithmic_model(bank, units: int, B_s: float, precision: str = "fp32"):
     2 in the 16-bit modes, 1 in E4M3).  FP32 mode: SNR series are FP32, each
     level's is written once and read once by the interpolation stage.  16-bit
     and 8-bit modes: mixing and interpolation are one stage ("mix"); each level
-    k >= 1 writes its y once and the next finer level reads it once (4 bytes per
-    sample, BF16 hi + lo); the top level writes only per-window partial maxima
-    (two 24-byte records per template and 128 samples).  Interpolation FLOPs are
+    k >= 1 writes its y once and the next finer level reads it once (2 bytes per
+    sample, one FP16 plane, in BF16 and E4M3 modes; 4 bytes, BF16 hi + lo, in
+    FP16 mode); the top level writes only per-window partial maxima (two 24-byte
+    records per template and 128 samples).  Interpolation FLOPs are
     the halfband filter's own (about 17 per output), however it is executed."""
     w = {"fp32": 4.0, "bf16": 2.0, "fp16": 2.0, "fp8": 1.0}[precision]
     fused = precision != "fp32"
+    yb = 4.0 if precision == "fp16" else 2.0                   # bytes per stored y sample
     f0 = bank.top_rate_hz
     M2 = 2 * bank.n_templates
     levels = {}
@@ -113,7 +115,7 @@ def algorithmic_model(bank, units: int, B_s: float, precision: str = "fp32"):
         N = B_s * f0 / 2 ** k
         fl["mix"] += 2.0 * M2 * Lk * N
         if fused:
-            by["mix"] += w * (M2 * Lk + Lk * N) + (8.0 * M2 * N if k >= 1 else 0.0)
+            by["mix"] += w * (M2 * Lk + Lk * N) + (2 * yb * M2 * N if k >= 1 else 0.0)
         else:
             by["mix"] += w * (M2 * Lk + Lk * N) + 4.0 * M2 * N * (2 if k < kmax else 1)
     if fused:

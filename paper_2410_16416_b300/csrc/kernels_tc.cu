@@ -268,7 +268,8 @@ struct UGeo {
 };
 constexpr int kUVariants = 16;                           // (parity, offset 0..7)
 // operand table: BF16 hi / lo terms of the 16 variants of the 64-wide blocks, then of the 128-wide
-// blocks; then the same two parts as FP16 hi / lo terms (for the one-plane FP16 y)
+// blocks; then the same two parts as FP16 hi / lo terms (one-plane FP16 y, BF16 mode); then FP16
+// hi / lo terms of U / kE4StoreScale (E4M3 mode)
 constexpr size_t kUTab128 = (size_t)kUVariants * UGeo<64>::kVarBytes;
 constexpr size_t kUTabPart = kUTab128 + (size_t)kUVariants * UGeo<128>::kVarBytes;
 constexpr int kMixStPlane = 32 * 64;                     // store staging per plane: 32 filters x 32 samples
@@ -276,7 +277,7 @@ constexpr int kMixThreads = 384;
 constexpr int kMixMaxWin = 6;
 constexpr size_t kMixSmemMax = 227 * 1024;               // dynamic shared memory per CTA (opt-in maximum)
 
-size_t tc_interp_table_bytes() { return 2 * kUTabPart; }
+size_t tc_interp_table_bytes() { return 3 * kUTabPart; }
 
 // U for variant (par, rem): output c of a block takes coarser sample
 // i = rem + 16 + ((c + par) >> 1) (even c + par: weight 1 = 2 g[0]) or the
@@ -284,7 +285,7 @@ size_t tc_interp_table_bytes() { return 2 * kUTabPart; }
 // lo terms (BF16, or FP16 with f16) in the no-swizzle K-major layout: element
 // (c, i) at byte ((c / 8) * (K / 8) + i / 8) * 128 + (c % 8) * 16 + (i % 8) * 2.
 template <int UB>
-static void interp_table_part(const Halfband &g, uint16_t *out, bool f16) {
+static void interp_table_part(const Halfband &g, uint16_t *out, bool f16, float gain) {
     using G = UGeo<UB>;
     auto bf16_bits = [](float v) {                       // round to nearest even
         uint32_t u;
@@ -327,7 +328,7 @@ static void interp_table_part(const Halfband &g, uint16_t *out, bool f16) {
         for (int c = 0; c < G::kBlk; ++c)
             for (int i = 0; i < G::kK; ++i) {
                 const size_t at = ((size_t)(c / 8) * (G::kK / 8) + i / 8) * 64 + (c % 8) * 8 + (i % 8);
-                const float u = U[(size_t)c * G::kK + i];
+                const float u = U[(size_t)c * G::kK + i] * gain;
                 const uint16_t h = bits(u);
                 hi[at] = h;
                 lo[at] = bits(u - val(h));
@@ -337,9 +338,10 @@ static void interp_table_part(const Halfband &g, uint16_t *out, bool f16) {
 
 void tc_interp_table(const Halfband &g, void *host_out) {
     uint8_t *out = static_cast<uint8_t *>(host_out);
-    for (int f = 0; f < 2; ++f) {
-        interp_table_part<64>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart), f == 1);
-        interp_table_part<128>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart + kUTab128), f == 1);
+    for (int f = 0; f < 3; ++f) {
+        const float gain = f == 2 ? 1.0f / kE4StoreScale : 1.0f;      // a power of two: exact
+        interp_table_part<64>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart), f >= 1, gain);
+        interp_table_part<128>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart + kUTab128), f >= 1, gain);
     }
 }
 
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     constexpr int NP = y_planes(MODE);                   // 1: FP16 y; 2: BF16 hi + lo
     constexpr int kWinBytes = NP * kWinHalfBytes;
     using G = UGeo<UB>;
-    utab += (NP == 1 ? kUTabPart : 0) + (UB == 128 ? kUTab128 : 0);
+    utab += (NP == 2 ? 0 : MODE == kModeE4M3 ? 2 * kUTabPart : kUTabPart) + (UB == 128 ? kUTab128 : 0);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -617,6 +619,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
             if (MODE == kModeE4M3 && row_ok) {
                 if (t.rscale) rsc = t.rscale[a];
                 if (t.rsc_next) inv_next = 1.0f / t.rsc_next[a];
+                inv_next *= kE4StoreScale;                   // the finer level's table carries the inverse
             }
             const bool top = t.part != nullptr;
             SegBest b0{-1.0f, 0.0f, 0.0f, -1}, b1{-1.0f, 0.0f, 0.0f, -1};

@@ -129,7 +129,7 @@ struct LevelDev {
     CUtensorMap *mapY = nullptr;     // yuni as the finer level's interpolation operand (box 64 x 128, 128-byte swizzle)
     // 16-bit modes, levels k >= 1: SNR rows [history (Hy) | new (B_k)] in one buffer, so the
     // next finer level's epilogue can stage a row segment with one TMA load
-    float *yuni = nullptr;    // FP32 mode: unused; BF16 mode: y as FP16 rows [0, 2M); FP16 / E4M3 modes: y as
+    float *yuni = nullptr;    // FP32 mode: unused; BF16 / E4M3 modes: y as FP16 rows [0, 2M); FP16 mode: y as
                               // BF16 hi rows [0, 2M), lo rows [2M, 4M); ld ldu
     int64_t ldu = 0;
     float *ytmp = nullptr;    // history shift staging, same layout with ld Hy
@@ -699,7 +699,7 @@ static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d, const std::ve
                 for (int s : L.slices)
                     for (int l = 0; l < u->slices[s].L; ++l)
                         m = std::max(m, std::fabs(d->slices[s].mixing[a * u->slices[s].L + l]) * so);
-                rs[a] = m > 0.0 ? (float)(m / 448.0) : 1.0f;
+                rs[a] = m > 0.0 ? std::max((float)(m / 448.0), kE4RowScaleMin) : 1.0f;
             }
             for (int s : L.slices)
                 for (int l = 0; l < u->slices[s].L; ++l) cs[u->slices[s].o_col16 + l] = vscale[s][l] / so;

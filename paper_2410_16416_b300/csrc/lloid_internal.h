@@ -159,11 +159,15 @@ struct TrigOut {
 constexpr int kTcM = 128;   // MMA M (rows of the A operand per tile)
 constexpr int kModeF16 = 0, kModeBF16 = 1, kModeE4M3 = 2;   // tensor-core operand modes
 constexpr int kTcN = 256;   // MMA N (columns of the accumulator per tile)
-// Planes of the stored per-level SNR y_k (levels k >= 1) in the tensor-core modes: BF16 mode keeps
-// y as one FP16 plane (11-bit significand; |y| is an SNR partial, far inside FP16's range); FP16
-// mode keeps BF16 hi + lo planes (about 16 significant bits) for its smaller error; E4M3 mode keeps
-// BF16 hi + lo too, since its stored y carries the finer level's row scale (1 / ~5e-4), beyond FP16.
-__host__ __device__ constexpr int y_planes(int mode) { return mode == kModeBF16 ? 1 : 2; }
+// Planes of the stored per-level SNR y_k (levels k >= 1) in the tensor-core modes: BF16 and E4M3
+// modes keep y as one FP16 plane (11-bit significand; |y| is an SNR partial, far inside FP16's
+// range); FP16 mode keeps BF16 hi + lo planes (about 16 significant bits) for its smaller error.
+// E4M3 stores y in the finer level's row-scale units (1 / rs, rs ~ 5e-4) times kE4StoreScale, and
+// its interpolation table carries 1 / kE4StoreScale, so the stored values stay near the SNR's own.
+__host__ __device__ constexpr int y_planes(int mode) { return mode == kModeF16 ? 2 : 1; }
+constexpr float kE4StoreScale = 1.0f / 2048.0f;
+// E4M3 mixing-row scales are at least this, so |y| / (rs * 2048) < 65504 for |y| < 1000
+constexpr float kE4RowScaleMin = 1.0f / 131072.0f;
 
 struct HalfConvTask {       // dst[i] = narrow(src[i]), i < n (E4M3: scaled by 448 / absmax)
     const float *src;
