@@ -56,6 +56,8 @@ extern "C" {
 /* ---- trigger flags --------------------------------------------------- */
 #define SB_TRIG_REFINED 1   /* SNR recomputed in FP32 around the peak           */
 #define SB_TRIG_SUBSAMPLE 2 /* snr_peak / dt_peak hold the sub-sample peak       */
+#define SB_TRIG_XI2 4       /* xi2 holds the signal-consistency value           */
+#define SB_XI2_HALF 16      /* xi^2 lags j = -16 .. 16 top-rate samples         */
 
 /* One time slice of an SVD bank (Sec. II.A "time slices ... SVD").
  * basis : [n_basis * n_taps] row-major; row l is v_l[q], q = 0 is the tap
@@ -81,7 +83,15 @@ typedef struct sb_slice {
  * refine_threshold: in SB_BF16/SB_FP16/SB_FP8 modes, window maxima above this
  *   are recomputed in FP32 (0 disables refinement).
  * window_s: trigger window length (windows start at multiples of window_s*f0).
- * max_push_samples: the largest n_samples a filter_push will pass (top rate). */
+ * max_push_samples: the largest n_samples a filter_push will pass (top rate).
+ * autocorr: NULL, or [n_templates][2 SB_XI2_HALF + 1][2] (re, im) doubles, the
+ *   normalised complex autocorrelation of each template at f0, lag j at index
+ *   j + SB_XI2_HALF: R_i[j] = sum_q h_i[q] conj(h_i[q - j]) / sum_q |h_i[q]|^2
+ *   with h_i = h_{2i} + i h_{2i+1}.  Given, every trigger whose lags n* - 16 ..
+ *   n* + 16 are computed in FP32 in one pass carries the signal-consistency
+ *   value of Sec. II.A (GstLAL's xi^2, a reading):
+ *     xi2 = sum_j |rho[n* + j] - rho[n*] R_i[j]|^2 / sum_j (2 - 2 |R_i[j]|^2).
+ *   Copied before return; |R_i[0] - 1| must be <= 1e-6 (SB_EINVAL otherwise). */
 typedef struct sb_desc {
     int32_t n_templates;
     int32_t n_slices;
@@ -94,6 +104,7 @@ typedef struct sb_desc {
     float refine_threshold;
     double window_s;
     int64_t max_push_samples;
+    const double *autocorr;
 } sb_desc;
 
 /* One trigger: the |rho| maximum of one template in one window (Sec. II.A).
@@ -118,7 +129,7 @@ typedef struct sb_trigger {
     float snr_peak;
     float dt_peak;
     int32_t flags;
-    int32_t reserved;
+    float xi2;      /* signal consistency (SB_TRIG_XI2 set; 0 otherwise)        */
 } sb_trigger;
 
 /* Read-only facts about a unit (for tests, benchmarks and admission). */
@@ -281,7 +292,7 @@ int sb_ctx_stage_times(sb_ctx *ctx, double *ms, int64_t *launches, int32_t n_sta
  * |rho| > threshold.  out_count: device int32[2] = {triggers, overflow flag},
  * zeroed by the call; at most cap triggers are stored.  Work is queued on
  * stream (a cudaStream_t; NULL = legacy default stream) and nothing blocks.
- * Scratch: a fixed device array of 2^18 partial records (8 MiB) that every
+ * Scratch: a fixed device array of 2^18 partial records (10 MiB) that every
  * GPU loading this library holds until the process exits; a call needs
  * 2 * M * ceil(n_samples / 256) records and returns SB_EINVAL (see
  * sb_last_error) beyond that, or when window_len < 256.  The first call on a

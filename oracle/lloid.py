@@ -164,3 +164,46 @@ def subsample_peak(x: np.ndarray, i: int, n: int):
     dt = 0.5 * (ym - yp) / den
     return float(np.sqrt(y0 - 0.25 * (ym - yp) * dt)), dt
 
+
+
+def autocorrelation(h: np.ndarray, J: int) -> np.ndarray:
+    """R_i[j], j = -J..J: the normalised complex autocorrelation of template i.
+
+    Sec. II.A computes the signal-consistency value xi^2 for every trigger,
+    following the GstLAL method it cites.  Reading: with h_i = h_{2i} + i h_{2i+1}
+    (the cosine and sine phases at f0),
+        R_i[j] = sum_q h_i[q] conj(h_i[q - j]) / sum_q |h_i[q]|^2,
+    so R_i[0] = 1, R_i[-j] = conj(R_i[j]), and in white unit-variance noise
+    E[rho_i[n + j] conj(rho_i[n])] = 2 R_i[j].  A matched signal of phase phi
+    gives rho_i[n_c + j] ~ A e^{i phi} R_i[j].  Returns [M, 2J + 1] complex.
+    """
+    M, N = h.shape[0] // 2, h.shape[1]
+    out = np.empty((M, 2 * J + 1), dtype=np.complex128)
+    for i in range(M):
+        c = h[2 * i].astype(np.float64) + 1j * h[2 * i + 1].astype(np.float64)
+        norm = float(np.sum(np.abs(c) ** 2))
+        for j in range(-J, J + 1):
+            if j >= 0:
+                s = np.sum(c[j:] * np.conj(c[:N - j]))
+            else:
+                s = np.sum(c[:N + j] * np.conj(c[-j:]))
+            out[i, j + J] = s / norm
+    return out
+
+
+def xi2(x: np.ndarray, R: np.ndarray, i: int, n: int, J: int):
+    """xi^2 of template i at sample n (Sec. II.A; reading of the cited method).
+
+        xi^2 = sum_{|j|<=J} |rho[n + j] - rho[n] R[j]|^2 / sum_{|j|<=J} (2 - 2 |R[j]|^2)
+
+    The denominator is the numerator's expectation in white noise, so xi^2 is
+    about 1 for noise and near 0 for a signal that matches the template.
+    Returns None unless all of n - J .. n + J lie inside the series.
+    """
+    if n - J < 0 or n + J >= x.shape[1]:
+        return None
+    z = x[2 * i, n - J:n + J + 1] + 1j * x[2 * i + 1, n - J:n + J + 1]
+    r = R[i] if R.ndim == 2 else R
+    num = float(np.sum(np.abs(z - z[J] * r) ** 2))
+    den = float(np.sum(2.0 - 2.0 * np.abs(r) ** 2))
+    return num / den

@@ -21,6 +21,8 @@ PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3}
 SB_FLAG_KEEP_SNR = 1
 SB_TRIG_REFINED = 1
 SB_TRIG_SUBSAMPLE = 2
+SB_TRIG_XI2 = 4
+SB_XI2_HALF = 16
 
 
 class SbSlice(C.Structure):
@@ -33,13 +35,14 @@ class SbDesc(C.Structure):
     _fields_ = [("n_templates", C.c_int32), ("n_slices", C.c_int32), ("top_rate_hz", C.c_double),
                 ("slices", C.POINTER(SbSlice)), ("template_ids", C.POINTER(C.c_int64)),
                 ("precision", C.c_int32), ("flags", C.c_int32), ("threshold", C.c_float),
-                ("refine_threshold", C.c_float), ("window_s", C.c_double), ("max_push_samples", C.c_int64)]
+                ("refine_threshold", C.c_float), ("window_s", C.c_double), ("max_push_samples", C.c_int64),
+                ("autocorr", C.POINTER(C.c_double))]
 
 
 class SbTrigger(C.Structure):
     _fields_ = [("unit", C.c_int64), ("template_id", C.c_int64), ("sample", C.c_int64), ("window", C.c_int64),
                 ("snr", C.c_float), ("phase", C.c_float), ("snr_peak", C.c_float), ("dt_peak", C.c_float),
-                ("flags", C.c_int32), ("reserved", C.c_int32)]
+                ("flags", C.c_int32), ("xi2", C.c_float)]
 
 
 class SbUnitInfo(C.Structure):
@@ -59,7 +62,7 @@ STAGES = ["history", "strain", "decimate", "fir", "upsample", "mix", "trigger", 
 
 TRIGGER_DTYPE = np.dtype([("unit", "<i8"), ("template_id", "<i8"), ("sample", "<i8"), ("window", "<i8"),
                           ("snr", "<f4"), ("phase", "<f4"), ("snr_peak", "<f4"), ("dt_peak", "<f4"),
-                          ("flags", "<i4"), ("reserved", "<i4")])
+                          ("flags", "<i4"), ("xi2", "<f4")])
 assert TRIGGER_DTYPE.itemsize == C.sizeof(SbTrigger)
 
 # name -> (restype, argtypes): every entry point declared in include/lloid.h
@@ -128,8 +131,9 @@ def _ptr(a) -> int:
 
 def make_desc(bank, precision: str = "fp32", threshold: float = 6.0, refine_threshold: float = 0.0,
               window_s: float = 1.0, max_push_samples: int = 0, keep_snr: bool = False,
-              template_ids: Optional[Sequence[int]] = None):
-    """(SbDesc, keep-alive list) for a bank; the arrays must outlive the C call."""
+              template_ids: Optional[Sequence[int]] = None, autocorr=None):
+    """(SbDesc, keep-alive list) for a bank; the arrays must outlive the C call.
+    autocorr: [M, 2 SB_XI2_HALF + 1] complex (or the bank's `autocorr` attribute) for xi^2."""
     keep = []
     sl = (SbSlice * len(bank.slices))()
     for i, s in enumerate(bank.slices):
@@ -143,10 +147,20 @@ def make_desc(bank, precision: str = "fp32", threshold: float = 6.0, refine_thre
     if template_ids is not None:
         ids = np.ascontiguousarray(template_ids, dtype=np.int64)
         keep.append(ids)
+    if autocorr is None:
+        autocorr = getattr(bank, "autocorr", None)
+    ac = None
+    if autocorr is not None:
+        a = np.asarray(autocorr, dtype=np.complex128)
+        if a.shape != (int(bank.n_templates), 2 * SB_XI2_HALF + 1):
+            raise ValueError(f"autocorr must be [{bank.n_templates}, {2 * SB_XI2_HALF + 1}] complex")
+        ac = np.ascontiguousarray(a).view(np.float64)
+        keep.append(ac)
     d = SbDesc(int(bank.n_templates), len(bank.slices), float(bank.top_rate_hz), sl,
                ids.ctypes.data_as(C.POINTER(C.c_int64)) if ids is not None else None,
                PRECISION[precision], SB_FLAG_KEEP_SNR if keep_snr else 0, float(threshold),
-               float(refine_threshold), float(window_s), int(max_push_samples))
+               float(refine_threshold), float(window_s), int(max_push_samples),
+               ac.ctypes.data_as(C.POINTER(C.c_double)) if ac is not None else None)
     return d, keep
 
 

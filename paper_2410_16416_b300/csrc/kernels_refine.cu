@@ -81,13 +81,14 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
         const int64_t w = rec.n / u.win_len;
         const int64_t half0 = u.first_n + (int64_t)kRefTile * tt + 128 * h;
         int64_t lo[kRefMaxLevels], hi[kRefMaxLevels];
-        // search range [slo, shi]; computed one sample wider on each side (the sub-sample peak's
-        // neighbours), inside the samples this push produces and n >= 0
+        // search range [slo, shi]; computed kXiJ samples wider on each side (the sub-sample peak's
+        // neighbours and the xi^2 lags), inside the samples this push produces and n >= 0.  The
+        // strain history reaches 128 samples below the push at every level, which covers it.
         const int64_t slo = max(rec.n - kRefR, max(half0, w * u.win_len));
         const int64_t shi = min(min(rec.n + kRefR, half0 + 127), min((w + 1) * u.win_len, u.first_n + u.B) - 1);
         if (shi < slo) continue;                        // block-uniform
-        lo[0] = max(slo - 1, (int64_t)0);
-        hi[0] = min(shi + 1, u.first_n + u.B - 1);
+        lo[0] = max(slo - kXiJ, (int64_t)0);
+        hi[0] = min(shi + kXiJ, u.first_n + u.B - 1);
         for (int k = 0; k < u.kmax; ++k) {
             lo[k + 1] = ceil_div2(lo[k] - (2 * kHalfK - 1));
             hi[k + 1] = floor_div2(hi[k] + (2 * kHalfK - 1));
@@ -178,17 +179,17 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
             __syncthreads();
             cur ^= 1;
         }
-        // z[cur] holds level 0 over [lo_0, hi_0] (<= 2R + 3 samples): maximum over [slo, shi], first on
-        // ties, then the sub-sample peak from its neighbours
+        // z[cur] holds level 0 over [lo_0, hi_0] (<= 2R + 1 + 2 kXiJ samples): maximum over
+        // [slo, shi] (<= 2R + 1 <= 32 columns, lane l takes column c0 + l), first on ties; then the
+        // sub-sample peak from its neighbours and xi^2 over the lags around it
         if (warp == 0) {
+            const float *zc = z[cur][0], *zs = z[cur][1];
             const int len0 = (int)(hi[0] - lo[0] + 1), c0 = (int)(slo - lo[0]), c1 = (int)(shi - lo[0]);
-            const float m2l = lane < len0 ? fmaf(z[cur][1][lane], z[cur][1][lane], z[cur][0][lane] * z[cur][0][lane])
-                                          : -1.0f;
             float best = -1.0f;
             int bc = -1;
-            if (lane >= c0 && lane <= c1) {
-                best = m2l;
-                bc = lane;
+            if (c0 + lane <= c1) {
+                bc = c0 + lane;
+                best = fmaf(zs[bc], zs[bc], zc[bc] * zc[bc]);
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
@@ -199,17 +200,43 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
                     bc = oc;
                 }
             }
-            const float ym = __shfl_sync(0xffffffffu, m2l, max(bc - 1, 0));
-            const float yp = __shfl_sync(0xffffffffu, m2l, min(bc + 1, 31));
+            // xi^2 (every lane holds bc): all lags inside the computed range and n >= 0
+            float xi = 0.0f;
+            const bool has_xi = u.acorr && bc >= kXiJ && bc + kXiJ < len0 && lo[0] + bc - kXiJ >= 0;
+            if (has_xi) {
+                const float z0c = zc[bc], z0s = zs[bc];
+                const float2 *Ri = u.acorr + (int64_t)i * kXiLags;
+                float num = 0.0f, den = 0.0f;
+                for (int j = lane; j < kXiLags; j += 32) {
+                    const float2 r = Ri[j];
+                    const float ec = zc[bc - kXiJ + j] - (z0c * r.x - z0s * r.y);
+                    const float es = zs[bc - kXiJ + j] - (z0c * r.y + z0s * r.x);
+                    num += fmaf(es, es, ec * ec);
+                    den += 2.0f - 2.0f * fmaf(r.y, r.y, r.x * r.x);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    num += __shfl_xor_sync(0xffffffffu, num, off);
+                    den += __shfl_xor_sync(0xffffffffu, den, off);
+                }
+                xi = num / den;
+            }
             if (lane == 0 && bc >= 0) {
                 rec.mag2 = best;
-                rec.re = z[cur][0][bc];
-                rec.im = z[cur][1][bc];
+                rec.re = zc[bc];
+                rec.im = zs[bc];
                 rec.n = lo[0] + bc;
                 rec.flags = SB_TRIG_REFINED_BIT;
-                rec.pk = rec.dt = 0.0f;
-                if (bc >= 1 && bc + 1 < len0 && subsample_peak(ym, best, yp, rec.pk, rec.dt))
-                    rec.flags |= SB_TRIG_SUBSAMPLE_BIT;
+                rec.pk = rec.dt = rec.xi2 = 0.0f;
+                if (bc >= 1 && bc + 1 < len0) {
+                    const float ym = fmaf(zs[bc - 1], zs[bc - 1], zc[bc - 1] * zc[bc - 1]);
+                    const float yp = fmaf(zs[bc + 1], zs[bc + 1], zc[bc + 1] * zc[bc + 1]);
+                    if (subsample_peak(ym, best, yp, rec.pk, rec.dt)) rec.flags |= SB_TRIG_SUBSAMPLE_BIT;
+                }
+                if (has_xi) {
+                    rec.xi2 = xi;
+                    rec.flags |= SB_TRIG_XI2_BIT;
+                }
                 u.part[idx] = rec;
             }
         }

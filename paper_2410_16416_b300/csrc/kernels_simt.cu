@@ -164,6 +164,29 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
         const int64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
         if (better(ob, on, best, bn)) { best = ob; bn = on; }
     }
+    // xi^2 over lags -kXiJ .. kXiJ when they all lie in this push (every lane holds bn)
+    float xi = 0.0f;
+    bool has_xi = false;
+    if (t.acorr && bn != INT64_MAX && bn - kXiJ >= 0 && bn - t.first_n - kXiJ >= 0 && bn - t.first_n + kXiJ < t.n) {
+        const int64_t p = bn - t.first_n;
+        const float z0c = xc[p], z0s = xs[p];
+        const float2 *Ri = t.acorr + (int64_t)i * kXiLags;
+        float num = 0.0f, den = 0.0f;
+        for (int j = lane; j < kXiLags; j += 32) {
+            const float2 r = Ri[j];
+            const float ec = xc[p - kXiJ + j] - (z0c * r.x - z0s * r.y);
+            const float es = xs[p - kXiJ + j] - (z0c * r.y + z0s * r.x);
+            num += fmaf(es, es, ec * ec);
+            den += 2.0f - 2.0f * fmaf(r.y, r.y, r.x * r.x);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, off);
+            den += __shfl_xor_sync(0xffffffffu, den, off);
+        }
+        xi = num / den;
+        has_xi = true;
+    }
     if (lane != 0) return;
     float re = 0.0f, im = 0.0f, pk = 0.0f, dt = 0.0f;
     int fl = 0;
@@ -176,11 +199,12 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
             const float yp = fmaf(xs[p + 1], xs[p + 1], xc[p + 1] * xc[p + 1]);
             if (subsample_peak(ym, best, yp, pk, dt)) fl = SB_TRIG_SUBSAMPLE_BIT;
         }
+        if (has_xi) fl |= SB_TRIG_XI2_BIT;
     }
     if (s == 0) {                          // the open window carried over from the last push
         const WinState st = t.state_in[i];
         if (st.mag2 >= 0.0f && !(best > st.mag2)) {
-            best = st.mag2; bn = st.n; re = st.re; im = st.im; pk = st.pk; dt = st.dt; fl = st.flags;
+            best = st.mag2; bn = st.n; re = st.re; im = st.im; pk = st.pk; dt = st.dt; xi = st.xi2; fl = st.flags;
         }
     }
     const bool complete = (w + 1) * t.win_len <= end_abs;
@@ -198,7 +222,7 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
                 r.snr_peak = (fl & SB_TRIG_SUBSAMPLE_BIT) ? pk : r.snr;
                 r.dt_peak = (fl & SB_TRIG_SUBSAMPLE_BIT) ? dt : 0.0f;
                 r.flags = fl;
-                r.reserved = 0;
+                r.xi2 = (fl & SB_TRIG_XI2_BIT) ? xi : 0.0f;
                 out.buf[slot] = r;
             } else {
                 atomicExch(out.count + 1, 1);
@@ -207,8 +231,8 @@ __global__ void __launch_bounds__(256) window_max_kernel(const WinTask *__restri
     }
     if (s == t.n_seg - 1) {
         WinState ns;
-        if (complete) { ns.mag2 = -1.0f; ns.re = ns.im = ns.pk = ns.dt = 0.0f; ns.n = -1; ns.flags = 0; }
-        else { ns.mag2 = best; ns.re = re; ns.im = im; ns.pk = pk; ns.dt = dt; ns.n = bn; ns.flags = fl; }
+        if (complete) { ns.mag2 = -1.0f; ns.re = ns.im = ns.pk = ns.dt = ns.xi2 = 0.0f; ns.n = -1; ns.flags = 0; }
+        else { ns.mag2 = best; ns.re = re; ns.im = im; ns.pk = pk; ns.dt = dt; ns.xi2 = xi; ns.n = bn; ns.flags = fl; }
         t.state_out[i] = ns;
     }
 }
@@ -241,14 +265,14 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
     const int64_t hi = min((w + 1) * t.win_len, t.end_abs) - t.first_n;
     const int r0 = (int)(lo / 128) * 2, r1 = (int)((hi - 1) / 128) * 2 + 2;
     const WinPart *rec = t.part + (int64_t)i * t.n_rec;
-    float best = -1.0f, re = 0.0f, im = 0.0f, pk = 0.0f, dt = 0.0f;
+    float best = -1.0f, re = 0.0f, im = 0.0f, pk = 0.0f, dt = 0.0f, xi = 0.0f;
     int64_t bn = INT64_MAX;
     int fl = 0;
     for (int r = r0 + lane; r < r1; r += 32) {
         const WinPart p = rec[r];
         if (p.mag2 < 0.0f || p.n / t.win_len != w) continue;
         if (p.mag2 > best || (p.mag2 == best && p.n < bn)) {
-            best = p.mag2; bn = p.n; re = p.re; im = p.im; pk = p.pk; dt = p.dt; fl = p.flags;
+            best = p.mag2; bn = p.n; re = p.re; im = p.im; pk = p.pk; dt = p.dt; xi = p.xi2; fl = p.flags;
         }
     }
 #pragma unroll
@@ -259,14 +283,17 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
         const float oim = __shfl_xor_sync(0xffffffffu, im, off);
         const float opk = __shfl_xor_sync(0xffffffffu, pk, off);
         const float odt = __shfl_xor_sync(0xffffffffu, dt, off);
+        const float oxi = __shfl_xor_sync(0xffffffffu, xi, off);
         const int ofl = __shfl_xor_sync(0xffffffffu, fl, off);
-        if (ob > best || (ob == best && on < bn)) { best = ob; bn = on; re = ore; im = oim; pk = opk; dt = odt; fl = ofl; }
+        if (ob > best || (ob == best && on < bn)) {
+            best = ob; bn = on; re = ore; im = oim; pk = opk; dt = odt; xi = oxi; fl = ofl;
+        }
     }
     if (lane != 0) return;
     if (s == 0) {                          // the window left open by the previous push (earlier samples)
         const WinState st = t.state_in[i];
         if (st.mag2 >= 0.0f && !(best > st.mag2)) {
-            best = st.mag2; bn = st.n; re = st.re; im = st.im; pk = st.pk; dt = st.dt; fl = st.flags;
+            best = st.mag2; bn = st.n; re = st.re; im = st.im; pk = st.pk; dt = st.dt; xi = st.xi2; fl = st.flags;
         }
     }
     const bool complete = (w + 1) * t.win_len <= t.end_abs;
@@ -283,7 +310,7 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
             r.snr_peak = (fl & SB_TRIG_SUBSAMPLE_BIT) ? pk : r.snr;
             r.dt_peak = (fl & SB_TRIG_SUBSAMPLE_BIT) ? dt : 0.0f;
             r.flags = fl;
-            r.reserved = 0;
+            r.xi2 = (fl & SB_TRIG_XI2_BIT) ? xi : 0.0f;
             out.buf[slot] = r;
         } else {
             atomicExch(out.count + 1, 1);
@@ -292,9 +319,9 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
     if (s == t.n_win - 1) {
         WinState ns;
         if (complete || bn == INT64_MAX) {
-            ns.mag2 = -1.0f; ns.re = ns.im = ns.pk = ns.dt = 0.0f; ns.n = -1; ns.flags = 0;
+            ns.mag2 = -1.0f; ns.re = ns.im = ns.pk = ns.dt = ns.xi2 = 0.0f; ns.n = -1; ns.flags = 0;
         } else {
-            ns.mag2 = best; ns.re = re; ns.im = im; ns.pk = pk; ns.dt = dt; ns.n = bn; ns.flags = fl;
+            ns.mag2 = best; ns.re = re; ns.im = im; ns.pk = pk; ns.dt = dt; ns.xi2 = xi; ns.n = bn; ns.flags = fl;
         }
         t.state_out[i] = ns;
     }

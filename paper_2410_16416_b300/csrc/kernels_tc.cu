@@ -765,8 +765,8 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                 seg_merge_pair(b1);
                 if ((a & 1) == 0 && row_ok) {
                     WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (m.tt * 2 + h) * 2;
-                    base[0] = WinPart{b0.mag2, b0.re, b0.im, 0.0f, 0.0f, 0, b0.n};
-                    base[1] = WinPart{b1.mag2, b1.re, b1.im, 0.0f, 0.0f, 0, b1.n};
+                    base[0] = WinPart{b0.mag2, b0.re, b0.im, 0.0f, 0.0f, 0.0f, 0, b0.n};
+                    base[1] = WinPart{b1.mag2, b1.re, b1.im, 0.0f, 0.0f, 0.0f, 0, b1.n};
                     if (t.wmax) {                    // window maxima for the refinement's candidate rule
                         uint32_t *wm = t.wmax + (int64_t)(a >> 1) * t.n_wslot - t.win0;
                         if (b0.mag2 > t.thr2) atomicMax(wm + b0.n / t.win_len, __float_as_uint(b0.mag2));

@@ -230,6 +230,7 @@ struct sb_unit {
     WinPart *part = nullptr;       // 16-bit modes: top-level partial window maxima (scratch)
     int64_t part_rec_max = 0;
     int64_t *tids = nullptr;
+    float2 *acorr = nullptr;       // [M][kXiLags] template autocorrelation (null: no xi^2)
     std::vector<void *> allocs;
     int64_t bytes = 0;
     int64_t flops_per_s = 0;
@@ -805,7 +806,7 @@ static int alloc_state(sb_unit *u) {
         off += round_up(p.bytes, 256);
     }
     std::vector<WinState> ws(u->M);
-    for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = w.pk = w.dt = 0.0f; w.flags = 0; w.n = -1; }
+    for (auto &w : ws) { w.mag2 = -1.0f; w.re = w.im = w.pk = w.dt = w.xi2 = 0.0f; w.flags = 0; w.n = -1; }
     for (int b = 0; b < 2; ++b)
         CK(cudaMemcpyAsync(u->wstate[b], ws.data(), u->M * sizeof(WinState), cudaMemcpyHostToDevice,
                            u->ctx->alloc_stream));
@@ -959,6 +960,20 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
     if ((rc = dev_alloc_w(u, (void **)&u->tids, u->M * 8))) return cleanup(rc);
     if (cudaMemcpy(u->tids, ids.data(), u->M * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         return cleanup(fail(SB_ECUDA, "template id upload"));
+    if (d->autocorr) {                        // xi^2 lag profiles, FP32 on the device
+        std::vector<float2> ac((size_t)u->M * kXiLags);
+        for (int i = 0; i < u->M; ++i)
+            for (int j = 0; j < kXiLags; ++j) {
+                const double re = d->autocorr[((size_t)i * kXiLags + j) * 2], im = d->autocorr[((size_t)i * kXiLags + j) * 2 + 1];
+                if (!std::isfinite(re) || !std::isfinite(im) || (j == kXiJ && std::fabs(re - 1.0) + std::fabs(im) > 1e-6))
+                    return cleanup(fail(SB_EINVAL, "autocorr of template " + std::to_string(i) +
+                                                       " is not finite or its lag 0 is not 1"));
+                ac[(size_t)i * kXiLags + j] = make_float2((float)re, (float)im);
+            }
+        if ((rc = dev_alloc_w(u, (void **)&u->acorr, ac.size() * sizeof(float2)))) return cleanup(rc);
+        if (cudaMemcpy(u->acorr, ac.data(), ac.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(SB_ECUDA, "autocorrelation upload"));
+    }
     if ((rc = alloc_state(u))) return cleanup(rc);
     {
         std::lock_guard<std::mutex> lk(c->mu);
@@ -1003,6 +1018,7 @@ extern "C" int svdbank_create_like(sb_ctx *c, sb_unit *src, int32_t detector, sb
     u->flops_per_s = src->flops_per_s;
     u->slices = src->slices;
     u->tids = src->tids;
+    u->acorr = src->acorr;
     u->levels = src->levels;
     for (auto &L : u->levels) {                  // fresh streaming state, shared weights
         L.amax = nullptr;
@@ -1630,6 +1646,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             r.n_rec = (int32_t)((B + kRefTile - 1) / kRefTile) * 4;
             r.B = (int32_t)B;
             r.n_slices = (int32_t)u->slices.size();
+            r.acorr = u->acorr;
             for (int k = 0; k <= u->kmax; ++k) {
                 LevelDev &L = u->levels[k];
                 r.lv_d[k] = L.dbuf[1 - L.dcur];
@@ -1678,6 +1695,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             w.M = u->M;
             w.n_seg = (int32_t)((end - 1) / u->win_len - start / u->win_len + 1);
             w.threshold = u->thr;
+            w.acorr = u->acorr;
             win.push_back(w);
             trig_need += (int64_t)u->M * w.n_seg;
         }

@@ -110,11 +110,15 @@ struct WinState {        // running maximum of one template in its open window
     float mag2;          // |rho|^2 (-1: empty)
     float re, im;
     float pk, dt;        // sub-sample peak |rho| and offset (valid with SB_TRIG_SUBSAMPLE_BIT)
+    float xi2;           // signal consistency (valid with SB_TRIG_XI2_BIT)
     int32_t flags;       // SB_TRIG_* bits of the maximum
     int64_t n;
 };
 constexpr int32_t SB_TRIG_REFINED_BIT = 1;
 constexpr int32_t SB_TRIG_SUBSAMPLE_BIT = 2;
+constexpr int32_t SB_TRIG_XI2_BIT = 4;
+constexpr int kXiJ = 16;                 // xi^2 lags -kXiJ .. kXiJ (SB_XI2_HALF)
+constexpr int kXiLags = 2 * kXiJ + 1;
 
 // Sub-sample peak: vertex of the parabola through |rho|^2 = ym, y0, yp at
 // n - 1, n, n + 1 when n is a local maximum: offset dt in [-1/2, 1/2] and |rho|.
@@ -129,7 +133,8 @@ __host__ __device__ __forceinline__ bool subsample_peak(float ym, float y0, floa
 struct DevTrigger {      // layout-identical to sb_trigger
     int64_t unit, template_id, sample, window;
     float snr, phase, snr_peak, dt_peak;
-    int32_t flags, reserved;
+    int32_t flags;
+    float xi2;
 };
 
 struct WinTask {
@@ -147,6 +152,7 @@ struct WinTask {
     int32_t warp_begin;  // first global warp of this task
     float threshold;
     int32_t pad;
+    const float2 *acorr; // [M][kXiLags] template autocorrelation R_i[j] at j + kXiJ; null: no xi^2
 };
 
 struct TrigOut {
@@ -200,7 +206,8 @@ struct WinPart {
     float mag2;                // |rho|^2 (-1: no valid sample)
     float re, im;
     float pk, dt;              // sub-sample peak (refined records with SB_TRIG_SUBSAMPLE_BIT)
-    int32_t flags;             // SB_TRIG_* bits (refined, sub-sample)
+    float xi2;                 // signal consistency (refined records with SB_TRIG_XI2_BIT)
+    int32_t flags;             // SB_TRIG_* bits (refined, sub-sample, xi^2)
     int64_t n;                 // absolute top-rate sample
 };
 
@@ -287,7 +294,7 @@ constexpr int kRefTile = 256;            // top-level samples per record tile (=
 constexpr int kRefR = 8;                 // refined samples on either side of a candidate maximum
 constexpr int kRefMaxLevels = 8;
 constexpr int kRefMaxSlices = 12;
-constexpr int kRefSpan = 64;             // level-k samples one candidate needs (<= 63 for R = 8)
+constexpr int kRefSpan = 64;             // level-k samples one candidate needs (<= 62 for R = 8 and 16 xi^2 lags)
 constexpr int kRefCandCap = 1 << 16;     // candidates one push refines at most
 
 struct RefUnit {                         // one unit of a push with refinement on
@@ -305,6 +312,7 @@ struct RefUnit {                         // one unit of a push with refinement o
     const float *sl_H[kRefMaxSlices];    // FP32 reconstructed slice filters [2M][ldh] (mixing x basis)
     int64_t sl_D[kRefMaxSlices];
     int32_t sl_Q[kRefMaxSlices], sl_ldh[kRefMaxSlices], sl_level[kRefMaxSlices];
+    const float2 *acorr;                 // [M][kXiLags] template autocorrelation; null: no xi^2
 };
 struct RefCand {                         // one partial record to refine
     int32_t unit;

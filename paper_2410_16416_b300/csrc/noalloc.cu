@@ -18,7 +18,7 @@
 namespace lloid {
 
 // Maximum partial-maximum records one call may need: 2 per (template, 256-sample chunk).
-constexpr int64_t kNoAllocRecords = int64_t(1) << 18;      // 262144 records x 32 B = 8 MiB
+constexpr int64_t kNoAllocRecords = int64_t(1) << 18;      // 262144 records x 40 B = 10 MiB
 constexpr int kNoAllocChunk = 256;
 
 static __device__ __align__(256) WinPart g_noalloc_scratch[kNoAllocRecords];
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) noalloc_partials_kernel(const float *__re
             WinPart r{-1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, -1};
             if (bn[s] != INT64_MAX) {
                 const int64_t p = bn[s] - first;
-                r = WinPart{best[s], xc[p], xs[p], 0.0f, 0.0f, 0, bn[s]};
+                r = WinPart{best[s], xc[p], xs[p], 0.0f, 0.0f, 0.0f, 0, bn[s]};
             }
             scratch[((int64_t)c * 2 + s) * M + i] = r;
         }
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) noalloc_merge_kernel(const WinPart *__res
         r.snr_peak = r.snr;
         r.dt_peak = 0.0f;
         r.flags = 0;
-        r.reserved = 0;
+        r.xi2 = 0.0f;
         out[slot] = r;
     };
     for (int r = 0; r < n_rec; ++r) {

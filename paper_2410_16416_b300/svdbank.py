@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -34,6 +34,7 @@ class SVDBank:
     n_templates: int
     top_rate_hz: float
     slices: List[BankSlice]
+    autocorr: Optional[np.ndarray] = None      # [M, 2 J + 1] complex, for the xi^2 of each trigger
 
     def basis_counts(self) -> List[int]:
         return [s.basis.shape[0] for s in self.slices]
@@ -58,4 +59,20 @@ def decompose(templates: np.ndarray, top_rate_hz: float, slice_specs: Sequence,
         rank = min(int(np.searchsorted(energy, keep_power * energy[-1])) + 1, sig.size)
         out.append(BankSlice(sp.rate_hz, sp.t_start_s, sp.t_end_s,
                              np.ascontiguousarray(vt[:rank]), np.ascontiguousarray(u[:, :rank] * sig[:rank])))
-    return SVDBank(twoM // 2, top_rate_hz, out)
+    return SVDBank(twoM // 2, top_rate_hz, out, template_autocorrelation(templates, XI2_HALF))
+
+
+XI2_HALF = 16        # lags -16 .. 16 (SB_XI2_HALF)
+
+
+def template_autocorrelation(templates: np.ndarray, half: int) -> np.ndarray:
+    """R_i[j] = sum_q h_i[q] conj(h_i[q - j]) / sum_q |h_i[q]|^2 for j = -half .. half, with
+    h_i = templates[2i] + i templates[2i + 1]: the lag profile of a matched peak (rho[n_c + j] ~
+    rho[n_c] R_i[j]) that the signal-consistency value compares against.  By FFT, zero padded."""
+    twoM, N = templates.shape
+    c = templates[0::2].astype(np.float64) + 1j * templates[1::2].astype(np.float64)
+    nfft = 1 << int(math.ceil(math.log2(2 * N)))
+    F = np.fft.fft(c, nfft, axis=1)
+    corr = np.fft.ifft(F * np.conj(F), axis=1)
+    lags = np.arange(-half, half + 1) % nfft
+    return corr[:, lags] / np.sum(np.abs(c) ** 2, axis=1, keepdims=True)

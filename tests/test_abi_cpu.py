@@ -106,3 +106,17 @@ def test_host_decomposition_matches_oracle_bank():
         assert s.basis.shape == o.basis.shape
         assert np.abs(s.mixing @ s.basis - o.mixing @ o.basis).max() <= 1e-10
         assert np.abs(s.basis @ s.basis.T - np.eye(s.basis.shape[0])).max() <= 1e-12
+
+
+def test_host_autocorrelation_matches_the_oracle():
+    """The host setup's FFT autocorrelation (the xi^2 lag profile handed to svdbank_create) equals
+    the oracle's direct sums."""
+    from paper_2410_16416_b300 import svdbank
+    spec = synth.SMALL_BIN
+    h, _ = synth.template_bank(6, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 4, 0, 0)
+    a = svdbank.template_autocorrelation(h, 16)
+    b = oracle.autocorrelation(h, 16)
+    assert a.shape == b.shape == (6, 33)
+    assert np.abs(a - b).max() <= 1e-12
+    bank = svdbank.decompose(h, spec.top_rate_hz, spec.slices)
+    assert bank.autocorr is not None and np.abs(bank.autocorr - b).max() <= 1e-12

@@ -348,3 +348,68 @@ def test_p11_subsample_peak_recovers_a_fractional_delay(cfg_small):
         pk, dt = oracle.subsample_peak(x, i, n_star)
         assert abs(pk - A) < abs(grid - A)
         assert abs(n_star + dt - (n_c + tau)) <= 0.1
+
+
+# ---------------------------------------------------------------- P12 xi^2 signal consistency
+XI_J = 16
+
+
+def test_p12_autocorrelation_matches_fft_and_symmetries(cfg_small):
+    """R_i[j] equals the FFT cross-correlation of the complex template with itself (zero padded),
+    R_i[0] = 1 and R_i[-j] = conj(R_i[j])."""
+    spec, h = cfg_small
+    R = oracle.autocorrelation(h[:8], XI_J)
+    for i in range(4):
+        c = h[2 * i].astype(np.float64) + 1j * h[2 * i + 1]
+        n = 2 * c.shape[0]
+        F = np.fft.fft(c, n)
+        corr = np.fft.ifft(F * np.conj(F))
+        ref = np.array([corr[j % n] for j in range(-XI_J, XI_J + 1)]) / np.sum(np.abs(c) ** 2)
+        assert np.abs(R[i] - ref).max() <= 1e-12
+        assert abs(R[i, XI_J] - 1.0) <= 1e-14
+        assert np.abs(R[i, :XI_J][::-1] - np.conj(R[i, XI_J + 1:])).max() <= 1e-14
+
+
+def test_p12_xi2_is_one_on_average_in_white_noise(cfg_small):
+    """In unit-variance white noise the numerator's expectation is the denominator, so the mean of
+    xi^2 at fixed samples is 1 (a missing factor 2, a conjugate or a reversed lag fails)."""
+    spec, h = cfg_small
+    hs = h[:8]
+    R = oracle.autocorrelation(hs, XI_J)
+    N = hs.shape[1]
+    d = synth.white_noise(N + 60 * 2048, 12, 0, 0)
+    x = oracle.direct_snr(hs, d)
+    vals = [oracle.xi2(x, R, i, n, XI_J) for i in range(4) for n in range(N + 64, x.shape[1] - 64, 97)]
+    m = float(np.mean(vals))
+    assert abs(m - 1.0) <= 0.04, m
+    assert np.all(np.array(vals) > 0.0)
+    # without the factor 2 of the complex series' variance the mean would be 2
+    half = [v * float(np.sum(2.0 - 2.0 * np.abs(R[i]) ** 2)) / float(np.sum(1.0 - np.abs(R[i]) ** 2))
+            for v, i in zip(vals, [i for i in range(4) for _ in range(N + 64, x.shape[1] - 64, 97)])]
+    assert abs(float(np.mean(half)) - 2.0) <= 0.08
+
+
+def test_p12_xi2_separates_a_matched_signal_from_a_mismatched_one(cfg_small):
+    """Noise-free: a template's own injection gives xi^2 ~ 0 at its peak; the same data filtered by
+    another template of the bank (its own SNR peak) gives xi^2 far above that; the lag-reversed
+    autocorrelation (R[-j] for R[j]) is not consistent with the matched peak either."""
+    spec, h = cfg_small
+    R = oracle.autocorrelation(h, XI_J)
+    N = h.shape[1]
+    n_c, A = N + 3 * 2048 + 11, 12.0
+    d = np.zeros(n_c + 2 * 2048)
+    synth.inject(d, h, 3, n_c, A, 0.7)
+    x = oracle.direct_snr(h, d)
+    rho = np.abs(oracle.complex_snr(x))
+    n3 = int(np.argmax(rho[3]))
+    assert n3 == n_c
+    matched = oracle.xi2(x, R, 3, n3, XI_J)
+    reversed_lag = oracle.xi2(x, R[3, ::-1], 3, n3, XI_J)
+    others = []
+    for i in (0, 9, 14):
+        n_i = n_c - 1024 + int(np.argmax(rho[i, n_c - 1024:n_c + 1024]))
+        others.append(oracle.xi2(x, R, i, n_i, XI_J) / (rho[i, n_i] ** 2))
+    per_snr2 = matched / A ** 2
+    assert per_snr2 <= 1e-4, per_snr2
+    assert reversed_lag / A ** 2 > 100 * per_snr2
+    assert min(others) > 100 * per_snr2, (others, per_snr2)

@@ -99,6 +99,32 @@ def test_fp32_subsample_peaks_match_oracle(lloid, small_case):
     assert np.all(plain["snr_peak"] == plain["snr"]) and np.all(plain["dt_peak"] == 0.0)
 
 
+def test_fp32_xi2_matches_oracle(lloid, small_case):
+    """Threshold 0: every window maximum whose lags n* - 16 .. n* + 16 lie in one push carries xi^2,
+    and it matches the oracle's xi^2 of the oracle's SNR at the same sample."""
+    spec, h, bank, d, x = small_case
+    R = oracle.autocorrelation(h, lloid.SB_XI2_HALF)
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, threshold=0.0, max_push_samples=8192, autocorr=R)
+    for t in range(0, d.shape[0], 8192):
+        u.push(d[t:t + 8192], t)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    ctx.close()
+    has = trig[(trig["flags"] & lloid.SB_TRIG_XI2) != 0]
+    assert len(has) >= 0.9 * len(trig)
+    worst, vals = 0.0, []
+    for t in has:
+        ref = oracle.xi2(x, R, int(t["template_id"]), int(t["sample"]), lloid.SB_XI2_HALF)
+        assert ref is not None
+        vals.append(ref)
+        worst = max(worst, abs(t["xi2"] - ref) / max(1.0, ref))
+    print(f"fp32 xi2: {len(has)} of {len(trig)}; max |xi2 error| / max(1, xi2) {worst:.2e}; "
+          f"median xi2 {np.median(vals):.3f}")
+    assert worst <= 2e-3
+    assert np.all(trig[(trig["flags"] & lloid.SB_TRIG_XI2) == 0]["xi2"] == 0.0)
+
+
 def test_streaming_is_bitwise_independent_of_buffer_sizes(lloid, small_case):
     spec, h, bank, d, x = small_case
     runs = []
@@ -390,7 +416,9 @@ def test_refined_production_injection(lloid):
     d = synth.white_noise(n, 2, 0, 1)
     synth.inject(d, h, 500, 80 * 4096 + 99, 30.0, -0.8)
     ctx = lloid.Context(0)
-    u = ctx.create_unit(bank, precision="bf16", threshold=6.0, refine_threshold=5.5, max_push_samples=16 * 4096)
+    R = oracle.autocorrelation(h, lloid.SB_XI2_HALF)
+    u = ctx.create_unit(bank, precision="bf16", threshold=6.0, refine_threshold=5.5, max_push_samples=16 * 4096,
+                        autocorr=R)
     for t in range(0, n, 16 * 4096):
         u.push(d[t:t + 16 * 4096], t)
     ctx.sync()
@@ -411,6 +439,12 @@ def test_refined_production_injection(lloid):
     print("refined sub-sample peak", hit["snr_peak"][0], hit["dt_peak"][0], "oracle", ref)
     assert hit["flags"][0] & lloid.SB_TRIG_SUBSAMPLE and ref is not None
     assert abs(hit["snr_peak"][0] - ref[0]) <= 1e-3 and abs(hit["dt_peak"][0] - ref[1]) <= 5e-3
+    xr = oracle.xi2(xo, R[500], 0, int(n_star[0, 0]), lloid.SB_XI2_HALF)
+    print("refined xi2", hit["xi2"][0], "oracle", xr)
+    assert hit["flags"][0] & lloid.SB_TRIG_XI2 and abs(hit["xi2"][0] - xr) <= 1e-3 * max(1.0, xr)
+    # every trigger is refined, and every refined one whose lags are all in its push has xi^2
+    assert np.all(trig["flags"] & lloid.SB_TRIG_REFINED)
+    assert np.mean((trig["flags"] & lloid.SB_TRIG_XI2) != 0) >= 0.9
 
 
 # ---------------------------------------------------------------- E4M3 mode (config 4)
