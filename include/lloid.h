@@ -260,8 +260,9 @@ int sb_ctx_graphs(sb_ctx *ctx, int32_t enable);
  * (a3 + a4) with a new launch shape (precision, K chunks per tile, whether the
  * level's SNR is stored, tile count rounded down to a power of two) times every
  * pipeline shape that fits in shared memory (mixing stages 1-2, interpolation
- * buffers 1-2, window-ring depth 2-4) on that push's own data and keeps the
- * fastest for later pushes; that push is not graph-captured.  The pipeline
+ * buffers 1-2, window-ring depth 2-6) on that push's own data, three times in
+ * interleaved rounds, and keeps the one with the smallest time for later
+ * pushes; that push is not graph-captured.  The pipeline
  * shape changes no arithmetic: results are bitwise the same for every choice.
  * enable == 0: later launches use the built-in shape for new launch shapes
  * (tuned shapes are kept). */

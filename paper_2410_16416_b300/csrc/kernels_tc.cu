@@ -906,28 +906,32 @@ static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, i
     if (known) cfg = *known;
     if (tuner && !known && may_tune && cands.size() == 1) tuner->best.emplace_back(key, cfg);
     if (tuner && !known && may_tune && cands.size() > 1) {
-        // time every candidate once on this push (each launch computes the same result)
-        std::vector<cudaEvent_t> ev(cands.size() + 1);
+        // time every candidate on this push, in kTuneRounds interleaved rounds (each launch computes
+        // the same result), and keep the candidate with the smallest of its times
+        constexpr int kTuneRounds = 3;
+        const size_t nc = cands.size();
+        std::vector<cudaEvent_t> ev(kTuneRounds * nc + 1);
         for (auto &x : ev) cudaEventCreate(&x);
         cudaError_t e = cudaEventRecord(ev[0], s);
-        for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
-            e = mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cands[i], n_stbuf, utab, err, s);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[i + 1], s);
+        for (size_t k = 0; k < kTuneRounds * nc && e == cudaSuccess; ++k) {
+            e = mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cands[k % nc], n_stbuf, utab, err, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[k + 1], s);
         }
         if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
-        float best_ms = 1e30f;
-        for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
+        std::vector<float> best_ms(nc, 1e30f);
+        for (size_t k = 0; k < kTuneRounds * nc && e == cudaSuccess; ++k) {
             float ms = 0.0f;
-            e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
-            if (e == cudaSuccess && ms < best_ms) {
-                best_ms = ms;
-                cfg = cands[i];
-            }
+            e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            if (e == cudaSuccess) best_ms[k % nc] = std::min(best_ms[k % nc], ms);
         }
         for (auto &x : ev) cudaEventDestroy(x);
         if (e != cudaSuccess) return e;
+        size_t bi = 0;
+        for (size_t i = 1; i < nc; ++i)
+            if (best_ms[i] < best_ms[bi]) bi = i;
+        cfg = cands[bi];
         tuner->best.emplace_back(key, cfg);
-        tuner->timed_launches += (int64_t)cands.size();
+        tuner->timed_launches += (int64_t)(kTuneRounds * nc);
         return cudaSuccess;
     }
     return mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cfg, n_stbuf, utab, err, s);
