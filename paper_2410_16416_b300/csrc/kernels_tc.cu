@@ -621,7 +621,10 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                 if (t.rsc_next) inv_next = 1.0f / t.rsc_next[a];
                 inv_next *= kE4StoreScale;                   // the finer level's table carries the inverse
             }
-            const bool top = t.part != nullptr;
+            // 128-wide interpolation blocks run only at the top level (trigger partials, no y stored);
+            // 64-wide blocks only below it (y stored): each instantiation keeps only its own epilogue
+            constexpr bool kTopKernel = UB == 128;
+            const bool top = kTopKernel && t.part != nullptr;
             SegBest b0{-1.0f, 0.0f, 0.0f, -1}, b1{-1.0f, 0.0f, 0.0f, -1};
             // top level: columns [vlo, vhi) of this half are real samples (n >= 0, inside the push);
             // columns >= cb belong to the next window (window length >= 128 columns)
@@ -635,17 +638,21 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                 const int64_t wend = (a0 >= 0 ? a0 / t.win_len + 1 : 1) * t.win_len;
                 cb = (int)min((int64_t)(1 << 30), wend - half_first);
             }
-#pragma unroll 1
+            // four 32-column chunks; chunk c + 1's TMEM load is in flight while chunk c is processed
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + b * kMixCols + 128 * h;
+            uint32_t va[32], vb[32];
+            tmem_ld32(tbase, va);
+#pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int c0 = 128 * h + 32 * c;
                 float x[32];
+                tmem_ld_wait();                              // chunk c is in registers
                 {
-                    uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * kMixCols + c0, v);
-                    tmem_ld_wait();
+                    uint32_t(&v)[32] = (c & 1) ? vb : va;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]) * rsc;
                 }
+                if (c + 1 < 4) tmem_ld32(tbase + 32 * (c + 1), (c & 1) ? va : vb);
                 const int64_t col0 = (int64_t)kMixCols * m.tt + c0;
                 const int64_t n0 = first_n + col0;
                 if (n0 < 0) {
@@ -653,7 +660,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     for (int j = 0; j < 32; ++j)
                         if (n0 + j < 0) x[j] = 0.0f;         // every rate starts at index 0
                 }
-                if (Yh && n_stbuf > 0) {
+                if (!kTopKernel && Yh && n_stbuf > 0) {
                     // y (FP16, or BF16 hi / lo) through a per-warp staging buffer: row `lane` of one
                     // 32 x 32 tile per plane (64-byte rows, 16-byte chunk i at chunk i ^ ((r >> 1) & 3):
                     // no bank conflicts), then each store instruction writes 8 whole 64-byte row segments
@@ -701,7 +708,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                                     *reinterpret_cast<const uint4 *>(sbuf + kMixStPlane + r * 64 + pc * 16);
                         }
                     }
-                } else if (Y && row_ok) {
+                } else if (kTopKernel && Y && row_ok) {
                     float *dst = Y + (int64_t)a * ldy + col0;
                     if (col0 + 32 <= Bk) {
 #pragma unroll
