@@ -83,7 +83,8 @@ typedef struct sb_slice {
  * refine_threshold: in SB_BF16/SB_FP16/SB_FP8 modes, window maxima above this
  *   are recomputed in FP32 (0 disables refinement).
  * window_s: trigger window length (windows start at multiples of window_s*f0).
- * max_push_samples: the largest n_samples a filter_push will pass (top rate).
+ * max_push_samples: the largest n_samples a filter_push will pass (top rate),
+ *   at most 2^30.
  * autocorr: NULL, or [n_templates][2 SB_XI2_HALF + 1][2] (re, im) doubles, the
  *   normalised complex autocorrelation of each template at f0, lag j at index
  *   j + SB_XI2_HALF: R_i[j] = sum_q h_i[q] conj(h_i[q - j]) / sum_q |h_i[q]|^2
@@ -293,7 +294,7 @@ int sb_ctx_stage_times(sb_ctx *ctx, double *ms, int64_t *launches, int32_t n_sta
  * |rho| > threshold.  out_count: device int32[2] = {triggers, overflow flag},
  * zeroed by the call; at most cap triggers are stored.  Work is queued on
  * stream (a cudaStream_t; NULL = legacy default stream) and nothing blocks.
- * Scratch: a fixed device array of 2^18 partial records (10 MiB) that every
+ * Scratch: a fixed device array of 2^18 partial records (8 MiB) that every
  * GPU loading this library holds until the process exits; a call needs
  * 2 * M * ceil(n_samples / 256) records and returns SB_EINVAL (see
  * sb_last_error) beyond that, or when window_len < 256.  The first call on a

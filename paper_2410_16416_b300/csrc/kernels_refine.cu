@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restr
         const WinPart p = u.part[idx];
         if (!(p.mag2 > u.thr2)) continue;
         const int i = (int)(idx / u.n_rec);
-        const float wm = __uint_as_float(u.wmax[(int64_t)i * u.n_wslot + (p.n / u.win_len - u.win0)]);
+        const float wm = __uint_as_float(u.wmax[(int64_t)i * u.n_wslot + ((u.first_n + p.nr) / u.win_len - u.win0)]);
         if (p.mag2 < u.keep2 * wm) continue;
         const int slot = atomicAdd(&counters[1], 1);
         if (slot < cand_cap) cands[slot] = RefCand{(int)blockIdx.y, idx};
@@ -78,14 +78,15 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
         WinPart rec = u.part[idx];
         const int i = (int)(idx / u.n_rec), r = (int)(idx % u.n_rec);
         const int tt = r / 4, h = (r / 2) % 2;
-        const int64_t w = rec.n / u.win_len;
+        const int64_t rn = u.first_n + rec.nr;          // absolute sample of the 16-bit maximum
+        const int64_t w = rn / u.win_len;
         const int64_t half0 = u.first_n + (int64_t)kRefTile * tt + 128 * h;
         int64_t lo[kRefMaxLevels], hi[kRefMaxLevels];
         // search range [slo, shi]; computed kXiJ samples wider on each side (the sub-sample peak's
         // neighbours and the xi^2 lags), inside the samples this push produces and n >= 0.  The
         // strain history reaches 128 samples below the push at every level, which covers it.
-        const int64_t slo = max(rec.n - kRefR, max(half0, w * u.win_len));
-        const int64_t shi = min(min(rec.n + kRefR, half0 + 127), min((w + 1) * u.win_len, u.first_n + u.B) - 1);
+        const int64_t slo = max(rn - kRefR, max(half0, w * u.win_len));
+        const int64_t shi = min(min(rn + kRefR, half0 + 127), min((w + 1) * u.win_len, u.first_n + u.B) - 1);
         if (shi < slo) continue;                        // block-uniform
         lo[0] = max(slo - kXiJ, (int64_t)0);
         hi[0] = min(shi + kXiJ, u.first_n + u.B - 1);
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
                 rec.mag2 = best;
                 rec.re = zc[bc];
                 rec.im = zs[bc];
-                rec.n = lo[0] + bc;
+                rec.nr = (int32_t)(lo[0] + bc - u.first_n);
                 rec.flags = SB_TRIG_REFINED_BIT;
                 rec.pk = rec.dt = rec.xi2 = 0.0f;
                 if (bc >= 1 && bc + 1 < len0) {

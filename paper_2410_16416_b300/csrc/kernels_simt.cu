@@ -270,9 +270,10 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
     int fl = 0;
     for (int r = r0 + lane; r < r1; r += 32) {
         const WinPart p = rec[r];
-        if (p.mag2 < 0.0f || p.n / t.win_len != w) continue;
-        if (p.mag2 > best || (p.mag2 == best && p.n < bn)) {
-            best = p.mag2; bn = p.n; re = p.re; im = p.im; pk = p.pk; dt = p.dt; xi = p.xi2; fl = p.flags;
+        const int64_t pn = t.first_n + p.nr;
+        if (p.mag2 < 0.0f || pn / t.win_len != w) continue;
+        if (p.mag2 > best || (p.mag2 == best && pn < bn)) {
+            best = p.mag2; bn = pn; re = p.re; im = p.im; pk = p.pk; dt = p.dt; xi = p.xi2; fl = p.flags;
         }
     }
 #pragma unroll

@@ -638,21 +638,17 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                 const int64_t wend = (a0 >= 0 ? a0 / t.win_len + 1 : 1) * t.win_len;
                 cb = (int)min((int64_t)(1 << 30), wend - half_first);
             }
-            // four 32-column chunks; chunk c + 1's TMEM load is in flight while chunk c is processed
-            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + b * kMixCols + 128 * h;
-            uint32_t va[32], vb[32];
-            tmem_ld32(tbase, va);
-#pragma unroll
+#pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int c0 = 128 * h + 32 * c;
                 float x[32];
-                tmem_ld_wait();                              // chunk c is in registers
                 {
-                    uint32_t(&v)[32] = (c & 1) ? vb : va;
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * kMixCols + c0, v);
+                    tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]) * rsc;
                 }
-                if (c + 1 < 4) tmem_ld32(tbase + 32 * (c + 1), (c & 1) ? va : vb);
                 const int64_t col0 = (int64_t)kMixCols * m.tt + c0;
                 const int64_t n0 = first_n + col0;
                 if (n0 < 0) {
@@ -772,8 +768,8 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                 seg_merge_pair(b1);
                 if ((a & 1) == 0 && row_ok) {
                     WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (m.tt * 2 + h) * 2;
-                    base[0] = WinPart{b0.mag2, b0.re, b0.im, 0.0f, 0.0f, 0.0f, 0, b0.n};
-                    base[1] = WinPart{b1.mag2, b1.re, b1.im, 0.0f, 0.0f, 0.0f, 0, b1.n};
+                    base[0] = WinPart{b0.mag2, b0.re, b0.im, 0.0f, 0.0f, 0.0f, 0, (int32_t)(b0.n - first_n)};
+                    base[1] = WinPart{b1.mag2, b1.re, b1.im, 0.0f, 0.0f, 0.0f, 0, (int32_t)(b1.n - first_n)};
                     if (t.wmax) {                    // window maxima for the refinement's candidate rule
                         uint32_t *wm = t.wmax + (int64_t)(a >> 1) * t.n_wslot - t.win0;
                         if (b0.mag2 > t.thr2) atomicMax(wm + b0.n / t.win_len, __float_as_uint(b0.mag2));

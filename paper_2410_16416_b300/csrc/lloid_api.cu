@@ -732,8 +732,9 @@ static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d, const std::ve
 static int validate_desc(const sb_desc *d, std::vector<int> &lvl, Plan &P) {
     if (!d) return fail(SB_EINVAL, "null description");
     if (d->n_templates <= 0 || d->n_slices <= 0 || !d->slices || !(d->top_rate_hz > 0) || !(d->window_s > 0) ||
-        d->max_push_samples <= 0)
-        return fail(SB_EINVAL, "bad bank description (templates, slices, rate, window or max_push_samples)");
+        d->max_push_samples <= 0 || d->max_push_samples > (int64_t(1) << 30))
+        return fail(SB_EINVAL, "bad bank description (templates, slices, rate, window or max_push_samples "
+                               "outside (0, 2^30])");
     if (d->precision != SB_FP32 && !is_tc(d->precision))
         return fail(SB_EINVAL, "precision mode not available in this build");
     const double wl = d->window_s * d->top_rate_hz;

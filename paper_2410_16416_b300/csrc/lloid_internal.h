@@ -208,8 +208,10 @@ struct WinPart {
     float pk, dt;              // sub-sample peak (refined records with SB_TRIG_SUBSAMPLE_BIT)
     float xi2;                 // signal consistency (refined records with SB_TRIG_XI2_BIT)
     int32_t flags;             // SB_TRIG_* bits (refined, sub-sample, xi^2)
-    int64_t n;                 // absolute top-rate sample
+    int32_t nr;                // top-rate sample relative to column 0 of the record set (records live
+                               // for one push; the carried window state keeps absolute samples)
 };
+static_assert(sizeof(WinPart) == 32, "window records are 32 bytes (two 16-byte stores)");
 
 // a3 + a4 on tensor cores (+ a5 partial maxima at the top level).
 // Tile (tt, at): time columns [256 tt, +256) of this level, filters [128 at, +128).

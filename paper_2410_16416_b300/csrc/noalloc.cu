@@ -18,7 +18,7 @@
 namespace lloid {
 
 // Maximum partial-maximum records one call may need: 2 per (template, 256-sample chunk).
-constexpr int64_t kNoAllocRecords = int64_t(1) << 18;      // 262144 records x 40 B = 10 MiB
+constexpr int64_t kNoAllocRecords = int64_t(1) << 18;      // 262144 records x 32 B = 8 MiB
 constexpr int kNoAllocChunk = 256;
 
 static __device__ __align__(256) WinPart g_noalloc_scratch[kNoAllocRecords];
@@ -60,10 +60,10 @@ __global__ void __launch_bounds__(256) noalloc_partials_kernel(const float *__re
     }
     if (lane == 0) {
         for (int s = 0; s < 2; ++s) {
-            WinPart r{-1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, -1};
+            WinPart r{-1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, -1};
             if (bn[s] != INT64_MAX) {
                 const int64_t p = bn[s] - first;
-                r = WinPart{best[s], xc[p], xs[p], 0.0f, 0.0f, 0.0f, 0, bn[s]};
+                r = WinPart{best[s], xc[p], xs[p], 0.0f, 0.0f, 0.0f, 0, (int32_t)p};
             }
             scratch[((int64_t)c * 2 + s) * M + i] = r;
         }
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) noalloc_partials_kernel(const float *__re
 // lies entirely inside [start_abs, end_abs) yields its maximum, a trigger when
 // |rho| > threshold.
 __global__ void __launch_bounds__(256) noalloc_merge_kernel(const WinPart *__restrict__ scratch, int M, int n_rec,
-                                                            const int64_t *__restrict__ template_ids,
+                                                            const int64_t *__restrict__ template_ids, int64_t first,
                                                             int64_t start_abs, int64_t end_abs, int64_t win_len,
                                                             float threshold, DevTrigger *out, int32_t *count,
                                                             int32_t cap) {
@@ -106,13 +106,14 @@ __global__ void __launch_bounds__(256) noalloc_merge_kernel(const WinPart *__res
     for (int r = 0; r < n_rec; ++r) {
         const WinPart p = scratch[(int64_t)r * M + i];
         if (p.mag2 < 0.0f) continue;
-        const int64_t w = p.n / win_len;
+        const int64_t pn = first + p.nr;
+        const int64_t w = pn / win_len;
         if (w != w_cur) {
             if (w_cur >= 0) close(w_cur);
             bm = -1.0f;
             w_cur = w;
         }
-        if (p.mag2 > bm) { bm = p.mag2; bre = p.re; bim = p.im; bnn = p.n; }
+        if (p.mag2 > bm) { bm = p.mag2; bre = p.re; bim = p.im; bnn = pn; }
     }
     if (w_cur >= 0) close(w_cur);
 }
@@ -185,7 +186,8 @@ extern "C" int sb_window_triggers_noalloc(const float *x, int64_t ldx, int32_t n
     noalloc_partials_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
         x, ldx, n_templates, n_samples, first_sample, start_abs, end_abs, window_len, (int)n_chunks, scratch);
     noalloc_merge_kernel<<<(n_templates + 255) / 256, 256, 0, st>>>(
-        scratch, n_templates, (int)(n_chunks * 2), template_ids, start_abs, end_abs, window_len, threshold,
+        scratch, n_templates, (int)(n_chunks * 2), template_ids, first_sample, start_abs, end_abs, window_len,
+        threshold,
         reinterpret_cast<DevTrigger *>(out), out_count, cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
