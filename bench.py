@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--graphs", default="on", choices=["on", "off"],
                    help="capture every push into a CUDA graph (reused per group shape)")
+    p.add_argument("--xi2", default="on", choices=["on", "off"],
+                   help="production bank: hand the templates' autocorrelation to svdbank_create (xi^2 of every trigger)")
     p.add_argument("--autotune", default="on", choices=["on", "off"],
                    help="time the mixing kernel's pipeline shapes on the first push of each launch shape")
     p.add_argument("--cpu-seconds", type=float, default=8.0, help="strain seconds per oracle worker")
@@ -417,6 +419,8 @@ def main():
     if args.workload == "production":
         spec, h = production_bank_templates(rank, args.templates)
         bank = lloid.decompose(h, spec.top_rate_hz, spec.slices)
+        if args.xi2 == "off":
+            bank.autocorr = None
         banks = [bank]
         f0 = int(spec.top_rate_hz)
     else:                       # uneven shape-only bins; rank r takes bins r, r + world, ...
@@ -564,6 +568,7 @@ def main():
                        "push_seconds": args.push_seconds, "precision": args.precision,
                        "parallelism": f"units sharded, {world} GPU(s)", "cuda_graphs": args.graphs,
                        "mix_autotune": args.autotune,
+                       "xi2": args.xi2 if spec is not None else "off",
                        "l2": "flushed between steps (256 MB write outside the step events)"},
             "roofline": roof, "e2e": e2e, "gpu_launches": prim["launches"], "clocks": prim["clocks"],
             "stages_ms_share": {k: round(v / total_stage_ms, 4) for k, v in busy.items()},
