@@ -202,7 +202,7 @@ struct TcFirTask {
 };
 
 // Partial window maximum of one template over one column run of one tile.
-struct WinPart {
+struct __align__(16) WinPart {
     float mag2;                // |rho|^2 (-1: no valid sample)
     float re, im;
     float pk, dt;              // sub-sample peak (refined records with SB_TRIG_SUBSAMPLE_BIT)
@@ -211,7 +211,7 @@ struct WinPart {
     int32_t nr;                // top-rate sample relative to column 0 of the record set (records live
                                // for one push; the carried window state keeps absolute samples)
 };
-static_assert(sizeof(WinPart) == 32, "window records are 32 bytes (two 16-byte stores)");
+static_assert(sizeof(WinPart) == 32 && alignof(WinPart) == 16, "window records: two 16-byte accesses each");
 
 // a3 + a4 on tensor cores (+ a5 partial maxima at the top level).
 // Tile (tt, at): time columns [256 tt, +256) of this level, filters [128 at, +128).
