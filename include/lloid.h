@@ -218,6 +218,30 @@ int triggers_pop(sb_ctx *ctx, sb_trigger *out, int64_t cap, int64_t *n_out);
  * n in [*first_sample, *first_sample + *n).  Needs SB_FLAG_KEEP_SNR. */
 int sb_unit_snr(sb_unit *unit, float *host_out, int64_t cap, int64_t *first_sample, int64_t *n);
 
+/* ---- coincidence generator (host only) ----------------------------------- */
+/* One coincidence: triggers index_a of detector A and index_b of detector B
+ * (indices into the arrays passed in), same template, |sample_a - sample_b|
+ * <= max_dt_samples; network_snr = sqrt(snr_a^2 + snr_b^2).                 */
+typedef struct sb_coinc {
+    int64_t template_id;
+    int64_t index_a, index_b;
+    int64_t sample_a, sample_b;
+    float snr_a, snr_b, network_snr;
+    int32_t reserved;
+} sb_coinc;
+/* The coincidence generator that follows the filter (Sec. II.A): every pair of
+ * a trigger of detector A and one of detector B with the same template_id and
+ * |sample_a - sample_b| <= max_dt_samples (top-rate samples: the light-travel
+ * time between the two sites, about 10 ms for the LIGO pair, plus any timing
+ * margin, times f0).  Inputs in any order (as triggers_pop returns them); the
+ * pairs are written to out ordered by (template_id, sample_a, sample_b,
+ * index_a, index_b).  *n_out = the number of coincidences.  Host memory only,
+ * no device.  Returns SB_OK, SB_EINVAL (null pointers with nonzero counts,
+ * negative max_dt_samples or cap), or SB_EOVERFLOW when more than cap pairs
+ * exist (the first cap are written). */
+int sb_coincidences(const sb_trigger *a, int64_t n_a, const sb_trigger *b, int64_t n_b, int64_t max_dt_samples,
+                    sb_coinc *out, int64_t cap, int64_t *n_out);
+
 /* ---- instrumentation ------------------------------------------------- */
 /* Stages of a push, in launch order (indices of sb_ctx_stage_times). */
 #define SB_STAGE_HISTORY   0  /* history shifts of the decimated strain          */

@@ -64,6 +64,9 @@ TRIGGER_DTYPE = np.dtype([("unit", "<i8"), ("template_id", "<i8"), ("sample", "<
                           ("snr", "<f4"), ("phase", "<f4"), ("snr_peak", "<f4"), ("dt_peak", "<f4"),
                           ("flags", "<i4"), ("xi2", "<f4")])
 assert TRIGGER_DTYPE.itemsize == C.sizeof(SbTrigger)
+COINC_DTYPE = np.dtype([("template_id", "<i8"), ("index_a", "<i8"), ("index_b", "<i8"), ("sample_a", "<i8"),
+                        ("sample_b", "<i8"), ("snr_a", "<f4"), ("snr_b", "<f4"), ("network_snr", "<f4"),
+                        ("reserved", "<i4")])
 
 # name -> (restype, argtypes): every entry point declared in include/lloid.h
 SIGNATURES = {
@@ -90,6 +93,8 @@ SIGNATURES = {
     "sb_window_triggers_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                                              C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                              C.c_void_p]),
+    "sb_coincidences": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
+                                  C.POINTER(C.c_int64)]),
     "sb_last_error": (C.c_char_p, []),
 }
 
@@ -162,6 +167,24 @@ def make_desc(bank, precision: str = "fp32", threshold: float = 6.0, refine_thre
                float(refine_threshold), float(window_s), int(max_push_samples),
                ac.ctypes.data_as(C.POINTER(C.c_double)) if ac is not None else None)
     return d, keep
+
+
+def coincidences(trig_a: np.ndarray, trig_b: np.ndarray, max_dt_samples: int) -> np.ndarray:
+    """sb_coincidences: same-template pairs of two detectors' triggers (TRIGGER_DTYPE arrays) within
+    max_dt_samples; a COINC_DTYPE array ordered by (template_id, sample_a, sample_b, index_a, index_b)."""
+    a = np.ascontiguousarray(trig_a, dtype=TRIGGER_DTYPE)
+    b = np.ascontiguousarray(trig_b, dtype=TRIGGER_DTYPE)
+    n = C.c_int64()
+    cap = 64
+    while True:
+        out = np.empty(cap, dtype=COINC_DTYPE)
+        rc = lib.sb_coincidences(a.ctypes.data if a.size else None, a.size, b.ctypes.data if b.size else None,
+                                 b.size, int(max_dt_samples), out.ctypes.data, cap, C.byref(n))
+        if rc == SB_EOVERFLOW and n.value > cap:
+            cap = n.value
+            continue
+        _check(rc, "sb_coincidences")
+        return out[: n.value]
 
 
 def plan(bank, **kw) -> SbUnitInfo:

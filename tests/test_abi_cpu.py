@@ -120,3 +120,52 @@ def test_host_autocorrelation_matches_the_oracle():
     assert np.abs(a - b).max() <= 1e-12
     bank = svdbank.decompose(h, spec.top_rate_hz, spec.slices)
     assert bank.autocorr is not None and np.abs(bank.autocorr - b).max() <= 1e-12
+
+
+def _trig(tid, sample, snr):
+    t = np.zeros(len(tid), dtype=lloid.TRIGGER_DTYPE)
+    t["template_id"], t["sample"], t["snr"] = tid, sample, snr
+    return t
+
+
+def test_coincidences_match_the_oracle_and_the_fixture():
+    """sb_coincidences (host only) against the oracle's brute force: the hand-worked fixture and
+    random trigger sets with shuffled order, equal samples and duplicates; integer fields exact."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "coinc_hand_worked.txt")
+    A, B = [], []
+    for line in open(path):
+        f = line.split()
+        if f and f[0] in ("A", "B"):
+            (A if f[0] == "A" else B).append((int(f[1]), int(f[2]), float(f[3])))
+    cases = [(_trig(*zip(*A)), _trig(*zip(*B)), dt) for dt in (41, 42, 0, 100000)]
+    g = np.random.default_rng(7)
+    for n_a, n_b, dt in ((0, 5, 10), (7, 0, 10), (300, 250, 41), (200, 200, 0), (50, 60, 5000)):
+        ta = _trig(g.integers(0, 12, n_a), g.integers(0, 4000, n_a), g.uniform(6, 30, n_a).astype(np.float32))
+        tb = _trig(g.integers(0, 12, n_b), g.integers(0, 4000, n_b), g.uniform(6, 30, n_b).astype(np.float32))
+        if n_a and n_b:
+            tb["sample"][: min(n_a, n_b) // 3] = ta["sample"][: min(n_a, n_b) // 3]     # equal samples
+        cases.append((ta, tb, dt))
+    for ta, tb, dt in cases:
+        got = lloid.coincidences(ta, tb, dt)
+        ref = oracle.coincidences(ta["template_id"], ta["sample"], ta["snr"], tb["template_id"], tb["sample"],
+                                  tb["snr"], dt)
+        assert len(got) == len(ref)
+        for r, w in zip(got, ref):
+            assert (int(r["template_id"]), int(r["index_a"]), int(r["index_b"]), int(r["sample_a"]),
+                    int(r["sample_b"])) == w[:5]
+            assert abs(float(r["network_snr"]) - w[5]) <= 1e-6 * w[5]
+
+
+def test_coincidences_arguments_and_overflow():
+    ta = _trig([1, 1, 2], [100, 200, 300], [7.0, 8.0, 9.0])
+    tb = _trig([1, 1, 2], [110, 190, 300], [7.5, 6.5, 8.5])
+    n = C.c_int64()
+    out = np.empty(2, dtype=lloid.COINC_DTYPE)
+    rc = lloid.lib.sb_coincidences(ta.ctypes.data, 3, tb.ctypes.data, 3, 100, out.ctypes.data, 2, C.byref(n))
+    assert rc == lloid.SB_EOVERFLOW and n.value == 5        # (100,110) (100,190) (200,110) (200,190) (300,300)
+    assert list(out["sample_a"]) == [100, 100] and list(out["sample_b"]) == [110, 190]
+    assert lloid.lib.sb_coincidences(ta.ctypes.data, 3, tb.ctypes.data, 3, -1, out.ctypes.data, 2,
+                                     C.byref(n)) == lloid.SB_EINVAL
+    assert lloid.lib.sb_coincidences(None, 3, tb.ctypes.data, 3, 5, out.ctypes.data, 2, C.byref(n)) == lloid.SB_EINVAL
+    assert lloid.lib.sb_coincidences(None, 0, None, 0, 5, None, 0, C.byref(n)) == lloid.SB_OK and n.value == 0
+    assert len(lloid.coincidences(ta, tb, 100)) == 5

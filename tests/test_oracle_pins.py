@@ -3,6 +3,7 @@
 Each test names the plausible oracle mistake it would catch.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -413,3 +414,48 @@ def test_p12_xi2_separates_a_matched_signal_from_a_mismatched_one(cfg_small):
     assert per_snr2 <= 1e-4, per_snr2
     assert reversed_lag / A ** 2 > 100 * per_snr2
     assert min(others) > 100 * per_snr2, (others, per_snr2)
+
+
+# ---------------------------------------------------------------- P13 coincidence generator
+def _coinc_fixture():
+    path = os.path.join(os.path.dirname(__file__), "golden", "coinc_hand_worked.txt")
+    A, B, P = [], [], {}
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "A":
+            A.append((int(f[1]), int(f[2]), float(f[3])))
+        elif f[0] == "B":
+            B.append((int(f[1]), int(f[2]), float(f[3])))
+        else:
+            P.setdefault(int(f[1]), []).append((int(f[2]), int(f[3]), int(f[4]), int(f[5]), int(f[6]), float(f[7])))
+    return A, B, P
+
+
+def test_p13_coincidences_match_the_hand_worked_fixture():
+    A, B, P = _coinc_fixture()
+    for max_dt, want in P.items():
+        got = oracle.coincidences([a[0] for a in A], [a[1] for a in A], [a[2] for a in A],
+                                  [b[0] for b in B], [b[1] for b in B], [b[2] for b in B], max_dt)
+        assert [g[:5] for g in got] == [w[:5] for w in want]
+        assert all(abs(g[5] ** 2 - w[5]) <= 1e-9 for g, w in zip(got, want))
+
+
+def test_p13_coincidences_symmetry_and_window_monotonicity():
+    """Swapping the detectors swaps the roles of every pair; a wider window keeps every pair of a
+    narrower one; max_dt = 0 pairs equal samples only."""
+    g = np.random.default_rng(13)
+    ta, sa, ra = g.integers(0, 6, 60), g.integers(0, 3000, 60), g.uniform(6, 20, 60)
+    tb, sb, rb = g.integers(0, 6, 50), g.integers(0, 3000, 50), g.uniform(6, 20, 50)
+    ab = oracle.coincidences(ta, sa, ra, tb, sb, rb, 40)
+    ba = oracle.coincidences(tb, sb, rb, ta, sa, ra, 40)
+    assert sorted((t, i, j) for t, i, j, *_ in ab) == sorted((t, j, i) for t, i, j, *_ in ba)
+    narrow = {(t, i, j) for t, i, j, *_ in oracle.coincidences(ta, sa, ra, tb, sb, rb, 10)}
+    assert narrow <= {(t, i, j) for t, i, j, *_ in ab} and len(narrow) < len(ab)
+    sb2 = sb.copy()
+    sb2[:10] = sa[:10]
+    tb2 = tb.copy()
+    tb2[:10] = ta[:10]
+    zero = oracle.coincidences(ta, sa, ra, tb2, sb2, rb, 0)
+    assert all(r[3] == r[4] for r in zero) and {(i, j) for _, i, j, *_ in zero} >= {(k, k) for k in range(10)}

@@ -125,6 +125,41 @@ def test_fp32_xi2_matches_oracle(lloid, small_case):
     assert np.all(trig[(trig["flags"] & lloid.SB_TRIG_XI2) == 0]["xi2"] == 0.0)
 
 
+def test_two_detector_coincidence_of_an_injection(lloid, small_case):
+    """Two detectors (one unit each, one grouped push per buffer) see the same template 13 samples
+    apart: the coincidence generator pairs their triggers of that template, as the oracle pairs the
+    oracle's triggers of the same strains."""
+    spec, h, bank, d, x = small_case
+    n = d.shape[0]
+    n_c = 12 * 2048 + 777
+    d1 = synth.white_noise(n, 1, 0, 1)
+    synth.inject(d1, h, 17, n_c + 13, 11.0, 0.4)
+    ctx = lloid.Context(0)
+    u0 = ctx.create_unit(bank, detector=0, threshold=6.0, max_push_samples=8192)
+    u1 = ctx.create_like(u0, detector=1)
+    for t in range(0, n, 8192):
+        ctx.push_group([u0, u1], [d[t:t + 8192], d1[t:t + 8192]], [t, t], False)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    ctx.close()
+    ta, tb = trig[trig["unit"] == u0.info().unit], trig[trig["unit"] == u1.info().unit]
+    max_dt = int(np.ceil(0.010 * spec.top_rate_hz)) + 2          # 10 ms of light travel + 2 samples
+    co = lloid.coincidences(ta, tb, max_dt)
+    hit = co[co["template_id"] == 17]
+    assert len(hit) >= 1 and np.any(np.abs(hit["sample_a"] - n_c) <= 2) and np.any(np.abs(hit["sample_b"] - n_c - 13) <= 2)
+    n_valid = n - u0.info().latency_samples
+    x1 = oracle.lloid_snr(bank, d1)
+    oa = oracle.triggers(x, int(spec.top_rate_hz), 6.0, n_valid)
+    ob = oracle.triggers(x1, int(spec.top_rate_hz), 6.0, n_valid)
+    ref = oracle.coincidences([t[0] for t in oa], [t[1] for t in oa], [t[3] for t in oa],
+                              [t[0] for t in ob], [t[1] for t in ob], [t[3] for t in ob], max_dt)
+    want = {(r[0], r[3], r[4]) for r in ref}
+    got = {(int(r["template_id"]), int(r["sample_a"]), int(r["sample_b"])) for r in co}
+    print(f"coincidences: {len(got)} on the device's triggers, {len(want)} on the oracle's")
+    assert any(t == 17 and abs(sa - n_c) <= 2 and abs(sb - n_c - 13) <= 2 for t, sa, sb in want)
+    assert want == got
+
+
 def test_streaming_is_bitwise_independent_of_buffer_sizes(lloid, small_case):
     spec, h, bank, d, x = small_case
     runs = []
