@@ -34,13 +34,23 @@ __global__ void __launch_bounds__(256) refine_flag_kernel(const RefUnit *__restr
                                                           int cand_cap) {
     griddep_wait();
     const RefUnit &u = units[blockIdx.y];
-    const int64_t total = (int64_t)u.M * u.n_rec;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+    // one warp per (template, window of this push); a window without a record above the refine
+    // threshold has a zero maximum and no candidate, so only its maximum is read
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (gw >= (int64_t)u.M * u.n_wslot) return;
+    const int i = (int)(gw / u.n_wslot), sl = (int)(gw % u.n_wslot);
+    const uint32_t wbits = u.wmax[gw];
+    if (wbits == 0u) return;
+    const float wm = __uint_as_float(wbits);
+    const int64_t w = u.win0 + sl;
+    const int64_t start = max(u.first_n, (int64_t)0), end = u.first_n + u.B;
+    const int64_t lo = max(w * u.win_len, start) - u.first_n, hi = min((w + 1) * u.win_len, end) - u.first_n;
+    const int r0 = (int)(lo / 128) * 2, r1 = min((int)((hi - 1) / 128) * 2 + 2, u.n_rec);
+    for (int r = r0 + lane; r < r1; r += 32) {
+        const int64_t idx = (int64_t)i * u.n_rec + r;
         const WinPart p = u.part[idx];
-        if (!(p.mag2 > u.thr2)) continue;
-        const int i = (int)(idx / u.n_rec);
-        const float wm = __uint_as_float(u.wmax[(int64_t)i * u.n_wslot + ((u.first_n + p.nr) / u.win_len - u.win0)]);
+        if (!(p.mag2 > u.thr2) || (u.first_n + p.nr) / u.win_len != w) continue;
         if (p.mag2 < u.keep2 * wm) continue;
         const int slot = atomicAdd(&counters[1], 1);
         if (slot < cand_cap) cands[slot] = RefCand{(int)blockIdx.y, idx};
@@ -245,10 +255,10 @@ __global__ void __launch_bounds__(kRefWarps * 32) refine_candidate_kernel(const 
     }
 }
 
-cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_records, RefCand *cands, int *counters,
+cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_windows, RefCand *cands, int *counters,
                           unsigned long long *cum, const Halfband &g, cudaStream_t s) {
-    if (n_units == 0) return cudaSuccess;
-    const int fb = (int)std::min<int64_t>(1024, (max_records + 255) / 256);
+    if (n_units == 0 || max_windows == 0) return cudaSuccess;
+    const int fb = (int)((max_windows + 7) / 8);                  // one warp per (template, window)
     // the window maxima were gathered by the top level's mixing epilogue
     cudaError_t e = launch_pdl(refine_flag_kernel, dim3(fb, n_units), dim3(256), 0, s, d_units, cands, counters,
                                kRefCandCap);

@@ -96,6 +96,25 @@ __global__ void __launch_bounds__(256) copy_kernel(const CopyTask *__restrict__ 
     t.dst[row * t.ld_dst + i] = v;
 }
 
+// 16-bit history shifts (the stored y_k of the tensor-core modes): one warp per row, each
+// instruction moving 32 consecutive columns (rows are a few dozen to a few hundred columns long).
+__global__ void __launch_bounds__(256) copy16_kernel(const CopyTask *__restrict__ tasks) {
+    griddep_wait();
+    const CopyTask t = tasks[blockIdx.y];
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= t.rows) return;
+    const uint16_t *hist = reinterpret_cast<const uint16_t *>(t.hist);
+    const uint16_t *cur = reinterpret_cast<const uint16_t *>(t.cur);
+    uint16_t *dst = reinterpret_cast<uint16_t *>(t.dst);
+    for (int part = 0; part < t.elem16; ++part) {
+        const int64_t r = row + (int64_t)part * t.rows;
+        for (int i = lane; i < t.n; i += 32) {
+            const int64_t pos = (int64_t)t.off + i;
+            dst[r * t.ld_dst + i] = pos < t.n_hist ? hist[r * t.ld_hist + pos] : cur[r * t.ld_cur + (pos - t.n_hist)];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FP32 tiled GEMM over a task list (64 x 128 tile, 256 threads, 4x8 per thread).
 // ---------------------------------------------------------------------------
@@ -260,6 +279,9 @@ __global__ void __launch_bounds__(256) win_finalize_kernel(const WinFinTask *__r
     const WinFinTask &t = tasks[find_task_by_warp(tasks, n_tasks, gw)];
     const int local = gw - t.warp_begin;
     const int i = local / t.n_win, s = local % t.n_win;
+    // a completed window that neither takes over nor hands on an open state, with no record above the
+    // (lower) refinement threshold, has no trigger
+    if (t.wmax && s > 0 && s < t.n_win - 1 && t.wmax[(int64_t)i * t.n_wslot + s] == 0u) return;
     const int64_t w = t.start_abs / t.win_len + s;
     const int64_t lo = max(w * t.win_len, t.start_abs) - t.first_n;        // push columns of window w
     const int64_t hi = min((w + 1) * t.win_len, t.end_abs) - t.first_n;
@@ -350,6 +372,11 @@ cudaError_t launch_upsample(const UpTask *d_tasks, int n_tasks, int max_rows, in
     if (n_tasks == 0 || max_out <= 0 || max_rows <= 0) return cudaSuccess;
     dim3 grid((max_out + kUpChunk - 1) / kUpChunk, max_rows, n_tasks);
     return launch_pdl(upsample_kernel, grid, dim3(256), 0, s, d_tasks, g);
+}
+
+cudaError_t launch_copy16(const CopyTask *d_tasks, int n_tasks, int max_rows, cudaStream_t s) {
+    if (n_tasks == 0 || max_rows <= 0) return cudaSuccess;
+    return launch_pdl(copy16_kernel, dim3((max_rows + 7) / 8, n_tasks), dim3(256), 0, s, d_tasks);
 }
 
 cudaError_t launch_copy(const CopyTask *d_tasks, int n_tasks, int max_rows, int max_n, cudaStream_t s) {

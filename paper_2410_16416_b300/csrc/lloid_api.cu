@@ -1436,7 +1436,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                                                       std::vector<std::vector<TcMixUpTask>>(kall + 1)};
     std::vector<WinFinTask> wfin;
     std::vector<RefUnit> refu;
-    int64_t ref_max_records = 0, ref_wmax_total = 0;
+    int64_t ref_max_windows = 0, ref_wmax_total = 0;
     std::vector<CopyTask> yshift1, yshift2;
     int kpad_max[NM] = {0, 0, 0};
     int max_hd = 0, max_hy = 0, max_rows = 0;
@@ -1662,7 +1662,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 r.sl_Q[si] = sd.Q;
                 r.sl_level[si] = sd.level;
             }
-            ref_max_records = std::max<int64_t>(ref_max_records, (int64_t)r.M * r.n_rec);
+            ref_max_windows = std::max<int64_t>(ref_max_windows, (int64_t)r.M * r.n_wslot);
             refu.push_back(r);
         }
         if (end > start && u->tc) {
@@ -1680,6 +1680,11 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             w.M = u->M;
             w.n_win = (int32_t)((end - 1) / u->win_len - start / u->win_len + 1);
             w.threshold = u->thr;
+            // the refinement's window maxima cover every possible trigger when its threshold is lower
+            if (refine_here && u->refine_thr < u->thr * (1.0f - 1e-6f)) {
+                w.n_wslot = n_wslot;
+                w.wmax = reinterpret_cast<const uint32_t *>(wmax_off + 1);   // offset + 1; the base is added at packing
+            }
             wfin.push_back(w);
             trig_need += (int64_t)u->M * w.n_win;
         } else if (end > start) {
@@ -1774,6 +1779,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             CK(cudaMalloc(&c->ref_wmax, c->ref_wmax_cap * sizeof(uint32_t)));
         }
         for (auto &r : refu) r.wmax = c->ref_wmax + reinterpret_cast<intptr_t>(r.wmax);   // offset -> address
+        for (auto &w : wfin)
+            if (w.wmax) w.wmax = c->ref_wmax + (reinterpret_cast<intptr_t>(w.wmax) - 1);
         for (int h = 0; h < NM; ++h)
             for (auto &m : tmix[h][0])
                 if (m.wmax) m.wmax = c->ref_wmax + (reinterpret_cast<intptr_t>(m.wmax) - 1);
@@ -1917,7 +1924,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
         if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
                  *n = 2;
-                 return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_records, c->ref_cands,
+                 return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_windows, c->ref_cands,
                                       c->ref_counters, c->ref_cum, c->g, st);
              })))
             return rc;
@@ -1936,9 +1943,9 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
              *n = (ycopy.empty() ? 0 : 1) + (yshift1.empty() ? 0 : 1) + (yshift2.empty() ? 0 : 1);
              cudaError_t e = launch_copy((CopyTask *)(D + o_ycopy), (int)ycopy.size(), max_rows, max_hy, st);
              if (e != cudaSuccess) return e;
-             e = launch_copy((CopyTask *)(D + o_ys1), (int)yshift1.size(), max_rows, max_hy, st);
+             e = launch_copy16((CopyTask *)(D + o_ys1), (int)yshift1.size(), max_rows, st);
              if (e != cudaSuccess) return e;
-             return launch_copy((CopyTask *)(D + o_ys2), (int)yshift2.size(), max_rows, max_hy, st);
+             return launch_copy16((CopyTask *)(D + o_ys2), (int)yshift2.size(), max_rows, st);
          })))
         return rc;
     // 8. triggers to the host (count plus an eager prefix; the rest on demand)

@@ -257,7 +257,10 @@ struct WinFinTask {
     int32_t n_rec, M, n_win;
     int32_t warp_begin;
     float threshold;
-    int32_t pad;
+    int32_t n_wslot;           // with wmax: window slots of this push (window start_abs / win_len + s)
+    const uint32_t *wmax;      // null, or [M][n_wslot] maxima of the records above a threshold below
+                               // `threshold` (16-bit |rho|^2 bits): a completed window in the middle of
+                               // the push with a zero maximum cannot trigger and is skipped
 };
 
 size_t tc_fir_smem_bytes(int kpad_max, int mode);
@@ -322,7 +325,8 @@ struct RefCand {                         // one partial record to refine
 };
 // cands: kRefCandCap entries; counters[1] = candidates found, counters[2] = 1 when some were dropped
 // cum: running totals [candidates, pushes with dropped candidates] (device, never reset)
-cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_records, RefCand *cands, int *counters,
+// max_windows: the largest M x n_wslot of the units (one candidate-scan warp per template and window)
+cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_windows, RefCand *cands, int *counters,
                           unsigned long long *cum, const Halfband &g, cudaStream_t s);
 // Margin of the candidate rule per operand mode: records within (1 - margin) of their window's
 // 16-bit maximum are refined (the 16-bit error stays well inside it).
@@ -335,6 +339,8 @@ cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, 
 cudaError_t launch_upsample(const UpTask *d_tasks, int n_tasks, int max_rows, int max_out,
                             const Halfband &g, cudaStream_t s);
 cudaError_t launch_copy(const CopyTask *d_tasks, int n_tasks, int max_rows, int max_n, cudaStream_t s);
+// 16-bit tasks only (elem16 > 0): one warp per row
+cudaError_t launch_copy16(const CopyTask *d_tasks, int n_tasks, int max_rows, cudaStream_t s);
 cudaError_t launch_gemm_fp32(const GemmTask *d_tasks, int n_tasks, int total_tiles, cudaStream_t s);
 cudaError_t launch_window_max(const WinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                               cudaStream_t s);
