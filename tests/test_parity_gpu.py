@@ -141,13 +141,14 @@ def test_two_detector_coincidence_of_an_injection(lloid, small_case):
         ctx.push_group([u0, u1], [d[t:t + 8192], d1[t:t + 8192]], [t, t], False)
     ctx.sync()
     trig = ctx.pop_triggers()
+    id0, id1, lat = u0.info().unit, u1.info().unit, u0.info().latency_samples
     ctx.close()
-    ta, tb = trig[trig["unit"] == u0.info().unit], trig[trig["unit"] == u1.info().unit]
+    ta, tb = trig[trig["unit"] == id0], trig[trig["unit"] == id1]
     max_dt = int(np.ceil(0.010 * spec.top_rate_hz)) + 2          # 10 ms of light travel + 2 samples
     co = lloid.coincidences(ta, tb, max_dt)
     hit = co[co["template_id"] == 17]
     assert len(hit) >= 1 and np.any(np.abs(hit["sample_a"] - n_c) <= 2) and np.any(np.abs(hit["sample_b"] - n_c - 13) <= 2)
-    n_valid = n - u0.info().latency_samples
+    n_valid = n - lat
     x1 = oracle.lloid_snr(bank, d1)
     oa = oracle.triggers(x, int(spec.top_rate_hz), 6.0, n_valid)
     ob = oracle.triggers(x1, int(spec.top_rate_hz), 6.0, n_valid)
