@@ -230,24 +230,27 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
 // into one TMEM tile:
 //   D[a][m] = sum_l M[a][l] O[m][l] + sum_i y_{k+1}[a][i] U[m][i]
 // (TMEM lanes = filters, columns = time; U[m][i] = 2 g[m - 2i] is the banded
-// halfband interpolator, Eq. 6).  The interpolation operands keep FP32
-// accuracy by a two-term BF16 split: y = y_hi + y_lo and U = U_hi + U_lo, and
-// D takes y_hi U_hi + y_hi U_lo + y_lo U_hi (the y_lo U_lo term is below 2^-16
-// of the result).  Every level stores its y in that split form for the next
-// finer level, so no conversion happens on the read side.
+// halfband interpolator, Eq. 6).  U is split into two terms U = U_hi + U_lo.
+// BF16 and E4M3 modes store y as one FP16 plane and D takes y U_hi + y U_lo;
+// FP16 mode stores y = y_hi + y_lo (BF16) and D takes y_hi U_hi + y_hi U_lo +
+// y_lo U_hi (the y_lo U_lo term is below 2^-16 of the result).  Every level
+// stores its y in the form the next finer level reads, so no conversion
+// happens on the read side.
 //
-// Tile = 128 filters x 256 samples, cut into four 64-sample blocks; block j
-// reads coarser samples [32 j, 32 j + 80) of the tile's window, and U is the
-// same 64 x 80 matrix for every block (one of 16 variants: the parity of the
-// tile's first sample and the window's offset inside its 16-byte-aligned
-// start).  Persistent CTAs (one per SM), warp roles:
-//   warp 0      TMA producer: mixing chunks (stage buffer), the tile's U
-//               variant (bulk copy, ring of 2) and its three window chunks of
-//               64 coarser samples, hi and lo (ring of n_win);
+// Tile = 128 filters x 256 samples.  Stored levels cut it into four 64-sample
+// blocks (block j reads coarser samples [32 j, 32 j + 80) of the tile's
+// window, U is one 64 x 80 matrix); the top level into two 128-sample blocks
+// (U is 128 x 112).  U is one of 16 variants: the parity of the tile's first
+// sample and the window's offset inside its 16-byte-aligned start.
+// Persistent CTAs (one per SM), warp roles:
+//   warp 0      TMA producer: mixing chunks (stage ring), the tile's U
+//               variant (bulk copy, ring of n_u) and its three window chunks
+//               of 64 coarser samples, one or two planes (ring of n_win);
 //   warp 1      MMA issuer into one of two TMEM accumulators (256 columns each);
 //   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) for half tile
 //               (w / 4 - 1); at the top level it reduces |rho|^2 into
-//               per-window partial maxima, below it stores y (hi / lo) by TMA.
+//               per-window partial maxima, below it stores y through a
+//               swizzled staging buffer with coalesced 16-byte stores.
 // ---------------------------------------------------------------------------
 constexpr int kMixRows = 128;                            // filters per tile (MMA M)
 constexpr int kMixCols = 256;                            // time samples per tile (MMA N)

@@ -180,7 +180,7 @@ struct sb_ctx {
     uint32_t *ref_wmax = nullptr;     // per (unit, template, window) 16-bit maxima of one push
     unsigned long long *ref_cum = nullptr;   // running [candidates, pushes with dropped candidates]
     int64_t ref_wmax_cap = 0;
-    void *utab = nullptr;      // tensor-core interpolation operand table (16 variants of U, BF16 hi / lo)
+    void *utab = nullptr;      // tensor-core interpolation operand table (16 variants of U as hi / lo terms)
     int *ref_counters = nullptr;
     // CUDA-graph pushes: one executable graph per group shape, updated in place
     bool graphs = false;

@@ -218,11 +218,12 @@ static_assert(sizeof(WinPart) == 32 && alignof(WinPart) == 16, "window records: 
 struct TcMixUpTask {
     const CUtensorMap *mapM;   // A: mixing [2M x Lk_pad] 16-bit, box 64 x 128 (unused when Lk_pad = 0)
     const CUtensorMap *mapO;   // B: basis outputs [rows x Lk_pad] 16-bit, box 64 x 256
-    const CUtensorMap *mapY;   // coarser level y_{k+1} as BF16 hi rows [0, 2M) and lo rows [2M, 4M),
-                               // box 64 x 128, 128-byte swizzle; null at the deepest level
+    const CUtensorMap *mapY;   // coarser level y_{k+1}: FP16 rows [0, 2M) (BF16 / E4M3 modes) or BF16 hi
+                               // rows [0, 2M) and lo rows [2M, 4M) (FP16 mode); box 64 x 128, 128-byte
+                               // swizzle; null at the deepest level
     float *Y;                  // top level with SB_FLAG_KEEP_SNR: FP32 SNR (row a at Y + a ldy); else null
     int64_t ldy;
-    uint16_t *Yh;              // this level's y as BF16 hi rows [0, 2M), lo rows [2M, 4M) (ld ldu); null at the top
+    uint16_t *Yh;              // this level's y in the layout of mapY (ld ldu); null at the top
     int64_t ldu;
     int64_t yst_col0;          // column of this push's first sample in Yh
     WinPart *part;             // top level: partials [i][n_rec], record (tt*2 + half)*2 + seg; null below
