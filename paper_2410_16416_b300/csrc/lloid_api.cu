@@ -749,6 +749,16 @@ static int validate_desc(const sb_desc *d, std::vector<int> &lvl, Plan &P) {
                                    std::to_string(kRefMaxSlices) + " slices");
     if (d->max_push_samples % (1LL << P.kmax))
         return fail(SB_EINVAL, "max_push_samples must be a multiple of 2^k_max");
+    if (d->autocorr)                          // xi^2 lag profiles: finite, lag 0 equal to 1
+        for (int i = 0; i < d->n_templates; ++i)
+            for (int j = 0; j < kXiLags; ++j) {
+                const double re = d->autocorr[((size_t)i * kXiLags + j) * 2];
+                const double im = d->autocorr[((size_t)i * kXiLags + j) * 2 + 1];
+                if (!std::isfinite(re) || !std::isfinite(im) ||
+                    (j == kXiJ && std::fabs(re - 1.0) + std::fabs(im) > 1e-6))
+                    return fail(SB_EINVAL, "autocorr of template " + std::to_string(i) +
+                                               " is not finite or its lag 0 is not 1");
+            }
     return SB_OK;
 }
 
@@ -962,15 +972,9 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
     if (cudaMemcpy(u->tids, ids.data(), u->M * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         return cleanup(fail(SB_ECUDA, "template id upload"));
     if (d->autocorr) {                        // xi^2 lag profiles, FP32 on the device
-        std::vector<float2> ac((size_t)u->M * kXiLags);
-        for (int i = 0; i < u->M; ++i)
-            for (int j = 0; j < kXiLags; ++j) {
-                const double re = d->autocorr[((size_t)i * kXiLags + j) * 2], im = d->autocorr[((size_t)i * kXiLags + j) * 2 + 1];
-                if (!std::isfinite(re) || !std::isfinite(im) || (j == kXiJ && std::fabs(re - 1.0) + std::fabs(im) > 1e-6))
-                    return cleanup(fail(SB_EINVAL, "autocorr of template " + std::to_string(i) +
-                                                       " is not finite or its lag 0 is not 1"));
-                ac[(size_t)i * kXiLags + j] = make_float2((float)re, (float)im);
-            }
+        std::vector<float2> ac((size_t)u->M * kXiLags);          // checked by validate_desc
+        for (size_t e = 0; e < ac.size(); ++e)
+            ac[e] = make_float2((float)d->autocorr[2 * e], (float)d->autocorr[2 * e + 1]);
         if ((rc = dev_alloc_w(u, (void **)&u->acorr, ac.size() * sizeof(float2)))) return cleanup(rc);
         if (cudaMemcpy(u->acorr, ac.data(), ac.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(fail(SB_ECUDA, "autocorrelation upload"));

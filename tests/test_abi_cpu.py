@@ -169,3 +169,23 @@ def test_coincidences_arguments_and_overflow():
     assert lloid.lib.sb_coincidences(None, 3, tb.ctypes.data, 3, 5, out.ctypes.data, 2, C.byref(n)) == lloid.SB_EINVAL
     assert lloid.lib.sb_coincidences(None, 0, None, 0, 5, None, 0, C.byref(n)) == lloid.SB_OK and n.value == 0
     assert len(lloid.coincidences(ta, tb, 100)) == 5
+
+
+def test_plan_checks_the_xi2_lag_profiles():
+    """svdbank_plan (no device) accepts the oracle's autocorrelation and rejects one whose lag 0 is
+    not 1 or that is not finite; a wrong shape is refused by the binding."""
+    spec = synth.SMALL_BIN
+    h, _ = synth.template_bank(4, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 5, 0, 0)
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    R = oracle.autocorrelation(h, lloid.SB_XI2_HALF)
+    lloid.plan(bank, max_push_samples=4096, autocorr=R)
+    bad = R.copy()
+    bad[2, lloid.SB_XI2_HALF] = 0.9
+    with pytest.raises(lloid.LloidError):
+        lloid.plan(bank, max_push_samples=4096, autocorr=bad)
+    bad = R.copy()
+    bad[1, 3] = np.nan
+    with pytest.raises(lloid.LloidError):
+        lloid.plan(bank, max_push_samples=4096, autocorr=bad)
+    with pytest.raises(ValueError):
+        lloid.plan(bank, max_push_samples=4096, autocorr=R[:, :5])
