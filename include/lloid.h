@@ -119,7 +119,10 @@ typedef struct sb_desc {
  * sample, sample + 1: |SNR| snr_peak at time sample + dt_peak (in samples,
  * |dt_peak| <= 1/2).  It is set where both neighbours are computed in FP32 in
  * the same pass (FP32 mode: inside one push; 16/8-bit modes: refined maxima)
- * and the sample is a local maximum; otherwise snr_peak = snr, dt_peak = 0. */
+ * and the sample is a local maximum; otherwise snr_peak = snr, dt_peak = 0.
+ * With SB_TRIG_XI2 set (the bank carries sb_desc.autocorr and the lags
+ * sample - 16 .. sample + 16 were computed in FP32 in the same pass), xi2 is
+ * the signal-consistency value defined at sb_desc.autocorr.                   */
 typedef struct sb_trigger {
     int64_t unit;
     int64_t template_id;
