@@ -108,12 +108,11 @@ typedef struct sb_desc {
     const double *autocorr;
 } sb_desc;
 
-/* One trigger: the |rho| maximum of one template in one window (Sec. II.A).
- * sample = absolute top-rate index n* of the maximum (first one on ties),
- * window = n* / (window_s * f0), snr = |rho(n*)|,
- * phase = atan2(x_{2i+1}(n*), x_{2i}(n*)) in radians.                        */
 /* One trigger: the |SNR| maximum of one template in one window (Sec. II.A: a
- * template, a time, an SNR and a phase).  With SB_TRIG_SUBSAMPLE set, the
+ * template, a time, an SNR and a phase).  sample = absolute top-rate index n*
+ * of the maximum (first one on ties), window = n* / (window_s * f0),
+ * snr = |rho(n*)|, phase = atan2(x_{2i+1}(n*), x_{2i}(n*)) in radians.
+ * With SB_TRIG_SUBSAMPLE set, the
  * peak between samples (the future feature named in Sec. III for the SNR gap
  * to GstLAL) is the vertex of the parabola through |rho|^2 at sample - 1,
  * sample, sample + 1: |SNR| snr_peak at time sample + dt_peak (in samples,
@@ -168,6 +167,13 @@ int sb_ctx_sync(sb_ctx *ctx);
  * device state (zeroed histories) and admits it against the budget.
  * Returns SB_EBUSY (nothing allocated) when the budget cannot hold it. */
 int svdbank_create(sb_ctx *ctx, const sb_desc *desc, int32_t detector, sb_unit **out);
+/* Release one unit (Sec. IV: one SVD bank per instrument, so one unit per
+ * (bank, detector) pair).  The unit's device state is freed in stream order,
+ * after every push already queued on the context's stream (the call does not
+ * block), and its bytes return to the context's budget; bank data shared
+ * through svdbank_create_like is freed with the last unit that uses it.
+ * Triggers the unit already produced stay in the queue.  NULL is a no-op
+ * (SB_OK); the pointer is invalid after the call. */
 int svdbank_destroy(sb_unit *unit);
 
 /* A new unit that filters with the same SVD bank as src (same precision,
@@ -185,7 +191,10 @@ int sb_unit_query(const sb_unit *unit, sb_unit_info *info);
  * *info that need a live unit (unit, samples_pushed) are set to 0. */
 int svdbank_plan(const sb_desc *desc, sb_unit_info *info);
 
-/* Push the next n_samples top-rate samples of whitened strain to one unit.
+/* Push the next n_samples top-rate samples of whitened strain to one unit:
+ * the filtering stage of Sec. II.A (down-sample, cross-correlate with the
+ * orthogonal basis, multiply by the SVD coefficients, up-sample and sum), run
+ * with the device-side trigger generator of Sec. II.B on its output.
  * strain: host pointer (on_device = 0) or device pointer (on_device = 1),
  * FP32, contiguous.  t0_sample must equal the unit's samples pushed so far
  * (SB_EGAP otherwise); n_samples must be a multiple of 2^k_max and at most
@@ -210,7 +219,9 @@ int filter_push_group(sb_ctx *ctx, int32_t n_units, sb_unit *const *units,
  * when *completed > i. */
 int sb_ctx_progress(sb_ctx *ctx, int64_t *pushed, int64_t *completed);
 
-/* Move up to cap finished triggers into out (never blocks on queued work).
+/* Move up to cap finished triggers into out (never blocks on queued work):
+ * the hand-off of the trigger generator that runs on the device (Sec. II.B),
+ * so that only triggers, never SNR series, cross to the host.
  * *n_out = number written.  Triggers come out push by push, and within a push
  * sorted by (window, unit, template).  Returns SB_EOVERFLOW once if triggers
  * were dropped because a push produced more than its buffer holds. */
@@ -318,16 +329,22 @@ int sb_ctx_stage_times(sb_ctx *ctx, double *ms, int64_t *launches, int32_t n_sta
  * [max(0, first_sample), first_sample + n_samples) gives its |rho| maximum
  * (first sample on ties); a trigger (unit = -1, template_id from the device
  * array template_ids or i when NULL) is written to the device array out when
- * |rho| > threshold.  out_count: device int32[2] = {triggers, overflow flag},
- * zeroed by the call; at most cap triggers are stored.  Work is queued on
- * stream (a cudaStream_t; NULL = legacy default stream) and nothing blocks.
+ * |rho| > threshold.  out_count: device int32[2] = {triggers stored, overflow
+ * flag}, zeroed by the call; at most cap triggers are stored, out_count[0]
+ * never exceeds cap, and out_count[1] = 1 when more windows qualified than
+ * cap (which ones were kept is then unspecified).  Work is queued on stream
+ * (a cudaStream_t; NULL = legacy default stream) and nothing blocks.
  * Scratch: a fixed device array of 2^18 partial records (8 MiB) that every
  * GPU loading this library holds until the process exits; a call needs
  * 2 * M * ceil(n_samples / 256) records and returns SB_EINVAL (see
  * sb_last_error) beyond that, or when window_len < 256.  The first call on a
- * device looks up the array's device address (make that first call before any
- * stream capture).  All calls share the array: calls that overlap on the GPU
- * (other streams, other threads) race; serialise them. */
+ * device looks up the array's device address; with CUDA's lazy module loading
+ * (the default) that lookup may load the library's device module, which can
+ * allocate device memory, so make the first call on each device before the
+ * phase in which nothing may allocate, and before any stream capture.  The
+ * looked-up address is cached per device ordinal and is no longer valid after
+ * cudaDeviceReset on that device.  All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race; serialise them. */
 int sb_window_triggers_noalloc(const float *x, int64_t ldx, int32_t n_templates, int64_t n_samples,
                                int64_t first_sample, int64_t window_len, float threshold,
                                const int64_t *template_ids, sb_trigger *out, int32_t *out_count, int32_t cap,

@@ -8,9 +8,9 @@
 // off when all M templates are filtered; for a handful of candidates it does
 // not, so the refinement filters the
 // strain directly with each template's reconstructed slice filters
-// H_s = M_s V_s (Eq. 4 summed over the basis, FP32, built once per bank):
+// H_s = M_s V_s (step a3's mixing summed over the basis, FP32, built once per bank):
 //   z_k[row][m] = sum_{slices s at level k} sum_q H_s[2i+row][q] d_k[m - D_s - q]
-// plus the x2 interpolation of z_{k+1} (Eq. 6), level by level from the coarsest.
+// plus the x2 interpolation of z_{k+1} (step a4), level by level from the coarsest.
 // That is the same sum as the basis path in exact arithmetic; per candidate it
 // costs 2 x sum_s Q_s x (<= 64) multiply-adds instead of a full basis output.
 //

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
 // into one TMEM tile:
 //   D[a][m] = sum_l M[a][l] O[m][l] + sum_i y_{k+1}[a][i] U[m][i]
 // (TMEM lanes = filters, columns = time; U[m][i] = 2 g[m - 2i] is the banded
-// halfband interpolator, Eq. 6).  U is split into two terms U = U_hi + U_lo.
+// halfband interpolator of step a4).  U is split into two terms U = U_hi + U_lo.
 // BF16 and E4M3 modes store y as one FP16 plane and D takes y U_hi + y U_lo;
 // FP16 mode stores y = y_hi + y_lo (BF16) and D takes y_hi U_hi + y_hi U_lo +
 // y_lo U_hi (the y_lo U_lo term is below 2^-16 of the result).  Every level

@@ -603,7 +603,7 @@ static int upload_map(sb_unit *u, const CUtensorMap &h, CUtensorMap **dev, bool 
 }
 
 // The refinement's filters: H_s = M_s V_s, each template's two real FP32
-// filters of slice s (Eq. 4 summed over the basis), one FP32 GEMM on the device
+// filters of slice s (step a3's mixing summed over the basis, Sec. II.A), one FP32 GEMM on the device
 // at create time; [2M][ldh] rows, ldh = Q rounded up to 4.
 static int build_refine_filters(sb_unit *u, SliceDev &sd, const sb_slice &sl) {
     const int64_t M2 = 2 * (int64_t)u->M;
