@@ -17,5 +17,5 @@ the exact parabola of numpy.polyfit and a fractional-delay injection.
 from .resample import bessel_i0, decimate, halfband, kaiser, upsample
 from .coinc import coincidences
 from .svdbank import OracleBank, OracleSlice, bank_from_arrays, build_bank, slice_filters, truncated_svd
-from .lloid import (autocorrelation, causal_correlate, complex_snr, decimation_cascade, direct_snr,
-                    lloid_levels, lloid_snr, subsample_peak, triggers, window_maxima, xi2)
+from .lloid import (autocorrelation, basis_outputs, causal_correlate, complex_snr, decimation_cascade, direct_snr,
+                    lloid_levels, lloid_snr, mix_and_sum, subsample_peak, triggers, window_maxima, xi2)

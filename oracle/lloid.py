@@ -80,19 +80,28 @@ def lloid_levels(bank: OracleBank, strain: np.ndarray, g: np.ndarray = None) -> 
     """y^(k) [2M, n/2^k] for every level k (steps a1-a4); y^(0) is the top-rate SNR x."""
     if g is None:
         g = halfband()
-    k_max = bank.k_max
     n = strain.shape[0]
-    if n % (2 ** k_max):
+    if n % (2 ** bank.k_max):
         raise ValueError("strain length must be a multiple of 2^k_max")
-    levels = decimation_cascade(strain, k_max, g)
-    o = basis_outputs(bank, levels)
+    levels = decimation_cascade(strain, bank.k_max, g)
+    return mix_and_sum(bank, basis_outputs(bank, levels), n, g)
+
+
+def mix_and_sum(bank: OracleBank, o: List[np.ndarray], n: int, g: np.ndarray = None,
+                rows: np.ndarray = None) -> Dict[int, np.ndarray]:
+    """Steps a3-a4 from the basis outputs o (one [L_s, n/2^k_s] array per slice): y^(k) for
+    every level, for the real filters `rows` (default: all 2M, in order)."""
+    if g is None:
+        g = halfband()
+    k_max = bank.k_max
     c_by_level: Dict[int, np.ndarray] = {}
     for s, os_ in zip(bank.slices, o):
-        c = s.mixing @ os_
+        mix = s.mixing if rows is None else s.mixing[rows]
+        c = mix @ os_
         c_by_level[s.level] = c_by_level.get(s.level, 0.0) + c
-    twoM = 2 * bank.n_templates
+    n_rows = 2 * bank.n_templates if rows is None else len(rows)
     y: Dict[int, np.ndarray] = {}
-    y[k_max] = c_by_level.get(k_max, np.zeros((twoM, n >> k_max)))
+    y[k_max] = c_by_level.get(k_max, np.zeros((n_rows, n >> k_max)))
     for k in range(k_max, 0, -1):
         y[k - 1] = upsample(y[k], g) + c_by_level.get(k - 1, 0.0)
     return y

@@ -99,9 +99,3 @@ def bank_from_arrays(n_templates: int, top_rate_hz: float, slices: Sequence) -> 
                                np.asarray(sp.basis, dtype=np.float64),
                                np.asarray(sp.mixing, dtype=np.float64), np.zeros(0)))
     return OracleBank(n_templates, top_rate_hz, out)
-
-
-def reconstructed_filters(bank: OracleBank, slice_index: int) -> np.ndarray:
-    """M_s V_s: the rank-L_s approximation of H_s."""
-    s = bank.slices[slice_index]
-    return s.mixing @ s.basis

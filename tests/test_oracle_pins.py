@@ -125,6 +125,22 @@ def test_p3_full_rate_untruncated_equals_direct():
 
 
 # ---------------------------------------------------------------- P4 resampler
+def test_p3_row_subsets_are_independent(cfg_small):
+    """mix_and_sum for a subset of the real filters returns exactly those rows of the full
+    computation (each filter's SNR depends only on its own mixing row)."""
+    spec, h = cfg_small
+    bank = oracle.build_bank(h, spec.top_rate_hz, spec.slices)
+    d = synth.white_noise(10 * 2048, 91, 0, 0).astype(np.float64)
+    g = oracle.halfband()
+    o = oracle.basis_outputs(bank, oracle.decimation_cascade(d, bank.k_max, g))
+    full = oracle.mix_and_sum(bank, o, d.shape[0], g)
+    rows = np.array([5, 6, 20, 21, 31])
+    sub = oracle.mix_and_sum(bank, o, d.shape[0], g, rows)
+    for k in full:
+        assert np.array_equal(sub[k], full[k][rows])
+    assert np.allclose(full[0], oracle.lloid_snr(bank, d), rtol=0, atol=1e-12)
+
+
 def test_p4_halfband_structure():
     g = oracle.halfband()
     K2 = 2 * HALF_K
