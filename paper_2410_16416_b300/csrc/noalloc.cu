@@ -9,6 +9,7 @@
 // device or fail.  It passes its own input and output buffers; the scratch
 // lives in the static array below, which every GPU that loads this library
 // holds until the process exits.
+#include <cstddef>
 #include <mutex>
 #include <string>
 
@@ -22,6 +23,19 @@ constexpr int64_t kNoAllocRecords = int64_t(1) << 18;      // 262144 records x 3
 constexpr int kNoAllocChunk = 256;
 
 static __device__ __align__(256) WinPart g_noalloc_scratch[kNoAllocRecords];
+
+// The merge kernel writes sb_trigger records through DevTrigger.
+static_assert(sizeof(DevTrigger) == sizeof(sb_trigger), "DevTrigger and sb_trigger differ in size");
+static_assert(offsetof(DevTrigger, template_id) == offsetof(sb_trigger, template_id) &&
+                  offsetof(DevTrigger, sample) == offsetof(sb_trigger, sample) &&
+                  offsetof(DevTrigger, window) == offsetof(sb_trigger, window) &&
+                  offsetof(DevTrigger, snr) == offsetof(sb_trigger, snr) &&
+                  offsetof(DevTrigger, phase) == offsetof(sb_trigger, phase) &&
+                  offsetof(DevTrigger, snr_peak) == offsetof(sb_trigger, snr_peak) &&
+                  offsetof(DevTrigger, dt_peak) == offsetof(sb_trigger, dt_peak) &&
+                  offsetof(DevTrigger, flags) == offsetof(sb_trigger, flags) &&
+                  offsetof(DevTrigger, xi2) == offsetof(sb_trigger, xi2),
+              "DevTrigger and sb_trigger differ in layout");
 
 // One warp per (template, chunk): the |rho|^2 maximum (first sample on ties) of
 // each of the (at most two) windows the chunk touches.  Records of samples
@@ -85,7 +99,13 @@ __global__ void __launch_bounds__(256) noalloc_merge_kernel(const WinPart *__res
     auto close = [&](int64_t w) {
         const bool whole = w * win_len >= start_abs && (w + 1) * win_len <= end_abs;
         if (!whole || bm < 0.0f || !(sqrtf(bm) > threshold)) return;
-        const int slot = atomicAdd(count, 1);
+        // claim a slot only while fewer than cap are taken, so count[0] never exceeds cap
+        int slot = *reinterpret_cast<volatile int32_t *>(count);
+        while (slot < cap) {
+            const int prev = atomicCAS(count, slot, slot + 1);
+            if (prev == slot) break;
+            slot = prev;
+        }
         if (slot >= cap) {
             atomicExch(count + 1, 1);
             return;
