@@ -1,21 +1,23 @@
-// Tensor-core (tcgen05, sm_103a) kernels of the two GEMM-shaped steps in the
-// 16-bit modes (SB_BF16, SB_FP16; FP32 accumulation in TMEM):
+// Tensor-core (tcgen05, sm_103a) kernels of the GEMM-shaped steps in the
+// reduced-precision modes (SB_BF16, SB_FP16, SB_FP8; FP32 accumulation in TMEM):
 //
-//  a2 basis FIR as a Hankel GEMM.  Output time m' = 8b + r (b = block of 8
-//     samples, r = phase).  With X[b][j] = x[X0 + 8b + j] the FIR is
-//         o[l][8b + r] = sum_j W[(l,r)][j] X[b][j],
-//         W[(l,r)][j]  = v[l][r + Q - 1 + phi - j]   (0 outside the taps),
+//  a2 basis FIR as a Hankel GEMM (tc_fir_kernel).  Output time m' = ph b + r
+//     (b = block of ph samples, r = phase; ph = 8 for 16-bit operands, 16 for
+//     E4M3).  With X[b][j] = x[X0 + ph b + j] the FIR is
+//         o[l][ph b + r] = sum_j W[(l,r)][j] X[b][j],
+//         W[(l,r)][j]    = v[l][r + Q - 1 + phi - j]   (0 outside the taps),
 //     so the data operand is a Hankel matrix whose rows start 16 bytes apart.
 //     A plain no-swizzle UMMA descriptor (core matrices 16 B apart along K,
 //     8-row groups 128 B apart) reads it straight from one strain window in
 //     shared memory: the strain is loaded once per tile, never expanded.  The
-//     8-phase weights W (8 L_s rows) are expanded once at bank creation and
-//     streamed by TMA with 128-byte swizzle.
-//  a3 mixing GEMM with time on the TMEM lanes: D[m][a] = sum_l O[m][l] M[a][l],
-//     so every epilogue store writes 32 consecutive time samples of one filter.
-//
-// One CTA = 4 warps: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, then
-// all four warps drain TMEM (each warp owns 32 TMEM lanes).
+//     ph-phase weights W are expanded once at bank creation and streamed by TMA
+//     with 128-byte swizzle.  In E4M3 the strain is two terms (hi + lo, one
+//     MMA each into the same accumulator) and the outputs are written in BF16.
+//     One CTA = 4 warps: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs,
+//     then all four warps drain TMEM (each warp owns 32 TMEM lanes).
+//  a3 + a4 (+ a5 partials) mixing GEMM and the x2 interpolation of the coarser
+//     level in one persistent warp-specialised kernel (tc_mixup_kernel,
+//     described at its definition), FP16 or BF16 operands.
 #include <cstring>
 #include <mutex>
 #include <set>
@@ -97,8 +99,20 @@ __global__ void __launch_bounds__(256) to_half_kernel(const HalfConvTask *__rest
         mul = amax > 0.0f ? 448.0f / amax : 1.0f;
         if (blockIdx.x == 0 && threadIdx.x == 0) t.amax_next[0] = 0.0f;   // reset for the next push
     }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = Op<MODE>::cvt(t.src[i] * mul);
+    if constexpr (MODE == kModeE4M3) {        // two terms: hi + lo carries about 7 significant bits
+        T *lo = reinterpret_cast<T *>(t.dst_lo);
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const float v = t.src[i] * mul;
+            const T h = Op<MODE>::cvt(v);
+            dst[i] = h;
+            lo[i] = Op<MODE>::cvt(v - static_cast<float>(h));
+        }
+    } else {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            dst[i] = Op<MODE>::cvt(t.src[i] * mul);
+    }
 }
 
 // |x| maximum of each task's source (E4M3 mode), as the bits of a non-negative float.
@@ -160,12 +174,16 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
     const uint32_t tmem = *tslot;
     griddep_wait();                                  // the prologue above overlaps the previous kernel's tail
     const int nk = t.Kpad / kKC;
+    // E4M3: the strain's second term sits right after the first (both windows a multiple of 16 bytes)
+    constexpr int kXTerms = MODE == kModeE4M3 ? 2 : 1;
+    const uint32_t wbytes = (uint32_t)(kTcN * kPh + t.Kpad) * kB;
 
     if (warp == 0 && lane == 0) {
         prefetch_tmap(t.mapW);
-        const uint32_t wbytes = (uint32_t)(kTcN * kPh + t.Kpad) * kB;
-        mbar_expect_tx(winb, wbytes);
-        bulk_load(win, reinterpret_cast<const uint8_t *>(t.x) + kB * (t.X0 + (int64_t)kPh * kTcN * nt), wbytes, winb);
+        const int64_t xoff = kB * (t.X0 + (int64_t)kPh * kTcN * nt);
+        mbar_expect_tx(winb, kXTerms * wbytes);
+        bulk_load(win, reinterpret_cast<const uint8_t *>(t.x) + xoff, wbytes, winb);
+        if (kXTerms == 2) bulk_load(win + wbytes, reinterpret_cast<const uint8_t *>(t.x_lo) + xoff, wbytes, winb);
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % kFirStages;
             if (kc >= kFirStages && !mbar_wait(&empty[s], ((kc / kFirStages) - 1) & 1, err, 1)) break;
@@ -183,9 +201,13 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
                 tc_fence_after();
                 const uint32_t aa = smem_u32(a_st + s * kFirStageBytes);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
+                for (int kk = 0; kk < 4; ++kk) {
                     mma_op<MODE>(tmem, desc_k_sw128(aa + kk * 32), desc_hankel(wa + kc * 128 + kk * 32), idesc,
                                  (kc | kk) != 0);
+                    if (kXTerms == 2)
+                        mma_op<MODE>(tmem, desc_k_sw128(aa + kk * 32), desc_hankel(wa + wbytes + kc * 128 + kk * 32),
+                                     idesc, 1u);
+                }
                 mma_commit(&empty[s]);
             }
             if (ok) mma_commit(accb);
@@ -200,9 +222,11 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
         const int R = warp * 32 + lane;
         const int r = R / lpt;
         const int col = t.o_col + mt * lpt + (R % lpt);
-        typename H::T *O = reinterpret_cast<typename H::T *>(t.O);
+        // basis outputs in the mixing kernel's operand type (E4M3 FIR: BF16)
+        using OT = typename Op<mix_mode(MODE)>::T;
+        OT *O = reinterpret_cast<OT *>(t.O);
         const int64_t m_base = (int64_t)kPh * kTcN * nt + r;
-        float oscale = 1.0f;                                 // E4M3: strain scale x basis/output scales
+        float oscale = 1.0f;                                 // E4M3: strain scale x basis-vector scale
         if (MODE == kModeE4M3) oscale = t.xamax[0] * (1.0f / 448.0f) * t.colscale[col];
 #pragma unroll 1
         for (int c0 = 0; c0 < kTcN; c0 += 32) {
@@ -212,7 +236,7 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int64_t m = m_base + kPh * (c0 + j);
-                if (m < t.Bk) O[m * t.ldo + col] = H::cvt(__uint_as_float(v[j]) * oscale);
+                if (m < t.Bk) O[m * t.ldo + col] = Op<mix_mode(MODE)>::cvt(__uint_as_float(v[j]) * oscale);
             }
         }
     }
@@ -231,7 +255,8 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
 //   D[a][m] = sum_l M[a][l] O[m][l] + sum_i y_{k+1}[a][i] U[m][i]
 // (TMEM lanes = filters, columns = time; U[m][i] = 2 g[m - 2i] is the banded
 // halfband interpolator of step a4).  U is split into two terms U = U_hi + U_lo.
-// BF16 and E4M3 modes store y as one FP16 plane and D takes y U_hi + y U_lo;
+// BF16 mode (also the mixing of SB_FP8 units) stores y as one FP16 plane and
+// D takes y U_hi + y U_lo;
 // FP16 mode stores y = y_hi + y_lo (BF16) and D takes y_hi U_hi + y_hi U_lo +
 // y_lo U_hi (the y_lo U_lo term is below 2^-16 of the result).  Every level
 // stores its y in the form the next finer level reads, so no conversion
@@ -271,8 +296,8 @@ struct UGeo {
 };
 constexpr int kUVariants = 16;                           // (parity, offset 0..7)
 // operand table: BF16 hi / lo terms of the 16 variants of the 64-wide blocks, then of the 128-wide
-// blocks; then the same two parts as FP16 hi / lo terms (one-plane FP16 y, BF16 mode); then FP16
-// hi / lo terms of U / kE4StoreScale (E4M3 mode)
+// blocks (FP16 mode, BF16 hi + lo y); then the same two parts as FP16 hi / lo terms (one-plane FP16
+// y, BF16 mode)
 constexpr size_t kUTab128 = (size_t)kUVariants * UGeo<64>::kVarBytes;
 constexpr size_t kUTabPart = kUTab128 + (size_t)kUVariants * UGeo<128>::kVarBytes;
 constexpr int kMixStPlane = 32 * 64;                     // store staging per plane: 32 filters x 32 samples
@@ -280,7 +305,7 @@ constexpr int kMixThreads = 384;
 constexpr int kMixMaxWin = 6;
 constexpr size_t kMixSmemMax = 227 * 1024;               // dynamic shared memory per CTA (opt-in maximum)
 
-size_t tc_interp_table_bytes() { return 3 * kUTabPart; }
+size_t tc_interp_table_bytes() { return 2 * kUTabPart; }
 
 // U for variant (par, rem): output c of a block takes coarser sample
 // i = rem + 16 + ((c + par) >> 1) (even c + par: weight 1 = 2 g[0]) or the
@@ -341,10 +366,9 @@ static void interp_table_part(const Halfband &g, uint16_t *out, bool f16, float 
 
 void tc_interp_table(const Halfband &g, void *host_out) {
     uint8_t *out = static_cast<uint8_t *>(host_out);
-    for (int f = 0; f < 3; ++f) {
-        const float gain = f == 2 ? 1.0f / kE4StoreScale : 1.0f;      // a power of two: exact
-        interp_table_part<64>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart), f >= 1, gain);
-        interp_table_part<128>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart + kUTab128), f >= 1, gain);
+    for (int f = 0; f < 2; ++f) {
+        interp_table_part<64>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart), f == 1, 1.0f);
+        interp_table_part<128>(g, reinterpret_cast<uint16_t *>(out + f * kUTabPart + kUTab128), f == 1, 1.0f);
     }
 }
 
@@ -411,7 +435,8 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     constexpr int NP = y_planes(MODE);                   // 1: FP16 y; 2: BF16 hi + lo
     constexpr int kWinBytes = NP * kWinHalfBytes;
     using G = UGeo<UB>;
-    utab += (NP == 2 ? 0 : MODE == kModeE4M3 ? 2 * kUTabPart : kUTabPart) + (UB == 128 ? kUTab128 : 0);
+    static_assert(MODE != kModeE4M3, "the mixing kernel runs in FP16 or BF16 (mix_mode)");
+    utab += (NP == 2 ? 0 : kUTabPart) + (UB == 128 ? kUTab128 : 0);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -617,13 +642,6 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
             const int M2 = t.M2;
             const int a = kMixRows * m.at + R;
             const bool row_ok = a < M2;
-            // E4M3: mixing-row scale of this level; the stored y is divided by the finer level's
-            float rsc = 1.0f, inv_next = 1.0f;
-            if (MODE == kModeE4M3 && row_ok) {
-                if (t.rscale) rsc = t.rscale[a];
-                if (t.rsc_next) inv_next = 1.0f / t.rsc_next[a];
-                inv_next *= kE4StoreScale;                   // the finer level's table carries the inverse
-            }
             // 128-wide interpolation blocks run only at the top level (trigger partials, no y stored);
             // 64-wide blocks only below it (y stored): each instantiation keeps only its own epilogue
             constexpr bool kTopKernel = UB == 128;
@@ -650,7 +668,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * kMixCols + c0, v);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]) * rsc;
+                    for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
                 }
                 const int64_t col0 = (int64_t)kMixCols * m.tt + c0;
                 const int64_t n0 = first_n + col0;
@@ -666,7 +684,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float y0 = x[2 * j] * inv_next, y1 = x[2 * j + 1] * inv_next;
+                        const float y0 = x[2 * j], y1 = x[2 * j + 1];
                         if constexpr (NP == 1) {
                             // saturate instead of overflowing to infinity (|SNR| > 65504)
                             const __half2 hv = __floats2half2_rn(fminf(fmaxf(y0, -65504.0f), 65504.0f),
@@ -799,8 +817,8 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
 // launchers
 // ---------------------------------------------------------------------------
 size_t tc_fir_smem_bytes(int kpad_max, int mode) {
-    const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2;
-    return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)(kTcN * ph + kpad_max) * by;
+    const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2, terms = mode == kModeE4M3 ? 2 : 1;
+    return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)terms * (kTcN * ph + kpad_max) * by;
 }
 size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk, int np) {
     const size_t uvar = ublk == 128 ? UGeo<128>::kVarBytes : UGeo<64>::kVarBytes;
@@ -961,7 +979,7 @@ cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_t
         return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune, s);
     if (mode == kModeF16)
         return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune, s);
-    return mixup_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune, s);
+    return cudaErrorInvalidValue;                        // E4M3 units mix in BF16 (mix_mode)
 }
 
 }  // namespace lloid

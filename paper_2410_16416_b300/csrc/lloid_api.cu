@@ -118,18 +118,17 @@ struct LevelDev {
     std::vector<int> slices;
     // tensor-core modes
     int Lk_pad = 0;           // padded width of the level's basis-output block
-    float *colscale = nullptr;   // E4M3: per output column, basis scale / output scale
-    float *rscale = nullptr;     // E4M3: per mixing row scale
+    float *colscale = nullptr;   // E4M3: per output column, the basis vector's scale
     float *amax = nullptr;       // E4M3: |strain| maximum accumulators [2] (state)
-    void *x16 = nullptr;      // 16-bit copy of the decimated strain (+ window slack)
-    int64_t x16_len = 0;
+    void *x16 = nullptr;      // 16-bit (E4M3: two 8-bit terms) copy of the decimated strain (+ window slack)
+    int64_t x16_len = 0;      // elements per term; E4M3: the second term starts x16_len bytes after x16
     void *O16 = nullptr;      // basis outputs [Bk_max x Lk_pad], time-major
     void *M16 = nullptr;      // stacked mixing [2M x Lk_pad]
     CUtensorMap *mapO = nullptr, *mapM = nullptr;   // device addresses (box 64 x 256 time rows, 64 x 128 filters)
     CUtensorMap *mapY = nullptr;     // yuni as the finer level's interpolation operand (box 64 x 128, 128-byte swizzle)
     // 16-bit modes, levels k >= 1: SNR rows [history (Hy) | new (B_k)] in one buffer, so the
     // next finer level's epilogue can stage a row segment with one TMA load
-    float *yuni = nullptr;    // FP32 mode: unused; BF16 / E4M3 modes: y as FP16 rows [0, 2M); FP16 mode: y as
+    float *yuni = nullptr;    // FP32 mode: unused; BF16 mixing: y as FP16 rows [0, 2M); FP16 mode: y as
                               // BF16 hi rows [0, 2M), lo rows [2M, 4M); ld ldu
     int64_t ldu = 0;
     float *ytmp = nullptr;    // history shift staging, same layout with ld Hy
@@ -213,7 +212,8 @@ struct sb_unit {
     int32_t detector = 0;
     int M = 0, precision = 0, flags = 0;
     bool tc = false, bf16 = false;
-    int mode = 0;                 // tensor-core operand mode (kModeF16 / kModeBF16 / kModeE4M3)
+    int mode = 0;                 // basis-FIR operand mode (kModeF16 / kModeBF16 / kModeE4M3)
+    int mmode = 0;                // mixing + interpolation operand mode (mix_mode(mode))
     int amax_cur = 0;
     bool refine = false;           // 16-bit modes with a refine threshold: FP32 copies kept for a6
     float thr = 0.f, refine_thr = 0.f;
@@ -307,9 +307,7 @@ static int tc_mode(int precision) {
 }
 static int mode_phases(int mode) { return mode == kModeE4M3 ? 16 : 8; }    // 16 bytes of samples
 static int mode_bytes(int mode) { return mode == kModeE4M3 ? 1 : 2; }
-// E4M3 static scale of level-k basis outputs: white noise gives o_l ~ N(0, 2^-k); the
-// scaled values have standard deviation 4, leaving 112 sigma below the E4M3 maximum.
-static float e4m3_out_scale(int k) { return std::ldexp(1.0f, -k) > 0 ? std::sqrt(std::ldexp(1.0f, -k)) / 4.0f : 1.0f; }
+static int mode_terms(int mode) { return mode == kModeE4M3 ? 2 : 1; }     // terms of the FIR's strain copy
 
 static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &P) {
     const int S = d->n_slices;
@@ -375,6 +373,7 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
     P.o_col16.assign(S, 0);
     std::vector<int64_t> kpad_max(NL, 0);
     const int mode = tc_mode(d->precision), ph = mode_phases(mode), by = mode_bytes(mode);
+    const int mmode = mix_mode(mode), mby = mode_bytes(mmode);
     const int lpt = kTcM / ph;                       // basis vectors per 128-row weight tile
     for (int s = 0; s < S; ++s) {
         const int k = levels_of_slice[s];
@@ -390,8 +389,9 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
         kpad_max[k] = std::max(kpad_max[k], P.Kpad[s]);
     }
     for (int k = 0; k < NL; ++k) {
-        if (mode == kModeE4M3) P.Lk_pad[k] = round_up(P.Lk_pad[k], 32);   // K per 8-bit MMA
-        P.x16_len[k] = P.Hd[k] + (d->max_push_samples >> k) + (int64_t)ph * kTcN + kpad_max[k] + 64;
+        P.Lk_pad[k] = round_up(P.Lk_pad[k], 16);        // K per 16-bit mixing MMA
+        // (a multiple of 256 elements, so the E4M3 second term starts 256-byte aligned)
+        P.x16_len[k] = round_up(P.Hd[k] + (d->max_push_samples >> k) + (int64_t)ph * kTcN + kpad_max[k] + 64, 256);
     }
     // bytes
     const int64_t M2 = 2 * (int64_t)d->n_templates;
@@ -404,10 +404,10 @@ static int plan_unit(const sb_desc *d, std::vector<int> &levels_of_slice, Plan &
         b += 2 * M2 * P.Hy[k] * 4;                   // SNR history ping-pong
         if (P.tc) {
             b -= M2 * ldy * 4 + 2 * M2 * P.Hy[k] * 4;   // replaced by the unified level buffer
-            if (k >= 1) b += (M2 * round_up(P.Hy[k] + Bk, 8) + M2 * P.Hy[k]) * 2 * y_planes(mode) + 128;
+            if (k >= 1) b += (M2 * round_up(P.Hy[k] + Bk, 8) + M2 * P.Hy[k]) * 2 * y_planes(mmode) + 128;
             else if (d->flags & SB_FLAG_KEEP_SNR) b += M2 * ldy * 4;
-            b += (P.x16_len[k] + (Bk + 256) * P.Lk_pad[k] + M2 * P.Lk_pad[k]) * by + 2 * 128;
-            if (mode == kModeE4M3) b += (P.Lk_pad[k] + M2 + 2) * 4;
+            b += P.x16_len[k] * by * mode_terms(mode) + ((Bk + 256) * P.Lk_pad[k] + M2 * P.Lk_pad[k]) * mby + 2 * 128;
+            if (mode == kModeE4M3) b += (P.Lk_pad[k] + 2) * 4;
         } else {
             b += M2 * P.Lk[k] * 4 + P.Lk[k] * Bk * 4;    // mixing + basis outputs
         }
@@ -683,45 +683,32 @@ static int upload_expanded_weights(sb_unit *u, SliceDev &sd, const double *basis
     return upload_map(u, m, &sd.mapW, true);
 }
 
-// Stacked mixing matrix of every level in the operand type.  E4M3: the basis
-// outputs are stored divided by a static per-level scale s_o, so the mixing
-// columns carry s_o, and each row is scaled by 448 / its absmax (kept in rscale
-// for the epilogue); colscale = basis scale / s_o for the basis FIR epilogue.
+// Stacked mixing matrix of every level in the mixing kernel's operand type
+// (BF16 for E4M3 units).  E4M3: colscale holds each basis vector's scale, which
+// the basis FIR epilogue applies before writing its BF16 outputs.
 static int upload_tc_mixing_and_maps(sb_unit *u, const sb_desc *d, const std::vector<std::vector<float>> &vscale) {
     const int64_t M2 = 2 * (int64_t)u->M;
-    const int by = mode_bytes(u->mode);
+    const int by = mode_bytes(u->mmode);
     for (auto &L : u->levels) {
         if (L.Lk_pad == 0) continue;
-        const float so = u->mode == kModeE4M3 ? e4m3_out_scale(L.k) : 1.0f;
-        std::vector<float> rs(M2, 1.0f), cs(L.Lk_pad, 0.0f);
-        if (u->mode == kModeE4M3) {
-            for (int64_t a = 0; a < M2; ++a) {
-                double m = 0.0;
-                for (int s : L.slices)
-                    for (int l = 0; l < u->slices[s].L; ++l)
-                        m = std::max(m, std::fabs(d->slices[s].mixing[a * u->slices[s].L + l]) * so);
-                rs[a] = m > 0.0 ? std::max((float)(m / 448.0), kE4RowScaleMin) : 1.0f;
-            }
-            for (int s : L.slices)
-                for (int l = 0; l < u->slices[s].L; ++l) cs[u->slices[s].o_col16 + l] = vscale[s][l] / so;
-        }
         std::vector<uint8_t> m((size_t)(M2 * L.Lk_pad * by), 0);
         for (int s : L.slices) {
             const SliceDev &sd = u->slices[s];
             const double *mx = d->slices[s].mixing;
             for (int64_t a = 0; a < M2; ++a)
                 for (int l = 0; l < sd.L; ++l)
-                    put_elem(m, a * L.Lk_pad + sd.o_col16 + l, (float)(mx[a * sd.L + l] * so / rs[a]), u->mode);
+                    put_elem(m, a * L.Lk_pad + sd.o_col16 + l, (float)mx[a * sd.L + l], u->mmode);
         }
         int rc;
         if ((rc = dev_alloc_w(u, &L.M16, m.size()))) return rc;
         CK(cudaMemcpy(L.M16, m.data(), m.size(), cudaMemcpyHostToDevice));
         CUtensorMap hm;
-        if ((rc = encode_map(&hm, L.M16, u->mode, L.Lk_pad, M2, 128, mix_kbytes(L.Lk_pad, u->mode)))) return rc;
+        if ((rc = encode_map(&hm, L.M16, u->mmode, L.Lk_pad, M2, 128, mix_kbytes(L.Lk_pad, u->mmode)))) return rc;
         if ((rc = upload_map(u, hm, &L.mapM, true))) return rc;
         if (u->mode == kModeE4M3) {
-            if ((rc = dev_alloc_w(u, (void **)&L.rscale, M2 * 4))) return rc;
-            CK(cudaMemcpy(L.rscale, rs.data(), M2 * 4, cudaMemcpyHostToDevice));
+            std::vector<float> cs(L.Lk_pad, 0.0f);
+            for (int s : L.slices)
+                for (int l = 0; l < u->slices[s].L; ++l) cs[u->slices[s].o_col16 + l] = vscale[s][l];
             if ((rc = dev_alloc_w(u, (void **)&L.colscale, L.Lk_pad * 4))) return rc;
             CK(cudaMemcpy(L.colscale, cs.data(), L.Lk_pad * 4, cudaMemcpyHostToDevice));
         }
@@ -791,13 +778,13 @@ static int alloc_state(sb_unit *u) {
             continue;
         }
         if (k >= 1) {
-            want((void **)&L.yuni, M2 * L.ldu * 2 * y_planes(u->mode));
-            want((void **)&L.ytmp, M2 * L.Hy * 2 * y_planes(u->mode));
+            want((void **)&L.yuni, M2 * L.ldu * 2 * y_planes(u->mmode));
+            want((void **)&L.ytmp, M2 * L.Hy * 2 * y_planes(u->mmode));
         } else if (u->flags & SB_FLAG_KEEP_SNR) {
             want((void **)&L.ynew, M2 * L.ldy * 4);
         }
-        want(&L.x16, L.x16_len * mode_bytes(u->mode));
-        if (L.Lk_pad > 0) want(&L.O16, (L.Bk_max + 256) * L.Lk_pad * mode_bytes(u->mode));
+        want(&L.x16, L.x16_len * mode_bytes(u->mode) * mode_terms(u->mode));
+        if (L.Lk_pad > 0) want(&L.O16, (L.Bk_max + 256) * L.Lk_pad * mode_bytes(u->mmode));
         if (u->mode == kModeE4M3) want((void **)&L.amax, 2 * 4);
     }
     if (u->tc) {
@@ -825,13 +812,13 @@ static int alloc_state(sb_unit *u) {
         if (!u->tc) continue;
         if (L.k >= 1) {                          // y as FP16 rows [2M x ldu], or BF16 hi / lo rows [4M x ldu]
             CUtensorMap hy;                      // level k - 1's interpolation operand (64 samples x 128 filters)
-            const int np = y_planes(u->mode);
+            const int np = y_planes(u->mmode);
             if ((rc = encode_map(&hy, L.yuni, np == 1 ? kModeF16 : kModeBF16, L.ldu, np * M2, 128))) return rc;
             if ((rc = upload_map(u, hy, &L.mapY, false))) return rc;
         }
         if (L.Lk_pad == 0) continue;
         CUtensorMap ho;
-        if ((rc = encode_map(&ho, L.O16, u->mode, L.Lk_pad, L.Bk_max + 256, 256, mix_kbytes(L.Lk_pad, u->mode))))
+        if ((rc = encode_map(&ho, L.O16, u->mmode, L.Lk_pad, L.Bk_max + 256, 256, mix_kbytes(L.Lk_pad, u->mmode))))
             return rc;
         if ((rc = upload_map(u, ho, &L.mapO, false))) return rc;
     }
@@ -880,6 +867,7 @@ extern "C" int svdbank_create(sb_ctx *c, const sb_desc *d, int32_t detector, sb_
     u->tc = is_tc(d->precision);
     u->bf16 = d->precision == SB_BF16;
     u->mode = tc_mode(d->precision);
+    u->mmode = mix_mode(u->mode);
     u->refine = u->tc && d->refine_threshold > 0.0f;
     u->flags = d->flags;
     u->thr = d->threshold;
@@ -1012,6 +1000,7 @@ extern "C" int svdbank_create_like(sb_ctx *c, sb_unit *src, int32_t detector, sb
     u->tc = src->tc;
     u->bf16 = src->bf16;
     u->mode = src->mode;
+    u->mmode = src->mmode;
     u->refine = src->refine;
     u->flags = src->flags;
     u->thr = src->thr;
@@ -1485,7 +1474,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 const int h = u->mode;
                 float *am = L.amax ? L.amax + u->amax_cur : nullptr;
                 float *am_next = L.amax ? L.amax + (1 - u->amax_cur) : nullptr;
-                conv[h].push_back(HalfConvTask{L.dbuf[nb], L.x16, L.Hd + Bk, am, am_next});
+                void *x_lo = mode_terms(u->mode) == 2 ? static_cast<uint8_t *>(L.x16) + L.x16_len : nullptr;
+                conv[h].push_back(HalfConvTask{L.dbuf[nb], L.x16, L.Hd + Bk, am, am_next, x_lo});
                 for (int s : L.slices) {
                     const SliceDev &sd = u->slices[s];
                     TcFirTask f{};
@@ -1502,6 +1492,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     f.tiles_m = sd.L16 / (kTcM / mode_phases(u->mode));
                     f.xamax = am;
                     f.colscale = L.colscale;
+                    f.x_lo = x_lo;
                     tfir[h].push_back(f);
                     kpad_max[h] = std::max(kpad_max[h], sd.Kpad);
                 }
@@ -1515,8 +1506,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     mt.Yh = k >= 1 ? reinterpret_cast<uint16_t *>(L.yuni) : nullptr;
                     mt.ldu = L.ldu;
                     mt.yst_col0 = L.Hy;
-                    mt.kbytes = mix_kbytes(L.Lk_pad, u->mode);
-                    mt.rsc_next = k >= 1 ? u->levels[k - 1].rscale : nullptr;
+                    mt.kbytes = mix_kbytes(L.Lk_pad, u->mmode);
                     mt.part = k == 0 ? u->part : nullptr;
                     if (k == 0 && refine_here) {
                         mt.wmax = reinterpret_cast<uint32_t *>(wmax_off + 1);   // offset + 1; address at packing
@@ -1535,8 +1525,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     mt.tiles_t = (int32_t)((Bk + 255) / 256);
                     mt.tiles_a = (M2 + 127) / 128;
                     mt.n_rec = mt.tiles_t * 4;
-                    mt.rscale = L.rscale;
-                    tmix[h][k].push_back(mt);
+                    tmix[u->mmode][k].push_back(mt);
                 }
                 if (k >= 1) {           // next push's interpolation history: columns [Bk, Bk + Hy) -> [0, Hy)
                     // (in place when the two ranges are disjoint, else through the staging buffer)
@@ -1549,7 +1538,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                     a.rows = M2;
                     a.n = (int32_t)L.Hy;
                     a.off = (int32_t)Bk;
-                    a.elem16 = y_planes(u->mode);
+                    a.elem16 = y_planes(u->mmode);
                     yshift1.push_back(a);
                     max_hy = std::max<int>(max_hy, (int)L.Hy);
                     if (!direct) {
@@ -1561,7 +1550,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                         bt.rows = M2;
                         bt.n = (int32_t)L.Hy;
                         bt.off = 0;
-                        bt.elem16 = y_planes(u->mode);
+                        bt.elem16 = y_planes(u->mmode);
                         yshift2.push_back(bt);
                     }
                 }

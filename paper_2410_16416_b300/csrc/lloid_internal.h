@@ -165,15 +165,17 @@ struct TrigOut {
 constexpr int kTcM = 128;   // MMA M (rows of the A operand per tile)
 constexpr int kModeF16 = 0, kModeBF16 = 1, kModeE4M3 = 2;   // tensor-core operand modes
 constexpr int kTcN = 256;   // MMA N (columns of the accumulator per tile)
-// Planes of the stored per-level SNR y_k (levels k >= 1) in the tensor-core modes: BF16 and E4M3
-// modes keep y as one FP16 plane (11-bit significand; |y| is an SNR partial, far inside FP16's
-// range); FP16 mode keeps BF16 hi + lo planes (about 16 significant bits) for its smaller error.
-// E4M3 stores y in the finer level's row-scale units (1 / rs, rs ~ 5e-4) times kE4StoreScale, and
-// its interpolation table carries 1 / kE4StoreScale, so the stored values stay near the SNR's own.
+// Planes of the stored per-level SNR y_k (levels k >= 1) in the tensor-core modes, by the mixing
+// kernel's operand mode: BF16 keeps y as one FP16 plane (11-bit significand; |y| is an SNR partial,
+// far inside FP16's range); FP16 keeps BF16 hi + lo planes (about 16 significant bits) for its
+// smaller error.  (The E4M3 precision runs its mixing in BF16: see mix_mode.)
 __host__ __device__ constexpr int y_planes(int mode) { return mode == kModeF16 ? 2 : 1; }
-constexpr float kE4StoreScale = 1.0f / 2048.0f;
-// E4M3 mixing-row scales are at least this, so |y| / (rs * 2048) < 65504 for |y| < 1000
-constexpr float kE4RowScaleMin = 1.0f / 131072.0f;
+// Operand mode of the mixing + interpolation kernel for a unit whose basis FIR runs in `mode`.
+// SB_FP8 takes E4M3 for the basis FIR only (weights one E4M3 term with a per-basis-vector scale,
+// strain two E4M3 terms with a per-buffer scale) and writes its basis outputs in BF16: one
+// single-term E4M3 operand adds about 0.027 of |SNR| (rms) in white noise, and a second one
+// (the mixing weights) would put the largest window-maximum errors above 0.15.
+__host__ __device__ constexpr int mix_mode(int mode) { return mode == kModeE4M3 ? kModeBF16 : mode; }
 
 struct HalfConvTask {       // dst[i] = narrow(src[i]), i < n (E4M3: scaled by 448 / absmax)
     const float *src;
@@ -181,6 +183,7 @@ struct HalfConvTask {       // dst[i] = narrow(src[i]), i < n (E4M3: scaled by 4
     int64_t n;
     float *amax;               // E4M3: this push's |src| maximum (accumulated by absmax_kernel)
     float *amax_next;          // E4M3: the next push's accumulator, zeroed here
+    void *dst_lo;              // E4M3: second term, dst_lo[i] = narrow(s src[i] - dst[i]); null otherwise
 };
 
 // a2 on tensor cores.  Tile (mt, nt): W rows [128 mt, 128 mt + 128) (16 basis
@@ -198,7 +201,8 @@ struct TcFirTask {
     int32_t tiles_n;
     int32_t tile_begin;
     const float *xamax;        // E4M3: |strain| maximum of this push at this level
-    const float *colscale;     // E4M3: per output column, basis scale / output scale
+    const float *colscale;     // E4M3: per output column, the basis vector's scale
+    const void *x_lo;          // E4M3: second term of the strain (same layout as x); O is BF16
 };
 
 // Partial window maximum of one template over one column run of one tile.
@@ -234,12 +238,10 @@ struct TcMixUpTask {
     int32_t lam;               // Lambda of this level
     int32_t in_off;            // Lambda_{k+1} + Hy_{k+1}: coarser position of (relative index 0) / 2
     int32_t tiles_t, tiles_a, tile_begin, n_rec;
-    const float *rscale;       // E4M3: per mixing row (filter) scale of this level (null: 1)
     uint32_t *wmax;            // top level with refinement: [M][n_wslot] 16-bit window maxima above thr2
     int64_t win0;              //   (mag2 bits, atomicMax), window of slot 0
     int32_t n_wslot;
     float thr2;                //   refine threshold squared
-    const float *rsc_next;     // E4M3: row scale of the finer level, which reads this level's y (null: 1)
 };
 
 // Window bookkeeping after the top-level partial maxima: one warp per
@@ -332,7 +334,7 @@ cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_windo
 // Margin of the candidate rule per operand mode: records within (1 - margin) of their window's
 // 16-bit maximum are refined (the 16-bit error stays well inside it).
 constexpr float kRefKeep16 = 0.81f;      // (1 - 0.1)^2, BF16 / FP16
-constexpr float kRefKeep8 = 0.25f;       // (1 - 0.5)^2, E4M3
+constexpr float kRefKeep8 = 0.64f;       // (1 - 0.2)^2, E4M3 (errors <= 0.15 near |rho| = 5.5)
 
 // ---- launchers (kernels_simt.cu) -------------------------------------------
 cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,

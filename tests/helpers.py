@@ -49,29 +49,41 @@ def check_triggers(trig, x_orc, win_len, threshold, n_valid, tol, unit=None, tem
     samples within tol of each other), the GPU's choice is checked for validity.
     Returns the number of matched triggers.
     """
+    maxima = oracle.window_maxima(x_orc, win_len, n_valid)
+    rho = oracle.complex_snr(x_orc)
+    return check_triggers_maxima(trig, maxima, lambda i, n: abs(rho[i, n]), rho.shape[0], threshold, tol,
+                                 unit=unit, template_ids=template_ids, absolute=absolute)
+
+
+def check_triggers_maxima(trig, maxima, rho_abs, n_templates, threshold, tol, unit=None, template_ids=None,
+                          absolute=False, errors=None):
+    """check_triggers against precomputed oracle window maxima (wins, n_star, amax, phase), with
+    rho_abs(i, n) = |rho_i[n]| of the oracle.  When `errors` is a list, every matched trigger's
+    |snr - oracle maximum| is appended to it."""
     if unit is not None:
         trig = trig[trig["unit"] == unit]
-    wins, n_star, amax, ph = oracle.window_maxima(x_orc, win_len, n_valid)
-    rho = oracle.complex_snr(x_orc)
+    wins, n_star, amax, ph = maxima
     scale = (lambda m: 1.0) if absolute else (lambda m: max(1.0, m))
     got = {}
     for t in trig:
         key = (int(t["template_id"]), int(t["window"]))
         assert key not in got, f"duplicate trigger {key}"
         got[key] = t
-    ids = template_ids if template_ids is not None else np.arange(rho.shape[0])
+    ids = template_ids if template_ids is not None else np.arange(n_templates)
     matched = 0
     for wi, w in enumerate(wins):
-        for i in range(rho.shape[0]):
+        for i in range(n_templates):
             key = (int(ids[i]), int(w))
             m = amax[wi, i]
             if key in got:
                 t = got.pop(key)
                 assert m > threshold - tol * scale(m), f"spurious trigger {key}: oracle max {m}"
                 assert abs(t["snr"] - m) <= tol * scale(m), (key, t["snr"], m)
+                if errors is not None:
+                    errors.append(abs(float(t["snr"]) - m))
                 n = int(t["sample"])
                 if n != n_star[wi, i]:
-                    assert abs(abs(rho[i, n]) - m) <= 2 * tol * scale(m), (key, n, n_star[wi, i])
+                    assert abs(rho_abs(i, n) - m) <= 2 * tol * scale(m), (key, n, n_star[wi, i])
                 else:
                     dphi = np.angle(np.exp(1j * (t["phase"] - ph[wi, i])))
                     assert abs(dphi) <= 10 * tol * scale(m) / max(m, 1e-3) + 1e-5, (key, dphi)

@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-4
 TOL_HALF = 0.05          # absolute |SNR| bound of the BF16 / FP16 modes, every sample
+TOL_FP8 = 0.15           # absolute |SNR| bound of SB_FP8 before refinement, every window maximum
 
 
 @pytest.fixture(scope="module")
@@ -485,25 +486,33 @@ def test_refined_production_injection(lloid):
 
 # ---------------------------------------------------------------- E4M3 mode (config 4)
 def test_fp8_small_bin_error_distribution_and_refinement(lloid, small_case):
-    """E4M3 basis FIR and mixing (per-vector / per-buffer absmax scales, FP32 accumulate):
-    the unrefined SNR error distribution is reported and bounded loosely; every trigger
-    (window maximum above 5.5) is refined in FP32 and matches the oracle within 1e-3."""
+    """E4M3 basis FIR (per-basis-vector weight scales, two-term strain with a per-buffer scale,
+    FP32 accumulate), BF16 mixing: before refinement every window maximum is within 0.15 of the
+    oracle (the every-sample distribution is reported); after refinement every trigger (window
+    maximum above 5.5) is recomputed in FP32 and matches the oracle within 1e-3."""
     spec, h, bank, d, x = small_case
     ctx = lloid.Context(0)
-    u = ctx.create_unit(bank, precision="fp8", threshold=6.0, refine_threshold=5.5, max_push_samples=4096,
+    u = ctx.create_unit(bank, precision="fp8", threshold=0.0, refine_threshold=0.0, max_push_samples=4096,
                         keep_snr=True)
     (xg,) = push_and_collect(ctx, [u], [d], [4096] * 8)
     ctx.sync()
-    trig = ctx.pop_triggers()
+    raw = ctx.pop_triggers()
     ctx.close()
     n = xg.shape[1]
     rg = xg[0::2].astype(np.float64) + 1j * xg[1::2]
     ro = x[0::2, :n] + 1j * x[1::2, :n]
-    err = np.abs(rg - ro)
-    rel = err / np.maximum(1.0, np.abs(ro))
-    q = np.percentile(err, [50, 99, 100])
-    print(f"fp8 unrefined |rho| error p50 {q[0]:.4f} p99 {q[1]:.4f} max {q[2]:.4f}; max rel {rel.max():.4f}")
-    assert q[1] <= 0.2 and q[2] <= 0.5          # 3-bit mantissas: a distribution, not a tight bound
+    q = np.percentile(np.abs(rg - ro), [50, 99, 100])
+    nmax = check_triggers(raw, x, 2048, 0.0, n, TOL_FP8, absolute=True)
+    print(f"fp8 unrefined: every-sample |rho| error p50 {q[0]:.4f} p99 {q[1]:.4f} max {q[2]:.4f}; "
+          f"{nmax} window maxima within {TOL_FP8}")
+    assert nmax == 64 * (n // 2048)
+    ctx = lloid.Context(0)
+    u = ctx.create_unit(bank, precision="fp8", threshold=6.0, refine_threshold=5.5, max_push_samples=4096)
+    for t in range(0, d.shape[0], 4096):
+        u.push(d[t:t + 4096], t)
+    ctx.sync()
+    trig = ctx.pop_triggers()
+    ctx.close()
     assert len(trig) >= 1 and np.all(trig["flags"] & lloid.SB_TRIG_REFINED)
     assert check_triggers(trig, x, 2048, 6.0, n, 1e-3, absolute=True) >= 1
 
