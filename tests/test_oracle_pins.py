@@ -475,3 +475,116 @@ def test_p13_coincidences_symmetry_and_window_monotonicity():
     tb2[:10] = ta[:10]
     zero = oracle.coincidences(ta, sa, ra, tb2, sb2, rb, 0)
     assert all(r[3] == r[4] for r in zero) and {(i, j) for _, i, j, *_ in zero} >= {(k, k) for k in range(10)}
+
+
+# ---------------------------------------------------------------- P14 whitening (R28)
+def test_p14_fixed_psd_returns_the_scaled_input():
+    """With a known flat PSD s^2 the whitener must return d / s exactly past the first hop (the
+    window's shifted copies sum to one and rfft / irfft are inverses) and w[n] d[n] / s in the
+    first hop.  A wrong window, hop, overlap-add offset or FFT normalisation fails this."""
+    N, s = 64, 2.5
+    d = np.random.default_rng(1).standard_normal(N * 10)
+    x, _ = oracle.condition.whiten(d, N, 4, psd=np.full(N // 2 + 1, s * s))
+    H = N // 2
+    assert x.shape[0] == (d.shape[0] - N) // H * H + H
+    assert np.allclose(x[H:], d[H:x.shape[0]] / s, rtol=0, atol=1e-12)
+    w = np.sin(np.pi * np.arange(H) / N) ** 2
+    assert np.allclose(x[:H], w * d[:H] / s, rtol=0, atol=1e-12)
+
+
+def test_p14_running_average_is_the_mean_then_exponential():
+    """For the first n_avg segments the running PSD equals numpy's mean of the periodograms so far;
+    a constant periodogram stays constant; later segments weigh 1 / n_avg."""
+    rng = np.random.default_rng(2)
+    S = rng.exponential(1.0, size=(12, 9))
+    P = oracle.condition.running_psd(S, 5)
+    for j in range(5):
+        assert np.allclose(P[j], S[:j + 1].mean(axis=0), rtol=1e-13, atol=0)
+    assert np.allclose(P[5], 0.8 * P[4] + 0.2 * S[5], rtol=1e-13, atol=0)
+    assert np.allclose(oracle.condition.running_psd(np.full((7, 3), 4.0), 3), 4.0, rtol=0, atol=1e-14)
+
+
+def test_p14_periodogram_normalisation_against_a_tone():
+    """A unit-amplitude cosine on bin k (not 0, not N/2) has |X[k]| = sum(w) / 2 = N / 4 under the
+    periodic Hann window (Parseval-free closed form), so S[k] = (N/4)^2 / (3N/8)."""
+    N, k = 128, 9
+    n = np.arange(N * 3)
+    d = np.cos(2 * np.pi * k * n / N)
+    X = oracle.condition.segment_spectra(d, N)
+    assert np.allclose(np.abs(X[:, k]), N / 4, rtol=1e-12)
+    w = oracle.condition.hann_periodic(N)
+    assert math.isclose(float(np.sum(w ** 2)), 3 * N / 8, rel_tol=1e-12)
+
+
+def test_p14_scale_invariance():
+    """Whitening divides by the data's own amplitude: c d whitens to the same series."""
+    d = np.random.default_rng(3).standard_normal(4096)
+    x1, _ = oracle.condition.whiten(d, 256, 8)
+    x2, _ = oracle.condition.whiten(7.5 * d, 256, 8)
+    assert np.allclose(x1, x2, rtol=1e-10, atol=1e-12)
+
+
+def test_p14_white_noise_stays_white_with_unit_variance():
+    """sigma = 3 white noise whitens to unit variance, uncorrelated samples (statistics over 2^18)."""
+    N = 512
+    d = 3.0 * np.random.default_rng(4).standard_normal(1 << 18)
+    x, P = oracle.condition.whiten(d, N, 32)
+    xs = x[32 * N:]                                    # past the running average's start-up
+    assert abs(xs.var() - 1.0) < 0.02
+    assert abs(np.corrcoef(xs[:-1], xs[1:])[0, 1]) < 0.01
+    assert abs(np.median(P[-1][1:-1]) / 9.0 - 1.0) < 0.2      # per-bin variance ~ sigma^2 (chi^2 spread)
+
+
+def test_p14_coloured_noise_whitens_to_a_flat_spectrum():
+    """AR(1) noise d[n] = a d[n-1] + e[n] has the per-bin variance 1 / |1 - a e^{-i w}|^2: the
+    running PSD follows it (band averages within 5 %) and the whitened output's averaged
+    periodogram is flat within 6 % with unit variance, although the input spans 25 dB."""
+    a, N = 0.9, 512
+    e = np.random.default_rng(5).standard_normal(1 << 19)
+    d = scipy.signal.lfilter([1.0], [1.0, -a], e)
+    x, P = oracle.condition.whiten(d, N, 64)
+    f = np.arange(N // 2 + 1)
+    theory = 1.0 / np.abs(1.0 - a * np.exp(-2j * np.pi * f / N)) ** 2
+    Pm = P[-64:].mean(axis=0)
+    for lo in range(8, N // 2 - 16, 16):                # band averages away from DC
+        r = Pm[lo:lo + 16].mean() / theory[lo:lo + 16].mean()
+        assert abs(r - 1.0) < 0.05, (lo, r)
+    xs = x[64 * N:]
+    assert abs(xs.var() - 1.0) < 0.03
+    _, pxx = scipy.signal.welch(xs, nperseg=256)
+    band = pxx[1:121].reshape(-1, 8).mean(axis=1)        # 15 bands of 8 bins (of 129), DC excluded
+    assert band.max() / band.min() < 1.12, band
+
+
+# ---------------------------------------------------------------- P15 gating (R29)
+def test_p15_gate_matches_the_hand_worked_fixture():
+    path = os.path.join(os.path.dirname(__file__), "golden", "gate_hand_worked.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    x = np.ones(40)
+    x[10], x[30] = 10.0, -12.0
+    y = oracle.condition.gate(x, 5.0, 2, 4)
+    for n, v in rows:
+        assert abs(y[int(n)] - float(v)) < 1e-12, (n, y[int(n)], v)
+    assert np.array_equal(oracle.condition.gate(x, 50.0, 2, 4), x)          # nothing above threshold
+
+
+def test_p15_a_loud_glitch_is_removed_and_the_rest_untouched():
+    """A sine-Gaussian glitch of peak 500 sigma in white noise: after conditioning every sample
+    within `half` of a sample above the threshold is zero, and samples farther than
+    half + taper from all of them equal the ungated whitened series exactly."""
+    N, half, taper, thr = 512, 200, 100, 25.0
+    rng = np.random.default_rng(6)
+    d = rng.standard_normal(1 << 16)
+    c = 40000
+    n = np.arange(d.shape[0])
+    d += 500.0 * np.exp(-0.5 * ((n - c) / 6.0) ** 2) * np.sin(0.9 * (n - c))
+    xw, _ = oracle.condition.whiten(d, N, 16)
+    xg, _ = oracle.condition.condition(d, N, 16, thr, half, taper)
+    centers = np.flatnonzero(np.abs(xw) > thr)
+    assert centers.size > 0 and np.all(np.abs(centers - c) < 64)
+    r = np.min(np.abs(np.arange(xw.shape[0])[:, None] - centers[None, :]), axis=1)
+    assert np.all(xg[r <= half] == 0.0)
+    assert np.array_equal(xg[r >= half + taper], xw[r >= half + taper])
+    mid = r == half + taper // 2
+    assert np.allclose(xg[mid], 0.5 * xw[mid], rtol=1e-12)
+
