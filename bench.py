@@ -1,18 +1,25 @@
 #!/usr/bin/env python
 """Throughput benchmark: template-seconds filtered per second on B300 (paper Eq. 1, cores = 1 per GPU).
 
-Workload (per GPU rank): one production-shaped SVD bin of 1000 templates
-(60 s Newtonian chirps, chirp mass 1.0-1.5 Msun, six time slices at 4096 ...
-128 Hz, SVD truncated at 99.99% of sigma^2) on two detectors (H1, L1: two
-units, independent seeded white noise, injections at SNR 8-30).  A step is one
-grouped push of ``--push-seconds`` of strain to both units: decimation, basis
-FIR, mixing, up-sampling + sum, window maxima and trigger hand-off.  Data are
-synthetic (seeded white Gaussian noise; random-parameter chirps).
+Headline workload (per GPU rank): one production-shaped SVD bin of 1000
+templates (60 s Newtonian chirps, chirp mass 1.0-1.5 Msun, six time slices at
+4096 ... 128 Hz, SVD truncated at 99.99% of sigma^2) on two detectors (H1, L1:
+two units, independent seeded white noise, injections at SNR 8-30).  A step is
+one grouped push of ``--push-seconds`` of strain to both units: decimation,
+basis FIR, mixing, up-sampling + sum, window maxima, FP32 refinement of the
+candidate maxima and trigger hand-off.  Data are synthetic (seeded white
+Gaussian noise; random-parameter chirps).
 
 The device-timed value has the strain already resident in HBM; L2 is flushed
 (256 MB write) between timed steps, outside the step's events.  ``e2e`` runs
 the same steps through the C ABI from host buffers, with the host->device
 strain copies and the trigger read-back inside the timed region.
+
+The same run also reports, as sub-results of the metric: the other precisions
+(``by_precision``), the production bin with 1-s buffers (``push_1s``), the
+grouped batch of uneven bins (``batch``: 200 bins x 2 detectors in one grouped
+launch per stage) and the serving loop (``serve``: 1-s buffers of 1000 bins x 2
+detectors with Poisson arrivals, p50 / p99 buffer-to-trigger latency).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
 """
@@ -38,13 +45,16 @@ import synth  # noqa: E402
 METRIC = "template-seconds filtered/s on 1 B300 (FP32 vs BF16/FP8 grouped); p99 latency"
 UNIT = "template-s/s"
 L2_FLUSH_BYTES = 256 << 20
+DTYPES = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}
+INTERP_FLOPS_PER_OUTPUT = 32.0      # halfband x2 interpolation: 32 multiply-adds per odd output, none per even
+RECORD_BYTES = 32                   # one top-level partial window record (sizeof WinPart)
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=240)       # 240 + 16 pushes of 16 s = 4096 s of strain
-    p.add_argument("--warmup", type=int, default=16)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="lloid", choices=["lloid", "reference"])
     p.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
     p.add_argument("--compare", default="fp32,fp16,fp8", help="other precisions timed for by_precision ('none': skip)")
@@ -57,11 +67,18 @@ def parse():
                    help="production bank: hand the templates' autocorrelation to svdbank_create (xi^2 of every trigger)")
     p.add_argument("--autotune", default="on", choices=["on", "off"],
                    help="time the mixing kernel's pipeline shapes on the first push of each launch shape")
-    p.add_argument("--cpu-seconds", type=float, default=8.0, help="strain seconds per oracle worker")
+    p.add_argument("--cpu-seconds", type=float, default=4.0, help="strain seconds per oracle worker")
     p.add_argument("--workload", default="production", choices=["production", "batch", "serve"],
-                   help="production: one 1000-template bin x 2 detectors; batch: --bins uneven bins x 2 detectors")
-    p.add_argument("--bins", type=int, default=200)
-    p.add_argument("--serve-seconds", type=int, default=30, help="serve: 1-s buffers per stream")
+                   help="production: one 1000-template bin x 2 detectors (+ sub-results); batch / serve: that "
+                        "sub-result alone as the line")
+    p.add_argument("--sub", default="push1s,batch,serve",
+                   help="sub-results of the production line ('none': skip)")
+    p.add_argument("--bins", type=int, default=200, help="batch: uneven bins (x 2 detectors)")
+    p.add_argument("--batch-steps", type=int, default=6)
+    p.add_argument("--batch-push-seconds", type=int, default=8)
+    p.add_argument("--serve-bins", type=int, default=1000)
+    p.add_argument("--serve-seconds", type=int, default=20, help="serve: 1-s buffers per stream")
+    p.add_argument("--serve-precisions", default="bf16,fp8")
     p.add_argument("--distinct-banks", type=int, default=20, help="serve: distinct banks the bins cycle through")
     p.add_argument("--time-scale", type=float, default=1.0, help="serve: arrival clock speed-up")
     return p.parse_args()
@@ -75,6 +92,13 @@ def production_bank_templates(bin_index: int, n_templates: int):
     return spec, h
 
 
+def production_config(spec, basis_counts, push_seconds: int) -> dict:
+    """The workload as both arms name it (the reference arm times a bounded sample of it)."""
+    return {"workload": f"production bin: {spec.n_templates} templates x 2 detectors, 6 slices 4096-128 Hz, "
+                        f"L={list(basis_counts)}, {push_seconds} s pushes",
+            "templates": 2 * spec.n_templates, "units_per_gpu": 2, "push_seconds": push_seconds}
+
+
 def make_strain(bin_index: int, detector: int, seconds: int, f0: float, h, n_templates: int):
     n = int(seconds * f0)
     d = synth.white_noise(n, 2, bin_index, detector + 1)
@@ -83,57 +107,80 @@ def make_strain(bin_index: int, detector: int, seconds: int, f0: float, h, n_tem
     return d
 
 
-def algorithmic_model(bank, units: int, B_s: float, precision: str = "fp32"):
-    """Per-stage algorithmic FLOPs and HBM bytes of one push (all units).
+def _levels(bank):
+    f0 = bank.top_rate_hz
+    lv = {}
+    for s in bank.slices:
+        k = int(round(math.log2(f0 / s.rate_hz)))
+        lv.setdefault(k, []).append(s)
+    return lv
 
-    Weights and basis outputs move in the operand width (4 bytes in FP32 mode,
-    2 in the 16-bit modes, 1 in E4M3).  FP32 mode: SNR series are FP32, each
-    level's is written once and read once by the interpolation stage.  16-bit
-    and 8-bit modes: mixing and interpolation are one stage ("mix"); each level
-    k >= 1 writes its y once and the next finer level reads it once (2 bytes per
-    sample, one FP16 plane, in BF16 and E4M3 modes; 4 bytes, BF16 hi + lo, in
-    FP16 mode); the top level writes only per-window partial maxima (two 24-byte
-    records per template and 128 samples).  Interpolation FLOPs are
-    the halfband filter's own (about 17 per output), however it is executed."""
-    w = {"fp32": 4.0, "bf16": 2.0, "fp16": 2.0, "fp8": 1.0}[precision]
+
+def algorithmic_model(bank, units: int, B_s: float, precision: str = "fp32"):
+    """Per-stage algorithmic FLOPs and HBM bytes of one push (all units), and the mix stage's own
+    intermediate traffic.
+
+    The method's work (a2-a5): FIR 2 L Q FLOPs per output; mixing 2 L_k FLOPs per output of each
+    real filter; the x2 interpolation 32 FLOPs per interpolated output (halfband: 32 odd taps
+    on odd outputs, a copy on even ones).  Bytes that must move: weights (re-read per push), the
+    basis outputs between the FIR and the mixing, the strain, and the top-level window records (two
+    32-byte records per template and 128 samples).  Weights and basis outputs move in the operand
+    width of their GEMM (SB_FP8: E4M3 FIR weights, BF16 basis outputs and mixing).  The per-level
+    SNR y_k (k >= 1) that one mixing launch writes and the next finer one reads is the design's own
+    intermediate, reported separately, not as algorithmic work."""
+    w_fir = {"fp32": 4.0, "bf16": 2.0, "fp16": 2.0, "fp8": 1.0}[precision]
+    w_mix = {"fp32": 4.0, "bf16": 2.0, "fp16": 2.0, "fp8": 2.0}[precision]
     fused = precision != "fp32"
     yb = 4.0 if precision == "fp16" else 2.0                   # bytes per stored y sample
     f0 = bank.top_rate_hz
     M2 = 2 * bank.n_templates
-    levels = {}
-    for s in bank.slices:
-        k = int(round(math.log2(f0 / s.rate_hz)))
-        levels.setdefault(k, []).append(s)
+    levels = _levels(bank)
     kmax = max(levels)
     fl = {k: 0.0 for k in ("fir", "mix", "upsample", "decimate", "trigger")}
     by = {k: 0.0 for k in fl}
+    inter = 0.0
     for s in bank.slices:
         L, Q = s.basis.shape
         N = B_s * s.rate_hz
         fl["fir"] += 2.0 * L * Q * N
-        by["fir"] += w * (L * Q + N + L * N)
+        by["fir"] += w_fir * L * Q + w_fir * N + w_mix * L * N
     for k, ss in levels.items():
         Lk = sum(s.basis.shape[0] for s in ss)
         N = B_s * f0 / 2 ** k
         fl["mix"] += 2.0 * M2 * Lk * N
-        if fused:
-            by["mix"] += w * (M2 * Lk + Lk * N) + (2 * yb * M2 * N if k >= 1 else 0.0)
-        else:
-            by["mix"] += w * (M2 * Lk + Lk * N) + 4.0 * M2 * N * (2 if k < kmax else 1)
+        by["mix"] += w_mix * (M2 * Lk + Lk * N)
+        if fused and k >= 1:
+            inter += 2 * yb * M2 * N
+        if not fused:
+            by["mix"] += 4.0 * M2 * N * (2 if k < kmax else 1)
     if fused:
-        by["mix"] += (M2 / 2) * (B_s * f0 / 128) * 2 * 24.0          # top-level window records
+        by["mix"] += (M2 / 2) * (B_s * f0 / 128) * 2 * RECORD_BYTES
+    for k in range(0, kmax):
+        N = B_s * f0 / 2 ** k                                   # interpolated outputs at level k
+        if fused:
+            fl["mix"] += M2 * N * INTERP_FLOPS_PER_OUTPUT
+        else:
+            fl["upsample"] += M2 * N * INTERP_FLOPS_PER_OUTPUT
+            by["upsample"] += 4.0 * M2 * (N / 2 + N)
     for k in range(1, kmax + 1):
         N = B_s * f0 / 2 ** k
-        if fused:
-            fl["mix"] += M2 * (2 * N) * 17                            # the halfband filter's own work
-        else:
-            fl["upsample"] += M2 * (2 * N) * 17
-            by["upsample"] += 4.0 * M2 * (N + 2 * N)
-        fl["decimate"] += 2 * N * 17
+        fl["decimate"] += 2 * N * 33
         by["decimate"] += 4.0 * (3 * N)
-    fl["trigger"] = 3.0 * M2 / 2 * B_s * f0
-    by["trigger"] = 4.0 * M2 * B_s * f0
-    return {k: fl[k] * units for k in fl}, {k: by[k] * units for k in by}
+    fl["trigger"] = 3.0 * M2 / 2 * B_s * f0 if not fused else 0.0
+    # FP32: the top-rate SNR block is read once; fused modes: the window records the mixing wrote
+    by["trigger"] = 4.0 * M2 * B_s * f0 if not fused else (M2 / 2) * (B_s * f0 / 128) * 2 * RECORD_BYTES
+    return {k: fl[k] * units for k in fl}, {k: by[k] * units for k in by}, inter * units
+
+
+def model_sum(banks_units, B_s, precision):
+    flops, bytes_, inter = {}, {}, 0.0
+    for b, n in banks_units:
+        f1, b1, i1 = algorithmic_model(b, n, B_s, precision)
+        for k in f1:
+            flops[k] = flops.get(k, 0.0) + f1[k]
+            bytes_[k] = bytes_.get(k, 0.0) + b1[k]
+        inter += i1
+    return flops, bytes_, inter
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -185,25 +232,23 @@ class ClockSampler:
 BLAS_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
 
-def _oracle_worker(args):
-    """One oracle run (FP64): SVD path + window maxima on a strain excerpt."""
-    bank, strain, win_len, threshold = args
+_WORKER_BANK = None
+
+
+def _init_worker(bank):
+    global _WORKER_BANK
+    _WORKER_BANK = bank
+
+
+def _oracle_task(args):
+    """One oracle run (FP64): SVD path + window maxima on a seeded strain excerpt."""
+    n, seed, win_len, threshold = args
     import oracle
+    strain = synth.white_noise(n, 7, *seed)
     t = time.perf_counter()
-    x = oracle.lloid_snr(bank, strain)
+    x = oracle.lloid_snr(_WORKER_BANK, strain)
     oracle.triggers(x, win_len, threshold, x.shape[1])
     return time.perf_counter() - t
-
-
-def _blas_threads() -> int:
-    """Threads numpy's BLAS uses in this process (threadpoolctl when present)."""
-    try:
-        from threadpoolctl import threadpool_info
-        n = [p.get("num_threads", 1) for p in threadpool_info() if p.get("user_api") == "blas"]
-        return max(n) if n else 1
-    except ImportError:
-        v = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
-        return int(v) if v else (os.cpu_count() or 1)
 
 
 def oracle_bank(h, spec):
@@ -211,60 +256,96 @@ def oracle_bank(h, spec):
     return oracle.build_bank(h, spec.top_rate_hz, spec.slices)
 
 
-def cpu_baseline(h, spec, seconds: float, workers: int):
+def _available_bytes() -> int:
+    try:
+        import psutil
+        return int(psutil.virtual_memory().available)
+    except ImportError:
+        return int(os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE"))
+
+
+def cpu_workers(seconds: float) -> int:
+    """All host cores, one oracle process each, as far as host memory holds them (about 0.35 GB per
+    second of excerpt per process for the production bin)."""
+    cores = os.cpu_count() or 1
+    per = 0.5e9 + 0.35e9 * seconds
+    return max(1, min(cores, int(0.7 * _available_bytes() / per)))
+
+
+class OraclePool:
+    """`workers` spawned host processes holding the oracle's bank, BLAS pinned to one thread each."""
+
+    def __init__(self, ob, workers: int):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.workers = workers
+        saved = {k: os.environ.get(k) for k in BLAS_ENV}
+        for k in BLAS_ENV:                       # children read these when they import numpy
+            os.environ[k] = "1"
+        try:
+            self.ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"),
+                                             initializer=_init_worker, initargs=(ob,))
+            list(self.ex.map(abs, range(workers)))          # start every process before timing
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def step(self, n: int, win_len: int, key: int) -> float:
+        """Wall time of one round: every process filters its own n-sample excerpt."""
+        t = time.perf_counter()
+        list(self.ex.map(_oracle_task, [(n, (key, w), win_len, 6.0) for w in range(self.workers)]))
+        return time.perf_counter() - t
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def cpu_baseline(ob, spec, seconds: float, workers: int):
     """The oracle as it stands on `workers` host processes, each on its own excerpt."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
-    ob = oracle_bank(h, spec)
     f0 = spec.top_rate_hz
     n = int(seconds * f0) // 32 * 32
-    jobs = [(ob, synth.white_noise(n, 7, w, 0), int(f0), 6.0) for w in range(workers)]
-    ctx = mp.get_context("spawn")
-    saved = {k: os.environ.get(k) for k in BLAS_ENV}
-    for k in BLAS_ENV:                       # children read these when they import numpy
-        os.environ[k] = "1"
+    pool = OraclePool(ob, workers)
     try:
-        t = time.perf_counter()
-        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
-            list(ex.map(_oracle_worker, jobs))
-        wall = time.perf_counter() - t
+        wall = pool.step(n, int(f0), 0)
     finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+        pool.close()
     value = workers * spec.n_templates * (n / f0) / wall
     return {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
-            "sample": f"{workers} processes x {n / f0:.0f} s excerpt of one unit of the production bin "
-                      f"({spec.n_templates} templates), FP64 SVD path + window maxima, BLAS 1 thread each; "
-                      f"wall {wall:.1f} s incl. process start"}
+            "host_cpu_count": os.cpu_count(),
+            "sample": f"{workers} processes (host has {os.cpu_count()} cores) x {n / f0:.0f} s excerpt "
+                      f"of one unit of the production bin ({spec.n_templates} templates), FP64 SVD path + window "
+                      f"maxima, BLAS 1 thread each; wall {wall:.1f} s (processes started before timing)"}
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle on the host cores, same metric and workload shape."""
+    """--impl reference: the FP64 oracle on the host cores, same metric, workload and config."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     spec, h = production_bank_templates(0, args.templates)
     ob = oracle_bank(h, spec)
+    del h
     f0 = spec.top_rate_hz
     n = int(min(args.cpu_seconds, 4.0) * f0) // 32 * 32
-    times = []
-    for step in range(args.warmup + args.steps):
-        d = synth.white_noise(n, 8, 0, step)
-        dt = _oracle_worker((ob, d, int(f0), 6.0))
-        if step >= args.warmup:
-            times.append(dt)
+    workers = cpu_workers(n / f0)
+    pool = OraclePool(ob, workers)
+    try:
+        times = [pool.step(n, int(f0), 1 + step) for step in range(args.warmup + args.steps)][args.warmup:]
+    finally:
+        pool.close()
     total = sum(times)
-    value = args.steps * spec.n_templates * (n / f0) / total
+    value = args.steps * workers * spec.n_templates * (n / f0) / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"production bin ({spec.n_templates} templates, 6 slices 4096-128 Hz), "
-                                   f"one unit, {n / f0:.0f} s excerpt per step", "templates": spec.n_templates},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
-                             "sample": f"{n / f0:.0f} s excerpt of one unit per step, one process"},
+            "config": production_config(spec, [s.basis.shape[0] for s in ob.slices], args.push_seconds),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "host_cpu_count": os.cpu_count(),
+                             "sample": f"each step: {workers} processes x a {n / f0:.0f} s excerpt of one unit "
+                                       f"(independent noise), FP64 SVD path + window maxima, BLAS 1 thread each"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -304,60 +385,132 @@ def measured_traffic(stage: str, workload: str, precision: str):
     return float(rec["dram_bytes_per_step"]) if sha == rec.get("kernel_source_sha256_16") else None
 
 
-def roofline_of(stages, flops, bytes_, precision, steps, peaks, workload="production"):
-    """Bound, achieved and fraction of the stage that takes the most device time among the stages
-    with an algorithmic model (the refinement's work depends on how many candidates the data
-    produce, so it has none and is reported through its time share only)."""
+def roofline_of(stages, flops, bytes_, inter, precision, steps, peaks, workload="production"):
+    """Roofline of the stage that takes the most device time among the stages with an
+    algorithmic model (the refinement's work depends on the candidates the data produce, so it
+    has none and is reported through its time share only).  `achieved` = the stage's
+    algorithmic work per push / its mean CUDA-event time per push."""
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12            # FP32 FFMA lanes x 2 FLOP x max clock
     tensor_peak = peaks.get("bf16_tflops", 1800.0)             # dense BF16 = FP16 rate, burst (short steps)
     busy = {k: v[0] for k, v in stages.items() if v[1] > 0 and (flops.get(k, 0.0) > 0 or bytes_.get(k, 0.0) > 0)}
     dom = max(busy, key=busy.get)
-    dom_ms, _ = stages[dom]
-    on_tensor = precision in ("bf16", "fp16") and dom in ("fir", "mix")
-    cpeak = tensor_peak if on_tensor else alu_peak
-    t_c = flops.get(dom, 0.0) / (cpeak * 1e12)
-    t_m = bytes_.get(dom, 0.0) / (hbm_peak * 1e9)
-    secs = dom_ms / 1e3
-    if t_c >= t_m:
-        ach = flops[dom] * steps / secs / 1e12
-        return dom, {"bound": "tensor" if on_tensor else "alu", "achieved": ach, "peak": cpeak, "unit": "TFLOP/s",
-                     "frac": ach / cpeak, "traffic": None, "kernel": dom,
-                     "peak_source": "measured bf16_tflops (burst)" if on_tensor else
-                     "derived: 148 SM x 128 FP32 lanes x 2 FLOP x max SM clock"}
-    ach = bytes_[dom] * steps / secs / 1e9
-    return dom, {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                 "traffic": measured_traffic(dom, workload, precision), "algorithmic_bytes": bytes_[dom],
-                 "kernel": dom, "peak_source": "measured hbm_gbs"}
+    out = {}
+    for st in sorted(busy, key=busy.get, reverse=True)[:2]:
+        st_ms, _ = stages[st]
+        on_tensor = precision != "fp32" and st in ("fir", "mix")
+        cpeak = tensor_peak if on_tensor else alu_peak
+        # SB_FP8's basis FIR: E4M3 operands (nominal 2x the BF16 rate) with the strain as two terms
+        src = "measured bf16_tflops (burst)" if on_tensor else "derived: 148 SM x 128 FP32 lanes x 2 FLOP x max SM clock"
+        if precision == "fp8" and st == "fir":
+            cpeak, src = 2.0 * tensor_peak, "measured bf16_tflops (burst) x 2 (E4M3 nominal ratio)"
+        t_c = flops.get(st, 0.0) / (cpeak * 1e12)
+        t_m = bytes_.get(st, 0.0) / (hbm_peak * 1e9)
+        secs = st_ms / 1e3 / steps
+        kname = {"mix": "tc_mixup_kernel (a3 mixing + a4 interpolation + a5 window partials)",
+                 "fir": "tc_fir_kernel (a2 basis FIR)"}.get(st, st) if precision != "fp32" else st
+        if t_c >= t_m:
+            ach = flops[st] / secs / 1e12
+            r = {"bound": "tensor" if on_tensor else "alu", "achieved": ach, "peak": cpeak, "unit": "TFLOP/s",
+                 "frac": ach / cpeak, "algorithmic_flops_per_push": flops[st],
+                 "algorithmic_bytes_per_push": bytes_.get(st, 0.0), "time_at_peak_us": 1e6 * t_c,
+                 "time_us": 1e6 * secs}
+        else:
+            ach = bytes_[st] / secs / 1e9
+            r = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                 "algorithmic_bytes_per_push": bytes_[st], "time_at_peak_us": 1e6 * t_m, "time_us": 1e6 * secs}
+            src = "measured hbm_gbs"
+        r["traffic"] = measured_traffic(st, workload, precision)
+        if st == "mix" and precision != "fp32":
+            r["intermediate_bytes_per_push"] = inter
+        r["kernel"] = kname
+        r["peak_source"] = src + " (of measured)" if "measured" in src else src
+        out[st] = r
+    return dom, out
 
 
-def run_serve(args):
-    """Streaming serving loop: bins x 2 detectors of 1-s buffers arriving as Poisson processes."""
-    import torch
-    import paper_2410_16416_b300 as lloid
-    from paper_2410_16416_b300 import serve
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:                                     # ranks serve disjoint bins; only the report is reduced
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+def make_units_for(ctx, banks, precision, B, xi2_on=True, threshold=6.0, refine=5.5):
+    """The two detectors of a bin share one copy of the bank's device data (svdbank_create_like)."""
+    units = []
+    for b in banks:
+        if not xi2_on:
+            b.autocorr = None
+        u0 = ctx.create_unit(b, detector=0, precision=precision, threshold=threshold, refine_threshold=refine,
+                             window_s=1.0, max_push_samples=B)
+        units += [u0, ctx.create_like(u0, detector=1)]
+    return units
+
+
+def device_arm(lloid, torch, stream, local, banks, precision, B, steps, warmup, dev, graphs, autotune, barrier,
+               flush, n_prof=None):
+    """Time `steps` grouped pushes of B samples per unit with the strain resident in HBM."""
+    ctx = lloid.Context(local, stream=stream.cuda_stream)
+    ctx.graphs(graphs)
+    ctx.autotune(autotune)
+    tc0 = time.perf_counter()
+    units = make_units_for(ctx, banks, precision, B)
+    create_s = time.perf_counter() - tc0
+    dets = [det for _ in banks for det in (0, 1)]
+    n_units = len(units)
+    n_prof = min(steps, 16) if n_prof is None else n_prof
+    t = 0
+    for _ in range(warmup):
+        ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
+        t += B
+    ctx.pop_triggers()
+    barrier()
+    st0 = ctx.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    w0 = time.perf_counter()
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
+        ev[i][1].record(stream)
+        t += B
+    barrier()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    st1 = ctx.stats()
+    # stage split from separate pushes with every launch bracketed by events (not timed above)
+    ctx.profile(True)
+    for i in range(n_prof):
+        flush.zero_()
+        ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
+        t += B
+    stages = ctx.stage_times()
+    ctx.profile(False)
+    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    trig = ctx.pop_triggers()
+    tuned = ctx.autotune_choices()
+    ctx.close()
+    return {"dev_s": dev_s, "wall": wall, "clocks": clk, "create_s": create_s, "stages": stages,
+            "launches": st1["kernel_launches"] - st0["kernel_launches"],
+            "autotune": {"choices": tuned, "timed_launches": st1["autotune_launches"],
+                         "in_timed_region": st1["autotune_launches"] - st0["autotune_launches"]},
+            "refine_candidates": st1["refine_candidates"] - st0["refine_candidates"], "prof_steps": n_prof,
+            "triggers": int(len(trig)), "n_units": n_units}
+
+
+def serve_once(lloid, serve, args, precision, rank, world, local):
+    """Serving loop (1-s buffers, Poisson arrivals) over this rank's bins; returns the report summary."""
     banks = [synth.production_shape_bank(i) for i in range(args.distinct_banks)]
     g = np.random.default_rng(20241016 + rank)
     reqs = []
-    for b in shard_bins(args.bins, rank, world):
+    for b in shard_bins(args.serve_bins, rank, world):
         bank = banks[b % len(banks)]
         for det in (0, 1):
             reqs.append(serve.StreamRequest(
                 name=f"bin{b}-det{det}", bank=bank, detector=det,
                 arrivals=serve.poisson_arrivals(g, args.serve_seconds, float(g.uniform(0.0, 5.0))),
                 strain=(lambda j, b=b, det=det: synth.white_noise_block(j, 4096, 9, b, det)),
-                unit_kwargs=dict(precision=args.precision, threshold=6.0, refine_threshold=5.5),
+                unit_kwargs=dict(precision=precision, threshold=6.0, refine_threshold=5.5),
                 share_key=f"bank{b % len(banks)}"))
-    ctx = lloid.Context(int(os.environ.get("LOCAL_RANK", "0")))
+    ctx = lloid.Context(local)
     tl = time.perf_counter()
     anchors = serve.preload(ctx, reqs, 4096)          # banks are loaded before data arrive
     load_s = time.perf_counter() - tl
@@ -365,30 +518,42 @@ def run_serve(args):
     st = ctx.stats()
     ctx.close()
     s = rep.summary()
-    value, wall = job_rate(rep.template_seconds, rep.wall_s, dist, "cuda")
-    p99 = s["p99_latency_s"] or 0.0
-    if dist is not None:                              # the slowest rank's p99 and max (a conservative merge)
-        lat = torch.tensor([p99, s["max_latency_s"] or 0.0], dtype=torch.float64, device="cuda")
-        dist.all_reduce(lat, op=dist.ReduceOp.MAX)
-        p99, s["max_latency_s"] = float(lat[0]), float(lat[1])
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+    s["bank_load_s"] = load_s
+    s["template_seconds"] = rep.template_seconds
+    s["gpu_launches"] = st["kernel_launches"]
+    return s
+
+
+def merge_serve(s, dist):
+    """Whole-job serving numbers: template-seconds summed, the slowest rank's wall, the largest p99."""
+    if dist is None:
+        return s
+    import torch
+    v = torch.tensor([s["template_seconds"], s["wall_s"], s["p99_latency_s"] or 0.0, s["max_latency_s"] or 0.0],
+                     dtype=torch.float64, device="cuda")
+    t = v[:1].clone()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    s = dict(s)
+    s["template_seconds"], s["wall_s"], s["p99_latency_s"], s["max_latency_s"] = float(t[0]), float(v[1]), \
+        float(v[2]), float(v[3])
+    s["template_seconds_per_s"] = s["template_seconds"] / s["wall_s"]
+    return s
+
+
+def serve_line(args, s, world, precision):
+    return {"metric": METRIC, "value": s["template_seconds_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": s["pushes"], "warmup": 0, "ms_per_step": 1e3 * s["wall_s"] / max(1, s["pushes"]),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[precision],
             "data": "synthetic (seeded white noise per (bin, detector, buffer); production-shaped random banks)",
-            "config": {"workload": f"serve: {args.bins} bins x 2 detectors, 1-s buffers, Poisson arrivals "
+            "config": {"workload": f"serve: {args.serve_bins} bins x 2 detectors, 1-s buffers, Poisson arrivals "
                                    f"(1/s per stream) for {args.serve_seconds} s, banks cycled from "
-                                   f"{len(banks)} production-shaped banks (~1000 templates, 6 slices)",
-                       "time_scale": args.time_scale, "precision": args.precision,
-                       "bank_load_s": load_s},
-            "latency": {"p50_s": s["p50_latency_s"], "p99_s": p99, "max_s": s["max_latency_s"],
+                                   f"{args.distinct_banks} production-shaped banks (~1000 templates, 6 slices)",
+                       "time_scale": args.time_scale, "precision": precision, "bank_load_s": s["bank_load_s"]},
+            "latency": {"p50_s": s["p50_latency_s"], "p99_s": s["p99_latency_s"], "max_s": s["max_latency_s"],
                         "buffers": s["buffers"], "definition": "buffer arrival -> its push finished and its "
                                                                "triggers host-visible"},
-            "serving": s, "gpu_launches": st["kernel_launches"]}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+            "serving": s, "gpu_launches": s["gpu_launches"]}
 
 
 def main():
@@ -396,11 +561,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload == "serve":
-        run_serve(args)
-        return
     import torch
     import paper_2410_16416_b300 as lloid
+    from paper_2410_16416_b300 import serve
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -416,116 +579,104 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    if args.workload == "production":
-        spec, h = production_bank_templates(rank, args.templates)
-        bank = lloid.decompose(h, spec.top_rate_hz, spec.slices)
-        if args.xi2 == "off":
-            bank.autocorr = None
-        banks = [bank]
-        f0 = int(spec.top_rate_hz)
-    else:                       # uneven shape-only bins; rank r takes bins r, r + world, ...
-        banks = [synth.shape_only_bank(b) for b in shard_bins(args.bins, rank, world)]
-        spec, h, bank = None, None, banks[0]
-        f0 = int(banks[0].top_rate_hz)
-    B = args.push_seconds * f0
-    n_prof = min(args.steps, 16)                       # profiled pushes after the timed ones (stage split)
-    total_s = (args.warmup + args.steps + n_prof) * args.push_seconds
-    if spec is not None:
-        strains = [make_strain(rank, det, total_s, f0, h, spec.n_templates) for det in (0, 1)]
-    else:                       # every bank of a detector filters that detector's strain
-        strains = [synth.white_noise(int(total_s * f0), 3, rank, det) for det in (0, 1)]
-    dev = [torch.from_numpy(s).cuda() for s in strains]
-    unit_specs = [(b, det) for b in banks for det in (0, 1)]
-    n_templates_all = sum(b.n_templates for b, _ in unit_specs)
+    if args.workload == "serve":                      # the serving loop alone as the line
+        s = merge_serve(serve_once(lloid, serve, args, args.precision, rank, world, local), dist)
+        if rank == 0:
+            print(json.dumps(serve_line(args, s, world, args.precision)), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
     # One non-default stream for the library, the L2 flush and the timing events.
     # (torch's default stream has handle 0, which the C ABI reads as "no stream".)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    n_units = len(unit_specs)
-    tpl_s_rank = n_templates_all * args.push_seconds * args.steps
+    graphs, autotune = args.graphs == "on", args.autotune == "on"
 
-    def make_units(ctx, precision):
-        # the two detectors of a bin share one copy of the bank's device data (svdbank_create_like)
-        units = []
-        for b in banks:
-            u0 = ctx.create_unit(b, detector=0, precision=precision, threshold=6.0, refine_threshold=5.5,
-                                 window_s=1.0, max_push_samples=B)
-            units += [u0, ctx.create_like(u0, detector=1)]
-        return units
+    def batch_run(precision, n_bins, steps, warmup, push_s):
+        banks = [synth.shape_only_bank(b) for b in shard_bins(n_bins, rank, world)]
+        f0 = int(banks[0].top_rate_hz)
+        B = push_s * f0
+        total = (warmup + steps + min(steps, 16)) * push_s
+        strains = [synth.white_noise(int(total * f0), 3, rank, det) for det in (0, 1)]
+        dev = [torch.from_numpy(s).cuda() for s in strains]
+        r = device_arm(lloid, torch, stream, local, banks, precision, B, steps, warmup, dev, graphs, autotune,
+                       barrier, flush)
+        tpl = sum(2 * b.n_templates for b in banks) * push_s * steps
+        r["value"], r["dev_s"] = job_rate(tpl, r["dev_s"], dist, "cuda")
+        r["banks"], r["B_s"] = banks, push_s
+        r["templates"] = sum(2 * b.n_templates for b in banks)
+        return r
 
-    def device_arm(precision):
-        ctx = lloid.Context(local, stream=stream.cuda_stream)
-        ctx.graphs(args.graphs == "on")
-        ctx.autotune(args.autotune == "on")
-        tc0 = time.perf_counter()
-        units = make_units(ctx, precision)
-        create_s = time.perf_counter() - tc0
-        dets = [det for _, det in unit_specs]
-        t = 0
-        for _ in range(args.warmup):
-            ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
-            t += B
-        ctx.pop_triggers()
-        barrier()
-        st0 = ctx.stats()
-        clocks = ClockSampler(local)
-        clocks.start()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        barrier()
-        w0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
-            ev[i][1].record(stream)
-            t += B
-        barrier()
-        wall = time.perf_counter() - w0
-        clk = clocks.stop()
-        st1 = ctx.stats()
-        # stage split from separate pushes with every launch bracketed by events (not timed above)
-        ctx.profile(True)
-        for i in range(n_prof):
-            flush.zero_()
-            ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
-            t += B
-        stages = ctx.stage_times()
-        ctx.profile(False)
-        value, dev_s = job_rate(tpl_s_rank, sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, "cuda")
-        trig = ctx.pop_triggers()
-        tuned = ctx.autotune_choices()
-        ctx.close()
-        return {"value": value, "autotune": {"choices": tuned, "timed_launches": st1["autotune_launches"],
-                                             "in_timed_region": st1["autotune_launches"] - st0["autotune_launches"]}, "dev_s": dev_s, "wall": wall, "clocks": clk, "create_s": create_s,
-                "stages": stages, "launches": st1["kernel_launches"] - st0["kernel_launches"],
-                "refine_candidates": st1["refine_candidates"] - st0["refine_candidates"], "prof_steps": n_prof,
-                "triggers": int(len(trig))}
+    if args.workload == "batch":                      # the grouped batch alone as the line
+        r = batch_run(args.precision, args.bins, args.steps, args.warmup, args.push_seconds)
+        flops, bytes_, inter = model_sum([(b, 2) for b in r["banks"]], args.push_seconds, args.precision)
+        dom, roofs = roofline_of(r["stages"], flops, bytes_, inter, args.precision, r["prof_steps"], peaks, "batch")
+        busy = {k: v[0] for k, v in r["stages"].items() if v[1] > 0}
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * r["dev_s"] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
+                "data": "synthetic (seeded white noise; shape-only random banks)",
+                "config": {"workload": f"batch: {args.bins} uneven SVD bins x 2 detectors (M logU[200,2000], "
+                                       f"3-8 slices, 2-120 s templates, L logU[50,600]), one grouped push per step, "
+                                       f"{args.push_seconds} s pushes", "templates": r["templates"],
+                           "units_per_gpu": r["n_units"], "setup_s": r["create_s"]},
+                "roofline": roofs[dom], "roofline_stages": roofs, "gpu_launches": r["launches"],
+                "clocks": r["clocks"],
+                "stages_ms_share": {k: round(v / sum(busy.values()), 4) for k, v in busy.items()}}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
-    prim = device_arm(args.precision)
+    # ---- headline: the production bin x 2 detectors
+    spec, h = production_bank_templates(rank, args.templates)
+    bank = lloid.decompose(h, spec.top_rate_hz, spec.slices)
+    if args.xi2 == "off":
+        bank.autocorr = None
+    f0 = int(spec.top_rate_hz)
+    B = args.push_seconds * f0
+    n_prof = min(args.steps, 16)
+    total_s = (args.warmup + args.steps + n_prof) * args.push_seconds
+    strains = [make_strain(rank, det, total_s, f0, h, spec.n_templates) for det in (0, 1)]
+    dev = [torch.from_numpy(s).cuda() for s in strains]
+    tpl_s_rank = 2 * spec.n_templates * args.push_seconds * args.steps
+
+    def prod_arm(precision, push_s=args.push_seconds, steps=args.steps):
+        r = device_arm(lloid, torch, stream, local, [bank], precision, push_s * f0, steps, args.warmup, dev, graphs,
+                       autotune, barrier, flush)
+        r["value"], r["dev_s"] = job_rate(2 * spec.n_templates * push_s * steps, r["dev_s"], dist, "cuda")
+        return r
+
+    prim = prod_arm(args.precision)
     others = {}
     for p in args.compare.split(","):
         p = p.strip()
         if p and p != "none" and p != args.precision:
-            others[p] = device_arm(p)
+            others[p] = prod_arm(p)
 
     # e2e: host strain in, triggers out, through the C ABI
     ctx2 = lloid.Context(local, stream=stream.cuda_stream)
-    ctx2.graphs(args.graphs == "on")
-    ctx2.autotune(args.autotune == "on")
-    u2 = make_units(ctx2, args.precision)
-    dets = [det for _, det in unit_specs]
+    ctx2.graphs(graphs)
+    ctx2.autotune(autotune)
+    u2 = make_units_for(ctx2, [bank], args.precision, B)
     t2 = 0
     for _ in range(args.warmup):
-        ctx2.push_group(u2, [strains[det][t2:t2 + B] for det in dets], [t2] * n_units, False)
+        ctx2.push_group(u2, [strains[det][t2:t2 + B] for det in (0, 1)], [t2] * 2, False)
         ctx2.pop_triggers()
         t2 += B
     barrier()
     s0 = ctx2.stats()
     w1 = time.perf_counter()
     for i in range(args.steps):
-        ctx2.push_group(u2, [strains[det][t2:t2 + B] for det in dets], [t2] * n_units, False)
+        ctx2.push_group(u2, [strains[det][t2:t2 + B] for det in (0, 1)], [t2] * 2, False)
         ctx2.pop_triggers()
         t2 += B
     ctx2.sync()
@@ -538,39 +689,23 @@ def main():
            "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // args.steps}
     ctx2.close()
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    flops, bytes_ = {}, {}
-    for b, _ in unit_specs:
-        f1, b1 = algorithmic_model(b, 1, args.push_seconds, args.precision)
-        for k in f1:
-            flops[k] = flops.get(k, 0.0) + f1[k]
-            bytes_[k] = bytes_.get(k, 0.0) + b1[k]
+    flops, bytes_, inter = model_sum([(bank, 2)], args.push_seconds, args.precision)
     flops["refine"], bytes_["refine"] = 0.0, 0.0          # data-dependent: no fixed algorithmic work
-    dom, roof = roofline_of(prim["stages"], flops, bytes_, args.precision, prim["prof_steps"], peaks, args.workload)
+    dom, roofs = roofline_of(prim["stages"], flops, bytes_, inter, args.precision, prim["prof_steps"], peaks)
     busy = {k: v[0] for k, v in prim["stages"].items() if v[1] > 0}
     total_stage_ms = sum(busy.values())
+    config = production_config(spec, bank.basis_counts(), args.push_seconds)
     line = {"metric": METRIC, "value": prim["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * prim["dev_s"] / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision],
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic (seeded white noise, random-parameter Newtonian chirp bank, injections)",
-            "config": {"workload": (f"production bin: {spec.n_templates} templates x 2 detectors, 6 slices "
-                                    f"4096-128 Hz, L={bank.basis_counts()}, {args.push_seconds} s pushes")
-                       if spec is not None else
-                       (f"batch: {len(banks)} uneven SVD bins x 2 detectors ({n_units} units, "
-                        f"{n_templates_all} templates; M logU[200,2000], 3-8 slices, 2-120 s templates, "
-                        f"L logU[50,600]), one grouped push per step, {args.push_seconds} s pushes"),
-                       "templates": n_templates_all, "units_per_gpu": n_units, "setup_s": prim["create_s"],
-                       "push_seconds": args.push_seconds, "precision": args.precision,
-                       "parallelism": f"units sharded, {world} GPU(s)", "cuda_graphs": args.graphs,
-                       "mix_autotune": args.autotune,
-                       "xi2": args.xi2 if spec is not None else "off",
-                       "l2": "flushed between steps (256 MB write outside the step events)"},
-            "roofline": roof, "e2e": e2e, "gpu_launches": prim["launches"], "clocks": prim["clocks"],
+            "config": config,
+            "run": {"setup_s": prim["create_s"], "precision": args.precision,
+                    "parallelism": f"units sharded, {world} GPU(s)", "cuda_graphs": args.graphs,
+                    "mix_autotune": args.autotune, "xi2": args.xi2,
+                    "l2": "flushed between steps (256 MB write outside the step events)"},
+            "roofline": roofs[dom], "roofline_stages": roofs, "e2e": e2e, "gpu_launches": prim["launches"],
+            "clocks": prim["clocks"],
             "stages_ms_share": {k: round(v / total_stage_ms, 4) for k, v in busy.items()},
             "by_precision": {p: {"value": r["value"], "ms_per_step": 1e3 * r["dev_s"] / args.steps,
                                  "gain_vs_fp32": None}
@@ -582,8 +717,44 @@ def main():
         ref = line["by_precision"]["fp32"]["value"]
         for p in line["by_precision"]:
             line["by_precision"][p]["gain_vs_fp32"] = line["by_precision"][p]["value"] / ref
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and spec is not None:
-        line["cpu_baseline"] = cpu_baseline(h, spec, args.cpu_seconds, max(1, min(os.cpu_count() or 1, 16)))
+    subs = [s.strip() for s in args.sub.split(",") if s.strip() and s.strip() != "none"]
+    if "push1s" in subs:                              # the same bin with 1-s buffers (weights re-read per second)
+        r1 = prod_arm(args.precision, push_s=1, steps=4 * args.steps)
+        f1, b1, i1 = model_sum([(bank, 2)], 1, args.precision)
+        _, roof1 = roofline_of(r1["stages"], f1, b1, i1, args.precision, r1["prof_steps"], peaks)
+        line["push_1s"] = {"value": r1["value"], "ms_per_step": 1e3 * r1["dev_s"] / (4 * args.steps),
+                           "steps": 4 * args.steps, "precision": args.precision,
+                           "mix_frac": roof1.get("mix", {}).get("frac"), "clocks": r1["clocks"]}
+    if "batch" in subs:                               # grouped batch of uneven bins (one launch per stage)
+        tb = time.perf_counter()
+        rb = batch_run(args.precision, args.bins, args.batch_steps, 2, args.batch_push_seconds)
+        fb, bb, ib = model_sum([(b, 2) for b in rb["banks"]], args.batch_push_seconds, args.precision)
+        _, roofb = roofline_of(rb["stages"], fb, bb, ib, args.precision, rb["prof_steps"], peaks, "batch")
+        bbusy = {k: v[0] for k, v in rb["stages"].items() if v[1] > 0}
+        line["batch"] = {"value": rb["value"], "ms_per_step": 1e3 * rb["dev_s"] / args.batch_steps,
+                         "steps": args.batch_steps, "precision": args.precision,
+                         "workload": f"{args.bins} uneven SVD bins x 2 detectors ({rb['n_units']} units, "
+                                     f"{rb['templates']} templates; M logU[200,2000], 3-8 slices, 2-120 s "
+                                     f"templates, L logU[50,600]), one grouped push of {args.batch_push_seconds} s "
+                                     f"per step, every stage one launch over all units",
+                         "gain_vs_fp32_production": None, "setup_s": rb["create_s"],
+                         "run_s": time.perf_counter() - tb, "gpu_launches_per_step": rb["launches"] / args.batch_steps,
+                         "roofline_stages": roofb, "clocks": rb["clocks"],
+                         "stages_ms_share": {k: round(v / sum(bbusy.values()), 4) for k, v in bbusy.items()}}
+        del rb
+    if "serve" in subs:                               # the serving loop, 1-s buffers, p50 / p99 latency
+        line["serve"] = {}
+        for p in [x.strip() for x in args.serve_precisions.split(",") if x.strip()]:
+            s = merge_serve(serve_once(lloid, serve, args, p, rank, world, local), dist)
+            line["serve"][p] = {"template_s_per_s": s["template_seconds_per_s"], "p50_latency_s": s["p50_latency_s"],
+                                "p99_latency_s": s["p99_latency_s"], "max_latency_s": s["max_latency_s"],
+                                "buffers": s["buffers"], "pushes": s["pushes"], "wall_s": s["wall_s"],
+                                "bank_load_s": s["bank_load_s"], "max_concurrent_streams": s["max_concurrent_streams"],
+                                "workload": f"{args.serve_bins} bins x 2 detectors, 1-s buffers, Poisson arrivals "
+                                            f"(1/s per stream) for {args.serve_seconds} s, real time"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ob = oracle_bank(h, spec)
+        line["cpu_baseline"] = cpu_baseline(ob, spec, args.cpu_seconds, cpu_workers(args.cpu_seconds))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -232,6 +232,60 @@ int triggers_pop(sb_ctx *ctx, sb_trigger *out, int64_t cap, int64_t *n_out);
  * n in [*first_sample, *first_sample + *n).  Needs SB_FLAG_KEEP_SNR. */
 int sb_unit_snr(sb_unit *unit, float *host_out, int64_t cap, int64_t *first_sample, int64_t *n);
 
+/* ---- data conditioning: PSD estimate, whitening, gating ------------------ */
+/* The conditioning stage that precedes the filter (Sec. II.A: the PSD is
+ * estimated, its running average whitens the strain, large deviations of the
+ * whitened data are gated and removed; Fig. 1: "whitening and gating").  The
+ * paper names the steps only; this library's readings:
+ *   whitening: segments of fft_len = N samples every H = N/2 samples
+ *     (segment j covers input samples [jH, jH + N); the strain is 0 before
+ *     sample 0), periodic Hann window w[n] = sin^2(pi n / N);
+ *     X_j = DFT(w d_j), S_j = |X_j|^2 / sum w^2 per frequency bin;
+ *     running average P_j = P_{j-1} + (S_j - P_{j-1}) / min(j + 1, n_avg);
+ *     segment j is divided by sqrt(P_{j-1}) (segment 0 by sqrt(P_0)), inverse
+ *     DFT, overlap-add.  White noise of variance s^2 comes out as d / s.
+ *   gating: every whitened sample with |x| > gate_threshold is a glitch
+ *     sample; samples within gate_half of one are set to 0 and the weight
+ *     returns to 1 as sin^2(pi (r - gate_half) / (2 gate_taper)) for distances
+ *     gate_half < r < gate_half + gate_taper.
+ * FP32 on the device (FFT in shared memory).  One sb_cond per detector stream;
+ * its work is queued on the context's stream, ordered with filter_push. */
+typedef struct sb_cond_desc {
+    double rate_hz;            /* sample rate of the strain (> 0; informational)   */
+    int32_t fft_len;           /* N: a power of two in [64, 16384]                  */
+    int32_t n_avg;             /* running-average length, >= 1                      */
+    float gate_threshold;      /* glitch level of the whitened data; <= 0: no gate   */
+    int32_t gate_half;         /* samples zeroed on each side of a glitch sample     */
+    int32_t gate_taper;        /* samples of the ramp back to full weight, >= 1      */
+    int64_t max_push_samples;  /* largest push, a multiple of N / 2, at most 2^30    */
+} sb_cond_desc;
+typedef struct sb_cond sb_cond;
+/* Allocates the conditioner's device state (zeroed: the strain is 0 before
+ * the first push) on the context's device.  SB_EINVAL for a bad description,
+ * SB_ENOMEM when an allocation fails.  Destroy conditioners before their
+ * context. */
+int sb_cond_create(sb_ctx *ctx, const sb_cond_desc *desc, sb_cond **out);
+/* Waits for the context's queued work and frees the device state (NULL: no-op). */
+int sb_cond_destroy(sb_cond *cond);
+/* latency = N/2 + gate_half + gate_taper: the look-ahead of the overlap-add
+ * and the gate.  Output sample i of the conditioned stream is the conditioned
+ * strain at input sample i - latency (0 for i < latency). */
+int sb_cond_latency(const sb_cond *cond, int64_t *latency_samples);
+/* Push the next n_samples input samples (a positive multiple of N/2, at most
+ * max_push_samples; t0_sample must equal the samples pushed so far, SB_EGAP
+ * otherwise).  strain: FP32, host (on_device = 0, copied before the call
+ * returns) or device (on_device = 1).  out: device FP32 [n_samples], written by
+ * the queued work with output samples [t0_sample, t0_sample + n_samples) of
+ * the conditioned stream, so that a filter_push of out with the same t0 on the
+ * same context follows it in stream order.  Non-blocking. */
+int sb_cond_push(sb_cond *cond, const float *strain, int64_t n_samples, int64_t t0_sample, int32_t on_device,
+                 float *out);
+/* The running PSD average after the segments processed so far (blocks):
+ * *n_bins = N/2 + 1 values P[f] (per-bin variance, bin f at f rate_hz / N Hz;
+ * the one-sided PSD is 2 P[f] / rate_hz) into host_out (cap >= *n_bins, or
+ * cap = 0 to query the sizes only), *segments = segments averaged. */
+int sb_cond_psd(sb_cond *cond, float *host_out, int64_t cap, int64_t *n_bins, int64_t *segments);
+
 /* ---- coincidence generator (host only) ----------------------------------- */
 /* One coincidence: triggers index_a of detector A and index_b of detector B
  * (indices into the arrays passed in), same template, |sample_a - sample_b|
@@ -296,21 +350,24 @@ int sb_ctx_profile(sb_ctx *ctx, int32_t enable);
  * Results are identical either way. */
 int sb_ctx_graphs(sb_ctx *ctx, int32_t enable);
 /* enable != 0 (the default): the first push that launches the mixing kernel
- * (a3 + a4) with a new launch shape (precision, K chunks per tile, whether the
- * level's SNR is stored, tile count rounded down to a power of two) times every
- * pipeline shape that fits in shared memory (mixing stages 1-2, interpolation
- * buffers 1-2, window-ring depth 2-6) on that push's own data, three times in
- * interleaved rounds, and keeps the one with the smallest time for later
- * pushes; that push is not graph-captured.  The pipeline
- * shape changes no arithmetic: results are bitwise the same for every choice.
- * enable == 0: later launches use the built-in shape for new launch shapes
- * (tuned shapes are kept). */
+ * (a3 + a4) with a new launch shape (operand type, whether the level's SNR is
+ * stored, whether it interpolates a coarser level, K chunks per tile, bytes of
+ * K per chunk, tile count rounded down to a power of two) times every pipeline
+ * shape that fits in shared memory (mixing stages 1, 2, 3, 4 or 6,
+ * interpolation buffers 1-2, window-ring depth 2, 3, 4 or 6) on that push's
+ * own data, three times in interleaved rounds, and keeps the one with the
+ * smallest time for later pushes; that push is not graph-captured.  The
+ * pipeline shape changes no arithmetic: results are bitwise the same for every
+ * choice.  enable == 0: later launches use the built-in shape for new launch
+ * shapes (tuned shapes are kept). */
 int sb_ctx_autotune(sb_ctx *ctx, int32_t enable);
 /* The tuned launch shapes: writes min(cap, number tuned) records of four int32
  * {shape key, mixing stages, interpolation buffers, window-ring depth} into out
  * (4 * cap entries) and returns the number of tuned shapes (>= 0), or a
- * negative SB_E* code.  Shape key bits: 0-1 precision (0 FP16, 1 BF16,
- * 2 E4M3), 2 SNR stored, 3-4 K chunks per tile (capped at 3), 5+ log2 tiles. */
+ * negative SB_E* code.  Shape key bits: 0-1 operand type of the mixing (0 FP16,
+ * 1 BF16; SB_FP8 units mix in BF16), 2 SNR stored, 3 interpolates a coarser
+ * level, 4-5 K chunks per tile (capped at 3), 6-7 bytes of K per chunk (0: 32,
+ * 1: 64, 2: 128), 8+ log2 tiles. */
 int sb_ctx_autotune_choices(sb_ctx *ctx, int32_t *out, int32_t cap);
 /* Blocks until queued work is done, then writes per stage the summed kernel
  * time (ms) and the number of launches since profiling was enabled

@@ -95,6 +95,11 @@ SIGNATURES = {
                                              C.c_void_p]),
     "sb_coincidences": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
                                   C.POINTER(C.c_int64)]),
+    "sb_cond_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sb_cond_destroy": (C.c_int, [C.c_void_p]),
+    "sb_cond_latency": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "sb_cond_push": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
+    "sb_cond_psd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sb_last_error": (C.c_char_p, []),
 }
 
@@ -247,7 +252,8 @@ class Context:
         _check(lib.sb_ctx_autotune(self.handle, int(bool(enable))), "sb_ctx_autotune")
 
     def autotune_choices(self) -> list:
-        """[{key, mode, store_y, k_chunks, log2_tiles, stages, u_buffers, window_ring}] tuned so far."""
+        """[{key, mode, store_y, interp, k_chunks, k_bytes, log2_tiles, stages, u_buffers, window_ring}]
+        tuned so far."""
         n = lib.sb_ctx_autotune_choices(self.handle, None, 0)
         _check(min(n, 0), "sb_ctx_autotune_choices")
         buf = (C.c_int32 * (4 * max(n, 1)))()
@@ -256,9 +262,10 @@ class Context:
         out = []
         for i in range(n):
             k = buf[4 * i]
-            out.append({"key": k, "mode": ("fp16", "bf16", "e4m3")[k & 3], "store_y": bool(k & 4),
-                        "k_chunks": (k >> 3) & 3, "log2_tiles": k >> 5, "stages": buf[4 * i + 1],
-                        "u_buffers": buf[4 * i + 2], "window_ring": buf[4 * i + 3]})
+            out.append({"key": k, "mode": ("fp16", "bf16", "?", "?")[k & 3], "store_y": bool(k & 4),
+                        "interp": bool(k & 8), "k_chunks": (k >> 4) & 3, "k_bytes": (32, 64, 128, 0)[(k >> 6) & 3],
+                        "log2_tiles": k >> 8, "stages": buf[4 * i + 1], "u_buffers": buf[4 * i + 2],
+                        "window_ring": buf[4 * i + 3]})
         return out
 
     def stage_times(self) -> dict:
@@ -308,6 +315,56 @@ class Context:
             if n.value < cap:
                 break
         return np.concatenate(chunks) if chunks else np.empty(0, dtype=TRIGGER_DTYPE)
+
+
+class SbCondDesc(C.Structure):
+    _fields_ = [("rate_hz", C.c_double), ("fft_len", C.c_int32), ("n_avg", C.c_int32),
+                ("gate_threshold", C.c_float), ("gate_half", C.c_int32), ("gate_taper", C.c_int32),
+                ("max_push_samples", C.c_int64)]
+
+
+class Conditioner:
+    """sb_cond: PSD running average, whitening and gating of one detector's strain on the device.
+
+    push(strain, out) conditions the next buffer (numpy FP32 or a CUDA tensor) into the CUDA
+    tensor `out` (FP32, same length), delayed by `latency` samples; out can then be pushed to a
+    unit of the same context (on_device)."""
+
+    def __init__(self, ctx: Context, rate_hz: float, fft_len: int, n_avg: int, gate_threshold: float,
+                 gate_half: int, gate_taper: int, max_push_samples: int):
+        d = SbCondDesc(float(rate_hz), int(fft_len), int(n_avg), float(gate_threshold), int(gate_half),
+                       int(gate_taper), int(max_push_samples))
+        h = C.c_void_p()
+        _check(lib.sb_cond_create(ctx.handle, C.byref(d), C.byref(h)), "sb_cond_create")
+        self.ctx, self.handle, self.fft_len = ctx, h, int(fft_len)
+        lat = C.c_int64()
+        _check(lib.sb_cond_latency(self.handle, C.byref(lat)), "sb_cond_latency")
+        self.latency = lat.value
+        self.pushed = 0
+
+    def push(self, strain, out):
+        on_device = hasattr(strain, "is_cuda") and strain.is_cuda
+        if not on_device:
+            strain = np.ascontiguousarray(strain, dtype=np.float32)
+        n = int(strain.shape[0])
+        assert out.is_cuda and out.shape[0] >= n
+        _check(lib.sb_cond_push(self.handle, C.c_void_p(_ptr(strain)), n, self.pushed, int(on_device),
+                                C.c_void_p(out.data_ptr())), "sb_cond_push")
+        self.pushed += n
+
+    def psd(self):
+        """(P [N/2 + 1] per-bin variance, segments averaged); blocks."""
+        nb, seg = C.c_int64(), C.c_int64()
+        _check(lib.sb_cond_psd(self.handle, None, 0, C.byref(nb), C.byref(seg)), "sb_cond_psd")
+        buf = np.empty(nb.value, dtype=np.float32)
+        _check(lib.sb_cond_psd(self.handle, C.c_void_p(buf.ctypes.data), nb.value, C.byref(nb), C.byref(seg)),
+               "sb_cond_psd")
+        return buf, seg.value
+
+    def close(self):
+        if self.handle:
+            lib.sb_cond_destroy(self.handle)
+            self.handle = None
 
 
 class Unit:

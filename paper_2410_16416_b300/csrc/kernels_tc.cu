@@ -18,6 +18,7 @@
 //  a3 + a4 (+ a5 partials) mixing GEMM and the x2 interpolation of the coarser
 //     level in one persistent warp-specialised kernel (tc_mixup_kernel,
 //     described at its definition), FP16 or BF16 operands.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <set>
@@ -279,9 +280,9 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
 // ---------------------------------------------------------------------------
 constexpr int kMixRows = 128;                            // filters per tile (MMA M)
 constexpr int kMixCols = 256;                            // time samples per tile (MMA N)
-constexpr int kMixABytes = kMixRows * 128;               // mixing tile: 128 filters x 128 bytes of K
-constexpr int kMixBBytes = kMixCols * 128;               // basis-output tile: 256 time x 128 bytes of K
-constexpr int kMixStageBytes = kMixABytes + kMixBBytes;
+// One mixing stage: the mixing tile (128 filters) and the basis-output tile (256 time rows), each row
+// `kbytes` of K (32, 64 or 128 bytes: the chunk's swizzle span), rounded to the 1024-byte swizzle atom
+constexpr int kMixMaxSt = 6;
 constexpr int kWinHalfBytes = kMixRows * 128;            // one plane: 64 coarser samples (16-bit) x 128 filters
 constexpr int kWinChunks = 3;                            // 192 >= 7 + 176 coarser samples per tile
 // Interpolation block geometry: UB outputs per block (MMA N); a block reads UB/2 + 48 coarser
@@ -303,6 +304,7 @@ constexpr size_t kUTabPart = kUTab128 + (size_t)kUVariants * UGeo<128>::kVarByte
 constexpr int kMixStPlane = 32 * 64;                     // store staging per plane: 32 filters x 32 samples
 constexpr int kMixThreads = 384;
 constexpr int kMixMaxWin = 6;
+size_t tc_mixup_stage_bytes(int kbytes) { return ((size_t)(kMixRows + kMixCols) * kbytes + 1023) / 1024 * 1024; }
 constexpr size_t kMixSmemMax = 227 * 1024;               // dynamic shared memory per CTA (opt-in maximum)
 
 size_t tc_interp_table_bytes() { return 2 * kUTabPart; }
@@ -429,7 +431,7 @@ __device__ __forceinline__ uint64_t desc_u(uint32_t saddr) {
 template <int MODE, int UB>
 __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
                                                                    int total_tiles, int n_st, int n_win, int n_u,
-                                                                   int n_stbuf,
+                                                                   int n_stbuf, int st_bytes,
                                                                    const uint8_t *__restrict__ utab, int *err) {
     constexpr int kKC = 128 / Op<MODE>::kBytes, kMK = Op<MODE>::kMmaK;
     constexpr int NP = y_planes(MODE);                   // 1: FP16 y; 2: BF16 hi + lo
@@ -440,8 +442,8 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + 2;
-    uint64_t *wfull = empty + 2;
+    uint64_t *empty = full + kMixMaxSt;
+    uint64_t *wfull = empty + kMixMaxSt;
     uint64_t *wempty = wfull + kMixMaxWin;
     uint64_t *ufull = wempty + kMixMaxWin;
     uint64_t *uempty = ufull + 2;
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
     uint64_t *mdrain = aempty + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mdrain + 1);
     uint8_t *stage = smem + 1024;                                  // n_st mixing stages
-    uint8_t *win = stage + n_st * kMixStageBytes;                  // n_win window chunks
+    uint8_t *win = stage + n_st * st_bytes;                        // n_win window chunks
     uint8_t *ubuf = win + n_win * kWinBytes;                       // n_u U variants
     uint8_t *stbuf = ubuf + n_u * G::kVarBytes;                    // n_stbuf per epilogue warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         tmem_relinquish();
     }
     if (threadIdx.x == 32) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kMixMaxSt; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -498,7 +500,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     ok = false;
                     break;
                 }
-                uint8_t *sa = stage + s * kMixStageBytes;
+                uint8_t *sa = stage + s * st_bytes;
                 mbar_expect_tx(&full[s], 3 * kMixRows * t.kbytes);
                 tma_load_2d(sa, t.mapM, kc * kKC, m.at * kMixRows, &full[s]);
                 tma_load_2d(sa + kMixRows * t.kbytes, t.mapO, kc * kKC, m.tt * kMixCols, &full[s]);
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                 tc_fence_after();
                 const int kb = m.t->kbytes;
                 // descriptors differ only in the start address field (address >> 4, no carry)
-                const uint32_t sa = smem_u32(stage + s * kMixStageBytes);
+                const uint32_t sa = smem_u32(stage + s * st_bytes);
                 const uint64_t da = desc_k_sw(sa, kb), db = desc_k_sw(sa + kMixRows * kb, kb);
                 const int nmma = min(kb / 32, (m.t->Lk_pad - kc * kKC) / kMK);     // 32 bytes of K per MMA
                 for (int kk = 0; kk < nmma; ++kk)
@@ -820,9 +822,9 @@ size_t tc_fir_smem_bytes(int kpad_max, int mode) {
     const int ph = mode == kModeE4M3 ? 16 : 8, by = mode == kModeE4M3 ? 1 : 2, terms = mode == kModeE4M3 ? 2 : 1;
     return 1024 + 1024 + kFirStages * kFirStageBytes + (size_t)terms * (kTcN * ph + kpad_max) * by;
 }
-size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk, int np) {
+size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk, int np, int kbytes) {
     const size_t uvar = ublk == 128 ? UGeo<128>::kVarBytes : UGeo<64>::kVarBytes;
-    return 1024 + 1024 + (size_t)n_st * kMixStageBytes + (size_t)n_win * np * kWinHalfBytes +
+    return 1024 + 1024 + (size_t)n_st * tc_mixup_stage_bytes(kbytes) + (size_t)n_win * np * kWinHalfBytes +
            (size_t)n_u * uvar + (size_t)8 * n_stbuf * np * kMixStPlane;
 }
 // Opts a kernel into the full 227 KB of dynamic shared memory, once.  The attribute is a limit on
@@ -886,46 +888,58 @@ static int sm_count() {
 
 template <int MODE, int UB>
 static cudaError_t mixup_launch_ub(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixCfg &cfg,
-                                   int n_stbuf, const void *utab, int *err, cudaStream_t s) {
-    const size_t smem = tc_mixup_smem_bytes(cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, UB, y_planes(MODE));
+                                   int n_stbuf, int kbytes, const void *utab, int *err, cudaStream_t s) {
+    const size_t smem = tc_mixup_smem_bytes(cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, UB, y_planes(MODE), kbytes);
     cudaError_t e = set_smem(tc_mixup_kernel<MODE, UB>, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total_tiles, sm_count());
     return launch_pdl(tc_mixup_kernel<MODE, UB>, dim3(grid), dim3(kMixThreads), smem, s, d_tasks, n_tasks,
-                      total_tiles, cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, static_cast<const uint8_t *>(utab), err);
+                      total_tiles, cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, (int)tc_mixup_stage_bytes(kbytes),
+                      static_cast<const uint8_t *>(utab), err);
 }
 
-uint32_t tc_mixup_shape_key(int mode, int max_nk, bool store_y, int total_tiles) {
+uint32_t tc_mixup_shape_key(int mode, const MixLaunch &ml, int total_tiles) {
     int lg = 0;
     while ((1 << (lg + 1)) <= total_tiles && lg < 30) ++lg;
-    return (uint32_t)mode | (store_y ? 4u : 0u) | ((uint32_t)std::min(max_nk, 3) << 3) | ((uint32_t)lg << 5);
+    const uint32_t kb = ml.kbytes <= 32 ? 0u : ml.kbytes <= 64 ? 1u : 2u;
+    return (uint32_t)mode | (ml.store_y ? 4u : 0u) | (ml.interp ? 8u : 0u) | ((uint32_t)std::min(ml.max_nk, 3) << 4) |
+           (kb << 6) | ((uint32_t)lg << 8);
 }
 
-// Pipeline shapes that fit in shared memory (<= 227 KB).  Several K chunks per tile may take two
-// mixing stages; one staging buffer per epilogue warp when the level's y is stored; the window
-// ring takes 2 .. 6 chunks (np planes each).  The default: two stages and one U buffer for several
-// K chunks, else one stage and two U buffers (one U buffer for the wider top-level blocks); the
-// deepest ring that fits.
-static std::vector<MixCfg> mix_candidates(int max_nk, bool store_y, int ub, int np) {
+// Pipeline shapes that fit in shared memory (<= 227 KB): 1, 2, 3, 4 or 6 mixing stages (each sized
+// for the launch's widest K row), one staging buffer per epilogue warp when the level's y is
+// stored, and, when a task interpolates a coarser level, 1-2 U buffers (1 for the wider top-level
+// blocks) and a window ring of 2, 3, 4 or 6 chunks (np planes each).  The first candidate is the
+// built-in default: the most stages up to 4 that fit beside a ring of 4.
+static std::vector<MixCfg> mix_candidates(const MixLaunch &ml, int ub, int np) {
     std::vector<MixCfg> out;
-    const int n_stbuf = store_y ? 1 : 0;
-    for (int n_st = (max_nk >= 2 ? 2 : 1); n_st >= 1; --n_st)
-        for (int n_u = (ub == 128 ? 1 : 2); n_u >= 1; --n_u) {
-            const size_t fixed = tc_mixup_smem_bytes(n_st, 0, n_u, n_stbuf, ub, np);
-            const int n_max = (int)std::min<size_t>(kMixMaxWin, (kMixSmemMax - fixed) / ((size_t)np * kWinHalfBytes));
-            for (int n_win = n_max; n_win >= 2; --n_win) out.push_back(MixCfg{n_st, n_u, n_win});
+    const int n_stbuf = ml.store_y ? 1 : 0;
+    const int st_opts[] = {6, 4, 3, 2, 1};
+    const int win_opts[] = {6, 4, 3, 2};
+    for (int n_st : st_opts) {
+        if (!ml.interp) {
+            if (tc_mixup_smem_bytes(n_st, 0, 0, n_stbuf, ub, np, ml.kbytes) <= kMixSmemMax)
+                out.push_back(MixCfg{n_st, 0, 0});
+            continue;
         }
+        for (int n_u = (ub == 128 ? 1 : 2); n_u >= 1; --n_u)
+            for (int n_win : win_opts)
+                if (tc_mixup_smem_bytes(n_st, n_win, n_u, n_stbuf, ub, np, ml.kbytes) <= kMixSmemMax)
+                    out.push_back(MixCfg{n_st, n_u, n_win});
+    }
+    auto score = [](const MixCfg &c) { return (c.n_st <= 4 ? c.n_st : 0) * 16 + std::min(c.n_win, 4) * 2 + c.n_u; };
+    std::stable_sort(out.begin(), out.end(), [&](const MixCfg &a, const MixCfg &b) { return score(a) > score(b); });
     return out;
 }
 
 template <int MODE, int UB>
-static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk,
-                                      bool store_y, const void *utab, int *err, MixTuner *tuner, bool may_tune,
-                                      cudaStream_t s) {
-    const int n_stbuf = store_y ? 1 : 0;
-    const std::vector<MixCfg> cands = mix_candidates(max_nk, store_y, UB, y_planes(MODE));
+static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixLaunch &ml,
+                                      const void *utab, int *err, MixTuner *tuner, bool may_tune, cudaStream_t s) {
+    const int n_stbuf = ml.store_y ? 1 : 0;
+    const std::vector<MixCfg> cands = mix_candidates(ml, UB, y_planes(MODE));
+    if (cands.empty()) return cudaErrorInvalidValue;
     MixCfg cfg = cands.front();
-    const uint32_t key = tc_mixup_shape_key(MODE, max_nk, store_y, total_tiles);
+    const uint32_t key = tc_mixup_shape_key(MODE, ml, total_tiles);
     const MixCfg *known = tuner ? tuner->find(key) : nullptr;
     if (known) cfg = *known;
     if (tuner && !known && may_tune && cands.size() == 1) tuner->best.emplace_back(key, cfg);
@@ -938,7 +952,8 @@ static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, i
         for (auto &x : ev) cudaEventCreate(&x);
         cudaError_t e = cudaEventRecord(ev[0], s);
         for (size_t k = 0; k < kTuneRounds * nc && e == cudaSuccess; ++k) {
-            e = mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cands[k % nc], n_stbuf, utab, err, s);
+            e = mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cands[k % nc], n_stbuf, ml.kbytes, utab,
+                                          err, s);
             if (e == cudaSuccess) e = cudaEventRecord(ev[k + 1], s);
         }
         if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
@@ -958,27 +973,23 @@ static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, i
         tuner->timed_launches += (int64_t)(kTuneRounds * nc);
         return cudaSuccess;
     }
-    return mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cfg, n_stbuf, utab, err, s);
+    return mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cfg, n_stbuf, ml.kbytes, utab, err, s);
 }
 
 template <int MODE>
-static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
+static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixLaunch &ml,
                                 const void *utab, int *err, MixTuner *tuner, bool may_tune, cudaStream_t s) {
     // levels that store nothing (the top) use 128-wide interpolation blocks (fewer, wider MMAs)
-    if (!store_y)
-        return mixup_launch_tuned<MODE, 128>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner,
-                                             may_tune, s);
-    return mixup_launch_tuned<MODE, 64>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune,
-                                        s);
+    if (!ml.store_y)
+        return mixup_launch_tuned<MODE, 128>(d_tasks, n_tasks, total_tiles, ml, utab, err, tuner, may_tune, s);
+    return mixup_launch_tuned<MODE, 64>(d_tasks, n_tasks, total_tiles, ml, utab, err, tuner, may_tune, s);
 }
 
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixLaunch &ml,
                             const void *utab, int mode, int *err, MixTuner *tuner, bool may_tune, cudaStream_t s) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    if (mode == kModeBF16)
-        return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune, s);
-    if (mode == kModeF16)
-        return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, max_nk, store_y, utab, err, tuner, may_tune, s);
+    if (mode == kModeBF16) return mixup_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, ml, utab, err, tuner, may_tune, s);
+    if (mode == kModeF16) return mixup_launch<kModeF16>(d_tasks, n_tasks, total_tiles, ml, utab, err, tuner, may_tune, s);
     return cudaErrorInvalidValue;                        // E4M3 units mix in BF16 (mix_mode)
 }
 

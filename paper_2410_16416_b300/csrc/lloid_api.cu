@@ -516,6 +516,16 @@ extern "C" int sb_ctx_destroy(sb_ctx *c) {
     return SB_OK;
 }
 
+// The context's work stream and device, with that device made current (for the conditioner,
+// condition.cu, whose work is ordered with the context's pushes).
+int lloid_ctx_stream(sb_ctx *c, cudaStream_t *stream, int *device) {
+    if (!c) return fail(SB_EINVAL, "ctx is null");
+    if (activate(c) != SB_OK) return SB_ECUDA;
+    *stream = c->stream;
+    *device = c->device;
+    return SB_OK;
+}
+
 extern "C" int sb_ctx_sync(sb_ctx *c) {
     if (!c) return fail(SB_EINVAL, "ctx is null");
     if (activate(c) != SB_OK) return SB_ECUDA;
@@ -1717,10 +1727,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     int tfir_tiles[NM] = {0, 0, 0};
     std::vector<int> tmix_tiles[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
                                        std::vector<int>(kall + 1, 0)};
-    std::vector<int> tmix_maxnk[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
-                                       std::vector<int>(kall + 1, 0)};
-    std::vector<int> tmix_tstore[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
-                                        std::vector<int>(kall + 1, 0)};
+    std::vector<MixLaunch> tmix_ml[NM] = {std::vector<MixLaunch>(kall + 1), std::vector<MixLaunch>(kall + 1),
+                                          std::vector<MixLaunch>(kall + 1)};
     for (int h = 0; h < NM; ++h) {
         for (auto &f : tfir[h]) {
             f.tile_begin = tfir_tiles[h];
@@ -1730,9 +1738,12 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             for (auto &m : tmix[h][k]) {
                 m.tile_begin = tmix_tiles[h][k];
                 tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
-                if (m.Yh) tmix_tstore[h][k] = 1;
+                MixLaunch &ml = tmix_ml[h][k];
+                if (m.Yh) ml.store_y = true;
+                if (m.mapY) ml.interp = true;
+                ml.kbytes = std::max(ml.kbytes, (int)m.kbytes);
                 const int kc = 128 / mode_bytes(h);                  // K elements per 128-byte chunk
-                tmix_maxnk[h][k] = std::max(tmix_maxnk[h][k], (m.Lk_pad + kc - 1) / kc);
+                ml.max_nk = std::max(ml.max_nk, (m.Lk_pad + kc - 1) / kc);
             }
     }
     int wfin_warps = 0;
@@ -1827,7 +1838,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         for (int h = 0; h < NM; ++h)
             for (int k = 0; k <= kall; ++k)
                 if (!tmix[h][k].empty() &&
-                    !c->tuner.find(tc_mixup_shape_key(h, tmix_maxnk[h][k], tmix_tstore[h][k] != 0, tmix_tiles[h][k])))
+                    !c->tuner.find(tc_mixup_shape_key(h, tmix_ml[h][k], tmix_tiles[h][k])))
                     tune_now = true;
     const bool capture = c->graphs && !c->prof && !tune_now;
     std::string gkey;
@@ -1904,7 +1915,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
                      const int64_t timed0 = c->tuner.timed_launches;
                      cudaError_t e = launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
-                                                     tmix_tiles[h][k], tmix_maxnk[h][k], tmix_tstore[h][k] != 0,
+                                                     tmix_tiles[h][k], tmix_ml[h][k],
                                                      c->utab, h, derr, c->autotune ? &c->tuner : nullptr, tune_now,
                                                      st);
                      *n = (int)std::max<int64_t>(1, c->tuner.timed_launches - timed0);

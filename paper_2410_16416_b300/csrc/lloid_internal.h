@@ -267,14 +267,24 @@ struct WinFinTask {
 };
 
 size_t tc_fir_smem_bytes(int kpad_max, int mode);
-size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk, int np);
+// Launch description of one tc_mixup launch, from its tasks: the most K chunks of a tile, whether
+// any task stores its y (levels below the top) or interpolates a coarser level, and the widest
+// mixing-operand row (bytes of K per chunk: 32, 64 or 128), which sets the stage size.
+struct MixLaunch {
+    int max_nk = 0;
+    bool store_y = false;
+    bool interp = false;
+    int kbytes = 32;
+};
+size_t tc_mixup_stage_bytes(int kbytes);
+size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk, int np, int kbytes);
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
                           cudaStream_t s);
 // Pipeline shape of one tc_mixup launch: mixing stages, interpolation-operand buffers and the
 // depth of the window ring.  None of them changes the arithmetic, so results do not depend on
 // the choice; the autotuner times the candidates that fit in shared memory once per launch
-// shape (mode, K chunks, whether y is stored, tile count) and keeps the fastest.
+// shape (mode, MixLaunch, tile count) and keeps the fastest.
 struct MixCfg {
     int n_st, n_u, n_win;
 };
@@ -287,10 +297,10 @@ struct MixTuner {
         return nullptr;
     }
 };
-uint32_t tc_mixup_shape_key(int mode, int max_nk, bool store_y, int total_tiles);
+uint32_t tc_mixup_shape_key(int mode, const MixLaunch &ml, int total_tiles);
 // utab: the interpolation operand table (tc_interp_table_bytes(), built by tc_interp_table).
 // tuner: null, or the context's tuner; may_tune: the shape may be timed now (no capture running).
-cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, int max_nk, bool store_y,
+cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixLaunch &ml,
                             const void *utab, int mode, int *err, MixTuner *tuner, bool may_tune, cudaStream_t s);
 size_t tc_interp_table_bytes();
 void tc_interp_table(const Halfband &g, void *host_out);
