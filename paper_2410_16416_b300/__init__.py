@@ -9,7 +9,7 @@ using the binding without the library raises ImportError (no CPU fallback).
 """
 from .svdbank import BankSlice, SVDBank, decompose
 
-_ABI_NAMES = {"Context", "Unit", "LloidError", "make_desc", "plan", "TRIGGER_DTYPE", "PRECISION", "SIGNATURES",
+_ABI_NAMES = {"Context", "Unit", "Conditioner", "LloidError", "make_desc", "plan", "TRIGGER_DTYPE", "PRECISION", "SIGNATURES",
               "lib", "LIB_PATH", "SB_OK", "SB_EINVAL", "SB_ENOMEM", "SB_EBUSY", "SB_EGAP", "SB_ETIMEOUT",
               "SB_ECUDA", "SB_EOVERFLOW", "SB_TRIG_REFINED", "SB_TRIG_SUBSAMPLE", "SB_TRIG_XI2", "SB_XI2_HALF", "coincidences",
               "COINC_DTYPE",
