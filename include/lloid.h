@@ -352,9 +352,9 @@ int sb_ctx_graphs(sb_ctx *ctx, int32_t enable);
 /* enable != 0 (the default): the first push that launches the mixing kernel
  * (a3 + a4) with a new launch shape (operand type, whether the level's SNR is
  * stored, whether it interpolates a coarser level, K chunks per tile, bytes of
- * K per chunk, tile count rounded down to a power of two) times every pipeline
- * shape that fits in shared memory (mixing stages 1, 2, 3, 4 or 6,
- * interpolation buffers 1-2, window-ring depth 2, 3, 4 or 6) on that push's
+ * K per chunk, tile count rounded down to a power of four) times every
+ * pipeline shape that fits in shared memory (mixing stages 1-4,
+ * interpolation buffers 1-2, window-ring depth 2-4) on that push's
  * own data, three times in interleaved rounds, and keeps the one with the
  * smallest time for later pushes; that push is not graph-captured.  The
  * pipeline shape changes no arithmetic: results are bitwise the same for every
@@ -367,8 +367,19 @@ int sb_ctx_autotune(sb_ctx *ctx, int32_t enable);
  * negative SB_E* code.  Shape key bits: 0-1 operand type of the mixing (0 FP16,
  * 1 BF16; SB_FP8 units mix in BF16), 2 SNR stored, 3 interpolates a coarser
  * level, 4-5 K chunks per tile (capped at 3), 6-7 bytes of K per chunk (0: 32,
- * 1: 64, 2: 128), 8+ log2 tiles. */
+ * 1: 64, 2: 128), 8+ log4 tiles. */
 int sb_ctx_autotune_choices(sb_ctx *ctx, int32_t *out, int32_t cap);
+/* Test hook of the bounded device waits (the paper has no counterpart): every
+ * later push's basis-FIR kernel (SB_BF16 / SB_FP16 / SB_FP8) bounds its waits
+ * by wait_limit_ns (0: the default, 2 s), and when skip_fir_chunk >= 0 the
+ * producer of the launch's first tile does not issue the load of that K chunk,
+ * so that the chunk's consumer waits until the bound expires; the kernel then
+ * lets every copy it issued land, lets its issued MMAs finish, frees its TMEM
+ * and returns, and triggers_pop reports SB_ETIMEOUT for that push (whose
+ * results are void).  Nothing faults and nothing stays in flight.  Make the
+ * test pushes with sb_ctx_graphs off; a negative skip_fir_chunk restores normal
+ * operation. */
+int sb_ctx_test_wait(sb_ctx *ctx, int64_t wait_limit_ns, int32_t skip_fir_chunk);
 /* Blocks until queued work is done, then writes per stage the summed kernel
  * time (ms) and the number of launches since profiling was enabled
  * (arrays of n_stages entries; n_stages <= SB_N_STAGES). */

@@ -100,6 +100,7 @@ SIGNATURES = {
     "sb_cond_latency": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "sb_cond_push": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
     "sb_cond_psd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "sb_ctx_test_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32]),
     "sb_last_error": (C.c_char_p, []),
 }
 
@@ -247,12 +248,16 @@ class Context:
         """Capture every push into a CUDA graph (reused per group shape); results are unchanged."""
         _check(lib.sb_ctx_graphs(self.handle, int(bool(enable))), "sb_ctx_graphs")
 
+    def test_wait(self, wait_limit_ns: int, skip_fir_chunk: int) -> None:
+        """sb_ctx_test_wait: bound the basis-FIR kernel's waits and skip one K chunk's load (test hook)."""
+        _check(lib.sb_ctx_test_wait(self.handle, int(wait_limit_ns), int(skip_fir_chunk)), "sb_ctx_test_wait")
+
     def autotune(self, enable: bool) -> None:
         """Time the mixing kernel's pipeline shapes on new launch shapes (default on)."""
         _check(lib.sb_ctx_autotune(self.handle, int(bool(enable))), "sb_ctx_autotune")
 
     def autotune_choices(self) -> list:
-        """[{key, mode, store_y, interp, k_chunks, k_bytes, log2_tiles, stages, u_buffers, window_ring}]
+        """[{key, mode, store_y, interp, k_chunks, k_bytes, log4_tiles, stages, u_buffers, window_ring}]
         tuned so far."""
         n = lib.sb_ctx_autotune_choices(self.handle, None, 0)
         _check(min(n, 0), "sb_ctx_autotune_choices")
@@ -264,7 +269,7 @@ class Context:
             k = buf[4 * i]
             out.append({"key": k, "mode": ("fp16", "bf16", "?", "?")[k & 3], "store_y": bool(k & 4),
                         "interp": bool(k & 8), "k_chunks": (k >> 4) & 3, "k_bytes": (32, 64, 128, 0)[(k >> 6) & 3],
-                        "log2_tiles": k >> 8, "stages": buf[4 * i + 1], "u_buffers": buf[4 * i + 2],
+                        "log4_tiles": k >> 8, "stages": buf[4 * i + 1], "u_buffers": buf[4 * i + 2],
                         "window_ring": buf[4 * i + 3]})
         return out
 

@@ -137,7 +137,10 @@ constexpr int kTmemCols = 256;
 
 template <int MODE>
 __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restrict__ tasks, int n_tasks,
-                                                        int *err) {
+                                                        int *err, uint64_t wait_ns, int skip_chunk) {
+    // wait_ns: bound of every wait (kWaitLimitNs in normal operation).  skip_chunk >= 0 is a test
+    // hook: tile 0's producer does not issue that K chunk's load, so its consumer's wait runs out
+    // (nothing is in flight for it) and the failure path below runs.
     using H = Op<MODE>;
     constexpr int kPh = H::kPhases, kB = H::kBytes, kKC = 128 / kB;   // K elements per 128-byte row
     extern __shared__ uint8_t smem_raw[];
@@ -146,7 +149,8 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
     uint64_t *empty = full + kFirStages;
     uint64_t *winb = empty + kFirStages;
     uint64_t *accb = winb + 1;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
+    uint64_t *drain = accb + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
     uint8_t *a_st = smem + 1024;
     uint8_t *win = a_st + kFirStages * kFirStageBytes;
 
@@ -166,6 +170,7 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
         }
         mbar_init(winb, 1);
         mbar_init(accb, 1);
+        mbar_init(drain, 1);
         fence_barrier_init();
         fence_proxy_async();
     }
@@ -185,20 +190,34 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
         mbar_expect_tx(winb, kXTerms * wbytes);
         bulk_load(win, reinterpret_cast<const uint8_t *>(t.x) + xoff, wbytes, winb);
         if (kXTerms == 2) bulk_load(win + wbytes, reinterpret_cast<const uint8_t *>(t.x_lo) + xoff, wbytes, winb);
+        int last[kFirStages] = {-1, -1, -1, -1};            // last K chunk whose load was issued, per stage
+        bool ok = true;
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % kFirStages;
-            if (kc >= kFirStages && !mbar_wait(&empty[s], ((kc / kFirStages) - 1) & 1, err, 1)) break;
+            if (kc >= kFirStages && !mbar_wait(&empty[s], ((kc / kFirStages) - 1) & 1, err, 1, wait_ns)) {
+                ok = false;
+                break;
+            }
+            if (kc == skip_chunk && blockIdx.x == 0) continue;   // test hook: this load is never issued
             mbar_expect_tx(&full[s], kFirStageBytes);
             tma_load_2d(a_st + s * kFirStageBytes, t.mapW, kc * kKC, mt * kTcM, &full[s]);
+            last[s] = kc;
         }
+        // every copy issued into this CTA's shared memory lands before the CTA leaves, also when a
+        // wait gave up here or in another role (normally these waits return at once)
+        (void)ok;
+        mbar_wait_bounded(winb, 0);
+        for (int s = 0; s < kFirStages; ++s)
+            if (last[s] >= 0) mbar_wait_bounded(&full[s], (last[s] / kFirStages) & 1);
     } else if (warp == 1 && lane == 0) {
-        if (mbar_wait(winb, 0, err, 2)) {
+        if (mbar_wait(winb, 0, err, 2, wait_ns)) {
             const uint32_t idesc = idesc_op<MODE>(kTcM, kTcN);
             const uint32_t wa = smem_u32(win);
-            bool ok = true;
+            bool ok = true, issued = false;
             for (int kc = 0; kc < nk && ok; ++kc) {
                 const int s = kc % kFirStages;
-                if (!mbar_wait(&full[s], (kc / kFirStages) & 1, err, 3)) { ok = false; break; }
+                if (!mbar_wait(&full[s], (kc / kFirStages) & 1, err, 3, wait_ns)) { ok = false; break; }
+                issued = true;
                 tc_fence_after();
                 const uint32_t aa = smem_u32(a_st + s * kFirStageBytes);
 #pragma unroll
@@ -211,11 +230,16 @@ __global__ void __launch_bounds__(128, 1) tc_fir_kernel(const TcFirTask *__restr
                 }
                 mma_commit(&empty[s]);
             }
-            if (ok) mma_commit(accb);
+            if (ok) {
+                mma_commit(accb);
+            } else if (issued) {                             // the issued MMAs finish before TMEM is freed
+                mma_commit(drain);
+                mbar_wait_bounded(drain, 0);
+            }
         }
     }
     __syncwarp();
-    const bool have = mbar_wait(accb, 0, err, 4);
+    const bool have = mbar_wait(accb, 0, err, 4, wait_ns);
     tc_fence_after();
     if (have) {
         // TMEM lane R = lpt r + l_loc (row of W in this tile), column c = block b - 256 nt
@@ -532,8 +556,9 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                 ++wu;
             }
         }
-        if (!ok) {
-            // copies still in flight land before the CTA leaves: wait for the last load of each buffer
+        {
+            // copies still in flight land before the CTA leaves (also when another role or CTA gave up;
+            // normally these waits return at once): wait for the last load of each buffer
             // (the last use of slot s of a ring of n is use s + n ((used - 1 - s) / n))
             for (int s = 0; s < n_st && s < (int)su; ++s) mbar_wait_bounded(&full[s], ((su - 1 - s) / n_st) & 1);
             for (int s = 0; s < n_u && s < (int)uu; ++s) mbar_wait_bounded(&ufull[s], ((uu - 1 - s) / n_u) & 1);
@@ -862,19 +887,23 @@ cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, c
 
 template <int MODE>
 static cudaError_t fir_launch(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int *err,
-                              cudaStream_t s) {
+                              uint64_t wait_ns, int skip_chunk, cudaStream_t s) {
     const size_t smem = tc_fir_smem_bytes(kpad_max, MODE);
     cudaError_t e = set_smem(tc_fir_kernel<MODE>, smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(tc_fir_kernel<MODE>, dim3(total_tiles), dim3(128), smem, s, d_tasks, n_tasks, err);
+    return launch_pdl(tc_fir_kernel<MODE>, dim3(total_tiles), dim3(128), smem, s, d_tasks, n_tasks, err, wait_ns,
+                      skip_chunk);
 }
 
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
-                          cudaStream_t s) {
+                          cudaStream_t s, uint64_t wait_ns, int skip_chunk) {
     if (n_tasks == 0 || total_tiles == 0) return cudaSuccess;
-    if (mode == kModeBF16) return fir_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, kpad_max, err, s);
-    if (mode == kModeF16) return fir_launch<kModeF16>(d_tasks, n_tasks, total_tiles, kpad_max, err, s);
-    return fir_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, kpad_max, err, s);
+    if (wait_ns == 0) wait_ns = kWaitLimitNs;
+    if (mode == kModeBF16)
+        return fir_launch<kModeBF16>(d_tasks, n_tasks, total_tiles, kpad_max, err, wait_ns, skip_chunk, s);
+    if (mode == kModeF16)
+        return fir_launch<kModeF16>(d_tasks, n_tasks, total_tiles, kpad_max, err, wait_ns, skip_chunk, s);
+    return fir_launch<kModeE4M3>(d_tasks, n_tasks, total_tiles, kpad_max, err, wait_ns, skip_chunk, s);
 }
 
 static int sm_count() {
@@ -899,23 +928,23 @@ static cudaError_t mixup_launch_ub(const TcMixUpTask *d_tasks, int n_tasks, int 
 }
 
 uint32_t tc_mixup_shape_key(int mode, const MixLaunch &ml, int total_tiles) {
-    int lg = 0;
-    while ((1 << (lg + 1)) <= total_tiles && lg < 30) ++lg;
+    int lg = 0;                                         // log4 of the tile count (coarse buckets)
+    while ((1 << (2 * lg + 2)) <= total_tiles && lg < 15) ++lg;
     const uint32_t kb = ml.kbytes <= 32 ? 0u : ml.kbytes <= 64 ? 1u : 2u;
     return (uint32_t)mode | (ml.store_y ? 4u : 0u) | (ml.interp ? 8u : 0u) | ((uint32_t)std::min(ml.max_nk, 3) << 4) |
            (kb << 6) | ((uint32_t)lg << 8);
 }
 
-// Pipeline shapes that fit in shared memory (<= 227 KB): 1, 2, 3, 4 or 6 mixing stages (each sized
+// Pipeline shapes that fit in shared memory (<= 227 KB): 1, 2, 3 or 4 mixing stages (each sized
 // for the launch's widest K row), one staging buffer per epilogue warp when the level's y is
 // stored, and, when a task interpolates a coarser level, 1-2 U buffers (1 for the wider top-level
-// blocks) and a window ring of 2, 3, 4 or 6 chunks (np planes each).  The first candidate is the
-// built-in default: the most stages up to 4 that fit beside a ring of 4.
+// blocks) and a window ring of 2, 3 or 4 chunks (np planes each).  The first candidate is the
+// built-in default: the most stages that fit beside a ring of 4.
 static std::vector<MixCfg> mix_candidates(const MixLaunch &ml, int ub, int np) {
     std::vector<MixCfg> out;
     const int n_stbuf = ml.store_y ? 1 : 0;
-    const int st_opts[] = {6, 4, 3, 2, 1};
-    const int win_opts[] = {6, 4, 3, 2};
+    const int st_opts[] = {4, 3, 2, 1};
+    const int win_opts[] = {4, 3, 2};
     for (int n_st : st_opts) {
         if (!ml.interp) {
             if (tc_mixup_smem_bytes(n_st, 0, 0, n_stbuf, ub, np, ml.kbytes) <= kMixSmemMax)
@@ -927,7 +956,7 @@ static std::vector<MixCfg> mix_candidates(const MixLaunch &ml, int ub, int np) {
                 if (tc_mixup_smem_bytes(n_st, n_win, n_u, n_stbuf, ub, np, ml.kbytes) <= kMixSmemMax)
                     out.push_back(MixCfg{n_st, n_u, n_win});
     }
-    auto score = [](const MixCfg &c) { return (c.n_st <= 4 ? c.n_st : 0) * 16 + std::min(c.n_win, 4) * 2 + c.n_u; };
+    auto score = [](const MixCfg &c) { return c.n_st * 16 + c.n_win * 2 + c.n_u; };
     std::stable_sort(out.begin(), out.end(), [&](const MixCfg &a, const MixCfg &b) { return score(a) > score(b); });
     return out;
 }

@@ -187,6 +187,10 @@ struct sb_ctx {
     int64_t graph_launches = 0;
     // mixing-kernel pipeline shapes chosen by timing (no effect on results)
     bool autotune = true;
+    // test hook (sb_ctx_test_wait): bound of the basis-FIR kernel's waits and a K chunk its first
+    // tile does not load (-1: none)
+    uint64_t test_wait_ns = 0;
+    int test_skip_chunk = -1;
     MixTuner tuner;
     // profiling: event pairs around each launch, summed per stage on query
     bool prof = false;
@@ -1153,6 +1157,15 @@ extern "C" int sb_ctx_graphs(sb_ctx *c, int32_t enable) {
     return SB_OK;
 }
 
+extern "C" int sb_ctx_test_wait(sb_ctx *c, int64_t wait_limit_ns, int32_t skip_fir_chunk) {
+    if (!c) return fail(SB_EINVAL, "ctx is null");
+    if (wait_limit_ns < 0) return fail(SB_EINVAL, "wait_limit_ns must be >= 0");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->test_wait_ns = (uint64_t)wait_limit_ns;
+    c->test_skip_chunk = skip_fir_chunk < 0 ? -1 : skip_fir_chunk;
+    return SB_OK;
+}
+
 extern "C" int sb_ctx_autotune(sb_ctx *c, int32_t enable) {
     if (!c) return fail(SB_EINVAL, "ctx is null");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -1892,7 +1905,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
         if (!tfir[h].empty() && (rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
                                      *n = 1;
                                      return launch_tc_fir((TcFirTask *)(D + o_tfir[h]), (int)tfir[h].size(),
-                                                          tfir_tiles[h], kpad_max[h], h, derr, st);
+                                                          tfir_tiles[h], kpad_max[h], h, derr, st, c->test_wait_ns,
+                                                          c->test_skip_chunk);
                                  })))
             return rc;
     // 5. a4 + a3 from the lowest rate up

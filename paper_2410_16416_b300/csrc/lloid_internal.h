@@ -279,8 +279,10 @@ struct MixLaunch {
 size_t tc_mixup_stage_bytes(int kbytes);
 size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk, int np, int kbytes);
 cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
+// wait_ns: bound of the kernel's waits (0: the default, 2 s); skip_chunk >= 0: test hook (the first
+// tile's producer skips that K chunk's load, so its consumer's wait runs out).
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
-                          cudaStream_t s);
+                          cudaStream_t s, uint64_t wait_ns = 0, int skip_chunk = -1);
 // Pipeline shape of one tc_mixup launch: mixing stages, interpolation-operand buffers and the
 // depth of the window ring.  None of them changes the arithmetic, so results do not depend on
 // the choice; the autotuner times the candidates that fit in shared memory once per launch

@@ -47,13 +47,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // Bounded wait: gives up after `limit_ns` of global time, records `code` in
 // *err and returns false (the caller then skips its remaining work).
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code,
+                                          uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*reinterpret_cast<volatile int *>(err) != 0) return false;    // another CTA already failed
-        if (globaltimer() - t0 > kWaitLimitNs) {
+        if (globaltimer() - t0 > limit_ns) {
             atomicCAS(err, 0, code);
             return false;
         }
