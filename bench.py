@@ -71,9 +71,12 @@ def parse():
     p.add_argument("--workload", default="production", choices=["production", "batch", "serve"],
                    help="production: one 1000-template bin x 2 detectors (+ sub-results); batch / serve: that "
                         "sub-result alone as the line")
-    p.add_argument("--sub", default="push1s,batch,serve",
+    p.add_argument("--sub", default="push1s,batch,paper,serve",
                    help="sub-results of the production line ('none': skip)")
     p.add_argument("--bins", type=int, default=200, help="batch: uneven bins (x 2 detectors)")
+    p.add_argument("--paper-banks", default="1,2,4,8,16,32",
+                   help="paper shape: numbers of (1,004-template, 73 s) banks per detector, 3 detectors")
+    p.add_argument("--paper-steps", type=int, default=5)
     p.add_argument("--batch-steps", type=int, default=6)
     p.add_argument("--batch-push-seconds", type=int, default=8)
     p.add_argument("--serve-bins", type=int, default=1000)
@@ -443,15 +446,19 @@ def make_units_for(ctx, banks, precision, B, xi2_on=True, threshold=6.0, refine=
 
 
 def device_arm(lloid, torch, stream, local, banks, precision, B, steps, warmup, dev, graphs, autotune, barrier,
-               flush, n_prof=None):
-    """Time `steps` grouped pushes of B samples per unit with the strain resident in HBM."""
+               flush, n_prof=None, make_units=None):
+    """Time `steps` grouped pushes of B samples per unit with the strain resident in HBM.
+    make_units(ctx) -> (units, detector of each unit); default: each bank on detectors 0 and 1."""
     ctx = lloid.Context(local, stream=stream.cuda_stream)
     ctx.graphs(graphs)
     ctx.autotune(autotune)
     tc0 = time.perf_counter()
-    units = make_units_for(ctx, banks, precision, B)
+    if make_units is None:
+        units = make_units_for(ctx, banks, precision, B)
+        dets = [det for _ in banks for det in (0, 1)]
+    else:
+        units, dets = make_units(ctx)
     create_s = time.perf_counter() - tc0
-    dets = [det for _ in banks for det in (0, 1)]
     n_units = len(units)
     n_prof = min(steps, 16) if n_prof is None else n_prof
     t = 0
@@ -494,6 +501,55 @@ def device_arm(lloid, torch, stream, local, banks, precision, B, steps, warmup, 
                          "in_timed_region": st1["autotune_launches"] - st0["autotune_launches"]},
             "refine_candidates": st1["refine_candidates"] - st0["refine_candidates"], "prof_steps": n_prof,
             "triggers": int(len(trig)), "n_units": n_units}
+
+
+def paper_sweep(lloid, torch, stream, local, args, rank, world, dist, barrier, flush, graphs, autotune, peaks):
+    """The paper's benchmark shape (Sec. IV, Fig. 3): one 1,004-template bank of 73 s templates per
+    detector, three detectors of white Gaussian noise, the same bank provided n times per detector
+    (svdbank_create_like shares its device data), one grouped push of 16 s per step; throughput
+    against the number of banks.  Ranks split the bank copies."""
+    spec = synth.PAPER_BIN
+    h, _ = synth.template_bank(spec.n_templates, spec.mc_lo, spec.mc_hi, spec.top_rate_hz, spec.duration_s, 5, 0, 0)
+    tb = time.perf_counter()
+    bank = lloid.decompose(h, spec.top_rate_hz, spec.slices)
+    del h
+    setup = time.perf_counter() - tb
+    f0 = int(spec.top_rate_hz)
+    push_s, steps, warmup = 16, args.paper_steps, 2
+    B = push_s * f0
+    total = (warmup + steps + min(steps, 16)) * push_s
+    dev = [torch.from_numpy(synth.white_noise(total * f0, 6, rank, det)).cuda() for det in range(3)]
+    curve = []
+    for nb in [int(x) for x in args.paper_banks.split(",") if x.strip()]:
+        mine = len(shard_bins(nb, rank, world))
+        if mine == 0:
+            continue
+
+        def make(ctx, mine=mine):
+            units, dets = [], []
+            for det in range(3):
+                u0 = ctx.create_unit(bank, detector=det, precision=args.precision, threshold=6.0,
+                                     refine_threshold=5.5, window_s=1.0, max_push_samples=B)
+                units.append(u0)
+                dets.append(det)
+                for _ in range(mine - 1):
+                    units.append(ctx.create_like(u0, detector=det))
+                    dets.append(det)
+            return units, dets
+
+        r = device_arm(lloid, torch, stream, local, [bank], args.precision, B, steps, warmup, dev, graphs, autotune,
+                       barrier, flush, make_units=make)
+        tpl = 3 * mine * spec.n_templates * push_s * steps
+        value, secs = job_rate(tpl, r["dev_s"], dist, "cuda")
+        flops, bytes_, inter = model_sum([(bank, 3 * mine)], push_s, args.precision)
+        _, roofs = roofline_of(r["stages"], flops, bytes_, inter, args.precision, r["prof_steps"], peaks, "paper")
+        curve.append({"banks_per_detector": nb, "units": 3 * nb, "value": value, "ms_per_step": 1e3 * secs / steps,
+                      "mix_frac": roofs.get("mix", {}).get("frac"), "fir_frac": roofs.get("fir", {}).get("frac")})
+    del dev
+    return {"workload": f"{spec.n_templates} templates of {spec.duration_s:.0f} s (6 slices 4096-128 Hz, "
+                        f"L={bank.basis_counts()}), 3 detectors of white Gaussian noise, the same bank n times per "
+                        f"detector, 16-s grouped pushes, {args.precision}",
+            "unit": UNIT, "bank_setup_s": setup, "curve": curve}
 
 
 def serve_once(lloid, serve, args, precision, rank, world, local):
@@ -742,6 +798,9 @@ def main():
                          "roofline_stages": roofb, "clocks": rb["clocks"],
                          "stages_ms_share": {k: round(v / sum(bbusy.values()), 4) for k, v in bbusy.items()}}
         del rb
+    if "paper" in subs:                               # the paper's benchmark shape: throughput vs banks
+        line["paper_banks"] = paper_sweep(lloid, torch, stream, local, args, rank, world, dist, barrier, flush,
+                                          graphs, autotune, peaks)
     if "serve" in subs:                               # the serving loop, 1-s buffers, p50 / p99 latency
         line["serve"] = {}
         for p in [x.strip() for x in args.serve_precisions.split(",") if x.strip()]:

@@ -175,6 +175,15 @@ PRODUCTION_BIN = BinSpec(1000, 1.0, 1.5, 4096.0, 60.0,
                           SliceSpec(256.0, 4.0, 20.0), SliceSpec(128.0, 20.0, 60.0)])
 
 
+# The paper's own benchmark bank (Sec. IV): 1,004 templates of 73 s, one bank per detector of a
+# three-detector search.  Same mass range and slicing as the production bin, the last slice
+# extended to the template span.
+PAPER_BIN = BinSpec(1004, 1.0, 1.5, 4096.0, 73.0,
+                    [SliceSpec(4096.0, 0.0, 1 / 32), SliceSpec(2048.0, 1 / 32, 1 / 8),
+                     SliceSpec(1024.0, 1 / 8, 1 / 2), SliceSpec(512.0, 1 / 2, 4.0),
+                     SliceSpec(256.0, 4.0, 20.0), SliceSpec(128.0, 20.0, 73.0)])
+
+
 def scaled_bin(spec: BinSpec, n_templates: int) -> BinSpec:
     return dataclasses.replace(spec, n_templates=n_templates)
 

@@ -1,8 +1,11 @@
-"""Serving: continuous batching under an HBM budget, each stream's result equal alone and in the mix."""
+"""Serving: continuous batching under an HBM budget, each stream's result equal alone and in the mix,
+and equal to the oracle's filter of the stream's buffers."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
+from helpers import check_triggers
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -63,6 +66,15 @@ def test_continuous_batching_matches_alone(lloid):
         alone = _alone(lloid, req, 6)
         assert len(alone) > 0
         assert np.array_equal(mine, alone), req.name
+    # and the served triggers are the oracle's: every stream's buffers, filtered in FP64, give the
+    # same window maxima (BF16 below the refine threshold: within 0.05; refined above it)
+    for r, req in enumerate(reqs):
+        d = np.concatenate([req.strain(j) for j in range(6)])
+        ob = oracle.bank_from_arrays(req.bank.n_templates, req.bank.top_rate_hz, req.bank.slices)
+        x = oracle.lloid_snr(ob, d)
+        lat = lloid.plan(req.bank, max_push_samples=4096, **req.unit_kwargs).latency_samples
+        mine = rep.triggers[rep.trigger_stream == r]
+        assert check_triggers(mine, x, 4096, 3.0, d.shape[0] - lat, 0.05, absolute=True) == len(mine) > 0
 
 
 def test_create_like_shares_the_bank(lloid):
