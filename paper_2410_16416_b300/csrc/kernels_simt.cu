@@ -32,7 +32,10 @@ __global__ void __launch_bounds__(256) decimate_kernel(const DecimTask *__restri
 // ---------------------------------------------------------------------------
 // One CTA per (task, row, chunk of kUpChunk outputs): the input segment (half
 // the chunk plus the 2K-1 tap halo on each side) is staged in shared memory with
-// coalesced loads, then every output is formed from shared memory.
+// coalesced loads.  Each thread then forms whole output pairs (the even output
+// of coarser sample a and the odd one after it), so no lane idles while its
+// neighbour filters, consecutive lanes read consecutive shared-memory words, and
+// the 2K-tap sum runs in four independent partial sums.
 __global__ void __launch_bounds__(256) upsample_kernel(const UpTask *__restrict__ tasks, Halfband g) {
     griddep_wait();
     constexpr int kSeg = kUpChunk / 2 + 2 * kHalfK + 2;
@@ -54,21 +57,28 @@ __global__ void __launch_bounds__(256) upsample_kernel(const UpTask *__restrict_
         seg[i] = v;
     }
     __syncthreads();
+    float c[kOddTaps];
+#pragma unroll
+    for (int k = 0; k < kOddTaps; ++k) c[k] = 2.0f * g.odd[k];
     float *out = t.out + row * t.ld_out;
     const int p_end = min(t.n_out, p0 + kUpChunk);
-    for (int p = p0 + threadIdx.x; p < p_end; p += blockDim.x) {
-        float v = 0.0f;
-        if (t.first_n + p >= 0) {
-            const int64_t nrel = (int64_t)p - t.lam_out;
-            if ((nrel & 1) == 0) {
-                v = seg[(nrel >> 1) + t.in_off - pos_lo];
-            } else {
-                const int lo = (int)(((nrel - 1) >> 1) + t.in_off - pos_lo);   // m for j = +1
+    // coarser samples a whose outputs 2a, 2a + 1 (relative to lam_out) fall in [p0, p_end)
+    const int64_t a_first = nrel0 >> 1;
+    const int64_t a_last = ((int64_t)p_end - 1 - t.lam_out) >> 1;
+    const int64_t off = t.in_off - pos_lo;                  // seg index of coarser sample a: a + off
+    for (int64_t a = a_first + threadIdx.x; a <= a_last; a += blockDim.x) {
+        const int lo = (int)(a + off);
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
 #pragma unroll
-                for (int k = 0; k < kOddTaps; ++k) v = fmaf(2.0f * g.odd[k], seg[lo - k] + seg[lo + 1 + k], v);
-            }
+        for (int k = 0; k < kOddTaps; k += 4) {
+            s0 = fmaf(c[k], seg[lo - k] + seg[lo + 1 + k], s0);
+            s1 = fmaf(c[k + 1], seg[lo - k - 1] + seg[lo + 2 + k], s1);
+            s2 = fmaf(c[k + 2], seg[lo - k - 2] + seg[lo + 3 + k], s2);
+            s3 = fmaf(c[k + 3], seg[lo - k - 3] + seg[lo + 4 + k], s3);
         }
-        out[p] = v;
+        const int64_t pe = 2 * a + t.lam_out;               // output index of the even sample
+        if (pe >= p0 && pe < p_end) out[pe] = t.first_n + pe >= 0 ? seg[lo] : 0.0f;
+        if (pe + 1 >= p0 && pe + 1 < p_end) out[pe + 1] = t.first_n + pe + 1 >= 0 ? (s0 + s1) + (s2 + s3) : 0.0f;
     }
 }
 

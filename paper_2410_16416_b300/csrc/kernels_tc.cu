@@ -430,21 +430,44 @@ struct MixTile {
     int tt, at, nk, var;
     int64_t xs0;        // first coarser position of the tile's window (16-byte aligned)
 };
-__device__ __forceinline__ MixTile mix_tile(const TcMixUpTask *tasks, int n_tasks, int tile, int kc_elems) {
-    MixTile m;
-    m.t = &tasks[find_tile(tasks, n_tasks, tile)];
-    const int local = tile - m.t->tile_begin;
-    m.tt = local / m.t->tiles_a;
-    m.at = local % m.t->tiles_a;
-    m.nk = (m.t->Lk_pad + kc_elems - 1) / kc_elems;
-    // output column c of the tile interpolates around coarser position A0 + (c + par) / 2
-    // (A0: position of relative column 0 halved); the window starts 16-byte aligned at xs0
-    const int64_t rel0 = (int64_t)kMixCols * m.tt - m.t->lam;
-    const int64_t A0 = (rel0 >> 1) + m.t->in_off;
-    m.xs0 = (A0 - 16) & ~int64_t(7);
-    m.var = (int)(rel0 & 1) * 8 + (int)((A0 - 16) - m.xs0);
-    return m;
-}
+// Per-role cursor over the task list.  A CTA's tiles come in increasing order (stride gridDim.x),
+// so each role walks the tasks forward and keeps the current task's tile-geometry fields in
+// registers, instead of searching the list and re-reading the fields for every tile.
+struct MixCursor {
+    const TcMixUpTask *t = nullptr;
+    int idx = -1, next = 0, begin = 0, tiles_a = 1, nk = 0, lam = 0, in_off = 0, kbytes = 32, Lk_pad = 0;
+    bool has_y = false;
+    __device__ __forceinline__ void seek(const TcMixUpTask *tasks, int n_tasks, int tile, int kc_elems) {
+        if (idx >= 0 && tile < next) return;
+        if (idx < 0) idx = find_tile(tasks, n_tasks, tile);
+        while (idx + 1 < n_tasks && tasks[idx + 1].tile_begin <= tile) ++idx;
+        t = &tasks[idx];
+        next = idx + 1 < n_tasks ? tasks[idx + 1].tile_begin : 0x7fffffff;
+        begin = t->tile_begin;
+        tiles_a = t->tiles_a;
+        nk = (t->Lk_pad + kc_elems - 1) / kc_elems;
+        lam = t->lam;
+        in_off = t->in_off;
+        kbytes = t->kbytes;
+        Lk_pad = t->Lk_pad;
+        has_y = t->mapY != nullptr;
+    }
+    __device__ __forceinline__ MixTile tile_of(int tile) const {
+        MixTile m;
+        m.t = t;
+        const int local = tile - begin;
+        m.tt = local / tiles_a;
+        m.at = local % tiles_a;
+        m.nk = nk;
+        // output column c of the tile interpolates around coarser position A0 + (c + par) / 2
+        // (A0: position of relative column 0 halved); the window starts 16-byte aligned at xs0
+        const int64_t rel0 = (int64_t)kMixCols * m.tt - lam;
+        const int64_t A0 = (rel0 >> 1) + in_off;
+        m.xs0 = (A0 - 16) & ~int64_t(7);
+        m.var = (int)(rel0 & 1) * 8 + (int)((A0 - 16) - m.xs0);
+        return m;
+    }
+};
 
 // no-swizzle K-major descriptor of U (core matrices 128 B apart along K, (K / 8) 128 B along N)
 template <int UB>
@@ -452,7 +475,7 @@ __device__ __forceinline__ uint64_t desc_u(uint32_t saddr) {
     return smem_desc(saddr, 128, (UGeo<UB>::kK / 8) * 128, 0);
 }
 
-template <int MODE, int UB>
+template <int MODE, int UB, bool TOP>
 __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpTask *__restrict__ tasks, int n_tasks,
                                                                    int total_tiles, int n_st, int n_win, int n_u,
                                                                    int n_stbuf, int st_bytes,
@@ -515,8 +538,10 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         uint32_t su = 0, wu = 0, uu = 0;
         int uvar = -1;                                       // U variant in the newest U buffer
         bool ok = true;
+        MixCursor cur;
         for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
-            const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
+            cur.seek(tasks, n_tasks, tile, kKC);
+            const MixTile m = cur.tile_of(tile);
             const TcMixUpTask &t = *m.t;
             for (int kc = 0; kc < m.nk; ++kc) {
                 const int s = su % n_st;
@@ -570,11 +595,13 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         uint32_t su = 0, wu = 0, uu = 0, au = 0;
         int uvar = -1;
         bool issued = false;
+        MixCursor cur;
         const uint32_t idesc = idesc_op<MODE>(kMixRows, kMixCols);
         const uint32_t idesc_u = idesc_op<NP == 1 ? kModeF16 : kModeBF16>(kMixRows, G::kBlk);
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-            const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
-            const bool has_src = m.t->mapY != nullptr;
+            cur.seek(tasks, n_tasks, tile, kKC);
+            const MixTile m = cur.tile_of(tile);
+            const bool has_src = cur.has_y;
             const int b = au & 1;
             if (au >= 2 && !mbar_wait(&aempty[b], ((au >> 1) - 1) & 1, err, 9)) break;
             tc_fence_after();
@@ -587,11 +614,11 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     break;
                 }
                 tc_fence_after();
-                const int kb = m.t->kbytes;
+                const int kb = cur.kbytes;
                 // descriptors differ only in the start address field (address >> 4, no carry)
                 const uint32_t sa = smem_u32(stage + s * st_bytes);
                 const uint64_t da = desc_k_sw(sa, kb), db = desc_k_sw(sa + kMixRows * kb, kb);
-                const int nmma = min(kb / 32, (m.t->Lk_pad - kc * kKC) / kMK);     // 32 bytes of K per MMA
+                const int nmma = min(kb / 32, (cur.Lk_pad - kc * kKC) / kMK);      // 32 bytes of K per MMA
                 for (int kk = 0; kk < nmma; ++kk)
                     mma_op<MODE>(d, da + 2 * kk, db + 2 * kk, idesc, (kc | kk) != 0);
                 issued = true;
@@ -656,8 +683,10 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
         const int R = 32 * q + lane;                         // TMEM lane = filter row in the tile
         uint8_t *sbuf = stbuf + (warp - 4) * (NP * kMixStPlane);
         uint32_t au = 0;
+        MixCursor cur;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-            const MixTile m = mix_tile(tasks, n_tasks, tile, kKC);
+            cur.seek(tasks, n_tasks, tile, kKC);
+            const MixTile m = cur.tile_of(tile);
             const TcMixUpTask &t = *m.t;
             const int b = au & 1;
             if (!mbar_wait(&afull[b], (au >> 1) & 1, err, 7)) break;
@@ -671,7 +700,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
             const bool row_ok = a < M2;
             // 128-wide interpolation blocks run only at the top level (trigger partials, no y stored);
             // 64-wide blocks only below it (y stored): each instantiation keeps only its own epilogue
-            constexpr bool kTopKernel = UB == 128;
+            constexpr bool kTopKernel = TOP;
             const bool top = kTopKernel && t.part != nullptr;
             SegBest b0{-1.0f, 0.0f, 0.0f, -1}, b1{-1.0f, 0.0f, 0.0f, -1};
             // top level: columns [vlo, vhi) of this half are real samples (n >= 0, inside the push);
@@ -713,10 +742,11 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                     for (int j = 0; j < 16; ++j) {
                         const float y0 = x[2 * j], y1 = x[2 * j + 1];
                         if constexpr (NP == 1) {
-                            // saturate instead of overflowing to infinity (|SNR| > 65504)
-                            const __half2 hv = __floats2half2_rn(fminf(fmaxf(y0, -65504.0f), 65504.0f),
-                                                                 fminf(fmaxf(y1, -65504.0f), 65504.0f));
-                            hw[j] = *reinterpret_cast<const uint32_t *>(&hv);
+                            // one packed conversion that saturates instead of overflowing to infinity
+                            // (|SNR| > 65504): y0 to the low half, y1 to the high half
+                            uint32_t hv;
+                            asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(hv) : "f"(y1), "f"(y0));
+                            hw[j] = hv;
                             lw[j] = 0u;
                         } else {
                             const __nv_bfloat162 hv = __floats2bfloat162_rn(y0, y1);   // hi: one packed convert
@@ -915,14 +945,14 @@ static int sm_count() {
     return count[dev];
 }
 
-template <int MODE, int UB>
+template <int MODE, int UB, bool TOP>
 static cudaError_t mixup_launch_ub(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixCfg &cfg,
                                    int n_stbuf, int kbytes, const void *utab, int *err, cudaStream_t s) {
     const size_t smem = tc_mixup_smem_bytes(cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, UB, y_planes(MODE), kbytes);
-    cudaError_t e = set_smem(tc_mixup_kernel<MODE, UB>, smem);
+    cudaError_t e = set_smem(tc_mixup_kernel<MODE, UB, TOP>, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total_tiles, sm_count());
-    return launch_pdl(tc_mixup_kernel<MODE, UB>, dim3(grid), dim3(kMixThreads), smem, s, d_tasks, n_tasks,
+    return launch_pdl(tc_mixup_kernel<MODE, UB, TOP>, dim3(grid), dim3(kMixThreads), smem, s, d_tasks, n_tasks,
                       total_tiles, cfg.n_st, cfg.n_win, cfg.n_u, n_stbuf, (int)tc_mixup_stage_bytes(kbytes),
                       static_cast<const uint8_t *>(utab), err);
 }
@@ -961,7 +991,7 @@ static std::vector<MixCfg> mix_candidates(const MixLaunch &ml, int ub, int np) {
     return out;
 }
 
-template <int MODE, int UB>
+template <int MODE, int UB, bool TOP>
 static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixLaunch &ml,
                                       const void *utab, int *err, MixTuner *tuner, bool may_tune, cudaStream_t s) {
     const int n_stbuf = ml.store_y ? 1 : 0;
@@ -981,7 +1011,7 @@ static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, i
         for (auto &x : ev) cudaEventCreate(&x);
         cudaError_t e = cudaEventRecord(ev[0], s);
         for (size_t k = 0; k < kTuneRounds * nc && e == cudaSuccess; ++k) {
-            e = mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cands[k % nc], n_stbuf, ml.kbytes, utab,
+            e = mixup_launch_ub<MODE, UB, TOP>(d_tasks, n_tasks, total_tiles, cands[k % nc], n_stbuf, ml.kbytes, utab,
                                           err, s);
             if (e == cudaSuccess) e = cudaEventRecord(ev[k + 1], s);
         }
@@ -1002,16 +1032,22 @@ static cudaError_t mixup_launch_tuned(const TcMixUpTask *d_tasks, int n_tasks, i
         tuner->timed_launches += (int64_t)(kTuneRounds * nc);
         return cudaSuccess;
     }
-    return mixup_launch_ub<MODE, UB>(d_tasks, n_tasks, total_tiles, cfg, n_stbuf, ml.kbytes, utab, err, s);
+    return mixup_launch_ub<MODE, UB, TOP>(d_tasks, n_tasks, total_tiles, cfg, n_stbuf, ml.kbytes, utab, err, s);
 }
 
 template <int MODE>
 static cudaError_t mixup_launch(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixLaunch &ml,
                                 const void *utab, int *err, MixTuner *tuner, bool may_tune, cudaStream_t s) {
-    // levels that store nothing (the top) use 128-wide interpolation blocks (fewer, wider MMAs)
+    // The top level (stores nothing) uses 128-wide interpolation blocks.  So do the stored levels of
+    // the one-plane (FP16 y) modes: an N = 128 MMA runs at the full rate, an N = 64 one at about half,
+    // and the 128 x 112 operand always fits beside one stage, two window chunks and the staging
+    // buffers.  The two-plane FP16 mode keeps 64-wide blocks, which always fit as well.  The block
+    // width depends on the operand mode only, so a unit's arithmetic never depends on its group.
     if (!ml.store_y)
-        return mixup_launch_tuned<MODE, 128>(d_tasks, n_tasks, total_tiles, ml, utab, err, tuner, may_tune, s);
-    return mixup_launch_tuned<MODE, 64>(d_tasks, n_tasks, total_tiles, ml, utab, err, tuner, may_tune, s);
+        return mixup_launch_tuned<MODE, 128, true>(d_tasks, n_tasks, total_tiles, ml, utab, err, tuner, may_tune, s);
+    if (y_planes(MODE) == 1)
+        return mixup_launch_tuned<MODE, 128, false>(d_tasks, n_tasks, total_tiles, ml, utab, err, tuner, may_tune, s);
+    return mixup_launch_tuned<MODE, 64, false>(d_tasks, n_tasks, total_tiles, ml, utab, err, tuner, may_tune, s);
 }
 
 cudaError_t launch_tc_mixup(const TcMixUpTask *d_tasks, int n_tasks, int total_tiles, const MixLaunch &ml,
