@@ -398,16 +398,18 @@ void tc_interp_table(const Halfband &g, void *host_out) {
     }
 }
 
+// Running maximum of one window segment; col is the column within the tile (32-bit arithmetic
+// in the per-sample path; the absolute sample is formed once, when the record is written).
 struct SegBest {
     float mag2, re, im;
-    int64_t n;
+    int col;
 };
-__device__ __forceinline__ void seg_update(SegBest &b, float m2, float re, float im, int64_t n) {
+__device__ __forceinline__ void seg_update(SegBest &b, float m2, float re, float im, int col) {
     if (m2 > b.mag2) {
         b.mag2 = m2;
         b.re = re;
         b.im = im;
-        b.n = n;
+        b.col = col;
     }
 }
 // Takes the other lane's maximum of the same segment when larger (the earlier sample on ties).
@@ -415,12 +417,12 @@ __device__ __forceinline__ void seg_merge_pair(SegBest &b) {
     const float om = __shfl_xor_sync(0xffffffffu, b.mag2, 1);
     const float ore = __shfl_xor_sync(0xffffffffu, b.re, 1);
     const float oim = __shfl_xor_sync(0xffffffffu, b.im, 1);
-    const long long on = __shfl_xor_sync(0xffffffffu, (long long)b.n, 1);
-    if (om > b.mag2 || (om == b.mag2 && om >= 0.0f && on < b.n)) {
+    const int oc = __shfl_xor_sync(0xffffffffu, b.col, 1);
+    if (om > b.mag2 || (om == b.mag2 && om >= 0.0f && oc < b.col)) {
         b.mag2 = om;
         b.re = ore;
         b.im = oim;
-        b.n = on;
+        b.col = oc;
     }
 }
 
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
             // 64-wide blocks only below it (y stored): each instantiation keeps only its own epilogue
             constexpr bool kTopKernel = TOP;
             const bool top = kTopKernel && t.part != nullptr;
-            SegBest b0{-1.0f, 0.0f, 0.0f, -1}, b1{-1.0f, 0.0f, 0.0f, -1};
+            SegBest b0{-1.0f, 0.0f, 0.0f, 0x7fffffff}, b1{-1.0f, 0.0f, 0.0f, 0x7fffffff};
             // top level: columns [vlo, vhi) of this half are real samples (n >= 0, inside the push);
             // columns >= cb belong to the next window (window length >= 128 columns)
             int vlo = 0, vhi = 0, cb = 1 << 30;
@@ -823,9 +825,9 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                                     oth[j] = oth[j + st];
                                 }
                         const float re = odd ? oth[0] : own[0], im = odd ? own[0] : oth[0];
-                        const int64_t nb = n0 + id[0] + (odd ? 16 : 0);
-                        if (cl >= cb) seg_update(b1, m2[0], re, im, nb);
-                        else seg_update(b0, m2[0], re, im, nb);
+                        const int cb_ = c0 + id[0] + (odd ? 16 : 0);       // column within the tile
+                        if (cl >= cb) seg_update(b1, m2[0], re, im, cb_);
+                        else seg_update(b0, m2[0], re, im, cb_);
                     } else {
                         // chunk at a push edge or a window boundary: both lanes scan every column
 #pragma unroll
@@ -835,8 +837,8 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                             if (cc < vlo || cc >= vhi) continue;
                             const float mm = fmaf(p, p, x[j] * x[j]);
                             const float re = odd ? p : x[j], im = odd ? x[j] : p;
-                            if (cc < cb) seg_update(b0, mm, re, im, n0 + j);
-                            else seg_update(b1, mm, re, im, n0 + j);
+                            if (cc < cb) seg_update(b0, mm, re, im, c0 + j);
+                            else seg_update(b1, mm, re, im, c0 + j);
                         }
                     }
                 }
@@ -846,12 +848,15 @@ __global__ void __launch_bounds__(kMixThreads, 1) tc_mixup_kernel(const TcMixUpT
                 seg_merge_pair(b1);
                 if ((a & 1) == 0 && row_ok) {
                     WinPart *base = t.part + (int64_t)(a >> 1) * t.n_rec + (m.tt * 2 + h) * 2;
-                    base[0] = WinPart{b0.mag2, b0.re, b0.im, 0.0f, 0.0f, 0.0f, 0, (int32_t)(b0.n - first_n)};
-                    base[1] = WinPart{b1.mag2, b1.re, b1.im, 0.0f, 0.0f, 0.0f, 0, (int32_t)(b1.n - first_n)};
+                    // sample offsets from the push's column 0 (empty records keep an unused offset)
+                    const int32_t r0 = b0.mag2 >= 0.0f ? kMixCols * m.tt + b0.col : -1;
+                    const int32_t r1 = b1.mag2 >= 0.0f ? kMixCols * m.tt + b1.col : -1;
+                    base[0] = WinPart{b0.mag2, b0.re, b0.im, 0.0f, 0.0f, 0.0f, 0, r0};
+                    base[1] = WinPart{b1.mag2, b1.re, b1.im, 0.0f, 0.0f, 0.0f, 0, r1};
                     if (t.wmax) {                    // window maxima for the refinement's candidate rule
                         uint32_t *wm = t.wmax + (int64_t)(a >> 1) * t.n_wslot - t.win0;
-                        if (b0.mag2 > t.thr2) atomicMax(wm + b0.n / t.win_len, __float_as_uint(b0.mag2));
-                        if (b1.mag2 > t.thr2) atomicMax(wm + b1.n / t.win_len, __float_as_uint(b1.mag2));
+                        if (b0.mag2 > t.thr2) atomicMax(wm + (first_n + r0) / t.win_len, __float_as_uint(b0.mag2));
+                        if (b1.mag2 > t.thr2) atomicMax(wm + (first_n + r1) / t.win_len, __float_as_uint(b1.mag2));
                     }
                 }
             }
