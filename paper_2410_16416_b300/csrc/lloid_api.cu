@@ -176,6 +176,8 @@ struct sb_ctx {
     sb_ctx_stats stats{};
     // FP32 refinement scratch (allocated on the first refined push, shared by later pushes)
     RefCand *ref_cands = nullptr;
+    float *ref_zpart = nullptr;       // per (candidate, FIR work item) FP32 partial sums of the refinement
+    int32_t ref_zpart_items = 0;      // work items per candidate ref_zpart holds
     uint32_t *ref_wmax = nullptr;     // per (unit, template, window) 16-bit maxima of one push
     unsigned long long *ref_cum = nullptr;   // running [candidates, pushes with dropped candidates]
     int64_t ref_wmax_cap = 0;
@@ -508,6 +510,7 @@ extern "C" int sb_ctx_destroy(sb_ctx *c) {
     for (auto &kv : c->graph_execs) cudaGraphExecDestroy(kv.second);
     c->graph_execs.clear();
     if (c->ref_cands) cudaFree(c->ref_cands);
+    if (c->ref_zpart) cudaFree(c->ref_zpart);
     if (c->ref_wmax) cudaFree(c->ref_wmax);
     if (c->ref_cum) cudaFree(c->ref_cum);
     if (c->utab) cudaFree(c->utab);
@@ -1453,6 +1456,7 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     std::vector<WinFinTask> wfin;
     std::vector<RefUnit> refu;
     int64_t ref_max_windows = 0, ref_wmax_total = 0;
+    int32_t ref_max_items = 0;                 // largest FIR work-item count of a refined unit
     std::vector<CopyTask> yshift1, yshift2;
     int kpad_max[NM] = {0, 0, 0};
     int max_hd = 0, max_hy = 0, max_rows = 0;
@@ -1677,7 +1681,9 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 r.sl_D[si] = sd.D;
                 r.sl_Q[si] = sd.Q;
                 r.sl_level[si] = sd.level;
+                r.sl_item0[si + 1] = r.sl_item0[si] + (sd.Q + kRefQC - 1) / kRefQC;
             }
+            ref_max_items = std::max(ref_max_items, r.sl_item0[u->slices.size()]);
             ref_max_windows = std::max<int64_t>(ref_max_windows, (int64_t)r.M * r.n_wslot);
             refu.push_back(r);
         }
@@ -1794,6 +1800,13 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
             c->ref_wmax = nullptr;
             c->ref_wmax_cap = std::max(ref_wmax_total, 2 * c->ref_wmax_cap);
             CK(cudaMalloc(&c->ref_wmax, c->ref_wmax_cap * sizeof(uint32_t)));
+        }
+        if (c->ref_zpart_items < ref_max_items) {       // per (candidate, FIR work item) partial sums
+            CK(cudaStreamSynchronize(st));
+            if (c->ref_zpart) cudaFree(c->ref_zpart);
+            c->ref_zpart = nullptr;
+            c->ref_zpart_items = ref_max_items;
+            CK(cudaMalloc(&c->ref_zpart, (size_t)kRefSplitCap * ref_max_items * 2 * kRefSpan * sizeof(float)));
         }
         for (auto &r : refu) r.wmax = c->ref_wmax + reinterpret_cast<intptr_t>(r.wmax);   // offset -> address
         for (auto &w : wfin)
@@ -1941,9 +1954,9 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     if (!refu.empty()) {
         CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
         if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
-                 *n = 2;
+                 *n = 3;
                  return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_windows, c->ref_cands,
-                                      c->ref_counters, c->ref_cum, c->g, st);
+                                      c->ref_counters, c->ref_cum, c->ref_zpart, ref_max_items, c->g, st);
              })))
             return rc;
     }

@@ -316,6 +316,8 @@ constexpr int kRefMaxLevels = 8;
 constexpr int kRefMaxSlices = 12;
 constexpr int kRefSpan = 64;             // level-k samples one candidate needs (<= 62 for R = 8 and 16 xi^2 lags)
 constexpr int kRefCandCap = 1 << 16;     // candidates one push refines at most
+constexpr int kRefSplitCap = 4096;       // candidates whose FIR chunks run as separate blocks (the rest inline)
+constexpr int kRefQC = 2048;             // filter taps of one FIR work item
 
 struct RefUnit {                         // one unit of a push with refinement on
     WinPart *part;                       // [M][n_rec] top-level partial maxima (refined in place)
@@ -332,6 +334,7 @@ struct RefUnit {                         // one unit of a push with refinement o
     const float *sl_H[kRefMaxSlices];    // FP32 reconstructed slice filters [2M][ldh] (mixing x basis)
     int64_t sl_D[kRefMaxSlices];
     int32_t sl_Q[kRefMaxSlices], sl_ldh[kRefMaxSlices], sl_level[kRefMaxSlices];
+    int32_t sl_item0[kRefMaxSlices + 1];  // FIR work items (kRefQC-tap chunks) of slice s: [sl_item0[s], sl_item0[s + 1])
     const float2 *acorr;                 // [M][kXiLags] template autocorrelation; null: no xi^2
 };
 struct RefCand {                         // one partial record to refine
@@ -340,9 +343,11 @@ struct RefCand {                         // one partial record to refine
 };
 // cands: kRefCandCap entries; counters[1] = candidates found, counters[2] = 1 when some were dropped
 // cum: running totals [candidates, pushes with dropped candidates] (device, never reset)
-// max_windows: the largest M x n_wslot of the units (one candidate-scan warp per template and window)
+// max_windows: the largest M x n_wslot of the units (one candidate-scan thread per template and window)
+// zpart: kRefSplitCap x max_items x 2 x kRefSpan floats of FIR scratch; max_items: the largest
+// sl_item0[n_slices] of the units
 cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_windows, RefCand *cands, int *counters,
-                          unsigned long long *cum, const Halfband &g, cudaStream_t s);
+                          unsigned long long *cum, float *zpart, int max_items, const Halfband &g, cudaStream_t s);
 // Margin of the candidate rule per operand mode: records within (1 - margin) of their window's
 // 16-bit maximum are refined (the 16-bit error stays well inside it).
 constexpr float kRefKeep16 = 0.81f;      // (1 - 0.1)^2, BF16 / FP16
