@@ -48,6 +48,14 @@ L2_FLUSH_BYTES = 256 << 20
 DTYPES = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}
 INTERP_FLOPS_PER_OUTPUT = 32.0      # halfband x2 interpolation: 32 multiply-adds per odd output, none per even
 RECORD_BYTES = 32                   # one top-level partial window record (sizeof WinPart)
+# With graphs on, a context keeps one executable graph per (group shape, trigger slot, task arena):
+# the 8-slot trigger ring cycles through 8 of them, each instantiated on its first use.  The
+# warm-up covers the whole ring, so no graph instantiation falls inside the timed steps.
+GRAPH_RING = 8
+
+
+def warm_pushes(warmup: int, graphs: bool) -> int:
+    return max(warmup, GRAPH_RING) if graphs else warmup
 
 
 def parse():
@@ -511,7 +519,7 @@ def device_arm(lloid, torch, stream, local, banks, precision, B, steps, warmup, 
     n_units = len(units)
     n_prof = min(steps, 16) if n_prof is None else n_prof
     t = 0
-    for _ in range(warmup):
+    for _ in range(warm_pushes(warmup, graphs)):
         ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
         t += B
     ctx.pop_triggers()
@@ -540,11 +548,13 @@ def device_arm(lloid, torch, stream, local, banks, precision, B, steps, warmup, 
         t += B
     stages = ctx.stage_times()
     ctx.profile(False)
-    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
     trig = ctx.pop_triggers()
     tuned = ctx.autotune_choices()
     ctx.close()
     return {"dev_s": dev_s, "wall": wall, "clocks": clk, "create_s": create_s, "stages": stages,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "launches": st1["kernel_launches"] - st0["kernel_launches"],
             "autotune": {"choices": tuned, "timed_launches": st1["autotune_launches"],
                          "in_timed_region": st1["autotune_launches"] - st0["autotune_launches"]},
@@ -566,7 +576,7 @@ def paper_sweep(lloid, torch, stream, local, args, rank, world, dist, barrier, f
     f0 = int(spec.top_rate_hz)
     push_s, steps, warmup = 16, args.paper_steps, 2
     B = push_s * f0
-    total = (warmup + steps + min(steps, 16)) * push_s
+    total = (warm_pushes(warmup, graphs) + steps + min(steps, 16)) * push_s
     dev = [torch.from_numpy(synth.white_noise(total * f0, 6, rank, det)).cuda() for det in range(3)]
     curve = []
     for nb in [int(x) for x in args.paper_banks.split(",") if x.strip()]:
@@ -708,7 +718,7 @@ def main():
         banks = [synth.shape_only_bank(b) for b in shard_bins(n_bins, rank, world)]
         f0 = int(banks[0].top_rate_hz)
         B = push_s * f0
-        total = (warmup + steps + min(steps, 16)) * push_s
+        total = (warm_pushes(warmup, graphs) + steps + min(steps, 16)) * push_s
         strains = [synth.white_noise(int(total * f0), 3, rank, det) for det in (0, 1)]
         dev = [torch.from_numpy(s).cuda() for s in strains]
         r = device_arm(lloid, torch, stream, local, banks, precision, B, steps, warmup, dev, graphs, autotune,
@@ -749,7 +759,7 @@ def main():
     f0 = int(spec.top_rate_hz)
     B = args.push_seconds * f0
     n_prof = min(args.steps, 16)
-    total_s = (args.warmup + args.steps + n_prof) * args.push_seconds
+    total_s = (warm_pushes(args.warmup, graphs) + args.steps + n_prof) * args.push_seconds
     strains = [make_strain(rank, det, total_s, f0, h, spec.n_templates) for det in (0, 1)]
     dev = [torch.from_numpy(s).cuda() for s in strains]
     tpl_s_rank = 2 * spec.n_templates * args.push_seconds * args.steps
@@ -773,7 +783,7 @@ def main():
     ctx2.autotune(autotune)
     u2 = make_units_for(ctx2, [bank], args.precision, B)
     t2 = 0
-    for _ in range(args.warmup):
+    for _ in range(warm_pushes(args.warmup, graphs)):
         ctx2.push_group(u2, [strains[det][t2:t2 + B] for det in (0, 1)], [t2] * 2, False)
         ctx2.pop_triggers()
         t2 += B
@@ -808,7 +818,8 @@ def main():
             "run": {"setup_s": prim["create_s"], "precision": args.precision,
                     "parallelism": f"units sharded, {world} GPU(s)", "cuda_graphs": args.graphs,
                     "mix_autotune": args.autotune, "xi2": args.xi2,
-                    "l2": "flushed between steps (256 MB write outside the step events)"},
+                    "l2": "flushed between steps (256 MB write outside the step events)",
+                    "warmup_pushes": warm_pushes(args.warmup, graphs), "step_ms": prim["step_ms"]},
             "roofline": roofs[dom], "roofline_stages": roofs, "e2e": e2e, "gpu_launches": prim["launches"],
             "clocks": prim["clocks"],
             "stages_ms_share": {k: round(v / total_stage_ms, 4) for k, v in busy.items()},
