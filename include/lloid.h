@@ -64,7 +64,7 @@ extern "C" {
  *         t_start_s seconds before coalescence, q grows back in time.
  * mixing: [2M * n_basis] row-major; row a = 2i + p holds the coefficients
  *         of real filter a on the basis vectors (h_{a,s} ~= sum_l M[a,l] v_l).
- * rate_hz must be top_rate_hz / 2^k (k >= 0); (t_end_s - t_start_s) * rate_hz
+ * rate_hz must be top_rate_hz / 2^k (0 <= k <= 7); (t_end_s - t_start_s) * rate_hz
  * and t_start_s * rate_hz must be integers.                                   */
 typedef struct sb_slice {
     double rate_hz;

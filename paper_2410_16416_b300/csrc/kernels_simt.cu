@@ -1,31 +1,12 @@
-// SIMT kernels of the LLOID hot path: halfband decimation (a1), interpolation
-// (a4), history copies, the FP32 GEMM used for the basis FIR (a2, Toeplitz B
-// operand) and the mixing step (a3) in SB_FP32 mode, and the window-maximum
-// trigger generator (a5).  Every kernel walks a device task list so that one
+// SIMT kernels of the LLOID hot path: interpolation (a4), history copies, the
+// FP32 GEMM used for the basis FIR (a2, Toeplitz B operand) and the mixing step
+// (a3) in SB_FP32 mode, and the window-maximum trigger generator (a5).  The
+// decimation cascade (a1) is in kernels_cascade.cu.  Every kernel walks a device task list so that one
 // launch serves all units of a grouped push.
 #include "gemm_fp32_tile.cuh"
 #include "lloid_internal.h"
 
 namespace lloid {
-
-// ---------------------------------------------------------------------------
-// a1: decimation by two with the halfband kernel (g[0] = 1/2, odd taps only).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) decimate_kernel(const DecimTask *__restrict__ tasks, Halfband g) {
-    griddep_wait();
-    const DecimTask t = tasks[blockIdx.y];
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= t.n_out) return;
-    if (t.first_m + p < 0) {               // every rate's signal starts at index 0
-        t.out[p] = 0.0f;
-        return;
-    }
-    const float *c = t.in + t.in_base + 2 * (int64_t)p;
-    float acc = 0.5f * c[0];
-#pragma unroll
-    for (int k = 0; k < kOddTaps; ++k) acc = fmaf(g.odd[k], c[-(2 * k + 1)] + c[2 * k + 1], acc);
-    t.out[p] = acc;
-}
 
 // ---------------------------------------------------------------------------
 // a4 (up-sampling half): y'[n] = sum_m 2 g[n - 2m] y[m]; even n copy y[n/2].
@@ -137,12 +118,12 @@ __device__ __forceinline__ int find_task_by_tile(const GemmTask *tasks, int n, i
     return lo;
 }
 
-__global__ void __launch_bounds__(256) gemm_fp32_kernel(const GemmTask *__restrict__ tasks, int n_tasks) {
+__global__ void __launch_bounds__(256, 2) gemm_fp32_kernel(const GemmTask *__restrict__ tasks, int n_tasks) {
     griddep_wait();
     const int ti = find_task_by_tile(tasks, n_tasks, blockIdx.x);
     const GemmTask t = tasks[ti];
     const int local = blockIdx.x - t.tile_begin;
-    gemm_fp32_tile<false>(t, (local / t.tiles_n) * kGemmTM, (local % t.tiles_n) * kGemmTN, 0);
+    gemm_fp32_tile(t, (local / t.tiles_n) * kGemmTM, (local % t.tiles_n) * kGemmTN);
 }
 
 // ---------------------------------------------------------------------------
@@ -368,13 +349,6 @@ cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int tota
     if (n_tasks == 0 || total_warps == 0) return cudaSuccess;
     return launch_pdl(win_finalize_kernel, dim3((total_warps * 32 + 255) / 256), dim3(256), 0, s, d_tasks, n_tasks,
                       total_warps, out);
-}
-
-cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,
-                            cudaStream_t s) {
-    if (n_tasks == 0 || max_out <= 0) return cudaSuccess;
-    dim3 grid((max_out + 255) / 256, n_tasks);
-    return launch_pdl(decimate_kernel, grid, dim3(256), 0, s, d_tasks, g);
 }
 
 cudaError_t launch_upsample(const UpTask *d_tasks, int n_tasks, int max_rows, int max_out,

@@ -86,49 +86,6 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 }
 
 // ---------------------------------------------------------------------------
-// FP32 -> 16-bit copies of the decimated strain (FIR data operand)
-// ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(256) to_half_kernel(const HalfConvTask *__restrict__ tasks) {
-    griddep_wait();
-    const HalfConvTask t = tasks[blockIdx.y];
-    using T = typename Op<MODE>::T;
-    T *dst = reinterpret_cast<T *>(t.dst);
-    float mul = 1.0f;
-    if (MODE == kModeE4M3) {                  // per-buffer absmax scaling: samples map to [-448, 448]
-        const float amax = t.amax[0];
-        mul = amax > 0.0f ? 448.0f / amax : 1.0f;
-        if (blockIdx.x == 0 && threadIdx.x == 0) t.amax_next[0] = 0.0f;   // reset for the next push
-    }
-    if constexpr (MODE == kModeE4M3) {        // two terms: hi + lo carries about 7 significant bits
-        T *lo = reinterpret_cast<T *>(t.dst_lo);
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            const float v = t.src[i] * mul;
-            const T h = Op<MODE>::cvt(v);
-            dst[i] = h;
-            lo[i] = Op<MODE>::cvt(v - static_cast<float>(h));
-        }
-    } else {
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n;
-             i += (int64_t)gridDim.x * blockDim.x)
-            dst[i] = Op<MODE>::cvt(t.src[i] * mul);
-    }
-}
-
-// |x| maximum of each task's source (E4M3 mode), as the bits of a non-negative float.
-__global__ void __launch_bounds__(256) absmax_kernel(const HalfConvTask *__restrict__ tasks) {
-    griddep_wait();
-    const HalfConvTask t = tasks[blockIdx.y];
-    float m = 0.0f;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n; i += (int64_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(t.src[i]));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(t.amax), __float_as_int(m));
-}
-
-// ---------------------------------------------------------------------------
 // a2: Hankel-operand basis FIR
 // ---------------------------------------------------------------------------
 constexpr int kFirStages = 4;
@@ -905,19 +862,6 @@ static cudaError_t set_smem(K kernel, size_t smem) {
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmemMax);
     if (e == cudaSuccess) done.insert(id);
     return e;
-}
-
-cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s) {
-    if (n_tasks == 0) return cudaSuccess;
-    dim3 grid(64, n_tasks);
-    if (mode == kModeBF16) return launch_pdl(to_half_kernel<kModeBF16>, grid, dim3(256), 0, s, d_tasks);
-    if (mode == kModeF16) return launch_pdl(to_half_kernel<kModeF16>, grid, dim3(256), 0, s, d_tasks);
-    else {
-        cudaError_t e = launch_pdl(absmax_kernel, grid, dim3(256), 0, s, d_tasks);
-        if (e == cudaSuccess) e = launch_pdl(to_half_kernel<kModeE4M3>, grid, dim3(256), 0, s, d_tasks);
-        return e;
-    }
-    return cudaGetLastError();
 }
 
 template <int MODE>

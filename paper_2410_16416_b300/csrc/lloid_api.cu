@@ -746,6 +746,9 @@ static int validate_desc(const sb_desc *d, std::vector<int> &lvl, Plan &P) {
         return fail(SB_EINVAL, "window_s * top_rate_hz must be a positive integer");
     int rc = plan_unit(d, lvl, P);
     if (rc) return rc;
+    if (P.kmax >= kRefMaxLevels)
+        return fail(SB_EINVAL, "slice rates go down to top_rate_hz / 2^" + std::to_string(kRefMaxLevels - 1) +
+                                   " at most");
     if (P.tc && std::llround(wl) < 128)
         return fail(SB_EINVAL, "tensor-core modes need window_s * top_rate_hz >= 128");
     if (P.tc && d->refine_threshold > 0.0f && (P.kmax >= kRefMaxLevels || d->n_slices > kRefMaxSlices))
@@ -1441,14 +1444,13 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     for (int i = 0; i < n_units; ++i) kall = std::max(kall, units[i]->kmax);
 
     std::vector<CopyTask> dcopy, ycopy;
-    std::vector<std::vector<DecimTask>> decim(kall);
+    std::vector<CascadeTask> casc(n_units);     // a1 cascade + 16-bit copies, one cluster per unit
     std::vector<GemmTask> fir;
     std::vector<std::vector<UpTask>> ups(kall + 1);
     std::vector<std::vector<GemmTask>> recon(kall + 1);
     std::vector<WinTask> win;
     // tensor-core modes, indexed by operand mode (kModeF16, kModeBF16, kModeE4M3)
     constexpr int NM = 3;
-    std::vector<HalfConvTask> conv[NM];
     std::vector<TcFirTask> tfir[NM];
     std::vector<std::vector<TcMixUpTask>> tmix[NM] = {std::vector<std::vector<TcMixUpTask>>(kall + 1),
                                                       std::vector<std::vector<TcMixUpTask>>(kall + 1),
@@ -1495,14 +1497,17 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 dt.in_base = L.Hd + L.e - 2 * N.e;
                 dt.first_m = (Tp >> (k + 1)) - N.e;
                 dt.n_out = (int32_t)(B >> (k + 1));
-                decim[k].push_back(dt);
+                casc[i].lev[k] = dt;
+                casc[i].n_lev = k + 1;
             }
             if (u->tc) {
                 const int h = u->mode;
                 float *am = L.amax ? L.amax + u->amax_cur : nullptr;
                 float *am_next = L.amax ? L.amax + (1 - u->amax_cur) : nullptr;
                 void *x_lo = mode_terms(u->mode) == 2 ? static_cast<uint8_t *>(L.x16) + L.x16_len : nullptr;
-                conv[h].push_back(HalfConvTask{L.dbuf[nb], L.x16, L.Hd + Bk, am, am_next, x_lo});
+                casc[i].conv[k] = HalfConvTask{L.dbuf[nb], L.x16, L.Hd + Bk, am, am_next, x_lo};
+                casc[i].n_conv = k + 1;
+                casc[i].mode = h;
                 for (int s : L.slices) {
                     const SliceDev &sd = u->slices[s];
                     TcFirTask f{};
@@ -1779,8 +1784,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     // pack task lists (and host strain) into one pinned block
     Packer pk;
     const size_t o_dcopy = pk.add(dcopy.data(), dcopy.size() * sizeof(CopyTask));
-    std::vector<size_t> o_decim(kall), o_ups(kall + 1), o_recon(kall + 1);
-    for (int k = 0; k < kall; ++k) o_decim[k] = pk.add(decim[k].data(), decim[k].size() * sizeof(DecimTask));
+    std::vector<size_t> o_ups(kall + 1), o_recon(kall + 1);
+    const size_t o_casc = pk.add(casc.data(), casc.size() * sizeof(CascadeTask));
     const size_t o_fir = pk.add(fir.data(), fir.size() * sizeof(GemmTask));
     for (int k = 0; k <= kall; ++k) {
         o_ups[k] = pk.add(ups[k].data(), ups[k].size() * sizeof(UpTask));
@@ -1816,11 +1821,10 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
                 if (m.wmax) m.wmax = c->ref_wmax + (reinterpret_cast<intptr_t>(m.wmax) - 1);
         CK(cudaMemsetAsync(c->ref_wmax, 0, ref_wmax_total * sizeof(uint32_t), st));   // before this push's kernels
     }
-    size_t o_conv[NM], o_tfir[NM];
+    size_t o_tfir[NM];
     std::vector<size_t> o_tmix[NM] = {std::vector<size_t>(kall + 1), std::vector<size_t>(kall + 1),
                                       std::vector<size_t>(kall + 1)};
     for (int h = 0; h < NM; ++h) {
-        o_conv[h] = pk.add(conv[h].data(), conv[h].size() * sizeof(HalfConvTask));
         o_tfir[h] = pk.add(tfir[h].data(), tfir[h].size() * sizeof(TcFirTask));
         for (int k = 0; k <= kall; ++k) o_tmix[h][k] = pk.add(tmix[h][k].data(), tmix[h][k].size() * sizeof(TcMixUpTask));
     }
@@ -1892,22 +1896,12 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
              return launch_copy((CopyTask *)(D + o_scopy), n_units, 1, (int)B, st);
          })))
         return rc;
-    // 3. a1 decimation cascade
-    for (int k = 0; k < kall; ++k)
-        if ((rc = run_stage(c, SB_STAGE_DECIMATE, [&](int *n) {
-                 *n = decim[k].empty() ? 0 : 1;
-                 return launch_decimate((DecimTask *)(D + o_decim[k]), (int)decim[k].size(), (int)(B >> (k + 1)),
-                                        c->g, st);
-             })))
-            return rc;
-    // 16-bit copies of the decimated strain for the tensor-core FIR
-    for (int h = 0; h < NM; ++h)
-        if (!conv[h].empty() && (rc = run_stage(c, SB_STAGE_DECIMATE, [&](int *n) {
-                                     *n = 1;
-                                     return launch_to_half((HalfConvTask *)(D + o_conv[h]), (int)conv[h].size(),
-                                                           h, st);
-                                 })))
-            return rc;
+    // 3. a1 decimation cascade of every unit and the 16-bit copies for the tensor-core FIR (one launch)
+    if ((rc = run_stage(c, SB_STAGE_DECIMATE, [&](int *n) {
+             *n = 1;
+             return launch_cascade((CascadeTask *)(D + o_casc), n_units, c->g, st);
+         })))
+        return rc;
     // 4. a2 basis FIR, all slices of all units at once
     if (!fir.empty() && (rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
                              *n = 1;

@@ -181,7 +181,7 @@ struct HalfConvTask {       // dst[i] = narrow(src[i]), i < n (E4M3: scaled by 4
     const float *src;
     void *dst;
     int64_t n;
-    float *amax;               // E4M3: this push's |src| maximum (accumulated by absmax_kernel)
+    float *amax;               // E4M3: this push's |src| maximum (accumulated by the cascade kernel)
     float *amax_next;          // E4M3: the next push's accumulator, zeroed here
     void *dst_lo;              // E4M3: second term, dst_lo[i] = narrow(s src[i] - dst[i]); null otherwise
 };
@@ -278,7 +278,6 @@ struct MixLaunch {
 };
 size_t tc_mixup_stage_bytes(int kbytes);
 size_t tc_mixup_smem_bytes(int n_st, int n_win, int n_u, int n_stbuf, int ublk, int np, int kbytes);
-cudaError_t launch_to_half(const HalfConvTask *d_tasks, int n_tasks, int mode, cudaStream_t s);
 // wait_ns: bound of the kernel's waits (0: the default, 2 s); skip_chunk >= 0: test hook (the first
 // tile's producer skips that K chunk's load, so its consumer's wait runs out).
 cudaError_t launch_tc_fir(const TcFirTask *d_tasks, int n_tasks, int total_tiles, int kpad_max, int mode, int *err,
@@ -353,9 +352,21 @@ cudaError_t launch_refine(const RefUnit *d_units, int n_units, int64_t max_windo
 constexpr float kRefKeep16 = 0.81f;      // (1 - 0.1)^2, BF16 / FP16
 constexpr float kRefKeep8 = 0.64f;       // (1 - 0.2)^2, E4M3 (errors <= 0.15 near |rho| = 5.5)
 
+// ---- a1 cascade and 16-bit copies in one launch (kernels_cascade.cu) --------
+// One unit per cluster of kCascadeCtas CTAs.  Levels run in order: the 16-bit copy of level k
+// (tensor-core units) and the decimation k -> k + 1 both read level k, then a cluster barrier makes
+// level k + 1 visible to every CTA of the cluster before the next step.
+constexpr int kCascadeCtas = 8;
+struct CascadeTask {
+    DecimTask lev[kRefMaxLevels];        // level k -> k + 1, k < n_lev
+    HalfConvTask conv[kRefMaxLevels];    // 16-bit operand copy of level k, k < n_conv
+    int32_t n_lev, n_conv;
+    int32_t mode;                        // operand mode of the copies (kModeF16, kModeBF16, kModeE4M3)
+    int32_t pad;
+};
+cudaError_t launch_cascade(const CascadeTask *d_tasks, int n_tasks, const Halfband &g, cudaStream_t s);
+
 // ---- launchers (kernels_simt.cu) -------------------------------------------
-cudaError_t launch_decimate(const DecimTask *d_tasks, int n_tasks, int max_out, const Halfband &g,
-                            cudaStream_t s);
 cudaError_t launch_upsample(const UpTask *d_tasks, int n_tasks, int max_rows, int max_out,
                             const Halfband &g, cudaStream_t s);
 cudaError_t launch_copy(const CopyTask *d_tasks, int n_tasks, int max_rows, int max_n, cudaStream_t s);
@@ -365,6 +376,6 @@ cudaError_t launch_gemm_fp32(const GemmTask *d_tasks, int n_tasks, int total_til
 cudaError_t launch_window_max(const WinTask *d_tasks, int n_tasks, int total_warps, TrigOut out,
                               cudaStream_t s);
 
-constexpr int kGemmTM = 64, kGemmTN = 128, kGemmTK = 16;
+constexpr int kGemmTM = 128, kGemmTN = 128, kGemmTK = 8;
 
 }  // namespace lloid
