@@ -1421,6 +1421,572 @@ static int slot_acquire(sb_ctx *c, int64_t need, TriggerSlot *&out, int &idx) {
     return SB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// push: the task lists of one grouped push, one builder per stage
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNM = 3;                           // tensor-core operand modes (kModeF16, kModeBF16, kModeE4M3)
+
+// Every task list of one grouped push.  Each builder appends one unit's tasks in level order, so
+// every list runs unit by unit; the counters size the launches and the scratch.
+struct PushPlan {
+    int kall = 0;                                // deepest level over the units
+    std::vector<CopyTask> dcopy, ycopy, yshift1, yshift2;
+    std::vector<CascadeTask> casc;               // a1 cascade + 16-bit copies, one cluster per unit
+    std::vector<GemmTask> fir;                   // SB_FP32 basis FIR
+    std::vector<std::vector<UpTask>> ups;        // SB_FP32 interpolation, per level
+    std::vector<std::vector<GemmTask>> recon;    // SB_FP32 mixing, per level
+    std::vector<WinTask> win;                    // SB_FP32 trigger generator
+    std::vector<TcFirTask> tfir[kNM];            // tensor-core basis FIR, per operand mode
+    std::vector<std::vector<TcMixUpTask>> tmix[kNM];   // tensor-core mixing, per operand mode and level
+    std::vector<WinFinTask> wfin;                // 16/8-bit window finalisation
+    std::vector<RefUnit> refu;                   // FP32 refinement of the 16/8-bit candidates
+    int64_t ref_max_windows = 0, ref_wmax_total = 0;
+    int32_t ref_max_items = 0;                   // largest FIR work-item count of a refined unit
+    int kpad_max[kNM] = {0, 0, 0};
+    int max_hd = 0, max_hy = 0, max_rows = 0;
+    int64_t trig_need = 0;
+    // launch sizes (assign_tiles)
+    int fir_tiles = 0;
+    std::vector<int> recon_tiles;
+    int tfir_tiles[kNM] = {0, 0, 0};
+    std::vector<int> tmix_tiles[kNM];
+    std::vector<MixLaunch> tmix_ml[kNM];
+    int wfin_warps = 0, win_warps = 0;
+
+    PushPlan(int n_units, int kall_)
+        : kall(kall_), casc(n_units), ups(kall_ + 1), recon(kall_ + 1), recon_tiles(kall_ + 1, 0) {
+        for (int h = 0; h < kNM; ++h) {
+            tmix[h].resize(kall + 1);
+            tmix_tiles[h].assign(kall + 1, 0);
+            tmix_ml[h].resize(kall + 1);
+        }
+    }
+};
+
+// This unit's slice of the refinement's window-maxima scratch during one push (an offset; the
+// addresses are set at packing).
+struct RefineWindows {
+    bool on = false;
+    int64_t win0 = 0;                            // window of slot 0
+    int32_t n_wslot = 0;
+    int64_t wmax_off = 0;
+};
+
+RefineWindows refine_windows(PushPlan &P, const sb_unit *u, int64_t B) {
+    RefineWindows rw;
+    const int64_t first_n0 = u->T - u->levels[0].lam;
+    const int64_t start0 = std::max<int64_t>(first_n0, 0), end0 = first_n0 + B;
+    rw.on = end0 > start0 && u->refine;
+    rw.win0 = rw.on ? start0 / u->win_len : 0;
+    rw.n_wslot = rw.on ? (int32_t)((end0 - 1) / u->win_len - rw.win0 + 1) : 0;
+    rw.wmax_off = P.ref_wmax_total;
+    if (rw.on) P.ref_wmax_total += (int64_t)u->M * rw.n_wslot;
+    return rw;
+}
+
+// History shifts of the decimated strain, the a1 cascade and (tensor-core units) the 16-bit copies.
+void plan_streams(PushPlan &P, int i, sb_unit *u, int64_t B) {
+    const int64_t Tp = u->T;
+    CascadeTask &cs = P.casc[i];
+    for (int k = 0; k <= u->kmax; ++k) {
+        LevelDev &L = u->levels[k];
+        const int nb = 1 - L.dcur;
+        CopyTask ct{};
+        ct.cur = L.dbuf[L.dcur];
+        ct.dst = L.dbuf[nb];
+        ct.rows = 1;
+        ct.n = (int32_t)L.Hd;
+        ct.off = (int32_t)L.last_Bk;
+        P.dcopy.push_back(ct);
+        P.max_hd = std::max<int>(P.max_hd, (int)L.Hd);
+        if (k < u->kmax) {
+            LevelDev &N = u->levels[k + 1];
+            DecimTask dt{};
+            dt.in = L.dbuf[nb];
+            dt.out = N.dbuf[1 - N.dcur] + N.Hd;
+            dt.in_base = L.Hd + L.e - 2 * N.e;
+            dt.first_m = (Tp >> (k + 1)) - N.e;
+            dt.n_out = (int32_t)(B >> (k + 1));
+            cs.lev[k] = dt;
+            cs.n_lev = k + 1;
+        }
+        if (u->tc) {
+            float *am = L.amax ? L.amax + u->amax_cur : nullptr;
+            float *am_next = L.amax ? L.amax + (1 - u->amax_cur) : nullptr;
+            void *x_lo = mode_terms(u->mode) == 2 ? static_cast<uint8_t *>(L.x16) + L.x16_len : nullptr;
+            cs.conv[k] = HalfConvTask{L.dbuf[nb], L.x16, L.Hd + (B >> k), am, am_next, x_lo};
+            cs.n_conv = k + 1;
+            cs.mode = u->mode;
+        }
+    }
+}
+
+// Tensor-core units: a2 basis FIR per slice, a3 + a4 (+ a5 partials at the top) per level, and the
+// interpolation history of every level below the top for the next push.
+void plan_tc(PushPlan &P, sb_unit *u, int64_t B, const RefineWindows &rw) {
+    const int64_t Tp = u->T;
+    const int M2 = 2 * u->M;
+    const int h = u->mode;
+    for (int k = 0; k <= u->kmax; ++k) {
+        LevelDev &L = u->levels[k];
+        const int64_t Bk = B >> k;
+        const float *am = L.amax ? L.amax + u->amax_cur : nullptr;
+        const void *x_lo = mode_terms(u->mode) == 2 ? static_cast<uint8_t *>(L.x16) + L.x16_len : nullptr;
+        for (int s : L.slices) {
+            const SliceDev &sd = u->slices[s];
+            TcFirTask f{};
+            f.mapW = sd.mapW;
+            f.x = L.x16;
+            f.X0 = sd.X0;
+            f.O = L.O16;
+            f.ldo = L.Lk_pad;
+            f.o_col = sd.o_col16;
+            f.Kpad = sd.Kpad;
+            f.Bk = (int32_t)Bk;
+            const int64_t ph = mode_phases(u->mode);       // samples per Hankel block
+            f.tiles_n = (int32_t)(((Bk + ph - 1) / ph + kTcN - 1) / kTcN);
+            f.tiles_m = sd.L16 / (kTcM / mode_phases(u->mode));
+            f.xamax = am;
+            f.colscale = L.colscale;
+            f.x_lo = x_lo;
+            P.tfir[h].push_back(f);
+            P.kpad_max[h] = std::max(P.kpad_max[h], sd.Kpad);
+        }
+        TcMixUpTask mt{};
+        mt.mapM = L.mapM;
+        mt.mapO = L.mapO;
+        if (k < u->kmax) mt.mapY = u->levels[k + 1].mapY;
+        mt.Y = k == 0 ? L.ynew : nullptr;             // SB_FLAG_KEEP_SNR
+        mt.ldy = L.ldy;
+        mt.Yh = k >= 1 ? reinterpret_cast<uint16_t *>(L.yuni) : nullptr;
+        mt.ldu = L.ldu;
+        mt.yst_col0 = L.Hy;
+        mt.kbytes = mix_kbytes(L.Lk_pad, u->mmode);
+        mt.part = k == 0 ? u->part : nullptr;
+        if (k == 0 && rw.on) {
+            mt.wmax = reinterpret_cast<uint32_t *>(rw.wmax_off + 1);   // offset + 1; address at packing
+            mt.win0 = rw.win0;
+            mt.n_wslot = rw.n_wslot;
+            mt.thr2 = u->refine_thr * u->refine_thr;
+        }
+        mt.first_n = (Tp >> k) - L.lam;
+        mt.win_len = u->win_len;
+        mt.Lk_pad = L.Lk_pad;
+        mt.M2 = M2;
+        mt.M = u->M;
+        mt.Bk = (int32_t)Bk;
+        mt.lam = (int32_t)L.lam;
+        mt.in_off = k < u->kmax ? (int32_t)(u->levels[k + 1].lam + u->levels[k + 1].Hy) : 0;
+        mt.tiles_t = (int32_t)((Bk + 255) / 256);
+        mt.tiles_a = (M2 + 127) / 128;
+        mt.n_rec = mt.tiles_t * 4;
+        P.tmix[u->mmode][k].push_back(mt);
+        if (k >= 1) {           // next push's interpolation history: columns [Bk, Bk + Hy) -> [0, Hy)
+            // (in place when the two ranges are disjoint, else through the staging buffer)
+            const bool direct = Bk >= L.Hy;
+            CopyTask a{};
+            a.cur = L.yuni;
+            a.ld_cur = L.ldu;
+            a.dst = direct ? L.yuni : L.ytmp;
+            a.ld_dst = direct ? L.ldu : L.Hy;
+            a.rows = M2;
+            a.n = (int32_t)L.Hy;
+            a.off = (int32_t)Bk;
+            a.elem16 = y_planes(u->mmode);
+            P.yshift1.push_back(a);
+            P.max_hy = std::max<int>(P.max_hy, (int)L.Hy);
+            if (!direct) {
+                CopyTask bt{};
+                bt.cur = L.ytmp;
+                bt.ld_cur = L.Hy;
+                bt.dst = L.yuni;
+                bt.ld_dst = L.ldu;
+                bt.rows = M2;
+                bt.n = (int32_t)L.Hy;
+                bt.off = 0;
+                bt.elem16 = y_planes(u->mmode);
+                P.yshift2.push_back(bt);
+            }
+        }
+    }
+}
+
+// SB_FP32 units: a2 basis FIR per slice (Toeplitz operand), a4 interpolation and a3 mixing per
+// level, and the SNR history of every level below the top.
+void plan_fp32(PushPlan &P, sb_unit *u, int64_t B) {
+    const int64_t Tp = u->T;
+    const int M2 = 2 * u->M;
+    for (int k = 0; k <= u->kmax; ++k) {
+        LevelDev &L = u->levels[k];
+        const int nb = 1 - L.dcur;
+        const int64_t Bk = B >> k;
+        for (int s : L.slices) {
+            const SliceDev &sd = u->slices[s];
+            GemmTask g{};
+            g.A = sd.V;
+            g.lda = sd.Q;
+            g.B = L.dbuf[nb];
+            g.ldb = L.Hd + L.e - L.lam - sd.D;
+            g.C = L.obuf + (int64_t)sd.o_row * L.Bk_max;
+            g.ldc = L.Bk_max;
+            g.M = sd.L;
+            g.N = (int32_t)Bk;
+            g.K = sd.Q;
+            g.beta = 0;
+            g.toeplitz = 1;
+            P.fir.push_back(g);
+        }
+        if (k < u->kmax) {
+            LevelDev &N = u->levels[k + 1];
+            UpTask ut{};
+            ut.hist = N.yhist[N.ycur];
+            ut.cur = N.ynew;
+            ut.out = L.ynew;
+            ut.ld_hist = N.Hy;
+            ut.ld_cur = N.ldy;
+            ut.ld_out = L.ldy;
+            ut.n_hist = (int32_t)N.Hy;
+            ut.rows = M2;
+            ut.n_out = (int32_t)Bk;
+            ut.lam_out = (int32_t)L.lam;
+            ut.in_off = (int32_t)(N.lam + N.Hy);
+            ut.n_cur = (int32_t)(B >> (k + 1));
+            ut.first_n = (Tp >> k) - L.lam;
+            P.ups[k].push_back(ut);
+        }
+        if (L.Lk > 0) {
+            GemmTask g{};
+            g.A = L.Mcat;
+            g.lda = L.Lk;
+            g.B = L.obuf;
+            g.ldb = L.Bk_max;
+            g.C = L.ynew;
+            g.ldc = L.ldy;
+            g.M = M2;
+            g.N = (int32_t)Bk;
+            g.K = L.Lk;
+            g.beta = k < u->kmax ? 1 : 0;
+            g.toeplitz = 0;
+            P.recon[k].push_back(g);
+        }
+        if (k >= 1 && L.Hy > 0) {
+            CopyTask yt{};
+            yt.hist = L.yhist[L.ycur];
+            yt.cur = L.ynew;
+            yt.dst = L.yhist[1 - L.ycur];
+            yt.ld_hist = L.Hy;
+            yt.ld_cur = L.ldy;
+            yt.ld_dst = L.Hy;
+            yt.n_hist = (int32_t)L.Hy;
+            yt.rows = M2;
+            yt.n = (int32_t)L.Hy;
+            yt.off = (int32_t)Bk;
+            P.ycopy.push_back(yt);
+            P.max_hy = std::max<int>(P.max_hy, (int)L.Hy);
+        }
+    }
+}
+
+// The trigger generator of the top level: window finalisation (16/8-bit units, after the mixing
+// kernel's partial maxima) with the FP32 refinement of the candidates, or the window maxima of
+// the FP32 SNR block (SB_FP32 units).
+void plan_triggers(PushPlan &P, sb_unit *u, int64_t B, const RefineWindows &rw) {
+    const int64_t Tp = u->T;
+    LevelDev &L0 = u->levels[0];
+    const int64_t first_n = Tp - L0.lam;
+    const int64_t start = std::max<int64_t>(first_n, 0), end = first_n + B;
+    if (end > start && u->refine) {
+        RefUnit r{};
+        r.part = u->part;
+        r.first_n = first_n;
+        r.win_len = u->win_len;
+        r.thr2 = u->refine_thr * u->refine_thr;
+        r.keep2 = u->mode == kModeE4M3 ? kRefKeep8 : kRefKeep16;
+        r.win0 = rw.win0;
+        r.n_wslot = rw.n_wslot;
+        r.wmax = reinterpret_cast<uint32_t *>(rw.wmax_off);         // offset; the base is added before packing
+        r.kmax = u->kmax;
+        r.M = u->M;
+        r.n_rec = (int32_t)((B + kRefTile - 1) / kRefTile) * 4;
+        r.B = (int32_t)B;
+        r.n_slices = (int32_t)u->slices.size();
+        r.acorr = u->acorr;
+        for (int k = 0; k <= u->kmax; ++k) {
+            LevelDev &L = u->levels[k];
+            r.lv_d[k] = L.dbuf[1 - L.dcur];
+            r.lv_origin[k] = (Tp >> k) - L.e - L.Hd;
+            r.lv_len[k] = L.Hd + (B >> k);
+        }
+        for (size_t si = 0; si < u->slices.size(); ++si) {
+            const SliceDev &sd = u->slices[si];
+            r.sl_H[si] = sd.H;
+            r.sl_ldh[si] = sd.ldh;
+            r.sl_D[si] = sd.D;
+            r.sl_Q[si] = sd.Q;
+            r.sl_level[si] = sd.level;
+            r.sl_item0[si + 1] = r.sl_item0[si] + (sd.Q + kRefQC - 1) / kRefQC;
+        }
+        P.ref_max_items = std::max(P.ref_max_items, r.sl_item0[u->slices.size()]);
+        P.ref_max_windows = std::max<int64_t>(P.ref_max_windows, (int64_t)r.M * r.n_wslot);
+        P.refu.push_back(r);
+    }
+    if (end > start && u->tc) {
+        WinFinTask w{};
+        w.part = u->part;
+        w.state_in = u->wstate[u->wcur];
+        w.state_out = u->wstate[1 - u->wcur];
+        w.template_ids = u->tids;
+        w.unit_id = u->id;
+        w.win_len = u->win_len;
+        w.first_n = first_n;
+        w.start_abs = start;
+        w.end_abs = end;
+        w.n_rec = (int32_t)(((B + 255) / 256) * 4);
+        w.M = u->M;
+        w.n_win = (int32_t)((end - 1) / u->win_len - start / u->win_len + 1);
+        w.threshold = u->thr;
+        // the refinement's window maxima cover every possible trigger when its threshold is lower
+        if (rw.on && u->refine_thr < u->thr * (1.0f - 1e-6f)) {
+            w.n_wslot = rw.n_wslot;
+            w.wmax = reinterpret_cast<const uint32_t *>(rw.wmax_off + 1);   // offset + 1; the base is added at packing
+        }
+        P.wfin.push_back(w);
+        P.trig_need += (int64_t)u->M * w.n_win;
+    } else if (end > start) {
+        WinTask w{};
+        w.x = L0.ynew;
+        w.ldx = L0.ldy;
+        w.state_in = u->wstate[u->wcur];
+        w.state_out = u->wstate[1 - u->wcur];
+        w.template_ids = u->tids;
+        w.first_n = first_n;
+        w.unit_id = u->id;
+        w.win_len = u->win_len;
+        w.n = (int32_t)B;
+        w.M = u->M;
+        w.n_seg = (int32_t)((end - 1) / u->win_len - start / u->win_len + 1);
+        w.threshold = u->thr;
+        w.acorr = u->acorr;
+        P.win.push_back(w);
+        P.trig_need += (int64_t)u->M * w.n_seg;
+    }
+}
+
+int assign_gemm_tiles(std::vector<GemmTask> &v) {
+    int tot = 0;
+    for (auto &g : v) {
+        g.tiles_n = (g.N + kGemmTN - 1) / kGemmTN;
+        const int tiles_m = (g.M + kGemmTM - 1) / kGemmTM;
+        g.tile_begin = tot;
+        tot += tiles_m * g.tiles_n;
+    }
+    return tot;
+}
+
+// Tile and warp offsets of every task list (each launch walks its tasks by global tile or warp),
+// and the launch description of every mixing launch.
+void assign_tiles(PushPlan &P) {
+    P.fir_tiles = assign_gemm_tiles(P.fir);
+    for (int k = 0; k <= P.kall; ++k) P.recon_tiles[k] = assign_gemm_tiles(P.recon[k]);
+    for (int h = 0; h < kNM; ++h) {
+        for (auto &f : P.tfir[h]) {
+            f.tile_begin = P.tfir_tiles[h];
+            P.tfir_tiles[h] += f.tiles_m * f.tiles_n;
+        }
+        for (int k = 0; k <= P.kall; ++k)
+            for (auto &m : P.tmix[h][k]) {
+                m.tile_begin = P.tmix_tiles[h][k];
+                P.tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
+                MixLaunch &ml = P.tmix_ml[h][k];
+                if (m.Yh) ml.store_y = true;
+                if (m.mapY) ml.interp = true;
+                ml.kbytes = std::max(ml.kbytes, (int)m.kbytes);
+                const int kc = 128 / mode_bytes(h);                  // K elements per 128-byte chunk
+                ml.max_nk = std::max(ml.max_nk, (m.Lk_pad + kc - 1) / kc);
+            }
+    }
+    for (auto &w : P.wfin) {
+        w.warp_begin = P.wfin_warps;
+        P.wfin_warps += w.M * w.n_win;
+    }
+    for (auto &w : P.win) {
+        w.warp_begin = P.win_warps;
+        P.win_warps += w.M * w.n_seg;
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// Offsets of one push's task lists in its packed task block.
+struct PushOffsets {
+    size_t dcopy = 0, casc = 0, fir = 0, win = 0, ycopy = 0, wfin = 0, refu = 0, ys1 = 0, ys2 = 0, scopy = 0;
+    std::vector<size_t> ups, recon;
+    size_t tfir[kNM] = {0, 0, 0};
+    std::vector<size_t> tmix[kNM];
+};
+
+// The refinement's scratch (window-maxima table, candidate list and counters, FIR partial sums),
+// grown on demand; the units' window-maxima offsets become addresses.  Runs before packing.
+int prepare_refine_scratch(sb_ctx *c, PushPlan &P, cudaStream_t st) {
+    if (P.refu.empty()) return SB_OK;
+    if (!c->ref_cands) {                   // candidate list, counters and running totals
+        CK(cudaMalloc(&c->ref_cands, kRefCandCap * sizeof(RefCand)));
+        CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
+        CK(cudaMalloc(&c->ref_cum, 2 * sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(c->ref_cum, 0, 2 * sizeof(unsigned long long), st));
+    }
+    if (c->ref_wmax_cap < P.ref_wmax_total) {
+        CK(cudaStreamSynchronize(st));
+        if (c->ref_wmax) cudaFree(c->ref_wmax);
+        c->ref_wmax = nullptr;
+        c->ref_wmax_cap = std::max(P.ref_wmax_total, 2 * c->ref_wmax_cap);
+        CK(cudaMalloc(&c->ref_wmax, c->ref_wmax_cap * sizeof(uint32_t)));
+    }
+    if (c->ref_zpart_items < P.ref_max_items) {       // per (candidate, FIR work item) partial sums
+        CK(cudaStreamSynchronize(st));
+        if (c->ref_zpart) cudaFree(c->ref_zpart);
+        c->ref_zpart = nullptr;
+        c->ref_zpart_items = P.ref_max_items;
+        CK(cudaMalloc(&c->ref_zpart, (size_t)kRefSplitCap * P.ref_max_items * 2 * kRefSpan * sizeof(float)));
+    }
+    for (auto &r : P.refu) r.wmax = c->ref_wmax + reinterpret_cast<intptr_t>(r.wmax);   // offset -> address
+    for (auto &w : P.wfin)
+        if (w.wmax) w.wmax = c->ref_wmax + (reinterpret_cast<intptr_t>(w.wmax) - 1);
+    for (int h = 0; h < kNM; ++h)
+        for (auto &m : P.tmix[h][0])
+            if (m.wmax) m.wmax = c->ref_wmax + (reinterpret_cast<intptr_t>(m.wmax) - 1);
+    CK(cudaMemsetAsync(c->ref_wmax, 0, P.ref_wmax_total * sizeof(uint32_t), st));   // before this push's kernels
+    return SB_OK;
+}
+
+PushOffsets pack_tasks(Packer &pk, const PushPlan &P) {
+    PushOffsets o;
+    o.ups.resize(P.kall + 1);
+    o.recon.resize(P.kall + 1);
+    o.dcopy = pk.add(P.dcopy.data(), P.dcopy.size() * sizeof(CopyTask));
+    o.casc = pk.add(P.casc.data(), P.casc.size() * sizeof(CascadeTask));
+    o.fir = pk.add(P.fir.data(), P.fir.size() * sizeof(GemmTask));
+    for (int k = 0; k <= P.kall; ++k) {
+        o.ups[k] = pk.add(P.ups[k].data(), P.ups[k].size() * sizeof(UpTask));
+        o.recon[k] = pk.add(P.recon[k].data(), P.recon[k].size() * sizeof(GemmTask));
+    }
+    o.win = pk.add(P.win.data(), P.win.size() * sizeof(WinTask));
+    for (int h = 0; h < kNM; ++h) {
+        o.tfir[h] = pk.add(P.tfir[h].data(), P.tfir[h].size() * sizeof(TcFirTask));
+        o.tmix[h].resize(P.kall + 1);
+        for (int k = 0; k <= P.kall; ++k)
+            o.tmix[h][k] = pk.add(P.tmix[h][k].data(), P.tmix[h][k].size() * sizeof(TcMixUpTask));
+    }
+    o.ycopy = pk.add(P.ycopy.data(), P.ycopy.size() * sizeof(CopyTask));
+    o.wfin = pk.add(P.wfin.data(), P.wfin.size() * sizeof(WinFinTask));
+    o.refu = pk.add(P.refu.data(), P.refu.size() * sizeof(RefUnit));
+    o.ys1 = pk.add(P.yshift1.data(), P.yshift1.size() * sizeof(CopyTask));
+    o.ys2 = pk.add(P.yshift2.data(), P.yshift2.size() * sizeof(CopyTask));
+    return o;
+}
+
+// Every stage of one push, in order, on the stream (inside the capture in graph mode).
+// derr: the push's device error word; to: its trigger slot.
+int launch_stages(sb_ctx *c, const PushPlan &P, const PushOffsets &o, char *D, int *derr, const TrigOut &to,
+                  int n_units, int64_t B, bool tune_now, cudaStream_t st) {
+    int rc;
+    // 1. history shifts of the decimated strain
+    if ((rc = run_stage(c, SB_STAGE_HISTORY, [&](int *n) {
+             *n = P.dcopy.empty() ? 0 : 1;
+             return launch_copy((CopyTask *)(D + o.dcopy), (int)P.dcopy.size(), 1, P.max_hd, st);
+         })))
+        return rc;
+    // 2. new top-rate strain
+    if ((rc = run_stage(c, SB_STAGE_STRAIN, [&](int *n) {
+             *n = 1;
+             return launch_copy((CopyTask *)(D + o.scopy), n_units, 1, (int)B, st);
+         })))
+        return rc;
+    // 3. a1 decimation cascade of every unit and the 16-bit copies for the tensor-core FIR (one launch)
+    if ((rc = run_stage(c, SB_STAGE_DECIMATE, [&](int *n) {
+             *n = 1;
+             return launch_cascade((CascadeTask *)(D + o.casc), n_units, c->g, st);
+         })))
+        return rc;
+    // 4. a2 basis FIR, all slices of all units at once
+    if (!P.fir.empty() && (rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
+                             *n = 1;
+                             return launch_gemm_fp32((GemmTask *)(D + o.fir), (int)P.fir.size(), P.fir_tiles, st);
+                         })))
+        return rc;
+    for (int h = 0; h < kNM; ++h)
+        if (!P.tfir[h].empty() && (rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
+                                     *n = 1;
+                                     return launch_tc_fir((TcFirTask *)(D + o.tfir[h]), (int)P.tfir[h].size(),
+                                                          P.tfir_tiles[h], P.kpad_max[h], h, derr, st, c->test_wait_ns,
+                                                          c->test_skip_chunk);
+                                 })))
+            return rc;
+    // 5. a4 + a3 from the lowest rate up
+    for (int k = P.kall; k >= 0; --k) {
+        if (!P.ups[k].empty() &&
+            (rc = run_stage(c, SB_STAGE_UPSAMPLE, [&](int *n) {
+                 *n = 1;
+                 return launch_upsample((UpTask *)(D + o.ups[k]), (int)P.ups[k].size(), P.max_rows, (int)(B >> k),
+                                        c->g, st);
+             })))
+            return rc;
+        if (!P.recon[k].empty() &&
+            (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
+                 *n = 1;
+                 return launch_gemm_fp32((GemmTask *)(D + o.recon[k]), (int)P.recon[k].size(), P.recon_tiles[k], st);
+             })))
+            return rc;
+        for (int h = 0; h < kNM; ++h)
+            if (!P.tmix[h][k].empty() &&
+                (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
+                     const int64_t timed0 = c->tuner.timed_launches;
+                     cudaError_t e = launch_tc_mixup((TcMixUpTask *)(D + o.tmix[h][k]), (int)P.tmix[h][k].size(),
+                                                     P.tmix_tiles[h][k], P.tmix_ml[h][k],
+                                                     c->utab, h, derr, c->autotune ? &c->tuner : nullptr, tune_now,
+                                                     st);
+                     *n = (int)std::max<int64_t>(1, c->tuner.timed_launches - timed0);
+                     return e;
+                 })))
+                return rc;
+    }
+    // a6: FP32 refinement of the top level's candidate maxima (16-bit modes)
+    if (!P.refu.empty()) {
+        CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
+        if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
+                 *n = 3;
+                 return launch_refine((RefUnit *)(D + o.refu), (int)P.refu.size(), P.ref_max_windows, c->ref_cands,
+                                      c->ref_counters, c->ref_cum, c->ref_zpart, P.ref_max_items, c->g, st);
+             })))
+            return rc;
+    }
+    // 6. a5 trigger generator
+    if ((rc = run_stage(c, SB_STAGE_TRIGGER, [&](int *n) {
+             *n = (P.win.empty() ? 0 : 1) + (P.wfin.empty() ? 0 : 1);
+             cudaError_t e = launch_window_max((WinTask *)(D + o.win), (int)P.win.size(), P.win_warps, to, st);
+             if (e != cudaSuccess) return e;
+             return launch_win_finalize((WinFinTask *)(D + o.wfin), (int)P.wfin.size(), P.wfin_warps, to, st);
+         })))
+        return rc;
+    // 7. SNR history for the interpolators of the next push
+    if ((rc = run_stage(c, SB_STAGE_SNRHIST, [&](int *n) {
+             *n = (P.ycopy.empty() ? 0 : 1) + (P.yshift1.empty() ? 0 : 1) + (P.yshift2.empty() ? 0 : 1);
+             cudaError_t e = launch_copy((CopyTask *)(D + o.ycopy), (int)P.ycopy.size(), P.max_rows, P.max_hy, st);
+             if (e != cudaSuccess) return e;
+             e = launch_copy16((CopyTask *)(D + o.ys1), (int)P.yshift1.size(), P.max_rows, st);
+             if (e != cudaSuccess) return e;
+             return launch_copy16((CopyTask *)(D + o.ys2), (int)P.yshift2.size(), P.max_rows, st);
+         })))
+        return rc;
+    return SB_OK;
+}
+
+}  // namespace
+
 extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *units, const float *const *strains,
                                  int64_t B, const int64_t *t0, int32_t on_device) {
     if (!c || n_units <= 0 || !units || !strains || !t0) return fail(SB_EINVAL, "null or empty argument");
@@ -1443,409 +2009,37 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     int kall = 0;
     for (int i = 0; i < n_units; ++i) kall = std::max(kall, units[i]->kmax);
 
-    std::vector<CopyTask> dcopy, ycopy;
-    std::vector<CascadeTask> casc(n_units);     // a1 cascade + 16-bit copies, one cluster per unit
-    std::vector<GemmTask> fir;
-    std::vector<std::vector<UpTask>> ups(kall + 1);
-    std::vector<std::vector<GemmTask>> recon(kall + 1);
-    std::vector<WinTask> win;
-    // tensor-core modes, indexed by operand mode (kModeF16, kModeBF16, kModeE4M3)
-    constexpr int NM = 3;
-    std::vector<TcFirTask> tfir[NM];
-    std::vector<std::vector<TcMixUpTask>> tmix[NM] = {std::vector<std::vector<TcMixUpTask>>(kall + 1),
-                                                      std::vector<std::vector<TcMixUpTask>>(kall + 1),
-                                                      std::vector<std::vector<TcMixUpTask>>(kall + 1)};
-    std::vector<WinFinTask> wfin;
-    std::vector<RefUnit> refu;
-    int64_t ref_max_windows = 0, ref_wmax_total = 0;
-    int32_t ref_max_items = 0;                 // largest FIR work-item count of a refined unit
-    std::vector<CopyTask> yshift1, yshift2;
-    int kpad_max[NM] = {0, 0, 0};
-    int max_hd = 0, max_hy = 0, max_rows = 0;
-    int64_t trig_need = 0;
-
+    PushPlan P(n_units, kall);
     for (int i = 0; i < n_units; ++i) {
         sb_unit *u = units[i];
-        const int64_t Tp = u->T;
-        const int M2 = 2 * u->M;
-        max_rows = std::max(max_rows, M2);
-        // refinement: this unit's slice of the window-maxima scratch (offset; addresses set at packing)
-        const int64_t first_n0 = Tp - u->levels[0].lam;
-        const int64_t start0 = std::max<int64_t>(first_n0, 0), end0 = first_n0 + B;
-        const bool refine_here = end0 > start0 && u->refine;
-        const int64_t win0 = refine_here ? start0 / u->win_len : 0;
-        const int32_t n_wslot = refine_here ? (int32_t)((end0 - 1) / u->win_len - win0 + 1) : 0;
-        const int64_t wmax_off = ref_wmax_total;
-        if (refine_here) ref_wmax_total += (int64_t)u->M * n_wslot;
-        for (int k = 0; k <= u->kmax; ++k) {
-            LevelDev &L = u->levels[k];
-            const int nb = 1 - L.dcur;
-            CopyTask ct{};
-            ct.cur = L.dbuf[L.dcur];
-            ct.dst = L.dbuf[nb];
-            ct.rows = 1;
-            ct.n = (int32_t)L.Hd;
-            ct.off = (int32_t)L.last_Bk;
-            dcopy.push_back(ct);
-            max_hd = std::max<int>(max_hd, (int)L.Hd);
-            const int64_t Bk = B >> k;
-            if (k < u->kmax) {
-                LevelDev &N = u->levels[k + 1];
-                DecimTask dt{};
-                dt.in = L.dbuf[nb];
-                dt.out = N.dbuf[1 - N.dcur] + N.Hd;
-                dt.in_base = L.Hd + L.e - 2 * N.e;
-                dt.first_m = (Tp >> (k + 1)) - N.e;
-                dt.n_out = (int32_t)(B >> (k + 1));
-                casc[i].lev[k] = dt;
-                casc[i].n_lev = k + 1;
-            }
-            if (u->tc) {
-                const int h = u->mode;
-                float *am = L.amax ? L.amax + u->amax_cur : nullptr;
-                float *am_next = L.amax ? L.amax + (1 - u->amax_cur) : nullptr;
-                void *x_lo = mode_terms(u->mode) == 2 ? static_cast<uint8_t *>(L.x16) + L.x16_len : nullptr;
-                casc[i].conv[k] = HalfConvTask{L.dbuf[nb], L.x16, L.Hd + Bk, am, am_next, x_lo};
-                casc[i].n_conv = k + 1;
-                casc[i].mode = h;
-                for (int s : L.slices) {
-                    const SliceDev &sd = u->slices[s];
-                    TcFirTask f{};
-                    f.mapW = sd.mapW;
-                    f.x = L.x16;
-                    f.X0 = sd.X0;
-                    f.O = L.O16;
-                    f.ldo = L.Lk_pad;
-                    f.o_col = sd.o_col16;
-                    f.Kpad = sd.Kpad;
-                    f.Bk = (int32_t)Bk;
-                    const int64_t ph = mode_phases(u->mode);       // samples per Hankel block
-                    f.tiles_n = (int32_t)(((Bk + ph - 1) / ph + kTcN - 1) / kTcN);
-                    f.tiles_m = sd.L16 / (kTcM / mode_phases(u->mode));
-                    f.xamax = am;
-                    f.colscale = L.colscale;
-                    f.x_lo = x_lo;
-                    tfir[h].push_back(f);
-                    kpad_max[h] = std::max(kpad_max[h], sd.Kpad);
-                }
-                {
-                    TcMixUpTask mt{};
-                    mt.mapM = L.mapM;
-                    mt.mapO = L.mapO;
-                    if (k < u->kmax) mt.mapY = u->levels[k + 1].mapY;
-                    mt.Y = k == 0 ? L.ynew : nullptr;             // SB_FLAG_KEEP_SNR
-                    mt.ldy = L.ldy;
-                    mt.Yh = k >= 1 ? reinterpret_cast<uint16_t *>(L.yuni) : nullptr;
-                    mt.ldu = L.ldu;
-                    mt.yst_col0 = L.Hy;
-                    mt.kbytes = mix_kbytes(L.Lk_pad, u->mmode);
-                    mt.part = k == 0 ? u->part : nullptr;
-                    if (k == 0 && refine_here) {
-                        mt.wmax = reinterpret_cast<uint32_t *>(wmax_off + 1);   // offset + 1; address at packing
-                        mt.win0 = win0;
-                        mt.n_wslot = n_wslot;
-                        mt.thr2 = u->refine_thr * u->refine_thr;
-                    }
-                    mt.first_n = (Tp >> k) - L.lam;
-                    mt.win_len = u->win_len;
-                    mt.Lk_pad = L.Lk_pad;
-                    mt.M2 = M2;
-                    mt.M = u->M;
-                    mt.Bk = (int32_t)Bk;
-                    mt.lam = (int32_t)L.lam;
-                    mt.in_off = k < u->kmax ? (int32_t)(u->levels[k + 1].lam + u->levels[k + 1].Hy) : 0;
-                    mt.tiles_t = (int32_t)((Bk + 255) / 256);
-                    mt.tiles_a = (M2 + 127) / 128;
-                    mt.n_rec = mt.tiles_t * 4;
-                    tmix[u->mmode][k].push_back(mt);
-                }
-                if (k >= 1) {           // next push's interpolation history: columns [Bk, Bk + Hy) -> [0, Hy)
-                    // (in place when the two ranges are disjoint, else through the staging buffer)
-                    const bool direct = Bk >= L.Hy;
-                    CopyTask a{};
-                    a.cur = L.yuni;
-                    a.ld_cur = L.ldu;
-                    a.dst = direct ? L.yuni : L.ytmp;
-                    a.ld_dst = direct ? L.ldu : L.Hy;
-                    a.rows = M2;
-                    a.n = (int32_t)L.Hy;
-                    a.off = (int32_t)Bk;
-                    a.elem16 = y_planes(u->mmode);
-                    yshift1.push_back(a);
-                    max_hy = std::max<int>(max_hy, (int)L.Hy);
-                    if (!direct) {
-                        CopyTask bt{};
-                        bt.cur = L.ytmp;
-                        bt.ld_cur = L.Hy;
-                        bt.dst = L.yuni;
-                        bt.ld_dst = L.ldu;
-                        bt.rows = M2;
-                        bt.n = (int32_t)L.Hy;
-                        bt.off = 0;
-                        bt.elem16 = y_planes(u->mmode);
-                        yshift2.push_back(bt);
-                    }
-                }
-            }
-            for (int s : L.slices) {
-                if (u->tc) break;
-                const SliceDev &sd = u->slices[s];
-                GemmTask g{};
-                g.A = sd.V;
-                g.lda = sd.Q;
-                g.B = L.dbuf[nb];
-                g.ldb = L.Hd + L.e - L.lam - sd.D;
-                g.C = L.obuf + (int64_t)sd.o_row * L.Bk_max;
-                g.ldc = L.Bk_max;
-                g.M = sd.L;
-                g.N = (int32_t)Bk;
-                g.K = sd.Q;
-                g.beta = 0;
-                g.toeplitz = 1;
-                fir.push_back(g);
-            }
-            if (k < u->kmax && !u->tc) {
-                LevelDev &N = u->levels[k + 1];
-                UpTask ut{};
-                ut.hist = N.yhist[N.ycur];
-                ut.cur = N.ynew;
-                ut.out = L.ynew;
-                ut.ld_hist = N.Hy;
-                ut.ld_cur = N.ldy;
-                ut.ld_out = L.ldy;
-                ut.n_hist = (int32_t)N.Hy;
-                ut.rows = M2;
-                ut.n_out = (int32_t)Bk;
-                ut.lam_out = (int32_t)L.lam;
-                ut.in_off = (int32_t)(N.lam + N.Hy);
-                ut.n_cur = (int32_t)(B >> (k + 1));
-                ut.first_n = (Tp >> k) - L.lam;
-                ups[k].push_back(ut);
-            }
-            if (L.Lk > 0 && !u->tc) {
-                GemmTask g{};
-                g.A = L.Mcat;
-                g.lda = L.Lk;
-                g.B = L.obuf;
-                g.ldb = L.Bk_max;
-                g.C = L.ynew;
-                g.ldc = L.ldy;
-                g.M = M2;
-                g.N = (int32_t)Bk;
-                g.K = L.Lk;
-                g.beta = k < u->kmax ? 1 : 0;
-                g.toeplitz = 0;
-                recon[k].push_back(g);
-            }
-            if (k >= 1 && L.Hy > 0 && !u->tc) {
-                CopyTask yt{};
-                yt.hist = L.yhist[L.ycur];
-                yt.cur = L.ynew;
-                yt.dst = L.yhist[1 - L.ycur];
-                yt.ld_hist = L.Hy;
-                yt.ld_cur = L.ldy;
-                yt.ld_dst = L.Hy;
-                yt.n_hist = (int32_t)L.Hy;
-                yt.rows = M2;
-                yt.n = (int32_t)L.Hy;
-                yt.off = (int32_t)Bk;
-                ycopy.push_back(yt);
-                max_hy = std::max<int>(max_hy, (int)L.Hy);
-            }
-        }
-        // trigger generator on the top level
-        LevelDev &L0 = u->levels[0];
-        const int64_t first_n = Tp - L0.lam;
-        const int64_t start = std::max<int64_t>(first_n, 0), end = first_n + B;
-        if (end > start && u->refine) {
-            RefUnit r{};
-            r.part = u->part;
-            r.first_n = first_n;
-            r.win_len = u->win_len;
-            r.thr2 = u->refine_thr * u->refine_thr;
-            r.keep2 = u->mode == kModeE4M3 ? kRefKeep8 : kRefKeep16;
-            r.win0 = win0;
-            r.n_wslot = n_wslot;
-            r.wmax = reinterpret_cast<uint32_t *>(wmax_off);         // offset; the base is added before packing
-            r.kmax = u->kmax;
-            r.M = u->M;
-            r.n_rec = (int32_t)((B + kRefTile - 1) / kRefTile) * 4;
-            r.B = (int32_t)B;
-            r.n_slices = (int32_t)u->slices.size();
-            r.acorr = u->acorr;
-            for (int k = 0; k <= u->kmax; ++k) {
-                LevelDev &L = u->levels[k];
-                r.lv_d[k] = L.dbuf[1 - L.dcur];
-                r.lv_origin[k] = (Tp >> k) - L.e - L.Hd;
-                r.lv_len[k] = L.Hd + (B >> k);
-            }
-            for (size_t si = 0; si < u->slices.size(); ++si) {
-                const SliceDev &sd = u->slices[si];
-                r.sl_H[si] = sd.H;
-                r.sl_ldh[si] = sd.ldh;
-                r.sl_D[si] = sd.D;
-                r.sl_Q[si] = sd.Q;
-                r.sl_level[si] = sd.level;
-                r.sl_item0[si + 1] = r.sl_item0[si] + (sd.Q + kRefQC - 1) / kRefQC;
-            }
-            ref_max_items = std::max(ref_max_items, r.sl_item0[u->slices.size()]);
-            ref_max_windows = std::max<int64_t>(ref_max_windows, (int64_t)r.M * r.n_wslot);
-            refu.push_back(r);
-        }
-        if (end > start && u->tc) {
-            WinFinTask w{};
-            w.part = u->part;
-            w.state_in = u->wstate[u->wcur];
-            w.state_out = u->wstate[1 - u->wcur];
-            w.template_ids = u->tids;
-            w.unit_id = u->id;
-            w.win_len = u->win_len;
-            w.first_n = first_n;
-            w.start_abs = start;
-            w.end_abs = end;
-            w.n_rec = (int32_t)(((B + 255) / 256) * 4);
-            w.M = u->M;
-            w.n_win = (int32_t)((end - 1) / u->win_len - start / u->win_len + 1);
-            w.threshold = u->thr;
-            // the refinement's window maxima cover every possible trigger when its threshold is lower
-            if (refine_here && u->refine_thr < u->thr * (1.0f - 1e-6f)) {
-                w.n_wslot = n_wslot;
-                w.wmax = reinterpret_cast<const uint32_t *>(wmax_off + 1);   // offset + 1; the base is added at packing
-            }
-            wfin.push_back(w);
-            trig_need += (int64_t)u->M * w.n_win;
-        } else if (end > start) {
-            WinTask w{};
-            w.x = L0.ynew;
-            w.ldx = L0.ldy;
-            w.state_in = u->wstate[u->wcur];
-            w.state_out = u->wstate[1 - u->wcur];
-            w.template_ids = u->tids;
-            w.first_n = first_n;
-            w.unit_id = u->id;
-            w.win_len = u->win_len;
-            w.n = (int32_t)B;
-            w.M = u->M;
-            w.n_seg = (int32_t)((end - 1) / u->win_len - start / u->win_len + 1);
-            w.threshold = u->thr;
-            w.acorr = u->acorr;
-            win.push_back(w);
-            trig_need += (int64_t)u->M * w.n_seg;
-        }
+        P.max_rows = std::max(P.max_rows, 2 * u->M);
+        const RefineWindows rw = refine_windows(P, u, B);
+        plan_streams(P, i, u, B);
+        if (u->tc) plan_tc(P, u, B, rw);
+        else plan_fp32(P, u, B);
+        plan_triggers(P, u, B, rw);
     }
-
-    // tile / warp offsets
-    auto assign_tiles = [](std::vector<GemmTask> &v) {
-        int tot = 0;
-        for (auto &g : v) {
-            g.tiles_n = (g.N + kGemmTN - 1) / kGemmTN;
-            const int tiles_m = (g.M + kGemmTM - 1) / kGemmTM;
-            g.tile_begin = tot;
-            tot += tiles_m * g.tiles_n;
-        }
-        return tot;
-    };
-    const int fir_tiles = assign_tiles(fir);
-    std::vector<int> recon_tiles(kall + 1);
-    for (int k = 0; k <= kall; ++k) recon_tiles[k] = assign_tiles(recon[k]);
-    int tfir_tiles[NM] = {0, 0, 0};
-    std::vector<int> tmix_tiles[NM] = {std::vector<int>(kall + 1, 0), std::vector<int>(kall + 1, 0),
-                                       std::vector<int>(kall + 1, 0)};
-    std::vector<MixLaunch> tmix_ml[NM] = {std::vector<MixLaunch>(kall + 1), std::vector<MixLaunch>(kall + 1),
-                                          std::vector<MixLaunch>(kall + 1)};
-    for (int h = 0; h < NM; ++h) {
-        for (auto &f : tfir[h]) {
-            f.tile_begin = tfir_tiles[h];
-            tfir_tiles[h] += f.tiles_m * f.tiles_n;
-        }
-        for (int k = 0; k <= kall; ++k)
-            for (auto &m : tmix[h][k]) {
-                m.tile_begin = tmix_tiles[h][k];
-                tmix_tiles[h][k] += m.tiles_t * m.tiles_a;
-                MixLaunch &ml = tmix_ml[h][k];
-                if (m.Yh) ml.store_y = true;
-                if (m.mapY) ml.interp = true;
-                ml.kbytes = std::max(ml.kbytes, (int)m.kbytes);
-                const int kc = 128 / mode_bytes(h);                  // K elements per 128-byte chunk
-                ml.max_nk = std::max(ml.max_nk, (m.Lk_pad + kc - 1) / kc);
-            }
-    }
-    int wfin_warps = 0;
-    for (auto &w : wfin) {
-        w.warp_begin = wfin_warps;
-        wfin_warps += w.M * w.n_win;
-    }
-    int win_warps = 0;
-    for (auto &w : win) {
-        w.warp_begin = win_warps;
-        win_warps += w.M * w.n_seg;
-    }
+    assign_tiles(P);
+    int rc = prepare_refine_scratch(c, P, st);
+    if (rc) return rc;
 
     // pack task lists (and host strain) into one pinned block
     Packer pk;
-    const size_t o_dcopy = pk.add(dcopy.data(), dcopy.size() * sizeof(CopyTask));
-    std::vector<size_t> o_ups(kall + 1), o_recon(kall + 1);
-    const size_t o_casc = pk.add(casc.data(), casc.size() * sizeof(CascadeTask));
-    const size_t o_fir = pk.add(fir.data(), fir.size() * sizeof(GemmTask));
-    for (int k = 0; k <= kall; ++k) {
-        o_ups[k] = pk.add(ups[k].data(), ups[k].size() * sizeof(UpTask));
-        o_recon[k] = pk.add(recon[k].data(), recon[k].size() * sizeof(GemmTask));
-    }
-    const size_t o_win = pk.add(win.data(), win.size() * sizeof(WinTask));
-    if (!refu.empty()) {                       // window-maxima scratch of the refinement (grown on demand)
-        if (!c->ref_cands) {                   // candidate list, counters and running totals
-            CK(cudaMalloc(&c->ref_cands, kRefCandCap * sizeof(RefCand)));
-            CK(cudaMalloc(&c->ref_counters, 4 * sizeof(int)));
-            CK(cudaMalloc(&c->ref_cum, 2 * sizeof(unsigned long long)));
-            CK(cudaMemsetAsync(c->ref_cum, 0, 2 * sizeof(unsigned long long), st));
-        }
-        if (c->ref_wmax_cap < ref_wmax_total) {
-            CK(cudaStreamSynchronize(st));
-            if (c->ref_wmax) cudaFree(c->ref_wmax);
-            c->ref_wmax = nullptr;
-            c->ref_wmax_cap = std::max(ref_wmax_total, 2 * c->ref_wmax_cap);
-            CK(cudaMalloc(&c->ref_wmax, c->ref_wmax_cap * sizeof(uint32_t)));
-        }
-        if (c->ref_zpart_items < ref_max_items) {       // per (candidate, FIR work item) partial sums
-            CK(cudaStreamSynchronize(st));
-            if (c->ref_zpart) cudaFree(c->ref_zpart);
-            c->ref_zpart = nullptr;
-            c->ref_zpart_items = ref_max_items;
-            CK(cudaMalloc(&c->ref_zpart, (size_t)kRefSplitCap * ref_max_items * 2 * kRefSpan * sizeof(float)));
-        }
-        for (auto &r : refu) r.wmax = c->ref_wmax + reinterpret_cast<intptr_t>(r.wmax);   // offset -> address
-        for (auto &w : wfin)
-            if (w.wmax) w.wmax = c->ref_wmax + (reinterpret_cast<intptr_t>(w.wmax) - 1);
-        for (int h = 0; h < NM; ++h)
-            for (auto &m : tmix[h][0])
-                if (m.wmax) m.wmax = c->ref_wmax + (reinterpret_cast<intptr_t>(m.wmax) - 1);
-        CK(cudaMemsetAsync(c->ref_wmax, 0, ref_wmax_total * sizeof(uint32_t), st));   // before this push's kernels
-    }
-    size_t o_tfir[NM];
-    std::vector<size_t> o_tmix[NM] = {std::vector<size_t>(kall + 1), std::vector<size_t>(kall + 1),
-                                      std::vector<size_t>(kall + 1)};
-    for (int h = 0; h < NM; ++h) {
-        o_tfir[h] = pk.add(tfir[h].data(), tfir[h].size() * sizeof(TcFirTask));
-        for (int k = 0; k <= kall; ++k) o_tmix[h][k] = pk.add(tmix[h][k].data(), tmix[h][k].size() * sizeof(TcMixUpTask));
-    }
-    const size_t o_ycopy = pk.add(ycopy.data(), ycopy.size() * sizeof(CopyTask));
-    const size_t o_wfin = pk.add(wfin.data(), wfin.size() * sizeof(WinFinTask));
-    const size_t o_refu = pk.add(refu.data(), refu.size() * sizeof(RefUnit));
-    const size_t o_ys1 = pk.add(yshift1.data(), yshift1.size() * sizeof(CopyTask));
-    const size_t o_ys2 = pk.add(yshift2.data(), yshift2.size() * sizeof(CopyTask));
+    PushOffsets o = pack_tasks(pk, P);
     std::vector<size_t> o_strain(n_units, 0);
     if (!on_device)
         for (int i = 0; i < n_units; ++i) o_strain[i] = pk.add(strains[i], B * sizeof(float));
     // the new top-rate strain of every unit is copied by one task-driven kernel (its source
     // pointers are data in the task block, not launch arguments)
-    const size_t o_scopy = pk.reserve(n_units * sizeof(CopyTask));
+    o.scopy = pk.reserve(n_units * sizeof(CopyTask));
+
 
     TaskArena *ar = nullptr;
-    int rc = arena_acquire(c, pk.buf.size(), ar);
+    rc = arena_acquire(c, pk.buf.size(), ar);
     if (rc) return rc;
     char *D = ar->d;
     {
-        CopyTask *sc = reinterpret_cast<CopyTask *>(pk.buf.data() + o_scopy);
+        CopyTask *sc = reinterpret_cast<CopyTask *>(pk.buf.data() + o.scopy);
         for (int i = 0; i < n_units; ++i) {
             LevelDev &L0 = units[i]->levels[0];
             CopyTask t{};
@@ -1858,17 +2052,17 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     }
     TriggerSlot *slot = nullptr;
     int slot_idx = 0;
-    if ((rc = slot_acquire(c, trig_need, slot, slot_idx))) return rc;
+    if ((rc = slot_acquire(c, P.trig_need, slot, slot_idx))) return rc;
     std::memcpy(ar->h, pk.buf.data(), pk.buf.size());
 
     // graph mode: everything from the task upload to the trigger read-back is one captured graph
     // a push that times a new mixing launch shape runs uncaptured (the tuner synchronises)
     bool tune_now = false;
     if (c->autotune)
-        for (int h = 0; h < NM; ++h)
-            for (int k = 0; k <= kall; ++k)
-                if (!tmix[h][k].empty() &&
-                    !c->tuner.find(tc_mixup_shape_key(h, tmix_ml[h][k], tmix_tiles[h][k])))
+        for (int h = 0; h < kNM; ++h)
+            for (int k = 0; k <= P.kall; ++k)
+                if (!P.tmix[h][k].empty() &&
+                    !c->tuner.find(tc_mixup_shape_key(h, P.tmix_ml[h][k], P.tmix_tiles[h][k])))
                     tune_now = true;
     const bool capture = c->graphs && !c->prof && !tune_now;
     std::string gkey;
@@ -1884,95 +2078,8 @@ extern "C" int filter_push_group(sb_ctx *c, int32_t n_units, sb_unit *const *uni
     CK(cudaMemcpyAsync(ar->d, ar->h, pk.buf.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(slot->dcount, 0, 3 * sizeof(int32_t), st));
     int *derr = slot->dcount + 2;
-    // 1. history shifts of the decimated strain
-    if ((rc = run_stage(c, SB_STAGE_HISTORY, [&](int *n) {
-             *n = dcopy.empty() ? 0 : 1;
-             return launch_copy((CopyTask *)(D + o_dcopy), (int)dcopy.size(), 1, max_hd, st);
-         })))
-        return rc;
-    // 2. new top-rate strain
-    if ((rc = run_stage(c, SB_STAGE_STRAIN, [&](int *n) {
-             *n = 1;
-             return launch_copy((CopyTask *)(D + o_scopy), n_units, 1, (int)B, st);
-         })))
-        return rc;
-    // 3. a1 decimation cascade of every unit and the 16-bit copies for the tensor-core FIR (one launch)
-    if ((rc = run_stage(c, SB_STAGE_DECIMATE, [&](int *n) {
-             *n = 1;
-             return launch_cascade((CascadeTask *)(D + o_casc), n_units, c->g, st);
-         })))
-        return rc;
-    // 4. a2 basis FIR, all slices of all units at once
-    if (!fir.empty() && (rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
-                             *n = 1;
-                             return launch_gemm_fp32((GemmTask *)(D + o_fir), (int)fir.size(), fir_tiles, st);
-                         })))
-        return rc;
-    for (int h = 0; h < NM; ++h)
-        if (!tfir[h].empty() && (rc = run_stage(c, SB_STAGE_FIR, [&](int *n) {
-                                     *n = 1;
-                                     return launch_tc_fir((TcFirTask *)(D + o_tfir[h]), (int)tfir[h].size(),
-                                                          tfir_tiles[h], kpad_max[h], h, derr, st, c->test_wait_ns,
-                                                          c->test_skip_chunk);
-                                 })))
-            return rc;
-    // 5. a4 + a3 from the lowest rate up
-    for (int k = kall; k >= 0; --k) {
-        if (!ups[k].empty() &&
-            (rc = run_stage(c, SB_STAGE_UPSAMPLE, [&](int *n) {
-                 *n = 1;
-                 return launch_upsample((UpTask *)(D + o_ups[k]), (int)ups[k].size(), max_rows, (int)(B >> k),
-                                        c->g, st);
-             })))
-            return rc;
-        if (!recon[k].empty() &&
-            (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
-                 *n = 1;
-                 return launch_gemm_fp32((GemmTask *)(D + o_recon[k]), (int)recon[k].size(), recon_tiles[k], st);
-             })))
-            return rc;
-        for (int h = 0; h < NM; ++h)
-            if (!tmix[h][k].empty() &&
-                (rc = run_stage(c, SB_STAGE_MIX, [&](int *n) {
-                     const int64_t timed0 = c->tuner.timed_launches;
-                     cudaError_t e = launch_tc_mixup((TcMixUpTask *)(D + o_tmix[h][k]), (int)tmix[h][k].size(),
-                                                     tmix_tiles[h][k], tmix_ml[h][k],
-                                                     c->utab, h, derr, c->autotune ? &c->tuner : nullptr, tune_now,
-                                                     st);
-                     *n = (int)std::max<int64_t>(1, c->tuner.timed_launches - timed0);
-                     return e;
-                 })))
-                return rc;
-    }
-    // a6: FP32 refinement of the top level's candidate maxima (16-bit modes)
-    if (!refu.empty()) {
-        CK(cudaMemsetAsync(c->ref_counters, 0, 4 * sizeof(int), st));
-        if ((rc = run_stage(c, SB_STAGE_REFINE, [&](int *n) {
-                 *n = 3;
-                 return launch_refine((RefUnit *)(D + o_refu), (int)refu.size(), ref_max_windows, c->ref_cands,
-                                      c->ref_counters, c->ref_cum, c->ref_zpart, ref_max_items, c->g, st);
-             })))
-            return rc;
-    }
-    // 6. a5 trigger generator
-    TrigOut to{slot->dbuf, slot->dcount, (int32_t)slot->cap};
-    if ((rc = run_stage(c, SB_STAGE_TRIGGER, [&](int *n) {
-             *n = (win.empty() ? 0 : 1) + (wfin.empty() ? 0 : 1);
-             cudaError_t e = launch_window_max((WinTask *)(D + o_win), (int)win.size(), win_warps, to, st);
-             if (e != cudaSuccess) return e;
-             return launch_win_finalize((WinFinTask *)(D + o_wfin), (int)wfin.size(), wfin_warps, to, st);
-         })))
-        return rc;
-    // 7. SNR history for the interpolators of the next push
-    if ((rc = run_stage(c, SB_STAGE_SNRHIST, [&](int *n) {
-             *n = (ycopy.empty() ? 0 : 1) + (yshift1.empty() ? 0 : 1) + (yshift2.empty() ? 0 : 1);
-             cudaError_t e = launch_copy((CopyTask *)(D + o_ycopy), (int)ycopy.size(), max_rows, max_hy, st);
-             if (e != cudaSuccess) return e;
-             e = launch_copy16((CopyTask *)(D + o_ys1), (int)yshift1.size(), max_rows, st);
-             if (e != cudaSuccess) return e;
-             return launch_copy16((CopyTask *)(D + o_ys2), (int)yshift2.size(), max_rows, st);
-         })))
-        return rc;
+    const TrigOut to{slot->dbuf, slot->dcount, (int32_t)slot->cap};
+    if ((rc = launch_stages(c, P, o, D, derr, to, n_units, B, tune_now, st))) return rc;
     // 8. triggers to the host (count plus an eager prefix; the rest on demand)
     CK(cudaMemcpyAsync(slot->hcount, slot->dcount, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(slot->hbuf, slot->dbuf, slot->eager * sizeof(DevTrigger), cudaMemcpyDeviceToHost, st));
