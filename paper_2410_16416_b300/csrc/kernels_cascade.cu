@@ -29,6 +29,10 @@ __device__ __forceinline__ int cluster_rank() {
     return (int)r;
 }
 
+// 1024 threads a CTA: the cascade runs on one cluster per unit, so each CTA keeps as many loads in
+// flight as it can.
+constexpr int kCascThreads = 1024;
+
 // This CTA's share [lo, hi) of n items (contiguous, rounded to 32).
 __device__ __forceinline__ void cta_share(int64_t n, int r, int64_t &lo, int64_t &hi) {
     const int64_t per = ((n + kCascadeCtas - 1) / kCascadeCtas + 31) / 32 * 32;
@@ -36,7 +40,7 @@ __device__ __forceinline__ void cta_share(int64_t n, int r, int64_t &lo, int64_t
     hi = min(n, lo + per);
 }
 
-constexpr int kCascChunk = 2048;                  // outputs per shared-memory pass
+constexpr int kCascChunk = 4096;                  // outputs per shared-memory pass
 constexpr int kCascSeg = 2 * kCascChunk + 4 * kOddTaps;   // their input span (2 n + 61 samples)
 
 // Decimation of this CTA's share, kCascChunk outputs at a time: the input span of the chunk is
@@ -98,7 +102,7 @@ __device__ void convert_share(const HalfConvTask &t, int mode, int r) {
     }
 }
 
-__global__ void __launch_bounds__(256) cascade_kernel(const CascadeTask *__restrict__ tasks, Halfband g) {
+__global__ void __launch_bounds__(kCascThreads) cascade_kernel(const CascadeTask *__restrict__ tasks, Halfband g) {
     griddep_wait();
     const CascadeTask &t = tasks[blockIdx.x / kCascadeCtas];
     const int r = cluster_rank();
@@ -118,7 +122,7 @@ cudaError_t launch_cascade(const CascadeTask *d_tasks, int n_tasks, const Halfba
     if (n_tasks == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_tasks * kCascadeCtas);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(kCascThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
