@@ -54,7 +54,13 @@ extern "C" {
 #define SB_FLAG_KEEP_SNR 1  /* keep the last push's top-rate SNR readable (sb_unit_snr) */
 
 /* ---- trigger flags --------------------------------------------------- */
-#define SB_TRIG_REFINED 1   /* SNR recomputed in FP32 around the peak           */
+#define SB_TRIG_REFINED 1   /* SNR recomputed in FP32 around the peak.  With
+                             * refinement on (16/8-bit units, refine_threshold
+                             * below threshold) every trigger carries it, except
+                             * in a push whose candidates overflowed the 65,536
+                             * list: its remaining triggers keep their 16-bit
+                             * value and phase (sb_ctx_stats.refine_dropped
+                             * counts such pushes).                              */
 #define SB_TRIG_SUBSAMPLE 2 /* snr_peak / dt_peak hold the sub-sample peak       */
 #define SB_TRIG_XI2 4       /* xi2 holds the signal-consistency value           */
 #define SB_XI2_HALF 16      /* xi^2 lags j = -16 .. 16 top-rate samples         */
