@@ -537,7 +537,8 @@ def device_arm(lloid, torch, stream, local, banks, precision, B, steps, warmup, 
         # a short spin on the device ahead of the step's start event: the host enqueues the push
         # (its graph update and launch) while the GPU spins, so a slow host call lands outside the
         # events (host time is part of e2e, not of the device-timed step)
-        torch.cuda._sleep(HOST_AHEAD_CYCLES)
+        if hasattr(torch.cuda, "_sleep"):
+            torch.cuda._sleep(HOST_AHEAD_CYCLES)
         flush.zero_()
         ev[i][0].record(stream)
         ctx.push_group(units, [dev[det][t:t + B] for det in dets], [t] * n_units, True)
