@@ -11,55 +11,92 @@ namespace lloid {
 // ---------------------------------------------------------------------------
 // a4 (up-sampling half): y'[n] = sum_m 2 g[n - 2m] y[m]; even n copy y[n/2].
 // ---------------------------------------------------------------------------
-// One CTA per (task, row, chunk of kUpChunk outputs): the input segment (half
-// the chunk plus the 2K-1 tap halo on each side) is staged in shared memory with
-// coalesced loads.  Each thread then forms whole output pairs (the even output
-// of coarser sample a and the odd one after it), so no lane idles while its
-// neighbour filters, consecutive lanes read consecutive shared-memory words, and
-// the 2K-tap sum runs in four independent partial sums.
-__global__ void __launch_bounds__(256) upsample_kernel(const UpTask *__restrict__ tasks, Halfband g) {
+// One CTA per (task, row, group of kUpGroup chunks of kUpChunk outputs).  Each
+// chunk's input segment (half the chunk plus the 2K-1 tap halo on each side) is
+// staged in shared memory with coalesced loads; the next chunk's segment is
+// fetched into registers while the current one is filtered (two shared-memory
+// buffers), so the loads' latency hides behind the arithmetic.  Each thread
+// forms whole output pairs (the even output of coarser sample a and the odd one
+// after it), so no lane idles while its neighbour filters, consecutive lanes
+// read consecutive shared-memory words, and the 2K-tap sum runs in four
+// independent partial sums.
+constexpr int kUpSeg = kUpChunk / 2 + 2 * kHalfK + 2;
+constexpr int kUpThreads = 256;
+constexpr int kUpLoads = (kUpSeg + kUpThreads - 1) / kUpThreads;   // segment samples per thread
+
+__global__ void __launch_bounds__(kUpThreads) upsample_kernel(const UpTask *__restrict__ tasks, Halfband g) {
     griddep_wait();
-    constexpr int kSeg = kUpChunk / 2 + 2 * kHalfK + 2;
-    __shared__ float seg[kSeg];
+    __shared__ float seg[2][kUpSeg];
     const UpTask &t = tasks[blockIdx.z];
     const int row = blockIdx.y;
-    const int p0 = blockIdx.x * kUpChunk;
-    if (row >= t.rows || p0 >= t.n_out) return;
-    // first input position touched by this chunk: output nrel = p0 - lam_out, tap j = 2K - 1
-    const int64_t nrel0 = (int64_t)p0 - t.lam_out;
-    const int64_t pos_lo = ((nrel0 - (2 * kHalfK - 1)) >> 1) + t.in_off;      // floor division
+    if (row >= t.rows) return;
     const int64_t n_valid = (int64_t)t.n_hist + t.n_cur;
     const float *hist = t.hist + row * t.ld_hist;
     const float *cur = t.cur + row * t.ld_cur;
-    for (int i = threadIdx.x; i < kSeg; i += blockDim.x) {
-        const int64_t pos = pos_lo + i;
-        float v = 0.0f;
-        if (pos >= 0 && pos < n_valid) v = pos < t.n_hist ? hist[pos] : cur[pos - t.n_hist];
-        seg[i] = v;
-    }
-    __syncthreads();
+    float *out = t.out + row * t.ld_out;
     float c[kOddTaps];
 #pragma unroll
     for (int k = 0; k < kOddTaps; ++k) c[k] = 2.0f * g.odd[k];
-    float *out = t.out + row * t.ld_out;
-    const int p_end = min(t.n_out, p0 + kUpChunk);
-    // coarser samples a whose outputs 2a, 2a + 1 (relative to lam_out) fall in [p0, p_end)
-    const int64_t a_first = nrel0 >> 1;
-    const int64_t a_last = ((int64_t)p_end - 1 - t.lam_out) >> 1;
-    const int64_t off = t.in_off - pos_lo;                  // seg index of coarser sample a: a + off
-    for (int64_t a = a_first + threadIdx.x; a <= a_last; a += blockDim.x) {
-        const int lo = (int)(a + off);
-        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    // first input position touched by the chunk at p0: output nrel = p0 - lam_out, tap j = 2K - 1
+    auto pos_lo_of = [&](int64_t p0) { return (((p0 - t.lam_out) - (2 * kHalfK - 1)) >> 1) + t.in_off; };
+    float rv[kUpLoads];
+    auto fetch = [&](int64_t p0) {
+        const int64_t pos_lo = pos_lo_of(p0);
 #pragma unroll
-        for (int k = 0; k < kOddTaps; k += 4) {
-            s0 = fmaf(c[k], seg[lo - k] + seg[lo + 1 + k], s0);
-            s1 = fmaf(c[k + 1], seg[lo - k - 1] + seg[lo + 2 + k], s1);
-            s2 = fmaf(c[k + 2], seg[lo - k - 2] + seg[lo + 3 + k], s2);
-            s3 = fmaf(c[k + 3], seg[lo - k - 3] + seg[lo + 4 + k], s3);
+        for (int r = 0; r < kUpLoads; ++r) {
+            const int i = threadIdx.x + kUpThreads * r;
+            const int64_t pos = pos_lo + i;
+            float v = 0.0f;
+            if (i < kUpSeg && pos >= 0 && pos < n_valid) v = pos < t.n_hist ? hist[pos] : cur[pos - t.n_hist];
+            rv[r] = v;
         }
-        const int64_t pe = 2 * a + t.lam_out;               // output index of the even sample
-        if (pe >= p0 && pe < p_end) out[pe] = t.first_n + pe >= 0 ? seg[lo] : 0.0f;
-        if (pe + 1 >= p0 && pe + 1 < p_end) out[pe + 1] = t.first_n + pe + 1 >= 0 ? (s0 + s1) + (s2 + s3) : 0.0f;
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < kUpLoads; ++r) {
+            const int i = threadIdx.x + kUpThreads * r;
+            if (i < kUpSeg) seg[buf][i] = rv[r];
+        }
+    };
+    const int64_t g0 = (int64_t)blockIdx.x * kUpGroup * kUpChunk;
+    if (g0 >= t.n_out) return;                               // block-uniform
+    fetch(g0);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (int ch = 0; ch < kUpGroup; ++ch) {
+        const int64_t p0 = g0 + (int64_t)ch * kUpChunk;
+        if (p0 >= t.n_out) break;                            // block-uniform
+        const bool more = ch + 1 < kUpGroup && p0 + kUpChunk < t.n_out;
+        if (more) fetch(p0 + kUpChunk);                      // in flight while this chunk is filtered
+        const float *sg = seg[buf];
+        const int64_t nrel0 = p0 - t.lam_out;
+        const int64_t pos_lo = pos_lo_of(p0);
+        const int64_t p_end = min((int64_t)t.n_out, p0 + kUpChunk);
+        // coarser samples a whose outputs 2a, 2a + 1 (relative to lam_out) fall in [p0, p_end)
+        const int64_t a_first = nrel0 >> 1;
+        const int64_t a_last = (p_end - 1 - t.lam_out) >> 1;
+        const int64_t off = t.in_off - pos_lo;              // seg index of coarser sample a: a + off
+        for (int64_t a = a_first + threadIdx.x; a <= a_last; a += kUpThreads) {
+            const int lo = (int)(a + off);
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kOddTaps; k += 4) {
+                s0 = fmaf(c[k], sg[lo - k] + sg[lo + 1 + k], s0);
+                s1 = fmaf(c[k + 1], sg[lo - k - 1] + sg[lo + 2 + k], s1);
+                s2 = fmaf(c[k + 2], sg[lo - k - 2] + sg[lo + 3 + k], s2);
+                s3 = fmaf(c[k + 3], sg[lo - k - 3] + sg[lo + 4 + k], s3);
+            }
+            const int64_t pe = 2 * a + t.lam_out;           // output index of the even sample
+            if (pe >= p0 && pe < p_end) out[pe] = t.first_n + pe >= 0 ? sg[lo] : 0.0f;
+            if (pe + 1 >= p0 && pe + 1 < p_end)
+                out[pe + 1] = t.first_n + pe + 1 >= 0 ? (s0 + s1) + (s2 + s3) : 0.0f;
+        }
+        if (more) {
+            stash(buf ^ 1);                                  // the other buffer: last read one chunk ago
+            __syncthreads();
+            buf ^= 1;
+        }
     }
 }
 
@@ -354,8 +391,8 @@ cudaError_t launch_win_finalize(const WinFinTask *d_tasks, int n_tasks, int tota
 cudaError_t launch_upsample(const UpTask *d_tasks, int n_tasks, int max_rows, int max_out,
                             const Halfband &g, cudaStream_t s) {
     if (n_tasks == 0 || max_out <= 0 || max_rows <= 0) return cudaSuccess;
-    dim3 grid((max_out + kUpChunk - 1) / kUpChunk, max_rows, n_tasks);
-    return launch_pdl(upsample_kernel, grid, dim3(256), 0, s, d_tasks, g);
+    dim3 grid((max_out + kUpGroup * kUpChunk - 1) / (kUpGroup * kUpChunk), max_rows, n_tasks);
+    return launch_pdl(upsample_kernel, grid, dim3(kUpThreads), 0, s, d_tasks, g);
 }
 
 cudaError_t launch_copy16(const CopyTask *d_tasks, int n_tasks, int max_rows, cudaStream_t s) {

@@ -71,7 +71,8 @@ struct UpTask {
     int32_t n_cur;       // valid columns of cur
     int64_t first_n;     // absolute index of output p = 0 (negative -> write 0)
 };
-constexpr int kUpChunk = 2048;   // outputs per CTA of the interpolation kernel
+constexpr int kUpChunk = 2048;   // outputs per shared-memory pass of the interpolation kernel
+constexpr int kUpGroup = 4;      // passes per CTA
 
 // Generic strided copy (history shifts): dst[r][i] = src_virtual[r][off + i],
 // src_virtual = [hist (n_hist cols) | cur].
