@@ -163,12 +163,12 @@ def algorithmic_model(bank, units: int, B_s: float, precision: str = "fp32"):
         N = B_s * f0 / 2 ** k
         fl["mix"] += 2.0 * M2 * Lk * N
         by["mix"] += w_mix * (M2 * Lk + Lk * N)
-        if fused and k >= 1:
-            inter += 2 * yb * M2 * N
         if not fused:
             by["mix"] += 4.0 * M2 * N * (2 if k < kmax else 1)
     if fused:
         by["mix"] += (M2 / 2) * (B_s * f0 / 128) * 2 * RECORD_BYTES
+        for k in range(1, kmax + 1):                            # every stored level, with a slice or not
+            inter += 2 * yb * M2 * B_s * f0 / 2 ** k
     for k in range(0, kmax):
         N = B_s * f0 / 2 ** k                                   # interpolated outputs at level k
         if fused:

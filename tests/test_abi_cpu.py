@@ -189,3 +189,24 @@ def test_plan_checks_the_xi2_lag_profiles():
         lloid.plan(bank, max_push_samples=4096, autocorr=bad)
     with pytest.raises(ValueError):
         lloid.plan(bank, max_push_samples=4096, autocorr=R[:, :5])
+
+
+def test_plan_limits_banks_to_eight_rates():
+    """A bank spans f0 down to f0 / 2^7: a slice at f0 / 2^8 is rejected, f0 / 2^7 is accepted."""
+    import copy
+    bank, _ = _small_bank()
+    rng = np.random.default_rng(3)
+    f0 = bank.top_rate_hz
+    for k, ok in ((7, True), (8, False)):
+        b = copy.deepcopy(bank)
+        s = b.slices[1]
+        s.rate_hz = f0 / 2 ** k
+        q = int(round((s.t_end_s - s.t_start_s) * s.rate_hz))
+        s.basis = np.linalg.qr(rng.standard_normal((q, s.basis.shape[0])))[0].T.copy()
+        if ok:
+            assert lloid.plan(b, max_push_samples=2 ** k * 4).k_max == k
+        else:
+            with pytest.raises(lloid.LloidError) as e:
+                lloid.plan(b, max_push_samples=2 ** k * 4)
+            assert e.value.code == lloid.SB_EINVAL
+            assert "2^7" in str(e.value)
